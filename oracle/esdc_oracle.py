@@ -1,0 +1,542 @@
+"""Plain FP64 CPU oracle of the entropy-stable collocation residual (arXiv 1911.10966).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports or calls this module; only the
+tests, the smoke check and the CPU-baseline leg of the benchmark do.  It shares no code with the
+CUDA path: it computes its own Gauss-Lobatto nodes, SBP operator and metric terms, evaluates the
+volume term over ALL node pairs (including j = i) with the plain D matrix, and applies the
+interface terms face by face.  Everything is float64 torch CPU tensors so that autograd gives the
+oracle's own vector-Jacobian products.
+
+Layouts: q [K, 5, N, N, N] (element, variable, xi3, xi2, xi1); metric Ja [K, 3, 3, N, N, N] with
+Ja[:, l, m] = J dxi_l/dx_m; faces are numbered 2*l + side (side 0 = xi_l = -1, side 1 = +1).
+
+Readings of points the paper leaves open (each one is repeated where it is used):
+  * metric terms: conservative curl form of the degree-p interpolant of the mapping; it meets the
+    discrete GCL (eq. discGCLconvection) exactly.  The same metrics serve the viscous terms.
+  * entropy variables: w = [(gamma - s)/(gamma - 1) - rho|u|^2/(2p), rho u/p, -rho/p] with
+    s = log(p rho^-gamma), i.e. S = -rho s/(gamma-1) (a positive rescaling of S = -rho s).
+  * inviscid interface term: EC two-point flux plus local Lax-Friedrichs dissipation in the
+    conserved variables, lambda = max over both sides of |u.n_J| + c |n_J|.
+  * viscous interface terms: BR1 (central) lifting of the entropy-variable jump into the gradient
+    and central viscous interface flux; no interior penalty.
+Parity status: every function below is pinned by tests in tests/test_oracle_*.py except the
+numerical values of the interface-dissipation and viscous-interface readings (only their
+conservation and entropy properties are pinned: "parity unpinned" for those constants).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import torch
+
+F64 = torch.float64
+
+
+# --------------------------------------------------------------------------------------------
+# 1D summation-by-parts operator on Legendre-Gauss-Lobatto nodes (Sec. 2, Definition 1)
+# --------------------------------------------------------------------------------------------
+
+def _legendre_and_derivative(p: int, x: float):
+    """P_p(x) and P_p'(x) by the three-term recurrence."""
+    if p == 0:
+        return 1.0, 0.0
+    pm1, pc = 1.0, x
+    dm1, dc = 0.0, 1.0
+    for k in range(1, p):
+        pn = ((2 * k + 1) * x * pc - k * pm1) / (k + 1)
+        dn = dm1 + (2 * k + 1) * pc           # P'_{k+1} = P'_{k-1} + (2k+1) P_k
+        pm1, pc = pc, pn
+        dm1, dc = dc, dn
+    return pc, dc
+
+
+def lgl_nodes_weights(p: int):
+    """Gauss-Lobatto nodes: +-1 and the roots of P_p'; weights 2/(p(p+1) P_p(x_i)^2).
+
+    Newton on q(x) = (1-x^2) P_p'(x), whose derivative is -p(p+1) P_p(x) by Legendre's equation.
+    """
+    if p < 1:
+        raise ValueError("p >= 1")
+    x = [math.cos(math.pi * i / p) for i in range(p + 1)]
+    x = [-v for v in x]                     # ascending from -1 to +1
+    for i in range(1, p):
+        xi = x[i]
+        for _ in range(100):
+            P, dP = _legendre_and_derivative(p, xi)
+            step = (1.0 - xi * xi) * dP / (-p * (p + 1) * P)
+            xi -= step
+            if abs(step) < 1e-17:
+                break
+        x[i] = xi
+    x[0], x[p] = -1.0, 1.0
+    w = [2.0 / (p * (p + 1) * _legendre_and_derivative(p, v)[0] ** 2) for v in x]
+    return torch.tensor(x, dtype=F64), torch.tensor(w, dtype=F64)
+
+
+@dataclass
+class SBP:
+    p: int
+    xi: torch.Tensor     # [N]
+    w: torch.Tensor      # [N]   diagonal of the norm P
+    D: torch.Tensor      # [N,N] D = P^-1 Q
+    Q: torch.Tensor
+    E: torch.Tensor      # diag(-1, 0, ..., 0, 1)
+
+    @property
+    def N(self):
+        return self.p + 1
+
+
+def sbp_operator(p: int) -> SBP:
+    """Collocation derivative by barycentric Lagrange differentiation (Definition 1, item 1)."""
+    xi, w = lgl_nodes_weights(p)
+    N = p + 1
+    lam = torch.ones(N, dtype=F64)
+    for j in range(N):
+        for k in range(N):
+            if k != j:
+                lam[j] = lam[j] / (xi[j] - xi[k])
+    D = torch.zeros(N, N, dtype=F64)
+    for i in range(N):
+        for j in range(N):
+            if i != j:
+                D[i, j] = (lam[j] / lam[i]) / (xi[i] - xi[j])
+        D[i, i] = -sum(D[i, j] for j in range(N) if j != i)
+    Q = torch.diag(w) @ D
+    E = torch.zeros(N, N, dtype=F64)
+    E[0, 0], E[-1, -1] = -1.0, 1.0
+    return SBP(p, xi, w, D, Q, E)
+
+
+def dxi(u: torch.Tensor, l: int, D: torch.Tensor) -> torch.Tensor:
+    """Apply D along reference direction l (0 -> xi1 = last axis) of the trailing three axes."""
+    a = -1 - l
+    ut = u.movedim(a, -1)
+    return torch.einsum("ij,...j->...i", D, ut).movedim(-1, a)
+
+
+def face(u: torch.Tensor, l: int, side: int) -> torch.Tensor:
+    """Nodes of the face xi_l = -1 (side 0) or +1 (side 1); remaining axes keep their order."""
+    N = u.shape[-1]
+    return u.select(-1 - l, 0 if side == 0 else N - 1)
+
+
+# --------------------------------------------------------------------------------------------
+# Mesh geometry: Jacobian and metric terms (Sec. 3, eqs. GCL and discGCLconvection)
+# --------------------------------------------------------------------------------------------
+
+@dataclass
+class Mesh:
+    sbp: SBP
+    x: torch.Tensor      # [K,3,N,N,N]
+    J: torch.Tensor      # [K,N,N,N]
+    Ja: torch.Tensor     # [K,3,3,N,N,N]
+    nbr: torch.Tensor    # [K,6] long, face neighbours
+    h_min: float
+
+
+def metric_terms(x: torch.Tensor, D: torch.Tensor):
+    """J = det(dx/dxi) and Ja[l][m] = J dxi_l/dx_m in conservative curl form.
+
+    For physical component m with (m, m+1, m+2) cyclic: v_j = X_{m+2} dX_{m+1}/dxi_j and
+    Ja[:, :, m] = -curl_xi(v).  Discrete derivatives in different directions commute, so
+    sum_l D_l Ja[l][m] = 0 (the discrete GCL) holds to round-off.
+    """
+    dX = [[dxi(x[:, m], a, D) for a in range(3)] for m in range(3)]     # dX[m][a] = dx_m/dxi_a
+    J = (dX[0][0] * (dX[1][1] * dX[2][2] - dX[1][2] * dX[2][1])
+         - dX[0][1] * (dX[1][0] * dX[2][2] - dX[1][2] * dX[2][0])
+         + dX[0][2] * (dX[1][0] * dX[2][1] - dX[1][1] * dX[2][0]))
+    K, _, N = x.shape[0], x.shape[1], x.shape[-1]
+    Ja = torch.empty((K, 3, 3, N, N, N), dtype=F64)
+    for m in range(3):
+        mp1, mp2 = (m + 1) % 3, (m + 2) % 3
+        v = [x[:, mp2] * dX[mp1][j] for j in range(3)]
+        curl = [dxi(v[2], 1, D) - dxi(v[1], 2, D),
+                dxi(v[0], 2, D) - dxi(v[2], 0, D),
+                dxi(v[1], 0, D) - dxi(v[0], 1, D)]
+        for l in range(3):
+            Ja[:, l, m] = -curl[l]
+    return J, Ja
+
+
+def box_neighbours(kx: int, ky: int, kz: int) -> torch.Tensor:
+    """Face neighbours of a fully periodic structured box, element e = ex + kx*(ey + ky*ez)."""
+    K = kx * ky * kz
+    e = torch.arange(K)
+    ex, ey, ez = e % kx, (e // kx) % ky, e // (kx * ky)
+    idx = lambda a, b, c: (a % kx) + kx * ((b % ky) + ky * (c % kz))
+    return torch.stack([idx(ex - 1, ey, ez), idx(ex + 1, ey, ez),
+                        idx(ex, ey - 1, ez), idx(ex, ey + 1, ez),
+                        idx(ex, ey, ez - 1), idx(ex, ey, ez + 1)], dim=1)
+
+
+def smallest_edge(x: torch.Tensor) -> float:
+    """Smallest distance between adjacent element corners along the 12 element edges."""
+    N = x.shape[-1]
+    c = lambda a, b, d: x[:, :, a, b, d]        # corner (xi3 idx, xi2 idx, xi1 idx)
+    e = [0, N - 1]
+    lens = []
+    for i in e:
+        for j in e:
+            lens.append((c(i, j, 0) - c(i, j, N - 1)).norm(dim=1))
+            lens.append((c(i, 0, j) - c(i, N - 1, j)).norm(dim=1))
+            lens.append((c(0, i, j) - c(N - 1, i, j)).norm(dim=1))
+    return float(torch.stack(lens).min())
+
+
+def make_mesh(p: int, x, kx: int, ky: int, kz: int) -> Mesh:
+    sbp = sbp_operator(p)
+    x = torch.as_tensor(x, dtype=F64)
+    J, Ja = metric_terms(x, sbp.D)
+    return Mesh(sbp, x, J, Ja, box_neighbours(kx, ky, kz), smallest_edge(x))
+
+
+# --------------------------------------------------------------------------------------------
+# Gas physics (Sec. 4: eq. ns_iflux, constitutive relations, entropy, eq. Fv, eq. tau)
+# --------------------------------------------------------------------------------------------
+
+@dataclass
+class Gas:
+    gamma: float = 1.4
+    R: float = 1.0
+    mu: float = 0.0
+    Pr: float = 0.72
+
+    @property
+    def cp(self):
+        return self.gamma * self.R / (self.gamma - 1.0)
+
+    @property
+    def kappa(self):
+        return self.mu * self.cp / self.Pr
+
+    @staticmethod
+    def from_mach(Ma, Re=0.0, gamma=1.4, Pr=0.72):
+        """rho_inf = T_inf = 1, R = 1/(gamma Ma^2), mu = 1/Re (Re <= 0: inviscid)."""
+        return Gas(gamma, 1.0 / (gamma * Ma * Ma), (1.0 / Re) if Re > 0 else 0.0, Pr)
+
+
+def primitives(q: torch.Tensor, gas: Gas):
+    """rho, u (list of 3), p = (gamma-1)(rho E - rho|u|^2/2), T = p/(rho R); variable axis is 1."""
+    rho = q[:, 0]
+    u = [q[:, 1 + d] / rho for d in range(3)]
+    p = (gas.gamma - 1.0) * (q[:, 4] - 0.5 * rho * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2))
+    return rho, u, p, p / (rho * gas.R)
+
+
+def entropy_function(q: torch.Tensor, gas: Gas) -> torch.Tensor:
+    """S = -rho s/(gamma-1) with s = log(p) - gamma log(rho)."""
+    rho, _, p, _ = primitives(q, gas)
+    return -rho * (torch.log(p) - gas.gamma * torch.log(rho)) / (gas.gamma - 1.0)
+
+
+def entropy_variables(q: torch.Tensor, gas: Gas) -> torch.Tensor:
+    """w = dS/dq = [(gamma - s)/(gamma-1) - rho|u|^2/(2p), rho u/p, -rho/p]."""
+    rho, u, p, _ = primitives(q, gas)
+    s = torch.log(p) - gas.gamma * torch.log(rho)
+    usq = u[0] ** 2 + u[1] ** 2 + u[2] ** 2
+    return torch.stack([(gas.gamma - s) / (gas.gamma - 1.0) - rho * usq / (2.0 * p),
+                        rho * u[0] / p, rho * u[1] / p, rho * u[2] / p, -rho / p], dim=1)
+
+
+def euler_flux_n(q: torch.Tensor, n, gas: Gas) -> torch.Tensor:
+    """sum_m n_m F_m(q) with F_m from eq. ns_iflux; n is a list of 3 tensors broadcastable to q[:,0]."""
+    rho, u, p, _ = primitives(q, gas)
+    un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2]
+    H = (q[:, 4] + p) / rho
+    return torch.stack([rho * un, rho * un * u[0] + p * n[0], rho * un * u[1] + p * n[1],
+                        rho * un * u[2] + p * n[2], rho * un * H], dim=1)
+
+
+def _phi(x):
+    """x/log(1+x), continuous at x = 0 with value 1."""
+    zero = x == 0
+    xs = torch.where(zero, torch.ones_like(x), x)
+    return torch.where(zero, torch.ones_like(x), xs / torch.log1p(xs))
+
+
+def _dphi(x):
+    """d/dx [x/log(1+x)]: Gregory-coefficient series for |x| < 1e-3, closed form otherwise."""
+    small = x.abs() < 1e-3
+    xs = torch.where(small, torch.ones_like(x), x)
+    lg = torch.log1p(xs)
+    closed = (lg - xs / (1.0 + xs)) / (lg * lg)
+    series = 0.5 + x * (-1.0 / 6.0 + x * (1.0 / 8.0 + x * (-19.0 / 180.0 + x * (3.0 / 32.0))))
+    return torch.where(small, series, closed)
+
+
+class _LogMean(torch.autograd.Function):
+    """Logarithmic mean (a - b)/(log a - log b) written as b*phi(a/b - 1)."""
+
+    @staticmethod
+    def forward(ctx, a, b):
+        x = (a - b) / b
+        ctx.save_for_backward(a, b, x)
+        return b * _phi(x)
+
+    @staticmethod
+    def backward(ctx, g):
+        a, b, x = ctx.saved_tensors
+        d = _dphi(x)
+        return g * d, g * (_phi(x) - (a / b) * d)
+
+
+def logmean(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """The logarithmic average of Sec. 4 (definition under the ES-C flux)."""
+    return _LogMean.apply(a, b)
+
+
+def ec_flux_n(qa: torch.Tensor, qb: torch.Tensor, n, gas: Gas) -> torch.Tensor:
+    """Chandrashekar two-point entropy-conservative flux contracted with n (ES-C flux, Sec. 4).
+
+    f1 = rho_ln ubar_n, f_{2..4} = f1 ubar + p_tilde n,
+    f5 = f1 (1/(2(gamma-1) beta_ln) - avg(|u|^2)/2) + ubar . f_{2..4},
+    beta = 1/(2RT), p_tilde = R rho_avg T_a T_b / T_avg; avg(|u|^2) is the arithmetic mean of |u|^2.
+    """
+    ra, ua, pa, Ta = primitives(qa, gas)
+    rb, ub, pb, Tb = primitives(qb, gas)
+    ba, bb = 1.0 / (2.0 * gas.R * Ta), 1.0 / (2.0 * gas.R * Tb)
+    rho_ln, beta_ln = logmean(ra, rb), logmean(ba, bb)
+    ubar = [0.5 * (ua[d] + ub[d]) for d in range(3)]
+    ubar_n = ubar[0] * n[0] + ubar[1] * n[1] + ubar[2] * n[2]
+    p_t = gas.R * 0.5 * (ra + rb) * Ta * Tb / (0.5 * (Ta + Tb))
+    usq_avg = 0.5 * ((ua[0] ** 2 + ua[1] ** 2 + ua[2] ** 2) + (ub[0] ** 2 + ub[1] ** 2 + ub[2] ** 2))
+    f1 = rho_ln * ubar_n
+    fm = [f1 * ubar[d] + p_t * n[d] for d in range(3)]
+    f5 = f1 * (1.0 / (2.0 * (gas.gamma - 1.0) * beta_ln) - 0.5 * usq_avg) \
+        + ubar[0] * fm[0] + ubar[1] * fm[1] + ubar[2] * fm[2]
+    return torch.stack([f1, fm[0], fm[1], fm[2], f5], dim=1)
+
+
+def sound_speed(q: torch.Tensor, gas: Gas) -> torch.Tensor:
+    rho, _, p, _ = primitives(q, gas)
+    return torch.sqrt(gas.gamma * p / rho)
+
+
+def viscous_flux(q: torch.Tensor, g: torch.Tensor, gas: Gas) -> torch.Tensor:
+    """F^V_m (eq. Fv, eq. tau) from the physical entropy-variable gradient g[:, m, v] = dw_v/dx_m.
+
+    u_k = -w_{k+1}/w_5 and T = -1/(R w_5), so du_k = -dw_{k+1}/w_5 + w_{k+1} dw_5/w_5^2 and
+    dT = dw_5/(R w_5^2).  Returns [K, 3 (m), 5, ...].
+    """
+    rho, u, p, T = primitives(q, gas)
+    w5 = -rho / p
+    wk = [rho * u[k] / p for k in range(3)]
+    du = [[-g[:, m, 1 + k] / w5 + wk[k] * g[:, m, 4] / (w5 * w5) for m in range(3)] for k in range(3)]
+    dT = [g[:, m, 4] / (gas.R * w5 * w5) for m in range(3)]         # du[k][m] = du_k/dx_m
+    div = du[0][0] + du[1][1] + du[2][2]
+    tau = [[gas.mu * (du[i][j] + du[j][i] - (2.0 / 3.0 if i == j else 0.0) * div) for j in range(3)]
+           for i in range(3)]
+    out = []
+    for m in range(3):
+        zero = torch.zeros_like(rho)
+        energy = tau[0][m] * u[0] + tau[1][m] * u[1] + tau[2][m] * u[2] + gas.kappa * dT[m]
+        out.append(torch.stack([zero, tau[0][m], tau[1][m], tau[2][m], energy], dim=1))
+    return torch.stack(out, dim=1)
+
+
+# --------------------------------------------------------------------------------------------
+# Semi-discrete residual (eq. discEL, eq. MacroForm, eq. NSL)
+# --------------------------------------------------------------------------------------------
+
+def _on_face(out: torch.Tensor, val: torch.Tensor, l: int, side: int) -> torch.Tensor:
+    """out + (val placed on face (l, side)); works under autograd."""
+    N = out.shape[-1]
+    shape = [1] * out.dim()
+    shape[out.dim() - 1 - l] = N
+    onehot = torch.zeros(shape, dtype=out.dtype)
+    onehot.view(-1)[0 if side == 0 else N - 1] = 1.0
+    return out + onehot * val.unsqueeze(out.dim() - 1 - l)
+
+
+def volume_term(q: torch.Tensor, Ja: torch.Tensor, sbp: SBP, gas: Gas, flux=None) -> torch.Tensor:
+    """-sum_l sum_j 2 D_l(i,j) f(q_i, q_j; (Ja_l(i) + Ja_l(j))/2): the Hadamard flux differencing
+    of eq. discEL (with A_lm on both sides of D_l), over every pair j of the xi_l line through i."""
+    flux = flux or ec_flux_n
+    out = torch.zeros_like(q)
+    for l in range(3):
+        a = -1 - l
+        qt = q.movedim(a, -1)
+        nt = Ja[:, l].movedim(a, -1)
+        qi, qj = qt.unsqueeze(-1), qt.unsqueeze(-2)
+        nbar = [0.5 * (nt[:, m].unsqueeze(-1) + nt[:, m].unsqueeze(-2)) for m in range(3)]
+        F = flux(qi, qj, nbar, gas)
+        out = out + (-2.0 * torch.einsum("ij,...ij->...i", sbp.D, F)).movedim(-1, a)
+    return out
+
+
+def inviscid_sat(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, dissipation=True,
+                 flux=None) -> torch.Tensor:
+    """SAT^(I) on elements E at every face node: -(1/P_ii) E_ii [f*(own, nbr) - f(own)].n_J minus
+    (1/P_ii) lambda/2 (q_own - q_nbr) when dissipation is on (local Lax-Friedrichs reading)."""
+    flux = flux or ec_flux_n
+    sbp = mesh.sbp
+    qE = q[E]
+    out = torch.zeros_like(qE)
+    wend = float(sbp.w[0])
+    for l in range(3):
+        for side in (0, 1):
+            f = 2 * l + side
+            qo = face(qE, l, side)
+            qn = face(q[mesh.nbr[E, f]], l, 1 - side)
+            nJ = face(mesh.Ja[E, l], l, side)
+            n = [nJ[:, m] for m in range(3)]
+            sgn = -1.0 if side == 0 else 1.0
+            val = -sgn * (flux(qo, qn, n, gas) - euler_flux_n(qo, n, gas))
+            if dissipation:
+                _, uo, _, _ = primitives(qo, gas)
+                _, un_, _, _ = primitives(qn, gas)
+                nn = torch.sqrt(n[0] ** 2 + n[1] ** 2 + n[2] ** 2)
+                lo = (uo[0] * n[0] + uo[1] * n[1] + uo[2] * n[2]).abs() + sound_speed(qo, gas) * nn
+                ln = (un_[0] * n[0] + un_[1] * n[1] + un_[2] * n[2]).abs() + sound_speed(qn, gas) * nn
+                lam = torch.maximum(lo, ln)
+                val = val - 0.5 * lam.unsqueeze(1) * (qo - qn)
+            out = _on_face(out, val / wend, l, side)
+    return out
+
+
+def entropy_gradient(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor) -> torch.Tensor:
+    """theta_a = D_a w + SAT^theta (eq. NSL), with the BR1 lift (1/P_ii) E_ii (w_nbr - w_own)/2 on
+    the faces normal to a.  Returns [|E|, 3 (a), 5, N, N, N]."""
+    sbp = mesh.sbp
+    wE = entropy_variables(q[E], gas)
+    wend = float(sbp.w[0])
+    th = []
+    for a in range(3):
+        t = dxi(wE, a, sbp.D)
+        for side in (0, 1):
+            wo = face(wE, a, side)
+            wn = face(entropy_variables(q[mesh.nbr[E, 2 * a + side]], gas), a, 1 - side)
+            sgn = -1.0 if side == 0 else 1.0
+            t = _on_face(t, sgn * 0.5 * (wn - wo) / wend, a, side)
+        th.append(t)
+    return torch.stack(th, dim=1)
+
+
+def physical_gradient(theta: torch.Tensor, J: torch.Tensor, Ja: torch.Tensor) -> torch.Tensor:
+    """g[:, m] = (1/J) sum_a Ja[a][m] theta_a (chain rule, Sec. 3)."""
+    return torch.stack([sum(Ja[:, a, m].unsqueeze(1) * theta[:, a] for a in range(3)) / J.unsqueeze(1)
+                        for m in range(3)], dim=1)
+
+
+def contravariant_viscous_flux(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor):
+    """Ftilde_l = sum_m Ja[l][m] F^V_m = sum_a Chat_la theta_a (eq. Chatij): [|E|, 3, 5, N, N, N].
+    Also returns the physical gradient g used to build it."""
+    th = entropy_gradient(q, mesh, gas, E)
+    g = physical_gradient(th, mesh.J[E], mesh.Ja[E])
+    FV = viscous_flux(q[E], g, gas)
+    Ja = mesh.Ja[E]
+    Ft = torch.stack([sum(Ja[:, l, m].unsqueeze(1) * FV[:, m] for m in range(3)) for l in range(3)], dim=1)
+    return Ft, g
+
+
+def viscous_term(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor) -> torch.Tensor:
+    """sum_l D_l Ftilde_l + SAT^(V), SAT^(V) = (1/P_ii) E_ii (Ftilde_l,nbr - Ftilde_l,own)/2 on the
+    xi_l faces (eq. MacroForm / eq. NSL with the BR1 reading; interior penalty off)."""
+    sbp = mesh.sbp
+    K = q.shape[0]
+    E1 = torch.unique(torch.cat([E, mesh.nbr[E].reshape(-1)]))
+    pos = torch.full((K,), -1, dtype=torch.long)
+    pos[E1] = torch.arange(E1.numel())
+    Ft, _ = contravariant_viscous_flux(q, mesh, gas, E1)
+    own = Ft[pos[E]]
+    wend = float(sbp.w[0])
+    out = sum(dxi(own[:, l], l, sbp.D) for l in range(3))
+    for l in range(3):
+        for side in (0, 1):
+            fo = face(own[:, l], l, side)
+            fn = face(Ft[pos[mesh.nbr[E, 2 * l + side]], l], l, 1 - side)
+            sgn = -1.0 if side == 0 else 1.0
+            out = _on_face(out, sgn * 0.5 * (fn - fo) / wend, l, side)
+    return out
+
+
+def rhs(q, mesh: Mesh, gas: Gas, dissipation=True, elems=None, flux=None) -> torch.Tensor:
+    """dq/dt = J^-1 [-volume + SAT^(I) + viscous + SAT^(V)] on elements `elems` (default all)."""
+    q = torch.as_tensor(q, dtype=F64)
+    K = q.shape[0]
+    E = torch.arange(K) if elems is None else torch.as_tensor(elems, dtype=torch.long)
+    r = volume_term(q[E], mesh.Ja[E], mesh.sbp, gas, flux) + inviscid_sat(q, mesh, gas, E, dissipation, flux)
+    if gas.mu > 0.0:
+        r = r + viscous_term(q, mesh, gas, E)
+    return r / mesh.J[E].unsqueeze(1)
+
+
+# --------------------------------------------------------------------------------------------
+# Time integration: Dormand-Prince 5(4) explicit Runge-Kutta, fixed step (Sec. 5)
+# --------------------------------------------------------------------------------------------
+
+DP5_A = [
+    [],
+    [1 / 5],
+    [3 / 40, 9 / 40],
+    [44 / 45, -56 / 15, 32 / 9],
+    [19372 / 6561, -25360 / 2187, 64448 / 6561, -212 / 729],
+    [9017 / 3168, -355 / 33, 46732 / 5247, 49 / 176, -5103 / 18656],
+]
+DP5_B = [35 / 384, 0.0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84]
+DP5_C = [0.0, 1 / 5, 3 / 10, 4 / 5, 8 / 9, 1.0]
+
+
+def rk_step(q, f, dt: float, nsteps: int = 1):
+    """nsteps fixed steps of the 5th-order Dormand-Prince solution: six new stages per step."""
+    for _ in range(nsteps):
+        k = []
+        for s in range(6):
+            qs = q
+            for j, a in enumerate(DP5_A[s]):
+                qs = qs + (dt * a) * k[j]
+            k.append(f(qs))
+        for j, b in enumerate(DP5_B):
+            if b != 0.0:
+                q = q + (dt * b) * k[j]
+    return q
+
+
+# --------------------------------------------------------------------------------------------
+# Budgets and time step
+# --------------------------------------------------------------------------------------------
+
+def quadrature_weights(mesh: Mesh) -> torch.Tensor:
+    """P J at every node: the tensor-product LGL weights times the Jacobian ([K,N,N,N])."""
+    w = mesh.sbp.w
+    return w[:, None, None] * w[None, :, None] * w[None, None, :] * mesh.J
+
+
+def kinetic_energy(q: torch.Tensor, mesh: Mesh) -> torch.Tensor:
+    """Integrated kinetic energy sum P J rho|u|^2/2 as a differentiable scalar (Sec. 5.3 diagnostic)."""
+    PJ = quadrature_weights(mesh)
+    return (PJ * 0.5 * (q[:, 1] ** 2 + q[:, 2] ** 2 + q[:, 3] ** 2) / q[:, 0]).sum()
+
+
+def budgets(q, dqdt, mesh: Mesh, gas: Gas):
+    """(S_total, KE, dS/dt, dKE/dt): P J-weighted sums of S(q), rho|u|^2/2, w.dq/dt and
+    dKE/dq.dq/dt with dKE/dq = [-|u|^2/2, u, 0]."""
+    q = torch.as_tensor(q, dtype=F64)
+    PJ = quadrature_weights(mesh)
+    rho, u, _, _ = primitives(q, gas)
+    usq = u[0] ** 2 + u[1] ** 2 + u[2] ** 2
+    S = float((PJ * entropy_function(q, gas)).sum())
+    KE = float((PJ * 0.5 * rho * usq).sum())
+    if dqdt is None:
+        return S, KE, 0.0, 0.0
+    dqdt = torch.as_tensor(dqdt, dtype=F64)
+    w = entropy_variables(q, gas)
+    dS = float((PJ * (w * dqdt).sum(dim=1)).sum())
+    dKE = float((PJ * (-0.5 * usq * dqdt[:, 0] + u[0] * dqdt[:, 1] + u[1] * dqdt[:, 2]
+                       + u[2] * dqdt[:, 3])).sum())
+    return S, KE, dS, dKE
+
+
+def cfl_dt(q, mesh: Mesh, gas: Gas, cfl=0.5) -> float:
+    """dt = cfl * min(h/((p+1)^2 max(|u|+c)), h^2/((p+1)^4 nu_max)), nu_max = max(4/3, gamma/Pr) mu/rho_min."""
+    q = torch.as_tensor(q, dtype=F64)
+    rho, u, _, _ = primitives(q, gas)
+    speed = float((torch.sqrt(u[0] ** 2 + u[1] ** 2 + u[2] ** 2) + sound_speed(q, gas)).max())
+    N = mesh.sbp.N
+    dt = mesh.h_min / (N * N * speed)
+    if gas.mu > 0.0:
+        nu = max(4.0 / 3.0, gas.gamma / gas.Pr) * gas.mu / float(rho.min())
+        dt = min(dt, mesh.h_min ** 2 / (N ** 4 * nu))
+    return cfl * dt
