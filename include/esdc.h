@@ -1,0 +1,164 @@
+/*
+ * esdc.h -- C ABI of the GB300 entropy-stable discontinuous collocation (ES-C) residual library.
+ *
+ * The library evaluates the semi-discrete residual of the compressible Navier-Stokes equations on
+ * conforming hexahedral meshes with Legendre-Gauss-Lobatto (LGL) collocation (arXiv 1911.10966,
+ * Sec. 4, eq. NSL): Chandrashekar flux differencing (eq. discEL), entropy-variable BR1 viscous
+ * terms (eq. MacroForm), entropy-stable interface SATs and curvilinear metric terms (Sec. 3), and
+ * advances it with the Dormand-Prince 5(4) explicit Runge-Kutta scheme at a fixed step (Sec. 5).
+ *
+ * Conventions for every entry point:
+ *   - Return value: ESDC_OK (0) or a negative ESDC_ERR_* code; esdc_last_error() gives a message
+ *     for the calling thread.  No C++ exception crosses this boundary and no kernel traps.
+ *   - "dev" pointers are CUDA device pointers owned by the CALLER; "host" pointers are ordinary
+ *     host memory owned by the caller.  The library owns its context, operators, geometry, face
+ *     trace buffers and small reduction scratch (allocated in esdc_create, freed in esdc_destroy).
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls enqueue work
+ *     asynchronously on it unless stated otherwise.
+ *   - State layout: q[K][5][N][N][N] float64, variable order (rho, rho u1, rho u2, rho u3, rho E),
+ *     node index (i3*N + i2)*N + i1 (xi1 fastest).  N = p + 1.  One element is one contiguous
+ *     5*N^3 block.  Element e of a kx*ky*kz box is e = ex + kx*(ey + ky*ez).
+ *   - Nondimensionalisation: rho_inf = T_inf = 1, R = 1/(gamma Ma^2), mu = 1/Re, kappa = mu cp/Pr.
+ */
+#ifndef ESDC_H
+#define ESDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ESDC_OK 0
+#define ESDC_ERR_ARG (-1)         /* bad argument, shape, null pointer or size                  */
+#define ESDC_ERR_MESH (-2)        /* non-positive or non-finite metric Jacobian at setup        */
+#define ESDC_ERR_CUDA (-3)        /* a CUDA runtime call failed                                 */
+#define ESDC_ERR_STATE (-4)       /* non-finite or non-physical state found by a reduction      */
+#define ESDC_ERR_UNSUPPORTED (-5) /* valid request this build does not implement                */
+
+#define ESDC_PREC_FP64 0          /* whole residual in float64                                  */
+#define ESDC_PREC_FP32 1          /* residual arithmetic in float32, state/RK/budgets float64   */
+
+typedef struct esdc_ctx esdc_ctx; /* opaque, library owned */
+
+/* Problem description.  Only fully periodic structured boxes are connected by this build. */
+typedef struct esdc_setup {
+    int p;                  /* polynomial degree, 1 <= p <= 7 (N = p + 1 LGL nodes per direction) */
+    int kx, ky, kz;         /* elements per direction, each >= 1                                  */
+    double gamma;           /* ratio of specific heats (> 1)                                      */
+    double Pr;              /* Prandtl number (> 0)                                               */
+    double Ma;              /* reference Mach number (> 0): sets R = 1/(gamma Ma^2)                */
+    double Re;              /* Reynolds number; Re <= 0 means inviscid (mu = 0)                   */
+    int dissipation;        /* 1: entropy-stable interface dissipation; 0: entropy conservative   */
+    int precision;          /* ESDC_PREC_FP64 or ESDC_PREC_FP32                                   */
+} esdc_setup_t;
+
+/*
+ * esdc_lgl -- the N = p+1 LGL nodes xi[N] (ascending on [-1, 1]) and quadrature weights w[N]
+ * (Sec. 2, Definition 1: the norm matrix P = diag(w) of the SBP operator).  Host only, no GPU.
+ * xi, w: host arrays of N doubles, caller owned.  Errors: ESDC_ERR_ARG for p out of range or NULL.
+ */
+int esdc_lgl(int p, double* xi_host, double* w_host);
+
+/*
+ * esdc_operators -- host copies of the library's degree-p SBP operator (Sec. 2, Definition 1):
+ * D[N*N] = P^-1 Q (row-major, D[i*N+j]) and S[N*N] = (Q - Q^T)/2, the skew part with Q = S + E/2.
+ * Host only, no GPU.  Either output may be NULL.  Errors: ESDC_ERR_ARG.
+ */
+int esdc_operators(int p, double* D_host, double* S_host);
+
+/*
+ * esdc_host_geometry -- the metric terms esdc_create would build, computed on the host without a
+ * GPU: J_host[K][N^3], Ja_host[K][9][N^3] (entry l*3 + m = J dxi_l/dx_m, conservative curl form,
+ * Sec. 3) and the smallest element edge h_min.  Any output may be NULL.
+ * Errors: ESDC_ERR_ARG, ESDC_ERR_MESH (J <= 0 or non-finite).
+ */
+int esdc_host_geometry(const esdc_setup_t* setup, const double* node_xyz_host, double* J_host,
+                       double* Ja_host, double* h_min);
+
+/*
+ * esdc_create -- build operators and geometry and allocate library buffers on the current device.
+ * node_xyz_host: [K][3][N][N][N] float64 node coordinates (component-major per element), the
+ *   degree-p mapping X of every element (Sec. 2, eq. 3d_mapping) sampled at the tensor LGL nodes;
+ *   faces shared by neighbours (including periodic images) must hold the same nodes (Assumption 1).
+ * Metric terms J dxi_l/dx_m are built on the host in float64 in conservative curl form, which
+ * meets the discrete GCL (Sec. 3, eq. discGCLconvection), and J = det(dx/dxi).
+ * Synchronous.  Errors: ESDC_ERR_ARG, ESDC_ERR_MESH (J <= 0 or non-finite), ESDC_ERR_CUDA.
+ */
+int esdc_create(const esdc_setup_t* setup, const double* node_xyz_host, esdc_ctx** out);
+
+/* esdc_destroy -- free everything the context owns (synchronises the device).  NULL is a no-op. */
+int esdc_destroy(esdc_ctx* ctx);
+
+/* esdc_layout -- K elements, N nodes per direction, n_nodes = K*N^3.  Any output may be NULL. */
+int esdc_layout(const esdc_ctx* ctx, int64_t* K, int* N, int64_t* n_nodes);
+
+/*
+ * esdc_geometry -- copy the float64 geometry to host arrays: J_host[K][N^3] and
+ * Ja_host[K][9][N^3] with entry (l*3 + m) = J dxi_l/dx_m (Sec. 3).  Either may be NULL.  Synchronous.
+ */
+int esdc_geometry(const esdc_ctx* ctx, double* J_host, double* Ja_host);
+
+/*
+ * esdc_rhs -- dq/dt = J^-1 [ -I^(E) + SAT^(I) + sum_la D_l Chat_la theta_a + SAT^(V) ] (eq. NSL),
+ * with I^(E) the Hadamard flux differencing of eq. discEL using the Chandrashekar two-point flux.
+ * q_dev: [K][5][N^3] float64 device state (read only).
+ * dqdt_dev: [K][5][N^3] device output; float64 for ESDC_PREC_FP64, float32 for ESDC_PREC_FP32.
+ * q_dev and dqdt_dev must not overlap.  Asynchronous on stream.
+ */
+int esdc_rhs(esdc_ctx* ctx, const double* q_dev, void* dqdt_dev, void* stream);
+
+/*
+ * esdc_rhs_host -- esdc_rhs on HOST buffers: copies q_host to library-owned device staging memory,
+ * evaluates the residual and copies dq/dt back (float64 or float32 as for esdc_rhs).  The staging
+ * buffers are allocated on the first call and kept until esdc_destroy.  Synchronous on stream.
+ */
+int esdc_rhs_host(esdc_ctx* ctx, const double* q_host, void* dqdt_host, void* stream);
+
+/*
+ * esdc_workspace_bytes -- device workspace needed by esdc_rk_step (what = 0): six stage
+ * derivatives and one stage state, each K*5*N^3 float64.
+ */
+int esdc_workspace_bytes(const esdc_ctx* ctx, int what, size_t* bytes);
+
+/*
+ * esdc_rk_step -- nsteps fixed steps of size dt of the 5th-order Dormand-Prince solution
+ * (six residual evaluations per step; Sec. 5 uses this integrator with adaptive steps).
+ * q_dev: [K][5][N^3] float64, updated in place.  workspace_dev: caller-owned device memory of at
+ * least esdc_workspace_bytes(ctx, 0) bytes, 256-byte aligned.  The stage state and accumulation
+ * are float64 in both precision modes.  Asynchronous on stream.
+ */
+int esdc_rk_step(esdc_ctx* ctx, double* q_dev, double dt, int nsteps, void* workspace_dev,
+                 size_t workspace_bytes, void* stream);
+
+/*
+ * esdc_budgets -- float64 reductions over all nodes with the quadrature weights P J (Sec. 5.3
+ * kinetic energy; entropy S = -rho s/(gamma-1), s = log(p rho^-gamma)):
+ *   out[0] = sum P J S(q),  out[1] = sum P J rho|u|^2/2,
+ *   out[2] = sum P J w(q).dq/dt,  out[3] = sum P J (dKE/dq).dq/dt   (out[2..3] = 0 if dqdt NULL).
+ * dqdt_dev: float64 for ESDC_PREC_FP64 contexts, float32 for ESDC_PREC_FP32 (same as esdc_rhs).
+ * Deterministic order (bitwise reproducible run to run).  Synchronises stream.
+ * Returns ESDC_ERR_STATE (out still written) if any node has non-finite values, rho <= 0 or p <= 0.
+ */
+int esdc_budgets(esdc_ctx* ctx, const double* q_dev, const void* dqdt_dev, double out_host[4],
+                 void* stream);
+
+/*
+ * esdc_dt_cfl -- dt = cfl * min(h/(N^2 max(|u|+c)), h^2/(N^4 nu)), nu = max(4/3, gamma/Pr) mu/rho_min,
+ * h = smallest element edge (the paper integrates adaptively; this fixed-step rule is the
+ * library's).  Synchronises stream.  ESDC_ERR_STATE on a non-physical state.
+ */
+int esdc_dt_cfl(esdc_ctx* ctx, const double* q_dev, double cfl, double* dt_host, void* stream);
+
+/* esdc_strerror -- static description of a status code. */
+const char* esdc_strerror(int status);
+
+/* esdc_last_error -- message of the last failing call on this thread ("" if none). */
+const char* esdc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESDC_H */

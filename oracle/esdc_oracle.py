@@ -143,6 +143,9 @@ def metric_terms(x: torch.Tensor, D: torch.Tensor):
     Ja[:, :, m] = -curl_xi(v).  Discrete derivatives in different directions commute, so
     sum_l D_l Ja[l][m] = 0 (the discrete GCL) holds to round-off.
     """
+    # the curl form is invariant under translation of X; coordinates relative to each element's
+    # first node keep the products X_l dX_m/dxi small and the round-off proportional to h, not |x|
+    x = x - x[:, :, :1, :1, :1]
     dX = [[dxi(x[:, m], a, D) for a in range(3)] for m in range(3)]     # dX[m][a] = dx_m/dxi_a
     J = (dX[0][0] * (dX[1][1] * dX[2][2] - dX[1][2] * dX[2][1])
          - dX[0][1] * (dX[1][0] * dX[2][2] - dX[1][2] * dX[2][0])

@@ -1,0 +1,82 @@
+"""ctypes binding of libesdc.so (include/esdc.h).  Argument marshalling only: every step of the
+residual, time step and reductions runs in the library's CUDA kernels.  If the shared library is
+missing the import of this module fails loudly: there is no fallback implementation."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libesdc.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "esdc.h")
+
+ESDC_OK = 0
+ESDC_ERR_ARG = -1
+ESDC_ERR_MESH = -2
+ESDC_ERR_CUDA = -3
+ESDC_ERR_STATE = -4
+ESDC_ERR_UNSUPPORTED = -5
+PREC_FP64 = 0
+PREC_FP32 = 1
+
+
+class Setup(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("kx", ctypes.c_int), ("ky", ctypes.c_int), ("kz", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Ma", ctypes.c_double),
+                ("Re", ctypes.c_double), ("dissipation", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class EsdcError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not found: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "esdc_lgl": (I, [I, P, P]),
+        "esdc_operators": (I, [I, P, P]),
+        "esdc_host_geometry": (I, [ctypes.POINTER(Setup), P, P, P, ctypes.POINTER(D)]),
+        "esdc_create": (I, [ctypes.POINTER(Setup), P, ctypes.POINTER(P)]),
+        "esdc_destroy": (I, [P]),
+        "esdc_layout": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]),
+        "esdc_geometry": (I, [P, P, P]),
+        "esdc_rhs": (I, [P, P, P, P]),
+        "esdc_rhs_host": (I, [P, P, P, P]),
+        "esdc_workspace_bytes": (I, [P, I, ctypes.POINTER(S)]),
+        "esdc_rk_step": (I, [P, P, D, I, P, S, P]),
+        "esdc_budgets": (I, [P, P, P, ctypes.POINTER(D), P]),
+        "esdc_dt_cfl": (I, [P, P, D, ctypes.POINTER(D), P]),
+        "esdc_strerror": (ctypes.c_char_p, [I]),
+        "esdc_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(code: int, where: str) -> int:
+    if code != ESDC_OK:
+        msg = lib().esdc_last_error().decode() or lib().esdc_strerror(code).decode()
+        raise EsdcError(code, where, msg)
+    return code
+
+
+def header_symbols() -> list[str]:
+    """Every function name declared in include/esdc.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(esdc_\w+)\s*\(", txt, flags=re.M)))

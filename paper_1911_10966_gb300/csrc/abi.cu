@@ -1,0 +1,357 @@
+// extern "C" entry points declared in include/esdc.h: argument checks, buffer ownership and the
+// sequencing of kernels.  No arithmetic of the method lives here.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "esdc_internal.h"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(ESDC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr)                                   \
+    do {                                                 \
+        cudaError_t _e = (expr);                         \
+        if (_e != cudaSuccess) return cuda_fail(_e, #expr); \
+    } while (0)
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Dormand-Prince 5(4) coefficients (Dormand & Prince 1980): stage matrix rows 2..6 and the
+// 5th-order weights (the 7th, FSAL stage only feeds the embedded error estimate, unused here).
+const double kA[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0}};
+const double kB[6] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0};
+
+int rhs_impl(esdc_ctx* c, const double* q, void* dqdt, cudaStream_t s) {
+    cudaError_t e;
+    if (c->setup.precision == ESDC_PREC_FP64) e = esdc::launch_rhs_f64(c, q, (double*)dqdt, s);
+    else return fail(ESDC_ERR_UNSUPPORTED, "float32 residual not available in this build");
+    if (e != cudaSuccess) return cuda_fail(e, "esdc_rhs launch");
+    return ESDC_OK;
+}
+
+void free_ctx(esdc_ctx* c) {
+    if (!c) return;
+    cudaFree(c->d_geom);
+    cudaFree(c->d_geomf);
+    cudaFree(c->d_nbr);
+    cudaFree(c->d_trace);
+    cudaFree(c->d_red);
+    cudaFree(c->d_red_out);
+    cudaFree(c->d_stage_q);
+    cudaFree(c->d_stage_r);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* esdc_last_error(void) { return g_err.c_str(); }
+
+const char* esdc_strerror(int status) {
+    switch (status) {
+        case ESDC_OK: return "ok";
+        case ESDC_ERR_ARG: return "invalid argument";
+        case ESDC_ERR_MESH: return "invalid mesh geometry";
+        case ESDC_ERR_CUDA: return "CUDA runtime error";
+        case ESDC_ERR_STATE: return "non-finite or non-physical state";
+        case ESDC_ERR_UNSUPPORTED: return "unsupported request";
+        default: return "unknown status";
+    }
+}
+
+int esdc_lgl(int p, double* xi_host, double* w_host) {
+    if (p < 1 || p > esdc::kMaxN - 1) return fail(ESDC_ERR_ARG, "p must be in [1, 7]");
+    if (!xi_host || !w_host) return fail(ESDC_ERR_ARG, "null output pointer");
+    return esdc::lgl(p, xi_host, w_host);
+}
+
+int esdc_operators(int p, double* D, double* S) {
+    if (p < 1 || p > esdc::kMaxN - 1) return fail(ESDC_ERR_ARG, "p must be in [1, 7]");
+    esdc::HostSetup hs;
+    int st = esdc::build_operators(p, hs);
+    if (st) return fail(st, "operator construction failed");
+    if (D) std::memcpy(D, hs.D.data(), hs.D.size() * sizeof(double));
+    if (S) std::memcpy(S, hs.S.data(), hs.S.size() * sizeof(double));
+    return ESDC_OK;
+}
+
+static int check_setup(const esdc_setup_t& s) {
+    if (s.p < 1 || s.p > esdc::kMaxN - 1) return fail(ESDC_ERR_ARG, "p must be in [1, 7]");
+    if (s.kx < 1 || s.ky < 1 || s.kz < 1) return fail(ESDC_ERR_ARG, "element counts must be >= 1");
+    if ((int64_t)s.kx * s.ky * s.kz > (int64_t)INT32_MAX / 6) return fail(ESDC_ERR_ARG, "too many elements");
+    if (!(s.gamma > 1.0) || !(s.Pr > 0.0) || !(s.Ma > 0.0) || !std::isfinite(s.Re))
+        return fail(ESDC_ERR_ARG, "gamma > 1, Pr > 0, Ma > 0 and finite Re required");
+    if (s.dissipation != 0 && s.dissipation != 1) return fail(ESDC_ERR_ARG, "dissipation must be 0 or 1");
+    if (s.precision != ESDC_PREC_FP64 && s.precision != ESDC_PREC_FP32)
+        return fail(ESDC_ERR_ARG, "precision must be ESDC_PREC_FP64 or ESDC_PREC_FP32");
+    return ESDC_OK;
+}
+
+int esdc_host_geometry(const esdc_setup_t* setup, const double* xyz, double* J, double* Ja, double* h_min) {
+    if (!setup || !xyz) return fail(ESDC_ERR_ARG, "null argument");
+    int st = check_setup(*setup);
+    if (st) return st;
+    esdc::HostSetup hs;
+    st = esdc::build_operators(setup->p, hs);
+    if (st) return fail(st, "operator construction failed");
+    std::string err;
+    st = esdc::build_geometry(*setup, xyz, hs, err);
+    if (st) return fail(st, err);
+    const int64_t K = (int64_t)setup->kx * setup->ky * setup->kz;
+    const size_t N3 = (size_t)hs.N * hs.N * hs.N;
+    for (int64_t e = 0; e < K; ++e) {
+        if (J) std::memcpy(J + e * N3, &hs.geom[e * 10 * N3], N3 * sizeof(double));
+        if (Ja) std::memcpy(Ja + e * 9 * N3, &hs.geom[(e * 10 + 1) * N3], 9 * N3 * sizeof(double));
+    }
+    if (h_min) *h_min = hs.h_min;
+    return ESDC_OK;
+}
+
+int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
+    if (!setup || !xyz || !out) return fail(ESDC_ERR_ARG, "null argument");
+    *out = nullptr;
+    const esdc_setup_t& s = *setup;
+    int st0 = check_setup(s);
+    if (st0) return st0;
+
+    esdc::HostSetup hs;
+    int st = esdc::build_operators(s.p, hs);
+    if (st) return fail(st, "operator construction failed");
+    std::string err;
+    st = esdc::build_geometry(s, xyz, hs, err);
+    if (st) return fail(st, err);
+
+    esdc_ctx* c = new (std::nothrow) esdc_ctx();
+    if (!c) return fail(ESDC_ERR_ARG, "out of host memory");
+    c->setup = s;
+    c->N = hs.N;
+    c->N3 = hs.N * hs.N * hs.N;
+    c->K = (int64_t)s.kx * s.ky * s.kz;
+    c->n_nodes = c->K * c->N3;
+    c->h_min = hs.h_min;
+    std::memset(&c->ops, 0, sizeof(c->ops));
+    std::memset(&c->opsf, 0, sizeof(c->opsf));
+    c->ops.N = c->opsf.N = hs.N;
+    for (int i = 0; i < hs.N; ++i) {
+        c->ops.w[i] = hs.w[i];
+        c->ops.winv[i] = 1.0 / hs.w[i];
+        c->opsf.w[i] = (float)hs.w[i];
+        c->opsf.winv[i] = (float)(1.0 / hs.w[i]);
+        for (int j = 0; j < hs.N; ++j) {
+            c->ops.D[i][j] = hs.D[i * hs.N + j];
+            c->ops.S2[i][j] = 2.0 * hs.S[i * hs.N + j];
+            c->opsf.D[i][j] = (float)hs.D[i * hs.N + j];
+            c->opsf.S2[i][j] = (float)(2.0 * hs.S[i * hs.N + j]);
+        }
+    }
+    const double R = 1.0 / (s.gamma * s.Ma * s.Ma);
+    const double mu = s.Re > 0.0 ? 1.0 / s.Re : 0.0;
+    const double cp = s.gamma * R / (s.gamma - 1.0);
+    c->phys.gamma = s.gamma;
+    c->phys.R = R;
+    c->phys.mu = mu;
+    c->phys.kappa = mu * cp / s.Pr;
+    c->phys.inv_gm1 = 1.0 / (s.gamma - 1.0);
+    c->phys.dissipation = s.dissipation;
+    c->phys.viscous = mu > 0.0;
+    c->physf.gamma = (float)s.gamma;
+    c->physf.R = (float)R;
+    c->physf.mu = (float)mu;
+    c->physf.kappa = (float)c->phys.kappa;
+    c->physf.inv_gm1 = (float)c->phys.inv_gm1;
+    c->physf.rho0 = 1.0f;
+    c->physf.p0 = (float)R;
+    c->physf.dissipation = s.dissipation;
+    c->physf.viscous = c->phys.viscous;
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    const size_t N2 = (size_t)hs.N * hs.N;
+    const size_t geom_bytes = (size_t)c->K * 10 * c->N3 * sizeof(double);
+    c->red_blocks = 1024;
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_geom, geom_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_nbr, (size_t)c->K * 6 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_trace, (size_t)c->K * 6 * 4 * N2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_red, (size_t)c->red_blocks * 5 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_red_out, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_geom, hs.geom.data(), geom_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_nbr, hs.nbr.data(), hs.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = esdc::prepare_rhs_f64(c);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return cuda_fail(e, "esdc_create");
+    }
+    *out = c;
+    return ESDC_OK;
+}
+
+int esdc_destroy(esdc_ctx* ctx) {
+    if (!ctx) return ESDC_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    free_ctx(ctx);
+    cudaSetDevice(prev);
+    return ESDC_OK;
+}
+
+int esdc_layout(const esdc_ctx* c, int64_t* K, int* N, int64_t* n_nodes) {
+    if (!c) return fail(ESDC_ERR_ARG, "null context");
+    if (K) *K = c->K;
+    if (N) *N = c->N;
+    if (n_nodes) *n_nodes = c->n_nodes;
+    return ESDC_OK;
+}
+
+int esdc_geometry(const esdc_ctx* c, double* J, double* Ja) {
+    if (!c) return fail(ESDC_ERR_ARG, "null context");
+    const size_t N3 = c->N3;
+    for (int64_t e = 0; e < c->K; ++e) {
+        if (J) CUDA_TRY(cudaMemcpy(J + e * N3, c->d_geom + e * 10 * N3, N3 * sizeof(double), cudaMemcpyDeviceToHost));
+        if (Ja)
+            CUDA_TRY(cudaMemcpy(Ja + e * 9 * N3, c->d_geom + (e * 10 + 1) * N3, 9 * N3 * sizeof(double),
+                                cudaMemcpyDeviceToHost));
+    }
+    return ESDC_OK;
+}
+
+int esdc_rhs(esdc_ctx* c, const double* q, void* dqdt, void* stream) {
+    if (!c || !q || !dqdt) return fail(ESDC_ERR_ARG, "null argument");
+    const size_t elt = c->setup.precision == ESDC_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const uintptr_t a = (uintptr_t)q, b = (uintptr_t)dqdt;
+    const uintptr_t na = c->n_nodes * 5 * sizeof(double), nb = c->n_nodes * 5 * elt;
+    if (a < b + nb && b < a + na) return fail(ESDC_ERR_ARG, "q and dqdt overlap");
+    return rhs_impl(c, q, dqdt, (cudaStream_t)stream);
+}
+
+int esdc_rhs_host(esdc_ctx* c, const double* q_host, void* dqdt_host, void* stream) {
+    if (!c || !q_host || !dqdt_host) return fail(ESDC_ERR_ARG, "null argument");
+    const size_t elt = c->setup.precision == ESDC_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const size_t qb = (size_t)c->n_nodes * 5 * sizeof(double), rb = (size_t)c->n_nodes * 5 * elt;
+    if (!c->d_stage_q) {
+        CUDA_TRY(cudaMalloc(&c->d_stage_q, qb));
+        CUDA_TRY(cudaMalloc(&c->d_stage_r, rb));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(c->d_stage_q, q_host, qb, cudaMemcpyHostToDevice, s));
+    int st = rhs_impl(c, c->d_stage_q, c->d_stage_r, s);
+    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(dqdt_host, c->d_stage_r, rb, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return ESDC_OK;
+}
+
+int esdc_workspace_bytes(const esdc_ctx* c, int what, size_t* bytes) {
+    if (!c || !bytes) return fail(ESDC_ERR_ARG, "null argument");
+    if (what != 0) return fail(ESDC_ERR_ARG, "unknown workspace kind");
+    *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(double));
+    return ESDC_OK;
+}
+
+int esdc_rk_step(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, size_t ws_bytes, void* stream) {
+    if (!c || !q || !ws) return fail(ESDC_ERR_ARG, "null argument");
+    if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
+    size_t need = 0;
+    esdc_workspace_bytes(c, 0, &need);
+    if (ws_bytes < need) return fail(ESDC_ERR_ARG, "workspace too small");
+    if (!aligned(ws, 256) || !aligned(q, 16)) return fail(ESDC_ERR_ARG, "q must be 16-byte and workspace 256-byte aligned");
+    if (c->setup.precision != ESDC_PREC_FP64) return fail(ESDC_ERR_UNSUPPORTED, "float32 residual not available in this build");
+    const int64_t n = c->n_nodes * 5;
+    const size_t sub = round256((size_t)n * sizeof(double));
+    double* k[6];
+    for (int j = 0; j < 6; ++j) k[j] = (double*)((char*)ws + j * sub);
+    double* stage = (double*)((char*)ws + 6 * sub);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int step = 0; step < nsteps; ++step) {
+        for (int st = 0; st < 6; ++st) {
+            const double* qs = q;
+            if (st > 0) {
+                esdc::Combine cb{};
+                cb.nk = st;
+                for (int j = 0; j < st; ++j) {
+                    cb.k[j] = k[j];
+                    cb.coef[j] = dt * kA[st][j];
+                }
+                cudaError_t e = esdc::launch_combine(stage, q, cb, n, s);
+                if (e != cudaSuccess) return cuda_fail(e, "stage combine");
+                qs = stage;
+            }
+            int r = rhs_impl(c, qs, k[st], s);
+            if (r) return r;
+        }
+        esdc::Combine cb{};
+        cb.nk = 0;
+        for (int j = 0; j < 6; ++j)
+            if (kB[j] != 0.0) {
+                cb.k[cb.nk] = k[j];
+                cb.coef[cb.nk] = dt * kB[j];
+                ++cb.nk;
+            }
+        cudaError_t e = esdc::launch_combine(q, q, cb, n, s);
+        if (e != cudaSuccess) return cuda_fail(e, "step combine");
+    }
+    return ESDC_OK;
+}
+
+int esdc_budgets(esdc_ctx* c, const double* q, const void* dqdt, double out[4], void* stream) {
+    if (!c || !q || !out) return fail(ESDC_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = esdc::launch_budgets(c, q, dqdt, c->setup.precision == ESDC_PREC_FP32, s);
+    if (e != cudaSuccess) return cuda_fail(e, "budgets launch");
+    double r[5];
+    CUDA_TRY(cudaMemcpyAsync(r, c->d_red_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < 4; ++i) out[i] = r[i];
+    if (!dqdt) out[2] = out[3] = 0.0;
+    if (r[4] > 0.0) return fail(ESDC_ERR_STATE, "non-finite or non-physical values at " + std::to_string((long long)r[4]) + " nodes");
+    return ESDC_OK;
+}
+
+int esdc_dt_cfl(esdc_ctx* c, const double* q, double cfl, double* dt, void* stream) {
+    if (!c || !q || !dt) return fail(ESDC_ERR_ARG, "null argument");
+    if (!(cfl > 0.0)) return fail(ESDC_ERR_ARG, "cfl must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = esdc::launch_cfl(c, q, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cfl launch");
+    double r[3];
+    CUDA_TRY(cudaMemcpyAsync(r, c->d_red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (r[2] > 0.0 || !(r[0] > 0.0)) return fail(ESDC_ERR_STATE, "non-physical state in esdc_dt_cfl");
+    const double N2 = (double)c->N * c->N;
+    double d = c->h_min / (N2 * r[0]);
+    if (c->phys.viscous) {
+        const double rho_min = -r[1];
+        const double nu = std::fmax(4.0 / 3.0, c->setup.gamma / c->setup.Pr) * c->phys.mu / rho_min;
+        d = std::fmin(d, c->h_min * c->h_min / (N2 * N2 * nu));
+    }
+    *dt = cfl * d;
+    return ESDC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal declarations shared by the host setup, the kernels and the C ABI layer.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/esdc.h"
+
+namespace esdc {
+
+constexpr int kMaxN = 8;   // p <= 7
+
+// Per-degree operators passed by value to kernels (lands in the constant bank).
+struct Ops {
+    int N;
+    double D[kMaxN][kMaxN];    // collocation derivative D = P^-1 Q (Sec. 2, Definition 1)
+    double S2[kMaxN][kMaxN];   // 2 S with S = Q - E/2 skew-symmetric
+    double w[kMaxN];           // LGL weights (diagonal of P)
+    double winv[kMaxN];        // 1/w
+};
+
+struct Phys {
+    double gamma, R, mu, kappa;
+    double inv_gm1;            // 1/(gamma-1)
+    int dissipation;           // 1: LLF interface dissipation on
+    int viscous;               // mu > 0
+};
+
+// FP32 copies used by the mixed-precision kernels.
+struct OpsF {
+    int N;
+    float D[kMaxN][kMaxN];
+    float S2[kMaxN][kMaxN];
+    float w[kMaxN];
+    float winv[kMaxN];
+};
+
+struct PhysF {
+    float gamma, R, mu, kappa, inv_gm1;
+    float rho0, p0;            // reference state subtracted in the FP32 kernels
+    int dissipation, viscous;
+};
+
+// Host-side results of setup (float64).
+struct HostSetup {
+    int p = 0, N = 0;
+    std::vector<double> xi, w;           // LGL nodes / weights
+    std::vector<double> D;               // N*N row-major
+    std::vector<double> S;               // N*N row-major, exactly skew
+    std::vector<double> geom;            // [K][10][N^3]: J, Ja_lm (l-major)
+    std::vector<int32_t> nbr;            // [K][6]
+    double h_min = 0.0;
+};
+
+int lgl(int p, double* xi, double* w);
+int build_operators(int p, HostSetup& hs);
+int build_geometry(const esdc_setup_t& s, const double* xyz, HostSetup& hs, std::string& err);
+void build_box_neighbours(int kx, int ky, int kz, std::vector<int32_t>& nbr);
+
+}  // namespace esdc
+
+struct esdc_ctx {
+    esdc_setup_t setup;
+    int device = 0;
+    int N = 0, N3 = 0;
+    int64_t K = 0, n_nodes = 0;
+    esdc::Ops ops;
+    esdc::OpsF opsf;
+    esdc::Phys phys;
+    esdc::PhysF physf;
+    double h_min = 0.0;
+    // device buffers owned by the library
+    double* d_geom = nullptr;        // [K][10][N3]
+    float* d_geomf = nullptr;        // [K][10][N3] float32 copy (mixed precision)
+    int32_t* d_nbr = nullptr;        // [K][6]
+    void* d_trace = nullptr;         // [K][6][4][N2] viscous normal-flux traces (f64 or f32)
+    double* d_red = nullptr;         // reduction partials
+    double* d_red_out = nullptr;     // reduction results
+    int red_blocks = 0;
+    // staging for esdc_rhs_host
+    double* d_stage_q = nullptr;
+    void* d_stage_r = nullptr;
+};

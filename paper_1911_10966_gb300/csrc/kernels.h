@@ -1,0 +1,25 @@
+// Kernel launchers (one per translation unit) used by the C ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "esdc_internal.h"
+
+namespace esdc {
+
+cudaError_t prepare_rhs_f64(const esdc_ctx* c);
+cudaError_t launch_rhs_f64(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s);
+
+// out = q0 + sum_j coef[j] * k[j]   (n doubles; k pointers may alias nothing but each other)
+struct Combine {
+    const double* k[6];
+    double coef[6];
+    int nk;
+};
+cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int64_t n, cudaStream_t s);
+
+// Reductions: budgets (4 sums + non-physical count) and CFL inputs (max |u|+c, min rho).
+cudaError_t launch_budgets(const esdc_ctx* c, const double* q, const void* dqdt, int dq_f32, cudaStream_t s);
+cudaError_t launch_cfl(const esdc_ctx* c, const double* q, cudaStream_t s);
+
+}  // namespace esdc

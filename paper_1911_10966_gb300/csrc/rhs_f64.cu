@@ -1,0 +1,422 @@
+// FP64 residual kernels: Chandrashekar flux differencing (eq. discEL), entropy-stable interface SAT,
+// BR1 entropy-variable gradients, viscous fluxes and their divergence (eq. MacroForm, eq. NSL).
+//
+// Kernel rhs_main: one element per group of N^3 threads (EPB elements per CTA).  The element's
+// state is loaded once, converted to primitive and entropy variables in shared memory, and then:
+//   1. volume: for each direction l (sequentially) one thread per xi_l line evaluates the
+//      N(N-1)/2 distinct node pairs of its line once each, using the skew part S of Q = S + E/2:
+//      r_i -= 2 S_ij f_ij / w_i, r_j += 2 S_ij f_ij / w_j.  The E/2 boundary part of the volume
+//      term, -E_ii f(q_i).n_J / w_i, cancels the own-flux part of the interface SAT and is dropped
+//      on both sides.
+//   2. interface: one thread per face node adds -(E_ii f_EC(own, nbr).n_J + lambda/2 (q_own - q_nbr))
+//      / w_i and records the neighbour's entropy variables for the gradient lift.
+//   3. viscous (mu > 0): one thread per node forms theta_a = D_a w + lift, the physical gradient,
+//      tau and the heat flux, and the contravariant viscous flux Ftilde_l = sum_m Ja_lm F^V_m;
+//      the normal component on each face is written to the trace buffer.
+//   4. divergence sum_l D_l Ftilde_l; dq/dt = r / J is written.
+// Kernel visc_sat then adds the BR1 interface term (E_ii/2)(Ftilde_nbr - Ftilde_own)/(w_i J) on
+// face nodes once every element's traces exist.
+#include <cuda_runtime.h>
+
+#include "esdc_internal.h"
+#include "kernels.h"
+
+namespace esdc {
+namespace {
+
+template <int N>
+struct Cfg {
+    static constexpr int N2 = N * N, N3 = N * N * N;
+    static constexpr int EPB = N3 >= 96 ? 1 : (N3 >= 48 ? 2 : (N3 >= 24 ? 4 : 16));
+    static constexpr int THREADS = EPB * N3;
+    // shared doubles per element: prim/w/Ftilde 12 x N3 | r 5 x N3 | geometry 10 x N3 | face w 24 x N2
+    static constexpr int SM = 27 * N3 + 24 * N2;
+    static constexpr int EPB_SAT = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
+};
+
+struct Prim {
+    double rho, u0, u1, u2, beta, usq;
+};
+
+__device__ __forceinline__ void to_prim(const double* q, const Phys& ph, Prim& s) {
+    const double ri = 1.0 / q[0];
+    s.rho = q[0];
+    s.u0 = q[1] * ri;
+    s.u1 = q[2] * ri;
+    s.u2 = q[3] * ri;
+    s.usq = s.u0 * s.u0 + s.u1 * s.u1 + s.u2 * s.u2;
+    const double p = (ph.gamma - 1.0) * (q[4] - 0.5 * q[0] * s.usq);
+    s.beta = 0.5 * q[0] / p;
+}
+
+// Logarithmic mean by the artanh series in f = (a-b)/(a+b), u = f^2 (Ismail-Roe style):
+// L = (a+b)/2 * G(u), G = 1/(1 + u/3 + u^2/5 + u^3/7 + ...) = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
+// for u < 1e-4 (truncation below 1e-17), else (a-b)/log(a/b).
+__device__ __forceinline__ double ln_mean(double a, double b) {
+    const double d = a - b, s = a + b;
+    const double f = d / s;
+    const double u = f * f;
+    if (u < 1.0e-4) return 0.5 * s * (1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0))));
+    return d / log(a / b);
+}
+
+// Reciprocal logarithmic mean given rs = 1/(a+b): 2 rs (1 + u/3 + u^2/5 + u^3/7) or log(a/b)/(a-b).
+__device__ __forceinline__ double inv_ln_mean(double a, double b, double rs) {
+    const double d = a - b;
+    const double f = d * rs;
+    const double u = f * f;
+    if (u < 1.0e-4) return 2.0 * rs * (1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0))));
+    return log(a / b) / d;
+}
+
+// Chandrashekar two-point flux contracted with n (Sec. 4):
+// f1 = rho_ln ubar.n, f_m = f1 ubar + p_t n, f5 = f1 (1/(2(g-1) beta_ln) - avg|u|^2/2) + ubar.f_m,
+// p_t = avg(rho)/(2 avg(beta)) = (rho_a + rho_b)/(2 (beta_a + beta_b)).
+__device__ __forceinline__ void ec_flux(const Prim& a, const Prim& b, double n0, double n1, double n2,
+                                        const Phys& ph, double f[5]) {
+    const double rho_ln = ln_mean(a.rho, b.rho);
+    const double rsb = 1.0 / (a.beta + b.beta);
+    const double ibeta_ln = inv_ln_mean(a.beta, b.beta, rsb);
+    const double ub0 = 0.5 * (a.u0 + b.u0), ub1 = 0.5 * (a.u1 + b.u1), ub2 = 0.5 * (a.u2 + b.u2);
+    const double un = ub0 * n0 + ub1 * n1 + ub2 * n2;
+    const double pt = 0.5 * (a.rho + b.rho) * rsb;
+    const double f1 = rho_ln * un;
+    f[0] = f1;
+    f[1] = f1 * ub0 + pt * n0;
+    f[2] = f1 * ub1 + pt * n1;
+    f[3] = f1 * ub2 + pt * n2;
+    f[4] = f1 * (0.5 * ph.inv_gm1 * ibeta_ln - 0.25 * (a.usq + b.usq)) + ub0 * f[1] + ub1 * f[2] + ub2 * f[3];
+}
+
+template <int N>
+__device__ __forceinline__ int line_base(int l, int t1, int t2) {
+    return l == 0 ? (t1 * N + t2 * N * N) : (l == 1 ? (t1 + t2 * N * N) : (t1 + t2 * N));
+}
+
+template <int N>
+__device__ __forceinline__ int dir_stride(int l) {
+    return l == 0 ? 1 : (l == 1 ? N : N * N);
+}
+
+__device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Prim& s) {
+    s.rho = sP[idx];
+    s.u0 = sP[N3 + idx];
+    s.u1 = sP[2 * N3 + idx];
+    s.u2 = sP[3 * N3 + idx];
+    s.beta = sP[4 * N3 + idx];
+    s.usq = sP[5 * N3 + idx];
+}
+
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const double* __restrict__ geom,
+             const int32_t* __restrict__ nbr, double* __restrict__ trace, int64_t K, const Ops ops,
+             const Phys ph) {
+    constexpr int N2 = Cfg<N>::N2, N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB;
+    extern __shared__ double smem[];
+    const int t = threadIdx.x;
+    const int el_loc = t / N3;
+    const int node = t - el_loc * N3;
+    const int64_t el = (int64_t)blockIdx.x * EPB + el_loc;
+    const bool active = el < K;
+    double* sP = smem + (size_t)el_loc * Cfg<N>::SM;   // [12][N3]: rho,u0,u1,u2,beta,usq,w2..w5 | Ftilde
+    double* sR = sP + 12 * N3;                          // [5][N3]
+    double* sG = sP + 17 * N3;                          // [10][N3]: J, Ja_lm
+    double* sWf = sP + 27 * N3;                         // [6][4][N2]
+    const int64_t eoff = el * 5 * N3;
+
+    // ---- node-local precompute
+    if (active) {
+        double qv[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qv[v] = q[eoff + v * N3 + node];
+        Prim s;
+        to_prim(qv, ph, s);
+        sP[node] = s.rho;
+        sP[N3 + node] = s.u0;
+        sP[2 * N3 + node] = s.u1;
+        sP[3 * N3 + node] = s.u2;
+        sP[4 * N3 + node] = s.beta;
+        sP[5 * N3 + node] = s.usq;
+        sP[6 * N3 + node] = 2.0 * s.beta * s.u0;
+        sP[7 * N3 + node] = 2.0 * s.beta * s.u1;
+        sP[8 * N3 + node] = 2.0 * s.beta * s.u2;
+        sP[9 * N3 + node] = -2.0 * s.beta;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) sG[c * N3 + node] = geom[(el * 10 + c) * N3 + node];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sR[v * N3 + node] = 0.0;
+    }
+    __syncthreads();
+
+    // ---- volume flux differencing, one xi_l line per thread
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        if (active && node < N2) {
+            const int base = line_base<N>(l, node % N, node / N);
+            const int st = dir_stride<N>(l);
+            const double* n0p = sG + (1 + 3 * l) * N3;
+            const double* n1p = n0p + N3;
+            const double* n2p = n1p + N3;
+            double acc[N][5];
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+#pragma unroll
+                for (int v = 0; v < 5; ++v) acc[i][v] = 0.0;
+#pragma unroll
+            for (int i = 0; i < N - 1; ++i) {
+                const int ii = base + i * st;
+                Prim si;
+                load_prim(sP, N3, ii, si);
+                const double a0 = n0p[ii], a1 = n1p[ii], a2 = n2p[ii];
+#pragma unroll
+                for (int j = i + 1; j < N; ++j) {
+                    const int jj = base + j * st;
+                    Prim sj;
+                    load_prim(sP, N3, jj, sj);
+                    double f[5];
+                    ec_flux(si, sj, 0.5 * (a0 + n0p[jj]), 0.5 * (a1 + n1p[jj]), 0.5 * (a2 + n2p[jj]), ph, f);
+                    const double c = ops.S2[i][j];
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) {
+                        acc[i][v] -= c * f[v];
+                        acc[j][v] += c * f[v];
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int ii = base + i * st;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sR[v * N3 + ii] += acc[i][v] * ops.winv[i];
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- inviscid interface SAT (and neighbour entropy variables for the gradient lift)
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        if (active && node < 2 * N2) {
+            const int side = node / N2, fi = node - side * N2;
+            const int st = dir_stride<N>(l);
+            const int base = line_base<N>(l, fi % N, fi / N);
+            const int own = base + (side ? (N - 1) * st : 0);
+            const int nbn = base + (side ? 0 : (N - 1) * st);
+            const int64_t nb = nbr[el * 6 + 2 * l + side];
+            double qo[5], qn[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                qo[v] = q[eoff + v * N3 + own];
+                qn[v] = q[nb * 5 * N3 + v * N3 + nbn];
+            }
+            Prim so, sn;
+            load_prim(sP, N3, own, so);
+            to_prim(qn, ph, sn);
+            const double n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own],
+                         n2 = sG[(3 + 3 * l) * N3 + own];
+            double f[5];
+            ec_flux(so, sn, n0, n1, n2, ph, f);
+            const double E = side ? 1.0 : -1.0;
+            double lam = 0.0;
+            if (ph.dissipation) {
+                const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+                const double lo = fabs(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + sqrt(0.5 * ph.gamma / so.beta) * nn;
+                const double ln = fabs(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + sqrt(0.5 * ph.gamma / sn.beta) * nn;
+                lam = 0.5 * fmax(lo, ln);
+            }
+            const double wi = ops.winv[side ? N - 1 : 0];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sR[v * N3 + own] += (-E * f[v] - lam * (qo[v] - qn[v])) * wi;
+            double* wf = sWf + (2 * l + side) * 4 * N2 + fi;
+            wf[0] = 2.0 * sn.beta * sn.u0;
+            wf[N2] = 2.0 * sn.beta * sn.u1;
+            wf[2 * N2] = 2.0 * sn.beta * sn.u2;
+            wf[3 * N2] = -2.0 * sn.beta;
+        }
+        __syncthreads();
+    }
+
+    const double Jinv = active ? 1.0 / sG[node] : 0.0;
+    if (ph.viscous) {
+        const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+        double Ft[3][4];
+        if (active) {
+            const double wown[4] = {sP[6 * N3 + node], sP[7 * N3 + node], sP[8 * N3 + node], sP[9 * N3 + node]};
+            double th[3][4];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int ia = a == 0 ? i1 : (a == 1 ? i2 : i3);
+                const int st = dir_stride<N>(a);
+                const int lb = node - ia * st;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int j = 0; j < N; ++j) s += ops.D[ia][j] * sP[(6 + k) * N3 + lb + j * st];
+                    th[a][k] = s;
+                }
+                if (ia == 0 || ia == N - 1) {
+                    const int side = ia == N - 1;
+                    const int fi = a == 0 ? (i2 + N * i3) : (a == 1 ? (i1 + N * i3) : (i1 + N * i2));
+                    const double E = side ? 0.5 : -0.5;
+                    const double* wf = sWf + (2 * a + side) * 4 * N2 + fi;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) th[a][k] += E * (wf[k * N2] - wown[k]) * ops.winv[ia];
+                }
+            }
+            // physical gradient g[m][k] = J^-1 sum_a Ja_am theta_a[k]
+            double g[3][4];
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    g[m][k] = Jinv * (sG[(1 + m) * N3 + node] * th[0][k] + sG[(4 + m) * N3 + node] * th[1][k]
+                                      + sG[(7 + m) * N3 + node] * th[2][k]);
+            const double beta = sP[4 * N3 + node];
+            const double RT = 0.5 / beta;
+            const double u[3] = {sP[N3 + node], sP[2 * N3 + node], sP[3 * N3 + node]};
+            // du_k/dx_m = RT (g_m[k] + u_k g_m[3]); dT/dx_m = (RT)^2/R g_m[3]
+            double du[3][3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) du[k][m] = RT * (g[m][k] + u[k] * g[m][3]);
+            const double div = du[0][0] + du[1][1] + du[2][2];
+            const double hc = ph.kappa / ph.R * RT * RT;
+            double FV[3][4];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    FV[m][i] = ph.mu * (du[i][m] + du[m][i] - (i == m ? (2.0 / 3.0) * div : 0.0));
+                FV[m][3] = FV[m][0] * u[0] + FV[m][1] * u[1] + FV[m][2] * u[2] + hc * g[m][3];
+            }
+#pragma unroll
+            for (int l = 0; l < 3; ++l)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    Ft[l][k] = sG[(1 + 3 * l) * N3 + node] * FV[0][k] + sG[(2 + 3 * l) * N3 + node] * FV[1][k]
+                             + sG[(3 + 3 * l) * N3 + node] * FV[2][k];
+        }
+        __syncthreads();   // every thread is done reading w / primitives
+        if (active) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) sP[(l * 4 + k) * N3 + node] = Ft[l][k];
+                const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
+                if (il == 0 || il == N - 1) {
+                    const int side = il == N - 1;
+                    const int fi = l == 0 ? (i2 + N * i3) : (l == 1 ? (i1 + N * i3) : (i1 + N * i2));
+                    double* tr = trace + ((el * 6 + 2 * l + side) * 4) * N2 + fi;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) tr[k * N2] = Ft[l][k];
+                }
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
+                const int st = dir_stride<N>(l);
+                const int lb = node - il * st;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int j = 0; j < N; ++j) s += ops.D[il][j] * sP[(l * 4 + k) * N3 + lb + j * st];
+                    sR[(1 + k) * N3 + node] += s;
+                }
+            }
+        }
+    }
+    if (active) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dqdt[eoff + v * N3 + node] = sR[v * N3 + node] * Jinv;
+    }
+}
+
+// BR1 viscous interface term on face nodes, direction by direction (edge nodes see up to 3 faces).
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::EPB_SAT * 2 * Cfg<N>::N2)
+visc_sat_f64(double* __restrict__ dqdt, const double* __restrict__ geom, const int32_t* __restrict__ nbr,
+             const double* __restrict__ trace, int64_t K, const Ops ops) {
+    constexpr int N2 = Cfg<N>::N2, N3 = Cfg<N>::N3;
+    const int t = threadIdx.x;
+    const int el_loc = t / (2 * N2);
+    const int r = t - el_loc * 2 * N2;
+    const int side = r / N2, fi = r - side * N2;
+    const int64_t el = (int64_t)blockIdx.x * Cfg<N>::EPB_SAT + el_loc;
+    const bool active = el < K;
+    const double E = side ? 0.5 : -0.5;
+    const double wi = ops.winv[side ? N - 1 : 0];
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        if (active) {
+            const int st = dir_stride<N>(l);
+            const int own = line_base<N>(l, fi % N, fi / N) + (side ? (N - 1) * st : 0);
+            const int64_t nb = nbr[el * 6 + 2 * l + side];
+            const double* to = trace + ((el * 6 + 2 * l + side) * 4) * N2 + fi;
+            const double* tn = trace + ((nb * 6 + 2 * l + 1 - side) * 4) * N2 + fi;
+            const double c = E * wi / geom[el * 10 * N3 + own];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dqdt[(el * 5 + 1 + k) * N3 + own] += c * (tn[k * N2] - to[k * N2]);
+        }
+        __syncthreads();
+    }
+}
+
+template <int N>
+cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s) {
+    using C = Cfg<N>;
+    const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
+    const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
+    rhs_main_f64<N><<<grid, C::THREADS, smem, s>>>(q, dqdt, c->d_geom, c->d_nbr, (double*)c->d_trace, c->K,
+                                                   c->ops, c->phys);
+    if (c->phys.viscous) {
+        const unsigned g2 = (unsigned)((c->K + C::EPB_SAT - 1) / C::EPB_SAT);
+        visc_sat_f64<N><<<g2, C::EPB_SAT * 2 * C::N2, 0, s>>>(dqdt, c->d_geom, c->d_nbr, (const double*)c->d_trace,
+                                                                c->K, c->ops);
+    }
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t prepare_n() {
+    using C = Cfg<N>;
+    const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
+    return cudaFuncSetAttribute(rhs_main_f64<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+// Opt the fused kernel into more than 48 KB of dynamic shared memory (on the current device).
+cudaError_t prepare_rhs_f64(const esdc_ctx* c) {
+    switch (c->N) {
+        case 2: return prepare_n<2>();
+        case 3: return prepare_n<3>();
+        case 4: return prepare_n<4>();
+        case 5: return prepare_n<5>();
+        case 6: return prepare_n<6>();
+        case 7: return prepare_n<7>();
+        case 8: return prepare_n<8>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rhs_f64(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s) {
+    switch (c->N) {
+        case 2: return launch_rhs_n<2>(c, q, dqdt, s);
+        case 3: return launch_rhs_n<3>(c, q, dqdt, s);
+        case 4: return launch_rhs_n<4>(c, q, dqdt, s);
+        case 5: return launch_rhs_n<5>(c, q, dqdt, s);
+        case 6: return launch_rhs_n<6>(c, q, dqdt, s);
+        case 7: return launch_rhs_n<7>(c, q, dqdt, s);
+        case 8: return launch_rhs_n<8>(c, q, dqdt, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace esdc

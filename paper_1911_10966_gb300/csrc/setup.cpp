@@ -1,0 +1,237 @@
+// Host setup: LGL nodes and weights, SBP operators, curvilinear metric terms, connectivity.
+// Everything here runs once per context in float64 (long double for the node iteration).
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "esdc_internal.h"
+
+namespace esdc {
+
+// Legendre P_n, P_n' and P_n'' at x (long double); P'' from Legendre's differential equation.
+static void legendre3(int n, long double x, long double& P, long double& dP, long double& d2P) {
+    long double p0 = 1.0L, p1 = x;
+    if (n == 0) { P = 1.0L; dP = 0.0L; d2P = 0.0L; return; }
+    for (int k = 1; k < n; ++k) {
+        long double p2 = ((2.0L * k + 1.0L) * x * p1 - k * p0) / (k + 1.0L);
+        p0 = p1;
+        p1 = p2;
+    }
+    P = p1;
+    // P_n' = n (x P_n - P_{n-1}) / (x^2 - 1), valid for |x| < 1
+    dP = n * (x * p1 - p0) / (x * x - 1.0L);
+    d2P = (2.0L * x * dP - n * (n + 1.0L) * P) / (1.0L - x * x);
+}
+
+// LGL nodes: +-1 and the zeros of P_p', found by Newton on P_p' with P_p'' from Legendre's
+// equation, in long double.  Weights 2/(p(p+1) P_p(x)^2) (Sec. 2, diagonal-norm SBP on LGL nodes).
+int lgl(int p, double* xi, double* w) {
+    if (p < 1 || p > kMaxN - 1 || !xi || !w) return ESDC_ERR_ARG;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<long double> x(p + 1);
+    x[0] = -1.0L;
+    x[p] = 1.0L;
+    for (int i = 1; i < p; ++i) {
+        long double g = -std::cos(pi * i / (long double)p);   // Chebyshev-Gauss-Lobatto guess
+        for (int it = 0; it < 60; ++it) {
+            long double P, dP, d2P;
+            legendre3(p, g, P, dP, d2P);
+            long double step = dP / d2P;
+            g -= step;
+            if (std::fabs((double)step) < 1e-19) break;
+        }
+        x[i] = g;
+    }
+    // enforce exact symmetry of the node set
+    for (int i = 0; i <= p / 2; ++i) {
+        long double m = 0.5L * (x[p - i] - x[i]);
+        x[i] = -m;
+        x[p - i] = m;
+    }
+    if (p % 2 == 0) x[p / 2] = 0.0L;
+    for (int i = 0; i <= p; ++i) {
+        long double P, dP, d2P;
+        if (i == 0 || i == p) {
+            P = (i == 0 && (p % 2 == 1)) ? -1.0L : 1.0L;
+        } else {
+            legendre3(p, x[i], P, dP, d2P);
+        }
+        xi[i] = (double)x[i];
+        w[i] = (double)(2.0L / (p * (p + 1.0L) * P * P));
+    }
+    return ESDC_OK;
+}
+
+// D_ij = P_p(x_i)/(P_p(x_j)(x_i - x_j)) for i != j, D_00 = -p(p+1)/4, D_pp = p(p+1)/4, else 0
+// (the closed form of the LGL collocation derivative).  S = (Q - Q^T)/2 with Q = diag(w) D, so
+// S is skew by construction and Q = S + E/2 (Definition 1, item 3).
+int build_operators(int p, HostSetup& hs) {
+    const int N = p + 1;
+    hs.p = p;
+    hs.N = N;
+    hs.xi.assign(N, 0.0);
+    hs.w.assign(N, 0.0);
+    int st = lgl(p, hs.xi.data(), hs.w.data());
+    if (st) return st;
+    std::vector<long double> P(N);
+    for (int i = 0; i < N; ++i) {
+        long double a, b, c;
+        if (i == 0) P[i] = (p % 2 == 1) ? -1.0L : 1.0L;
+        else if (i == p) P[i] = 1.0L;
+        else { legendre3(p, hs.xi[i], a, b, c); P[i] = a; }
+    }
+    hs.D.assign(N * N, 0.0);
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            long double v;
+            if (i != j) v = P[i] / (P[j] * ((long double)hs.xi[i] - (long double)hs.xi[j]));
+            else if (i == 0) v = -p * (p + 1.0L) / 4.0L;
+            else if (i == p) v = p * (p + 1.0L) / 4.0L;
+            else v = 0.0L;
+            hs.D[i * N + j] = (double)v;
+        }
+    hs.S.assign(N * N, 0.0);
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            hs.S[i * N + j] = 0.5 * (hs.w[i] * hs.D[i * N + j] - hs.w[j] * hs.D[j * N + i]);
+    return ESDC_OK;
+}
+
+void build_box_neighbours(int kx, int ky, int kz, std::vector<int32_t>& nbr) {
+    const int64_t K = (int64_t)kx * ky * kz;
+    nbr.assign(K * 6, 0);
+    auto id = [&](int a, int b, int c) {
+        a = (a % kx + kx) % kx;
+        b = (b % ky + ky) % ky;
+        c = (c % kz + kz) % kz;
+        return (int32_t)(a + (int64_t)kx * (b + (int64_t)ky * c));
+    };
+    for (int64_t e = 0; e < K; ++e) {
+        int ex = (int)(e % kx), ey = (int)((e / kx) % ky), ez = (int)(e / ((int64_t)kx * ky));
+        int32_t* n = &nbr[e * 6];
+        n[0] = id(ex - 1, ey, ez);
+        n[1] = id(ex + 1, ey, ez);
+        n[2] = id(ex, ey - 1, ez);
+        n[3] = id(ex, ey + 1, ez);
+        n[4] = id(ex, ey, ez - 1);
+        n[5] = id(ex, ey, ez + 1);
+    }
+}
+
+namespace {
+
+// Apply D along direction a (0: xi1 fastest) to a nodal field of one element.
+void apply_d(const std::vector<double>& D, int N, int a, const double* u, double* out) {
+    const int stride = (a == 0) ? 1 : (a == 1 ? N : N * N);
+    for (int i3 = 0; i3 < N; ++i3)
+        for (int i2 = 0; i2 < N; ++i2)
+            for (int i1 = 0; i1 < N; ++i1) {
+                const int node = (i3 * N + i2) * N + i1;
+                const int ia = (a == 0) ? i1 : (a == 1 ? i2 : i3);
+                const int base = node - ia * stride;
+                double s = 0.0;
+                for (int j = 0; j < N; ++j) s += D[ia * N + j] * u[base + j * stride];
+                out[node] = s;
+            }
+}
+
+// Geometry of one element: J and Ja_lm = J dxi_l/dx_m in conservative curl form,
+// Ja[l][m] = -(curl_xi v)_l with v_j = X_{m+2} dX_{m+1}/dxi_j, (m, m+1, m+2) cyclic.
+// Coordinates are taken relative to the element's first node (the curl form is invariant under
+// translation; relative coordinates keep the products small).
+bool element_geometry(const std::vector<double>& D, int N, const double* xyz, double* g) {
+    const int N3 = N * N * N;
+    std::vector<double> X(3 * N3), dX(9 * N3), v(3 * N3), t1(N3), t2(N3);
+    for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < N3; ++n) X[m * N3 + n] = xyz[m * N3 + n] - xyz[m * N3];
+    for (int m = 0; m < 3; ++m)
+        for (int a = 0; a < 3; ++a) apply_d(D, N, a, &X[m * N3], &dX[(m * 3 + a) * N3]);
+    bool ok = true;
+    for (int n = 0; n < N3; ++n) {
+        auto F = [&](int m, int a) { return dX[(m * 3 + a) * N3 + n]; };
+        double J = F(0, 0) * (F(1, 1) * F(2, 2) - F(1, 2) * F(2, 1))
+                 - F(0, 1) * (F(1, 0) * F(2, 2) - F(1, 2) * F(2, 0))
+                 + F(0, 2) * (F(1, 0) * F(2, 1) - F(1, 1) * F(2, 0));
+        g[n] = J;
+        if (!(J > 0.0) || !std::isfinite(J)) ok = false;
+    }
+    for (int m = 0; m < 3; ++m) {
+        const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
+        for (int j = 0; j < 3; ++j)
+            for (int n = 0; n < N3; ++n) v[j * N3 + n] = X[m2 * N3 + n] * dX[(m1 * 3 + j) * N3 + n];
+        // l = 0: D_2 v_3 - D_3 v_2 ; l = 1: D_3 v_1 - D_1 v_3 ; l = 2: D_1 v_2 - D_2 v_1 (1-based)
+        const int pa[3][2] = {{1, 2}, {2, 0}, {0, 1}};   // (derivative dir of first term, of second term)
+        const int pv[3][2] = {{2, 1}, {0, 2}, {1, 0}};   // (component of first term, of second term)
+        for (int l = 0; l < 3; ++l) {
+            apply_d(D, N, pa[l][0], &v[pv[l][0] * N3], t1.data());
+            apply_d(D, N, pa[l][1], &v[pv[l][1] * N3], t2.data());
+            double* dst = g + (1 + l * 3 + m) * N3;
+            for (int n = 0; n < N3; ++n) {
+                dst[n] = -(t1[n] - t2[n]);
+                if (!std::isfinite(dst[n])) ok = false;
+            }
+        }
+    }
+    return ok;
+}
+
+double element_min_edge(int N, const double* xyz) {
+    const int N3 = N * N * N;
+    auto corner = [&](int i3, int i2, int i1, int m) { return xyz[m * N3 + (i3 * N + i2) * N + i1]; };
+    const int e[2] = {0, N - 1};
+    double best = 1e300;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const int A = e[a], B = e[b];
+            const int ends[3][2][3] = {{{A, B, 0}, {A, B, N - 1}}, {{A, 0, B}, {A, N - 1, B}}, {{0, A, B}, {N - 1, A, B}}};
+            for (int d = 0; d < 3; ++d) {
+                double s = 0.0;
+                for (int m = 0; m < 3; ++m) {
+                    double diff = corner(ends[d][0][0], ends[d][0][1], ends[d][0][2], m)
+                                - corner(ends[d][1][0], ends[d][1][1], ends[d][1][2], m);
+                    s += diff * diff;
+                }
+                best = std::min(best, std::sqrt(s));
+            }
+        }
+    return best;
+}
+
+}  // namespace
+
+int build_geometry(const esdc_setup_t& s, const double* xyz, HostSetup& hs, std::string& err) {
+    const int N = hs.N, N3 = N * N * N;
+    const int64_t K = (int64_t)s.kx * s.ky * s.kz;
+    hs.geom.assign((size_t)K * 10 * N3, 0.0);
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (K < 64) nt = 1;
+    std::vector<int> bad(nt, 0);
+    std::vector<double> hmin(nt, 1e300);
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) {
+        th.emplace_back([&, t]() {
+            for (int64_t e = t; e < K; e += nt) {
+                const double* x = xyz + (size_t)e * 3 * N3;
+                if (!element_geometry(hs.D, N, x, &hs.geom[(size_t)e * 10 * N3])) bad[t] = 1;
+                hmin[t] = std::min(hmin[t], element_min_edge(N, x));
+            }
+        });
+    }
+    for (auto& x : th) x.join();
+    for (unsigned t = 0; t < nt; ++t)
+        if (bad[t]) {
+            err = "metric Jacobian J <= 0 or non-finite geometry in the node coordinates";
+            return ESDC_ERR_MESH;
+        }
+    hs.h_min = *std::min_element(hmin.begin(), hmin.end());
+    if (!(hs.h_min > 0.0)) {
+        err = "degenerate element edge";
+        return ESDC_ERR_MESH;
+    }
+    build_box_neighbours(s.kx, s.ky, s.kz, hs.nbr);
+    return ESDC_OK;
+}
+
+}  // namespace esdc

@@ -1,0 +1,159 @@
+"""Python front end: a thin owner of one library context plus torch tensors for device memory.
+
+Every computation (residual, Runge-Kutta stages, budgets, CFL reduction) is a call into
+libesdc.so; this module only checks shapes/dtypes and passes pointers and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as nat
+from . import inputs
+
+
+def lgl(p: int):
+    """The library's LGL nodes and weights (Sec. 2, Definition 1)."""
+    xi = np.zeros(p + 1)
+    w = np.zeros(p + 1)
+    nat.check(nat.lib().esdc_lgl(p, xi.ctypes.data, w.ctypes.data), "esdc_lgl")
+    return xi, w
+
+
+def _stream_ptr() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Solver:
+    """ES-C residual and DP5 time stepping on one GPU for a periodic kx*ky*kz hexahedral box.
+
+    coords: numpy [K, 3, N, N, N] node coordinates (degree-p mapping at the LGL nodes).
+    precision: "fp64" (whole residual in float64) or "fp32" (float32 residual, float64 state).
+    """
+
+    def __init__(self, p, kx, ky, kz, coords, *, gamma=1.4, Pr=0.72, Ma=0.1, Re=0.0, dissipation=True,
+                 precision="fp64", device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU implementation exists)")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
+        self.p, self.N = p, p + 1
+        self.kx, self.ky, self.kz = kx, ky, kz
+        self.K = kx * ky * kz
+        self.gamma, self.Pr, self.Ma, self.Re = gamma, Pr, Ma, Re
+        self.precision = precision
+        self.dtype_r = torch.float64 if precision == "fp64" else torch.float32
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        if coords.shape != (self.K, 3, self.N, self.N, self.N):
+            raise ValueError(f"coords must have shape {(self.K, 3, self.N, self.N, self.N)}, got {coords.shape}")
+        self.coords = coords
+        st = nat.Setup(p, kx, ky, kz, gamma, Pr, Ma, Re, 1 if dissipation else 0,
+                       nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32)
+        self._ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_create(ctypes.byref(st), coords.ctypes.data, ctypes.byref(self._ctx)),
+                      "esdc_create")
+        self._ws = None
+
+    @classmethod
+    def box(cls, p, kx, ky, kz, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, warp=0.0, seed=0, **kw):
+        xi, _ = lgl(p)
+        return cls(p, kx, ky, kz, inputs.box_coords(xi, kx, ky, kz, lo, hi, warp=warp, seed=seed), **kw)
+
+    # -- lifetime
+    def close(self):
+        if self._ctx is not None and self._ctx.value:
+            nat.lib().esdc_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers
+    @property
+    def n_nodes(self):
+        return self.K * self.N ** 3
+
+    @property
+    def state_shape(self):
+        return (self.K, 5, self.N, self.N, self.N)
+
+    def _check_state(self, q, dtype=torch.float64):
+        if not (isinstance(q, torch.Tensor) and q.is_cuda and q.dtype == dtype and q.is_contiguous()
+                and tuple(q.shape) == self.state_shape and q.device == self.device):
+            raise ValueError(f"expected a contiguous {dtype} CUDA tensor of shape {self.state_shape} on {self.device}")
+
+    def to_device(self, q_np):
+        return torch.as_tensor(np.ascontiguousarray(q_np), dtype=torch.float64, device=self.device)
+
+    def geometry(self):
+        N3 = self.N ** 3
+        J = np.zeros((self.K, N3))
+        Ja = np.zeros((self.K, 9, N3))
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_geometry(self._ctx, J.ctypes.data, Ja.ctypes.data), "esdc_geometry")
+        return J.reshape(self.K, self.N, self.N, self.N), Ja.reshape(self.K, 3, 3, self.N, self.N, self.N)
+
+    # -- the hot path
+    def rhs(self, q, out=None):
+        self._check_state(q)
+        if out is None:
+            out = torch.empty(self.state_shape, dtype=self.dtype_r, device=self.device)
+        else:
+            self._check_state(out, self.dtype_r)
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_rhs(self._ctx, q.data_ptr(), out.data_ptr(), _stream_ptr()), "esdc_rhs")
+        return out
+
+    def rhs_host(self, q_host, out_host=None):
+        """Residual of a host (CPU, preferably pinned) float64 state; returns a host tensor."""
+        if not (isinstance(q_host, torch.Tensor) and not q_host.is_cuda and q_host.dtype == torch.float64
+                and q_host.is_contiguous() and tuple(q_host.shape) == self.state_shape):
+            raise ValueError("q_host must be a contiguous float64 CPU tensor of the state shape")
+        if out_host is None:
+            out_host = torch.empty(self.state_shape, dtype=self.dtype_r, pin_memory=True)
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_rhs_host(self._ctx, q_host.data_ptr(), out_host.data_ptr(), _stream_ptr()),
+                      "esdc_rhs_host")
+        return out_host
+
+    def workspace_bytes(self):
+        b = ctypes.c_size_t()
+        nat.check(nat.lib().esdc_workspace_bytes(self._ctx, 0, ctypes.byref(b)), "esdc_workspace_bytes")
+        return b.value
+
+    def rk_step(self, q, dt, nsteps=1):
+        """Advance q in place by nsteps fixed Dormand-Prince 5 steps."""
+        self._check_state(q)
+        nb = self.workspace_bytes()
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_rk_step(self._ctx, q.data_ptr(), float(dt), int(nsteps), self._ws.data_ptr(),
+                                             self._ws.numel(), _stream_ptr()), "esdc_rk_step")
+        return q
+
+    def budgets(self, q, dqdt=None, check=True):
+        """(sum PJ S, KE, sum PJ w.dq/dt, dKE/dt) in float64 (synchronises)."""
+        self._check_state(q)
+        if dqdt is not None:
+            self._check_state(dqdt, self.dtype_r)
+        out = (ctypes.c_double * 4)()
+        with torch.cuda.device(self.device):
+            code = nat.lib().esdc_budgets(self._ctx, q.data_ptr(), dqdt.data_ptr() if dqdt is not None else None,
+                                          out, _stream_ptr())
+        if check:
+            nat.check(code, "esdc_budgets")
+        return tuple(out)
+
+    def dt_cfl(self, q, cfl=0.5):
+        self._check_state(q)
+        dt = ctypes.c_double()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_dt_cfl(self._ctx, q.data_ptr(), float(cfl), ctypes.byref(dt), _stream_ptr()),
+                      "esdc_dt_cfl")
+        return dt.value

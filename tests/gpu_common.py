@@ -1,0 +1,85 @@
+"""Helpers shared by the GPU tests: build the CUDA solver and the oracle on the same seeded workload.
+
+Each side computes its own LGL nodes and feeds them to the shared input module (node placement and
+initial states only); nothing computed by one side is handed to the other.
+"""
+import math
+
+import numpy as np
+import torch
+
+from oracle import esdc_oracle as O
+from paper_1911_10966_gb300 import inputs as I
+
+TWO_PI_BOX = ([-math.pi] * 3, [math.pi] * 3)
+
+
+def make_pair(p, k, *, warp=0.0, seed=0, Ma=0.1, Re=1600.0, dissipation=True, box=TWO_PI_BOX,
+              state="tgv", noise=0.0, noise_seed=1, precision="fp64"):
+    from paper_1911_10966_gb300.solver import Solver, lgl
+    kx, ky, kz = k
+    lo, hi = box
+    xi_gpu, _ = lgl(p)
+    x_gpu = I.box_coords(xi_gpu, kx, ky, kz, lo, hi, warp=warp, seed=seed)
+    solver = Solver(p, kx, ky, kz, x_gpu, Ma=Ma, Re=Re, dissipation=dissipation, precision=precision)
+    s = O.sbp_operator(p)
+    x_ora = I.box_coords(s.xi.numpy(), kx, ky, kz, lo, hi, warp=warp, seed=seed)
+    mesh = O.make_mesh(p, x_ora, kx, ky, kz)
+    gas = O.Gas.from_mach(Ma, Re)
+
+    def st(x):
+        if state == "tgv":
+            q = I.taylor_green(x, Ma=Ma)
+        elif state == "freestream":
+            q = I.freestream(x, Ma=Ma)
+        elif state == "vortex":
+            q = I.isentropic_vortex(x, Ma=Ma, u_inf=(1 / math.sqrt(2), -1 / math.sqrt(2), 0.0))
+        else:
+            raise ValueError(state)
+        return I.perturb(q, seed=noise_seed, rel=noise) if noise > 0 else q
+
+    return solver, solver.to_device(st(x_gpu)), mesh, gas, torch.tensor(st(x_ora))
+
+
+EPS64 = 2.220446049250313e-16
+
+
+def term_scale(q, mesh, gas, elems=None):
+    """T_v = max over nodes of sum_l sum_j |2 D_ij| |f_v(q_i, q_j)| / J: the magnitude of the terms
+    whose sum is the residual.  Rounding in any float64 evaluation of the residual (the oracle's
+    included) is of order eps * T_v, which exceeds 1e-12 ||R_v|| for smooth low-Mach states where
+    the pressure flux (~1/(gamma Ma^2)) cancels to O(1)."""
+    import dataclasses
+    q = torch.as_tensor(q, dtype=torch.float64)
+    E = torch.arange(q.shape[0]) if elems is None else torch.as_tensor(elems)
+    sabs = dataclasses.replace(mesh.sbp, D=mesh.sbp.D.abs())
+    t = O.volume_term(q[E], mesh.Ja[E], sabs, gas, flux=lambda a, b, n, g: O.ec_flux_n(a, b, n, g).abs())
+    t = t.abs() / mesh.J[E].unsqueeze(1)
+    return [float(t[:, v].max()) for v in range(5)]
+
+
+def assert_parity(r_gpu, r_ora, q_ora, mesh, gas, elems=None, tol=1e-12, c_round=4.0):
+    """Per variable: ||R_gpu - R_ora||_inf <= max(tol ||R_ora||_inf, c_round eps T_v)."""
+    a = r_gpu.detach().double().cpu()
+    b = torch.as_tensor(r_ora).double()
+    T = term_scale(q_ora, mesh, gas, elems)
+    rep = []
+    for v in range(5):
+        err = float((a[:, v] - b[:, v]).abs().max())
+        R = float(b[:, v].abs().max())
+        bound = max(tol * R, c_round * EPS64 * T[v])
+        rep.append((v, err / R if R > 0 else err, EPS64 * T[v] / R if R > 0 else float("inf")))
+        assert err <= bound, f"variable {v}: |dR| = {err:.3e}, ||R|| = {R:.3e}, eps*T = {EPS64 * T[v]:.3e}"
+    print("parity (v, normwise, eps*kappa):", " ".join(f"{v}:{e:.1e}/{k:.1e}" for v, e, k in rep))
+    return rep
+
+
+def normwise_errors(r_gpu, r_ora, abs_floor=0.0):
+    """Per-variable ||R_gpu - R_ora||_inf / max(||R_ora||_inf, abs_floor)."""
+    a = r_gpu.detach().double().cpu()
+    b = torch.as_tensor(r_ora).double()
+    out = []
+    for v in range(5):
+        den = max(float(b[:, v].abs().max()), abs_floor)
+        out.append(float((a[:, v] - b[:, v]).abs().max()) / den)
+    return out

@@ -1,0 +1,101 @@
+"""CPU tests of the C ABI library: it loads, exports every declared symbol, and its host-side setup
+(LGL operator, curl-form metrics, smallest edge, argument checks) matches the oracle.  No kernel is
+launched here."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import esdc_oracle as O
+from paper_1911_10966_gb300 import _native as nat
+from paper_1911_10966_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def L():
+    return nat.lib()
+
+
+def test_exports_every_header_symbol(L):
+    names = nat.header_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("p", range(1, 8))
+def test_operators_match_oracle(L, p):
+    N = p + 1
+    xi, w = np.zeros(N), np.zeros(N)
+    D, S = np.zeros(N * N), np.zeros(N * N)
+    nat.check(L.esdc_lgl(p, xi.ctypes.data, w.ctypes.data), "lgl")
+    nat.check(L.esdc_operators(p, D.ctypes.data, S.ctypes.data), "ops")
+    s = O.sbp_operator(p)
+    assert np.abs(xi - s.xi.numpy()).max() < 1e-15
+    assert np.abs(w - s.w.numpy()).max() < 1e-15
+    D = D.reshape(N, N)
+    S = S.reshape(N, N)
+    assert np.abs(D - s.D.numpy()).max() < 2e-13 * max(1, p * p)
+    assert np.abs(S + S.T).max() == 0.0
+    Q = np.diag(w) @ D
+    E = np.zeros((N, N))
+    E[0, 0], E[-1, -1] = -1, 1
+    assert np.abs(S + 0.5 * E - Q).max() < 1e-13
+
+
+def _setup(p, kx, ky, kz, Re=1600.0):
+    return nat.Setup(p, kx, ky, kz, 1.4, 0.72, 0.1, Re, 1, 0)
+
+
+@pytest.mark.parametrize("p,warp", [(2, 0.0), (3, 0.1), (4, 0.1), (7, 0.1)])
+def test_host_geometry_matches_oracle(L, p, warp):
+    k = (3, 2, 2)
+    s = O.sbp_operator(p)
+    x = I.box_coords(s.xi.numpy(), *k, [-math.pi] * 3, [math.pi] * 3, warp=warp, seed=0)
+    K, N3 = x.shape[0], (p + 1) ** 3
+    J, Ja, h = np.zeros((K, N3)), np.zeros((K, 9, N3)), ctypes.c_double()
+    st = _setup(p, *k)
+    nat.check(L.esdc_host_geometry(ctypes.byref(st), np.ascontiguousarray(x).ctypes.data, J.ctypes.data,
+                                   Ja.ctypes.data, ctypes.byref(h)), "geometry")
+    m = O.make_mesh(p, x, *k)
+    Jo = m.J.numpy().reshape(K, N3)
+    Jao = m.Ja.numpy().reshape(K, 9, N3)
+    # the curl form applies D twice: round-off grows like p^2 (both sides are float64)
+    assert np.abs(J - Jo).max() < 1e-14 * p * p * np.abs(Jo).max()
+    assert np.abs(Ja - Jao).max() < 1e-14 * p * p * np.abs(Jao).max()
+    assert abs(h.value - m.h_min) < 1e-14 * m.h_min
+
+
+def test_argument_errors(L):
+    xi = np.zeros(9)
+    assert L.esdc_lgl(0, xi.ctypes.data, xi.ctypes.data) == nat.ESDC_ERR_ARG
+    assert L.esdc_lgl(8, xi.ctypes.data, xi.ctypes.data) == nat.ESDC_ERR_ARG
+    assert L.esdc_lgl(3, None, xi.ctypes.data) == nat.ESDC_ERR_ARG
+    x = I.box_coords(O.sbp_operator(2).xi.numpy(), 2, 2, 2, [0] * 3, [1] * 3)
+    bad = _setup(2, 2, 2, 2)
+    bad.gamma = 1.0
+    assert L.esdc_host_geometry(ctypes.byref(bad), x.ctypes.data, None, None, None) == nat.ESDC_ERR_ARG
+    bad = _setup(2, 0, 2, 2)
+    assert L.esdc_host_geometry(ctypes.byref(bad), x.ctypes.data, None, None, None) == nat.ESDC_ERR_ARG
+    out = ctypes.c_void_p()
+    assert L.esdc_create(None, x.ctypes.data, ctypes.byref(out)) == nat.ESDC_ERR_ARG
+    assert L.esdc_rhs(None, None, None, None) == nat.ESDC_ERR_ARG
+    assert b"null" in L.esdc_last_error()
+
+
+def test_inverted_mesh_rejected(L):
+    """A mesh whose elements are mirrored (J < 0) is refused at setup with ESDC_ERR_MESH."""
+    p = 2
+    x = I.box_coords(O.sbp_operator(p).xi.numpy(), 2, 2, 2, [0] * 3, [1] * 3)
+    x = np.ascontiguousarray(x[..., ::-1])       # reverse xi1 inside every element
+    st = _setup(p, 2, 2, 2)
+    assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_MESH
+    out = ctypes.c_void_p()
+    assert L.esdc_create(ctypes.byref(st), x.ctypes.data, ctypes.byref(out)) == nat.ESDC_ERR_MESH
+    assert out.value is None
+
+
+def test_strerror(L):
+    for c in (0, -1, -2, -3, -4, -5):
+        assert len(L.esdc_strerror(c)) > 0
