@@ -1,0 +1,352 @@
+"""Benchmark of the ES-C residual + DP5 step on one GB300 (prints one JSON line).
+
+Workload (default): Taylor-Green vortex, Re = 1600, Ma = 0.1, on a 16^3 periodic box of hexahedra with
+smooth sinusoidal node warping (amplitude 0.1 h, phases from seed 0), p = 4 (125 nodes per element,
+512,000 nodes), float64 residual.  One step = one fixed Dormand-Prince 5 step (six residual
+evaluations, stage combinations) plus the float64 budget reduction of the new state.
+Metric: residual DOF/s = nodes x residual evaluations / s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): every rank advances an independent replica of the workload (no data-path
+collective); value = all ranks' node-residuals / max-over-ranks time ("weak" scaling).
+--impl reference times the CPU oracle (plain float64 torch) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="tgv_16cubed_p4_warped", p=4, k=16, warp=0.1, seed=0, Ma=0.1, Re=1600.0, cfl=0.5)
+RHS_PER_STEP = 6
+L2_BYTES = 129 * 2 ** 20
+
+
+# ------------------------------------------------------------------------------------------------
+# Algorithmic work per node per residual evaluation (convention: +, -, * = 1 flop; fma = 2;
+# division, square root and logarithm = 1 each).  Counted from the operations the method needs on
+# a curvilinear mesh with the viscous terms on and the log means on their series branch.
+# ------------------------------------------------------------------------------------------------
+FLOPS_PAIR = 82          # one two-point flux contracted with the averaged metric + pair accumulation
+FLOPS_LINE_NODE = 30     # per node: three directions x (5 mul + 5 add) scaling by 1/w
+FLOPS_NODE_PRE = 22      # primitives, beta and entropy variables
+FLOPS_SAT_NODE = 140     # per face node: neighbour primitives, EC flux, LLF dissipation, lift
+FLOPS_VISC_NODE = 211    # physical gradient, tau, heat flux, contravariant fluxes (plus 24N + 96/N)
+FLOPS_DIV_NODE = 12      # (plus 24N) divergence of the contravariant viscous fluxes
+FLOPS_SCALE_NODE = 5
+FLOPS_VSAT_NODE = 15     # per face node: BR1 viscous interface term
+
+
+def element_kernel_flops_per_node(p: int, viscous: bool = True) -> float:
+    N = p + 1
+    f = FLOPS_PAIR * 3 * (N - 1) / 2 + FLOPS_LINE_NODE + FLOPS_NODE_PRE + FLOPS_SAT_NODE * 6 / N + FLOPS_SCALE_NODE
+    if viscous:
+        f += FLOPS_VISC_NODE + 24 * N + 96 / N + FLOPS_DIV_NODE + 24 * N
+    return f
+
+
+def residual_flops_per_node(p: int, viscous: bool = True) -> float:
+    return element_kernel_flops_per_node(p, viscous) + (FLOPS_VSAT_NODE * 6 / (p + 1) if viscous else 0.0)
+
+
+def element_kernel_bytes_per_node(p: int) -> float:
+    """Compulsory HBM bytes of the element kernel: read q (40) and geometry (80), write dq/dt (40)
+    and the viscous face traces (6 N^2 x 32 per element).  Neighbour face states are L2 hits."""
+    N = p + 1
+    return 40 + 80 + 40 + 6 * 32 / N
+
+
+def _sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def _ncu_traffic(kernel_src):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current source."""
+    f = os.path.join(ROOT, "profiles", "rhs_main_f64_tgv_16cubed_p4.md")
+    if not os.path.exists(f):
+        return None
+    txt = open(f).read()
+    sha = None
+    val = None
+    for line in txt.splitlines():
+        if line.startswith("source_sha256_16:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            val = float(line.split(":", 1)[1].strip())
+    return val if (sha == _sha(kernel_src) and val is not None) else None
+
+
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"esdc_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _config(args, extra=None):
+    c = {"workload": WORKLOAD["name"], "mesh": f"{WORKLOAD['k']}^3 hexahedra, sinusoidal warp 0.1h",
+         "p": WORKLOAD["p"], "nodes": WORKLOAD["k"] ** 3 * (WORKLOAD["p"] + 1) ** 3, "Re": WORKLOAD["Re"],
+         "Ma": WORKLOAD["Ma"], "step": "DP5 step (6 residuals) + float64 budgets", "replicas": args.gpus,
+         "l2": "flushed between timed steps (256 MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+REF_SAMPLE_ELEMENTS = 512
+
+
+def _oracle_problem():
+    from oracle import esdc_oracle as O
+    from paper_1911_10966_gb300 import inputs as I
+    p, k = WORKLOAD["p"], WORKLOAD["k"]
+    s = O.sbp_operator(p)
+    x = I.box_coords(s.xi.numpy(), k, k, k, [-math.pi] * 3, [math.pi] * 3, warp=WORKLOAD["warp"], seed=WORKLOAD["seed"])
+    mesh = O.make_mesh(p, x, k, k, k)
+    gas = O.Gas.from_mach(WORKLOAD["Ma"], WORKLOAD["Re"])
+    q = torch.tensor(I.taylor_green(x, Ma=WORKLOAD["Ma"]))
+    return O, mesh, gas, q
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on the host cores.  Each step: the six residual evaluations of a
+    DP5 step restricted to a fixed seeded sample of 512 of the 4096 elements (each with its
+    neighbour closure), so that the whole run stays within minutes."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    O, mesh, gas, q = _oracle_problem()
+    E = torch.tensor(np.sort(np.random.default_rng(0).choice(mesh.J.shape[0], REF_SAMPLE_ELEMENTS, replace=False)))
+    for _ in range(args.warmup):
+        O.rhs(q, mesh, gas, elems=E)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(RHS_PER_STEP):
+            O.rhs(q, mesh, gas, elems=E)
+    el = time.perf_counter() - t0
+    n = REF_SAMPLE_ELEMENTS * (WORKLOAD["p"] + 1) ** 3
+    val = n * RHS_PER_STEP * args.steps / el
+    cores = torch.get_num_threads()
+    line = {"impl": "reference", "metric": "residual DOF/s (nodes x RHS / s), FP64", "value": val,
+            "unit": "node-RHS/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(args),
+            "cpu_baseline": {"value": val, "unit": "node-RHS/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step 6 oracle residuals on {REF_SAMPLE_ELEMENTS} of 4096 elements, "
+                                       f"{cores} threads"},
+            "e2e": {"value": val, "unit": "node-RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """Oracle timed on the host cores: one DP5 step (6 residuals) of the full workload."""
+    O, mesh, gas, q = _oracle_problem()
+    p, k = WORKLOAD["p"], WORKLOAD["k"]
+    dt = O.cfl_dt(q, mesh, gas, WORKLOAD["cfl"])
+    t0 = time.perf_counter()
+    O.rk_step(q, lambda st: O.rhs(st, mesh, gas), dt, 1)
+    el = time.perf_counter() - t0
+    cores = torch.get_num_threads()
+    return {"value": k ** 3 * (p + 1) ** 3 * RHS_PER_STEP / el, "unit": "node-RHS/s", "cores": cores, "kind": "oracle",
+            "sample": f"one DP5 step (6 residuals) of the full 16^3 p=4 workload, {el:.1f} s on {cores} threads"}
+
+
+def run_ours(args):
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1911_10966_gb300 import inputs as I
+    from paper_1911_10966_gb300.solver import Solver, probe_fma
+
+    W = WORKLOAD
+    solver = Solver.box(W["p"], W["k"], W["k"], W["k"], warp=W["warp"], seed=W["seed"], Ma=W["Ma"], Re=W["Re"])
+    q_init = I.taylor_green(solver.coords, Ma=W["Ma"])
+    q = solver.to_device(q_init)
+    dt = solver.dt_cfl(q, W["cfl"])
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=q.device)
+    n = solver.n_nodes
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        solver.rk_step(q, dt, 1)
+        solver.budgets(q)
+    peak_f64 = probe_fma("f64")
+
+    # ---- device-timed region: inputs resident in HBM
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    solver.profile(True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.6)          # let the sampler start before the timed region
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            solver.rk_step(q, dt, 1)
+            solver.budgets(q)
+            evs[i][1].record(stream)
+        barrier()
+    ms_main, ms_face, nres = solver.profile_read()
+    solver.profile(False)
+    ms_step = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ms_max = ms_step
+    if dist is not None:
+        t = torch.tensor([ms_step], device=q.device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t)
+    value = ws * n * RHS_PER_STEP / (ms_max * 1e-3)
+
+    # ---- end to end through the public API with host buffers
+    q_host = torch.from_numpy(np.ascontiguousarray(q_init)).pin_memory()
+    q_back = torch.empty_like(q_host).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        qd = q.copy_(q_host, non_blocking=True)
+        solver.rk_step(qd, dt, 1)
+        solver.budgets(qd)
+        q_back.copy_(qd, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_val = ws * n * RHS_PER_STEP / e2e_s
+
+    # ---- residual-only throughput (the metric's unit operation), same stream and inputs
+    r = torch.empty_like(q)
+    solver.rhs(q, out=r)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    flush.fill_(0.0)
+    a.record(stream)
+    for _ in range(reps):
+        solver.rhs(q, out=r)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_rhs = a.elapsed_time(b) / reps
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    src = os.path.join(ROOT, "paper_1911_10966_gb300", "csrc", "rhs_f64.cu")
+    fl = element_kernel_flops_per_node(W["p"]) * n
+    kernel_ms = ms_main / max(nres, 1)
+    achieved = fl / (kernel_ms * 1e-3) / 1e12
+    peak = peak_f64 / 1e12
+    clocks = clk.summary()
+    line = {
+        "metric": "residual DOF/s (nodes x RHS / s), FP64", "value": value, "unit": "node-RHS/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(args),
+        "roofline": {"bound": "alu", "kernel": "rhs_main_f64<5>", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _ncu_traffic(src),
+                     "peak_source": "measured float64 FMA throughput (esdc_probe_fma) in this run",
+                     "flops_per_launch": fl, "kernel_ms": kernel_ms,
+                     "hbm_frac": element_kernel_bytes_per_node(W["p"]) * n / (kernel_ms * 1e-3) / 6690.1e9},
+        "cpu_baseline": cpu_baseline_sample() if (ws == 1 and not args.no_cpu_baseline) else None,
+        "e2e": {"value": e2e_val, "unit": "node-RHS/s", "h2d_bytes_per_step": n * 40,
+                "d2h_bytes_per_step": n * 40 + 40},
+        "gpu_launches": args.steps * (RHS_PER_STEP * 2 + RHS_PER_STEP + 2),
+        "clocks": clocks,
+        "rhs_only": {"value": n / (ms_rhs * 1e-3), "unit": "node-RHS/s", "ms": ms_rhs,
+                     "face_kernel_ms": ms_face / max(nres, 1)},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

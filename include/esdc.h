@@ -151,6 +151,25 @@ int esdc_budgets(esdc_ctx* ctx, const double* q_dev, const void* dqdt_dev, doubl
  */
 int esdc_dt_cfl(esdc_ctx* ctx, const double* q_dev, double cfl, double* dt_host, void* stream);
 
+/*
+ * esdc_profile -- enable (on = 1) or disable CUDA-event timing of the residual kernels of this
+ * context: every esdc_rhs (also inside esdc_rk_step) then records an event pair around the fused
+ * element kernel and another around the viscous interface kernel on the call's stream.
+ * esdc_profile_read synchronises, returns the summed milliseconds of each kernel and the number of
+ * residual evaluations timed since profiling was enabled, and resets the sums.  Not part of the
+ * method (a measurement aid).
+ */
+int esdc_profile(esdc_ctx* ctx, int on);
+int esdc_profile_read(esdc_ctx* ctx, double* ms_element_kernel, double* ms_face_kernel, int64_t* count);
+
+/*
+ * esdc_probe_fma -- measured FMA throughput of the current device in FLOP/s (2 per FMA): kind 0
+ * float64, kind 1 float32; eight independent chains per thread, 8 CTAs of 256 threads per SM,
+ * best of three timed launches.  Allocates and frees a small scratch buffer.  Synchronous.
+ * Not part of the method: it supplies the arithmetic roofline denominators.
+ */
+int esdc_probe_fma(int kind, double* flops_per_s, void* stream);
+
 /* esdc_strerror -- static description of a status code. */
 const char* esdc_strerror(int status);
 

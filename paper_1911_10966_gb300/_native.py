@@ -58,6 +58,9 @@ def lib() -> ctypes.CDLL:
         "esdc_rk_step": (I, [P, P, D, I, P, S, P]),
         "esdc_budgets": (I, [P, P, P, ctypes.POINTER(D), P]),
         "esdc_dt_cfl": (I, [P, P, D, ctypes.POINTER(D), P]),
+        "esdc_profile": (I, [P, I]),
+        "esdc_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)]),
+        "esdc_probe_fma": (I, [I, ctypes.POINTER(D), P]),
         "esdc_strerror": (ctypes.c_char_p, [I]),
         "esdc_last_error": (ctypes.c_char_p, []),
     }

@@ -45,9 +45,24 @@ const double kA[6][5] = {
     {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0}};
 const double kB[6] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0};
 
+// Four profiling events for the next residual evaluation (NULL when profiling is off).
+cudaEvent_t* next_events(esdc_ctx* c) {
+    if (!c->profiling) return nullptr;
+    if (c->prof_used + 4 > c->prof_events.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+            c->prof_events.push_back((void*)ev);
+        }
+    }
+    cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(&c->prof_events[c->prof_used]);
+    c->prof_used += 4;
+    return ev;
+}
+
 int rhs_impl(esdc_ctx* c, const double* q, void* dqdt, cudaStream_t s) {
     cudaError_t e;
-    if (c->setup.precision == ESDC_PREC_FP64) e = esdc::launch_rhs_f64(c, q, (double*)dqdt, s);
+    if (c->setup.precision == ESDC_PREC_FP64) e = esdc::launch_rhs_f64(c, q, (double*)dqdt, s, next_events(c));
     else return fail(ESDC_ERR_UNSUPPORTED, "float32 residual not available in this build");
     if (e != cudaSuccess) return cuda_fail(e, "esdc_rhs launch");
     return ESDC_OK;
@@ -55,6 +70,7 @@ int rhs_impl(esdc_ctx* c, const double* q, void* dqdt, cudaStream_t s) {
 
 void free_ctx(esdc_ctx* c) {
     if (!c) return;
+    for (void* ev : c->prof_events) cudaEventDestroy((cudaEvent_t)ev);
     cudaFree(c->d_geom);
     cudaFree(c->d_geomf);
     cudaFree(c->d_nbr);
@@ -351,6 +367,40 @@ int esdc_dt_cfl(esdc_ctx* c, const double* q, double cfl, double* dt, void* stre
         d = std::fmin(d, c->h_min * c->h_min / (N2 * N2 * nu));
     }
     *dt = cfl * d;
+    return ESDC_OK;
+}
+
+int esdc_profile(esdc_ctx* c, int on) {
+    if (!c) return fail(ESDC_ERR_ARG, "null context");
+    c->profiling = on ? 1 : 0;
+    c->prof_used = 0;
+    return ESDC_OK;
+}
+
+int esdc_profile_read(esdc_ctx* c, double* ms_main, double* ms_face, int64_t* count) {
+    if (!c) return fail(ESDC_ERR_ARG, "null context");
+    double a = 0.0, b = 0.0;
+    const size_t n = c->prof_used / 4;
+    for (size_t i = 0; i < n; ++i) {
+        cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(&c->prof_events[4 * i]);
+        CUDA_TRY(cudaEventSynchronize(ev[3]));
+        float x = 0.f, y = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&x, ev[0], ev[1]));
+        CUDA_TRY(cudaEventElapsedTime(&y, ev[2], ev[3]));
+        a += x;
+        b += y;
+    }
+    if (ms_main) *ms_main = a;
+    if (ms_face) *ms_face = b;
+    if (count) *count = (int64_t)n;
+    c->prof_used = 0;
+    return ESDC_OK;
+}
+
+int esdc_probe_fma(int kind, double* flops_per_s, void* stream) {
+    if (!flops_per_s || (kind != 0 && kind != 1)) return fail(ESDC_ERR_ARG, "kind 0 or 1 and an output pointer");
+    cudaError_t e = esdc::probe_fma(kind, flops_per_s, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "esdc_probe_fma");
     return ESDC_OK;
 }
 

@@ -79,6 +79,10 @@ struct esdc_ctx {
     double* d_red = nullptr;         // reduction partials
     double* d_red_out = nullptr;     // reduction results
     int red_blocks = 0;
+    // CUDA-event profiling of the residual kernels (esdc_profile)
+    int profiling = 0;
+    std::vector<void*> prof_events;  // cudaEvent_t quadruples: main start/stop, face start/stop
+    size_t prof_used = 0;
     // staging for esdc_rhs_host
     double* d_stage_q = nullptr;
     void* d_stage_r = nullptr;

@@ -8,7 +8,8 @@
 namespace esdc {
 
 cudaError_t prepare_rhs_f64(const esdc_ctx* c);
-cudaError_t launch_rhs_f64(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s);
+// ev: NULL, or four events recorded around the element kernel and the face kernel
+cudaError_t launch_rhs_f64(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev);
 
 // out = q0 + sum_j coef[j] * k[j]   (n doubles; k pointers may alias nothing but each other)
 struct Combine {
@@ -21,5 +22,7 @@ cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int
 // Reductions: budgets (4 sums + non-physical count) and CFL inputs (max |u|+c, min rho).
 cudaError_t launch_budgets(const esdc_ctx* c, const double* q, const void* dqdt, int dq_f32, cudaStream_t s);
 cudaError_t launch_cfl(const esdc_ctx* c, const double* q, cudaStream_t s);
+
+cudaError_t probe_fma(int kind, double* flops_per_s, cudaStream_t s);
 
 }  // namespace esdc

@@ -369,17 +369,21 @@ visc_sat_f64(double* __restrict__ dqdt, const double* __restrict__ geom, const i
 }
 
 template <int N>
-cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s) {
+cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev) {
     using C = Cfg<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
+    if (ev) cudaEventRecord(ev[0], s);
     rhs_main_f64<N><<<grid, C::THREADS, smem, s>>>(q, dqdt, c->d_geom, c->d_nbr, (double*)c->d_trace, c->K,
                                                    c->ops, c->phys);
+    if (ev) cudaEventRecord(ev[1], s);
+    if (ev) cudaEventRecord(ev[2], s);
     if (c->phys.viscous) {
         const unsigned g2 = (unsigned)((c->K + C::EPB_SAT - 1) / C::EPB_SAT);
         visc_sat_f64<N><<<g2, C::EPB_SAT * 2 * C::N2, 0, s>>>(dqdt, c->d_geom, c->d_nbr, (const double*)c->d_trace,
                                                                 c->K, c->ops);
     }
+    if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
 
@@ -406,15 +410,15 @@ cudaError_t prepare_rhs_f64(const esdc_ctx* c) {
     }
 }
 
-cudaError_t launch_rhs_f64(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s) {
+cudaError_t launch_rhs_f64(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev) {
     switch (c->N) {
-        case 2: return launch_rhs_n<2>(c, q, dqdt, s);
-        case 3: return launch_rhs_n<3>(c, q, dqdt, s);
-        case 4: return launch_rhs_n<4>(c, q, dqdt, s);
-        case 5: return launch_rhs_n<5>(c, q, dqdt, s);
-        case 6: return launch_rhs_n<6>(c, q, dqdt, s);
-        case 7: return launch_rhs_n<7>(c, q, dqdt, s);
-        case 8: return launch_rhs_n<8>(c, q, dqdt, s);
+        case 2: return launch_rhs_n<2>(c, q, dqdt, s, ev);
+        case 3: return launch_rhs_n<3>(c, q, dqdt, s, ev);
+        case 4: return launch_rhs_n<4>(c, q, dqdt, s, ev);
+        case 5: return launch_rhs_n<5>(c, q, dqdt, s, ev);
+        case 6: return launch_rhs_n<6>(c, q, dqdt, s, ev);
+        case 7: return launch_rhs_n<7>(c, q, dqdt, s, ev);
+        case 8: return launch_rhs_n<8>(c, q, dqdt, s, ev);
         default: return cudaErrorInvalidValue;
     }
 }

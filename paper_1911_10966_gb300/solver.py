@@ -22,6 +22,14 @@ def lgl(p: int):
     return xi, w
 
 
+def probe_fma(kind: str = "f64") -> float:
+    """Measured FMA throughput of the current GPU in FLOP/s (library microbenchmark)."""
+    out = ctypes.c_double()
+    nat.check(nat.lib().esdc_probe_fma(0 if kind == "f64" else 1, ctypes.byref(out), _stream_ptr()),
+              "esdc_probe_fma")
+    return out.value
+
+
 def _stream_ptr() -> int:
     return torch.cuda.current_stream().cuda_stream
 
@@ -149,6 +157,18 @@ class Solver:
         if check:
             nat.check(code, "esdc_budgets")
         return tuple(out)
+
+    def profile(self, on=True):
+        """Record CUDA events around the residual kernels of every following evaluation."""
+        nat.check(nat.lib().esdc_profile(self._ctx, 1 if on else 0), "esdc_profile")
+
+    def profile_read(self):
+        """(ms in the element kernel, ms in the face kernel, evaluations) since profile(True)."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_profile_read(self._ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+                      "esdc_profile_read")
+        return a.value, b.value, n.value
 
     def dt_cfl(self, q, cfl=0.5):
         self._check_state(q)
