@@ -170,6 +170,28 @@ int esdc_profile_read(esdc_ctx* ctx, double* ms_element_kernel, double* ms_face_
  */
 int esdc_probe_fma(int kind, double* flops_per_s, void* stream);
 
+/*
+ * esdc_budgets_noalloc -- the four float64 budgets of esdc_budgets for callers that cannot
+ * allocate device memory: code running where cudaMalloc is forbidden or unsafe (while another
+ * component captures the stream into a graph, inside a fixed device-memory budget handed out once
+ * at start-up, or in hosts whose allocator owns all device memory).  It needs no context and
+ * performs no cudaMalloc, cudaFree or other allocating call.  The paper has no counterpart: it is
+ * a deployment variant of the budget reduction, not part of the method.
+ *   N: nodes per direction (2..8); K: elements; gamma: ratio of specific heats;
+ *   w_host[N]: the LGL weights (esdc_lgl); q_dev, dqdt_dev (nullable), J_dev: float64 device
+ *   arrays in the esdc_rhs layouts, J_dev[K][N^3] the metric Jacobian (esdc_geometry);
+ *   out_dev[5]: caller-owned device memory receiving (sum PJ S, KE, sum PJ w.dq/dt, dKE/dt, number
+ *   of non-finite or non-physical nodes); out_dev[2..3] are 0 when dqdt_dev is NULL.
+ * Scratch: a static device array of 65536 x 5 doubles (2.6 MB) in every process that loads the
+ * library, held on each GPU until exit; inputs above 268,435,456 nodes are rejected with
+ * ESDC_ERR_ARG.  The first call on a device looks the array's device address up (cudaGetSymbolAddress
+ * with that device current), so make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other threads) race and give wrong sums.
+ * Asynchronous on stream; deterministic order.  Errors: ESDC_ERR_ARG, ESDC_ERR_CUDA.
+ */
+int esdc_budgets_noalloc(int N, int64_t K, double gamma, const double* w_host, const double* q_dev,
+                         const double* dqdt_dev, const double* J_dev, double* out_dev, void* stream);
+
 /* esdc_strerror -- static description of a status code. */
 const char* esdc_strerror(int status);
 

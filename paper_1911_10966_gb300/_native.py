@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         "esdc_profile": (I, [P, I]),
         "esdc_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)]),
         "esdc_probe_fma": (I, [I, ctypes.POINTER(D), P]),
+        "esdc_budgets_noalloc": (I, [I, ctypes.c_int64, D, P, P, P, P, P, P]),
         "esdc_strerror": (ctypes.c_char_p, [I]),
         "esdc_last_error": (ctypes.c_char_p, []),
     }

@@ -84,6 +84,10 @@ void free_ctx(esdc_ctx* c) {
 
 }  // namespace
 
+namespace esdc {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace esdc
+
 extern "C" {
 
 const char* esdc_last_error(void) { return g_err.c_str(); }

@@ -58,6 +58,7 @@ int lgl(int p, double* xi, double* w);
 int build_operators(int p, HostSetup& hs);
 int build_geometry(const esdc_setup_t& s, const double* xyz, HostSetup& hs, std::string& err);
 void build_box_neighbours(int kx, int ky, int kz, std::vector<int32_t>& nbr);
+void set_last_error(const std::string& msg);   // message returned by esdc_last_error on this thread
 
 }  // namespace esdc
 
