@@ -69,6 +69,13 @@ def element_kernel_bytes_per_node(p: int) -> float:
     return 40 + 80 + 40 + 6 * 32 / N
 
 
+def element_kernel_bytes_per_node_f32(p: int) -> float:
+    """float32 form: read the float32 perturbation state (20) and float32 geometry (40), write
+    dq/dt (20) and the float32 viscous traces (6 N^2 x 16 per element)."""
+    N = p + 1
+    return 20 + 40 + 20 + 6 * 16 / N
+
+
 def _sha(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
@@ -299,6 +306,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms_rhs = a.elapsed_time(b) / reps
 
+    fp32 = _fp32_leg(args, solver, q_init, dt, flush, barrier, dist, ws) if not args.no_fp32 else None
+    if fp32 is not None:
+        fp32["speedup_vs_f64_rhs"] = (ms_main / max(nres, 1)) / fp32["roofline"]["kernel_ms"]
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -326,10 +337,74 @@ def run_ours(args):
         "clocks": clocks,
         "rhs_only": {"value": n / (ms_rhs * 1e-3), "unit": "node-RHS/s", "ms": ms_rhs,
                      "face_kernel_ms": ms_face / max(nres, 1)},
+        "fp32_mixed": fp32,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _fp32_leg(args, s64, q_init, dt, flush, barrier, dist, ws):
+    """The mixed-precision form on the same workload: float32 residual, float64 state and budgets."""
+    from paper_1911_10966_gb300.solver import Solver, probe_fma
+    W = WORKLOAD
+    s32 = Solver(W["p"], W["k"], W["k"], W["k"], s64.coords, Ma=W["Ma"], Re=W["Re"], precision="fp32")
+    n = s32.n_nodes
+    q = s32.to_device(q_init)
+    # error of the float32 residual against the float64 path (itself parity-checked against the oracle)
+    r64 = s64.rhs(q)
+    r32 = s32.rhs(q)
+    e_v = [float((r32[:, v].double() - r64[:, v]).abs().max() / r64[:, v].abs().max()) for v in range(5)]
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        s32.rk_step(q, dt, 1)
+        s32.budgets(q)
+    peak32 = probe_fma("f32")
+    steps = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    s32.profile(True)
+    barrier()
+    for i in range(steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        s32.rk_step(q, dt, 1)
+        s32.budgets(q)
+        evs[i][1].record(stream)
+    barrier()
+    ms_main, ms_face, nres = s32.profile_read()
+    s32.profile(False)
+    ms_step = sum(a.elapsed_time(b) for a, b in evs) / steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device=q.device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t)
+    # kinetic-energy dissipation rate after the same number of steps in both precisions
+    qa = s64.to_device(q_init)
+    qb = s32.to_device(q_init)
+    s64.rk_step(qa, dt, 5)
+    s32.rk_step(qb, dt, 5)
+    k64 = s64.budgets(qa, s64.rhs(qa))[3]
+    k32 = s32.budgets(qb, s32.rhs(qb))[3]
+    kernel_ms = ms_main / max(nres, 1)
+    fl = element_kernel_flops_per_node(W["p"]) * n
+    by = element_kernel_bytes_per_node_f32(W["p"]) * n
+    t_alu = fl / peak32
+    t_hbm = by / 6690.1e9
+    bound = "alu" if t_alu >= t_hbm else "hbm"
+    if bound == "alu":
+        roof = {"bound": "alu", "achieved": fl / (kernel_ms * 1e-3) / 1e12, "peak": peak32 / 1e12, "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": by / (kernel_ms * 1e-3) / 1e9, "peak": 6690.1, "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update({"kernel": "rhs_main_f32<5>", "kernel_ms": kernel_ms, "flops_per_launch": fl, "bytes_per_launch": by,
+                 "alu_frac": fl / (kernel_ms * 1e-3) / peak32, "hbm_frac": by / (kernel_ms * 1e-3) / 6690.1e9,
+                 "peak_source": "measured float32 FMA throughput (esdc_probe_fma) / MEASURED_PEAKS hbm_gbs"})
+    return {"value": ws * n * RHS_PER_STEP / (ms_step * 1e-3), "unit": "node-RHS/s", "ms_per_step": ms_step,
+            "dtype": "f32 residual, f64 state/update/budgets", "roofline": roof,
+            "residual_error_vs_f64": {"per_variable": e_v, "variables": ["rho", "rho u1", "rho u2", "rho u3", "rho E"]},
+            "ke_rate_rel_error_5_steps": abs(k32 - k64) / abs(k64),
+            "gpu_launches": steps * (RHS_PER_STEP * 2 + RHS_PER_STEP + 1 + 2),
+            "speedup_vs_f64_rhs": None}
 
 
 def main():
@@ -339,6 +414,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the mixed-precision leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

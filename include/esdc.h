@@ -105,6 +105,9 @@ int esdc_geometry(const esdc_ctx* ctx, double* J_host, double* Ja_host);
  * with I^(E) the Hadamard flux differencing of eq. discEL using the Chandrashekar two-point flux.
  * q_dev: [K][5][N^3] float64 device state (read only).
  * dqdt_dev: [K][5][N^3] device output; float64 for ESDC_PREC_FP64, float32 for ESDC_PREC_FP32.
+ * ESDC_PREC_FP32: q is first rounded to the float32 perturbation (rho - 1, rho u, rho E - E0) in a
+ * library buffer (the subtraction in float64), and the whole residual is then float32 arithmetic
+ * with the reference state rho = 1, p = R split off exactly (see csrc/rhs_f32.cu).
  * q_dev and dqdt_dev must not overlap.  Asynchronous on stream.
  */
 int esdc_rhs(esdc_ctx* ctx, const double* q_dev, void* dqdt_dev, void* stream);
@@ -117,8 +120,9 @@ int esdc_rhs(esdc_ctx* ctx, const double* q_dev, void* dqdt_dev, void* stream);
 int esdc_rhs_host(esdc_ctx* ctx, const double* q_host, void* dqdt_host, void* stream);
 
 /*
- * esdc_workspace_bytes -- device workspace needed by esdc_rk_step (what = 0): six stage
- * derivatives and one stage state, each K*5*N^3 float64.
+ * esdc_workspace_bytes -- device workspace needed by esdc_rk_step (what = 0): for ESDC_PREC_FP64
+ * six stage derivatives and one stage state, each K*5*N^3 float64; for ESDC_PREC_FP32 six float32
+ * stage derivatives and two float32 perturbation states (each sub-buffer 256-byte aligned).
  */
 int esdc_workspace_bytes(const esdc_ctx* ctx, int what, size_t* bytes);
 
@@ -126,8 +130,10 @@ int esdc_workspace_bytes(const esdc_ctx* ctx, int what, size_t* bytes);
  * esdc_rk_step -- nsteps fixed steps of size dt of the 5th-order Dormand-Prince solution
  * (six residual evaluations per step; Sec. 5 uses this integrator with adaptive steps).
  * q_dev: [K][5][N^3] float64, updated in place.  workspace_dev: caller-owned device memory of at
- * least esdc_workspace_bytes(ctx, 0) bytes, 256-byte aligned.  The stage state and accumulation
- * are float64 in both precision modes.  Asynchronous on stream.
+ * least esdc_workspace_bytes(ctx, 0) bytes, 256-byte aligned.  The solution q and its update
+ * q += dt sum_j b_j k_j are float64 in both precision modes; in ESDC_PREC_FP32 the stage states that
+ * feed the float32 residual are float32 perturbations (rho - 1, rho u, rho E - E0) formed from the
+ * float64 state.  Asynchronous on stream.
  */
 int esdc_rk_step(esdc_ctx* ctx, double* q_dev, double dt, int nsteps, void* workspace_dev,
                  size_t workspace_bytes, void* stream);

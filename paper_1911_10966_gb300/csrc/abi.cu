@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "esdc_internal.h"
 #include "kernels.h"
@@ -62,9 +63,54 @@ cudaEvent_t* next_events(esdc_ctx* c) {
 
 int rhs_impl(esdc_ctx* c, const double* q, void* dqdt, cudaStream_t s) {
     cudaError_t e;
-    if (c->setup.precision == ESDC_PREC_FP64) e = esdc::launch_rhs_f64(c, q, (double*)dqdt, s, next_events(c));
-    else return fail(ESDC_ERR_UNSUPPORTED, "float32 residual not available in this build");
+    if (c->setup.precision == ESDC_PREC_FP64) {
+        e = esdc::launch_rhs_f64(c, q, (double*)dqdt, s, next_events(c));
+    } else {
+        e = esdc::launch_shadow(c, q, c->d_shadow, s);
+        if (e == cudaSuccess) e = esdc::launch_rhs_f32(c, c->d_shadow, (float*)dqdt, s, next_events(c));
+    }
     if (e != cudaSuccess) return cuda_fail(e, "esdc_rhs launch");
+    return ESDC_OK;
+}
+
+// Mixed precision: nsteps DP5 steps with float32 residuals on float32 perturbation stage states and
+// the float64 solution update q += dt sum_j b_j k_j (accumulated in float64).
+int rk_step_f32(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s) {
+    const int64_t n = c->n_nodes * 5;
+    const size_t sub = round256((size_t)n * sizeof(float));
+    float* k[6];
+    for (int j = 0; j < 6; ++j) k[j] = (float*)((char*)ws + j * sub);
+    float* stage = (float*)((char*)ws + 6 * sub);
+    float* base = (float*)((char*)ws + 7 * sub);
+    cudaError_t e = esdc::launch_shadow(c, q, base, s);
+    if (e != cudaSuccess) return cuda_fail(e, "shadow");
+    for (int step = 0; step < nsteps; ++step) {
+        for (int st = 0; st < 6; ++st) {
+            const float* in = base;
+            if (st > 0) {
+                esdc::CombineF cb{};
+                cb.nk = st;
+                for (int j = 0; j < st; ++j) {
+                    cb.k[j] = k[j];
+                    cb.coef[j] = (float)(dt * kA[st][j]);
+                }
+                e = esdc::launch_stage_f32(base, cb, stage, n, s);
+                if (e != cudaSuccess) return cuda_fail(e, "stage combine (float32)");
+                in = stage;
+            }
+            e = esdc::launch_rhs_f32(c, in, k[st], s, next_events(c));
+            if (e != cudaSuccess) return cuda_fail(e, "residual (float32)");
+        }
+        esdc::Combine64F cb{};
+        for (int j = 0; j < 6; ++j)
+            if (kB[j] != 0.0) {
+                cb.k[cb.nk] = k[j];
+                cb.coef[cb.nk] = dt * kB[j];
+                ++cb.nk;
+            }
+        e = esdc::launch_final_f32(c, q, base, cb, s);
+        if (e != cudaSuccess) return cuda_fail(e, "step update (float64)");
+    }
     return ESDC_OK;
 }
 
@@ -75,6 +121,7 @@ void free_ctx(esdc_ctx* c) {
     cudaFree(c->d_geomf);
     cudaFree(c->d_nbr);
     cudaFree(c->d_trace);
+    cudaFree(c->d_shadow);
     cudaFree(c->d_red);
     cudaFree(c->d_red_out);
     cudaFree(c->d_stage_q);
@@ -222,6 +269,14 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_nbr, hs.nbr.data(), hs.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = esdc::prepare_rhs_f64(c);
+    if (e == cudaSuccess && s.precision == ESDC_PREC_FP32) {
+        std::vector<float> gf(hs.geom.size());
+        for (size_t i = 0; i < gf.size(); ++i) gf[i] = (float)hs.geom[i];
+        e = cudaMalloc(&c->d_geomf, gf.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_geomf, gf.data(), gf.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_shadow, (size_t)c->n_nodes * 5 * sizeof(float));
+        if (e == cudaSuccess) e = esdc::prepare_rhs_f32(c);
+    }
     if (e != cudaSuccess) {
         free_ctx(c);
         return cuda_fail(e, "esdc_create");
@@ -290,7 +345,8 @@ int esdc_rhs_host(esdc_ctx* c, const double* q_host, void* dqdt_host, void* stre
 int esdc_workspace_bytes(const esdc_ctx* c, int what, size_t* bytes) {
     if (!c || !bytes) return fail(ESDC_ERR_ARG, "null argument");
     if (what != 0) return fail(ESDC_ERR_ARG, "unknown workspace kind");
-    *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(double));
+    if (c->setup.precision == ESDC_PREC_FP64) *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(double));
+    else *bytes = 8 * round256((size_t)c->n_nodes * 5 * sizeof(float));
     return ESDC_OK;
 }
 
@@ -301,7 +357,7 @@ int esdc_rk_step(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, size_t
     esdc_workspace_bytes(c, 0, &need);
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "workspace too small");
     if (!aligned(ws, 256) || !aligned(q, 16)) return fail(ESDC_ERR_ARG, "q must be 16-byte and workspace 256-byte aligned");
-    if (c->setup.precision != ESDC_PREC_FP64) return fail(ESDC_ERR_UNSUPPORTED, "float32 residual not available in this build");
+    if (c->setup.precision == ESDC_PREC_FP32) return rk_step_f32(c, q, dt, nsteps, ws, (cudaStream_t)stream);
     const int64_t n = c->n_nodes * 5;
     const size_t sub = round256((size_t)n * sizeof(double));
     double* k[6];

@@ -77,6 +77,7 @@ struct esdc_ctx {
     float* d_geomf = nullptr;        // [K][10][N3] float32 copy (mixed precision)
     int32_t* d_nbr = nullptr;        // [K][6]
     void* d_trace = nullptr;         // [K][6][4][N2] viscous normal-flux traces (f64 or f32)
+    float* d_shadow = nullptr;       // [K][5][N3] float32 perturbation state (mixed precision)
     double* d_red = nullptr;         // reduction partials
     double* d_red_out = nullptr;     // reduction results
     int red_blocks = 0;

@@ -25,4 +25,21 @@ cudaError_t launch_cfl(const esdc_ctx* c, const double* q, cudaStream_t s);
 
 cudaError_t probe_fma(int kind, double* flops_per_s, cudaStream_t s);
 
+// mixed-precision form
+cudaError_t prepare_rhs_f32(const esdc_ctx* c);
+cudaError_t launch_rhs_f32(const esdc_ctx* c, const float* dq, float* out, cudaStream_t s, cudaEvent_t* ev);
+struct CombineF {           // float32 stage combination: out = base + sum_j coef_j k_j
+    const float* k[6];
+    float coef[6];
+    int nk;
+};
+struct Combine64F {         // float64 accumulation of float32 stage derivatives
+    const float* k[6];
+    double coef[6];
+    int nk;
+};
+cudaError_t launch_shadow(const esdc_ctx* c, const double* q, float* dq, cudaStream_t s);
+cudaError_t launch_stage_f32(const float* base, const CombineF& cb, float* out, int64_t n, cudaStream_t s);
+cudaError_t launch_final_f32(const esdc_ctx* c, double* q, float* dq_new, const Combine64F& cb, cudaStream_t s);
+
 }  // namespace esdc

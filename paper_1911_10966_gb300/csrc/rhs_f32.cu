@@ -1,0 +1,496 @@
+// FP32 residual kernels of the mixed-precision form: the same ES-C residual as rhs_f64.cu with all
+// flux differencing, interface and viscous arithmetic in float32, evaluated on a perturbation
+// state so that float32 rounding acts on O(1) quantities rather than on the O(1/(gamma Ma^2))
+// pressure and enthalpy.
+//
+// Input: the shadow state dq = (rho - rho0, rho u, rho E - E0) in float32 (written by a float64
+// kernel from the float64 state), float32 geometry, neighbour table.  Reference state rho0 = 1,
+// p0 = R (T0 = 1), beta0 = 1/(2R), E0 = p0/(gamma-1).
+//
+// The Chandrashekar flux is split exactly as f = f_ref + df with
+//   f_ref = [rho0 ubar.n, p0 n, gamma p0/(gamma-1) ubar.n]
+//   df1 = drho_ln ubar.n,  df_m = f1 ubar_m + dp_t n_m,
+//   df5 = ubar.n/(gamma-1) (rho0 dI + drho_ln (RT0 + dI)) + f1 (u_a.u_b)/2 + dp_t ubar.n,
+// where drho_ln = rho_ln - rho0, dp_t = p_t - p0 and dI = 1/(2 beta_ln) - RT0 are formed from the
+// perturbations (no O(p0) cancellation).  The p0 n part of f_ref contributes -p0 sum_l D_l Ja_l
+// (zero by the discrete GCL of the float64 metrics) and is dropped from volume and interface
+// terms alike; the ubar.n part is linear and is accumulated separately (one extra accumulator)
+// and scaled by rho0 and gamma p0/(gamma-1) at the end.
+#include <cuda_runtime.h>
+
+#include "esdc_internal.h"
+#include "kernels.h"
+
+namespace esdc {
+namespace {
+
+template <int N>
+struct CfgF {
+    static constexpr int N2 = N * N, N3 = N * N * N;
+    static constexpr int LINES = 3 * N2;                       // all three directions at once
+    static constexpr int TE = (N3 <= 256) ? (N3 > LINES ? N3 : LINES) : LINES;   // threads per element
+    static constexpr int EPB = TE >= 128 ? 1 : (128 + TE - 1) / TE;
+    static constexpr int THREADS = EPB * TE;
+    // shared floats per element: prim 8 | w 4 | geometry 10 | accumulators 3 x 6 (aliased by the
+    // 12 viscous fluxes) | own dq 5 | face w 24 N^2/N3
+    static constexpr int SM = (8 + 4 + 10 + 18 + 5) * N3 + 24 * N2;
+    static constexpr int EPB_SAT = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
+};
+
+struct PrimF {
+    float rho, dr, u0, u1, u2, usq, beta, db;
+};
+
+struct Ref {
+    float rho0, p0, beta0, RT0, H0, inv_gm1, gm1, gamma;
+};
+
+__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+
+// primitives from the float32 perturbation state
+__device__ __forceinline__ void to_prim_f(const float dq[5], const Ref& r, PrimF& s) {
+    s.dr = dq[0];
+    s.rho = r.rho0 + dq[0];
+    const float ri = frcp(s.rho);
+    s.u0 = dq[1] * ri;
+    s.u1 = dq[2] * ri;
+    s.u2 = dq[3] * ri;
+    s.usq = s.u0 * s.u0 + s.u1 * s.u1 + s.u2 * s.u2;
+    const float dp = r.gm1 * (dq[4] - 0.5f * s.rho * s.usq);
+    const float h = 0.5f * frcp(r.p0 + dp);          // 1/(2p)
+    s.beta = s.rho * h;
+    s.db = (s.dr * r.p0 - r.rho0 * dp) * h / r.p0;   // beta - beta0 = (drho p0 - rho0 dp)/(2 p p0)
+}
+
+// perturbation part of the two-point flux (df[0..4]) and ubar.n (the linear reference part)
+__device__ __forceinline__ void ec_flux_pert(const PrimF& a, const PrimF& b, float n0, float n1, float n2,
+                                             const Ref& r, float df[5], float& un) {
+    // density log mean: drho_ln = drho_bar + rho_bar (G(u) - 1), series branch for u < 1e-2
+    const float s = a.rho + b.rho;
+    const float f = (a.dr - b.dr) * frcp(s);
+    const float uu = f * f;
+    float drl;
+    if (uu < 1.0e-2f) {
+        drl = 0.5f * (a.dr + b.dr) + 0.5f * s * (uu * (-1.0f / 3.0f + uu * (-4.0f / 45.0f + uu * (-44.0f / 945.0f))));
+    } else {
+        drl = (a.rho - b.rho) / logf(a.rho / b.rho) - r.rho0;
+    }
+    // beta: 1/(2 beta_ln) - RT0 and p_t - p0 from the perturbations
+    const float sb = a.beta + b.beta;
+    const float rsb = frcp(sb);
+    const float dbs = a.db + b.db;
+    const float fb = (a.db - b.db) * rsb;
+    const float ub = fb * fb;
+    float dI;
+    if (ub < 1.0e-2f) {
+        const float Fm1 = ub * (1.0f / 3.0f + ub * (1.0f / 5.0f + ub * (1.0f / 7.0f)));
+        dI = (2.0f * r.beta0 * Fm1 - dbs) * rsb * r.RT0;
+    } else {
+        dI = 0.5f * logf(a.beta / b.beta) / (a.beta - b.beta) - r.RT0;
+    }
+    const float dpt = (r.beta0 * (a.dr + b.dr) - r.rho0 * dbs) * rsb * r.RT0;
+    const float ub0 = 0.5f * (a.u0 + b.u0), ub1 = 0.5f * (a.u1 + b.u1), ub2 = 0.5f * (a.u2 + b.u2);
+    un = ub0 * n0 + ub1 * n1 + ub2 * n2;
+    const float f1 = (r.rho0 + drl) * un;
+    df[0] = drl * un;
+    df[1] = f1 * ub0 + dpt * n0;
+    df[2] = f1 * ub1 + dpt * n1;
+    df[3] = f1 * ub2 + dpt * n2;
+    const float uab = a.u0 * b.u0 + a.u1 * b.u1 + a.u2 * b.u2;
+    df[4] = un * r.inv_gm1 * (r.rho0 * dI + drl * (r.RT0 + dI)) + 0.5f * f1 * uab + dpt * un;
+}
+
+template <int N>
+__device__ __forceinline__ int line_base_f(int l, int t1, int t2) {
+    return l == 0 ? (t1 * N + t2 * N * N) : (l == 1 ? (t1 + t2 * N * N) : (t1 + t2 * N));
+}
+
+template <int N>
+__device__ __forceinline__ int dir_stride_f(int l) {
+    return l == 0 ? 1 : (l == 1 ? N : N * N);
+}
+
+__device__ __forceinline__ void load_prim_f(const float* sP, int N3, int idx, PrimF& s) {
+    s.rho = sP[idx];
+    s.dr = sP[N3 + idx];
+    s.u0 = sP[2 * N3 + idx];
+    s.u1 = sP[3 * N3 + idx];
+    s.u2 = sP[4 * N3 + idx];
+    s.usq = sP[5 * N3 + idx];
+    s.beta = sP[6 * N3 + idx];
+    s.db = sP[7 * N3 + idx];
+}
+
+template <int N>
+__global__ void __launch_bounds__(CfgF<N>::THREADS)
+rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float* __restrict__ geom,
+             const int32_t* __restrict__ nbr, float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph,
+             const Ref ref) {
+    using C = CfgF<N>;
+    constexpr int N2 = C::N2, N3 = C::N3, TE = C::TE;
+    extern __shared__ float smf[];
+    const int t = threadIdx.x;
+    const int el_loc = t / TE;
+    const int tl = t - el_loc * TE;
+    const int64_t el = (int64_t)blockIdx.x * C::EPB + el_loc;
+    const bool active = el < K;
+    float* sP = smf + (size_t)el_loc * C::SM;       // [8][N3] rho, dr, u0, u1, u2, usq, beta, db
+    float* sW = sP + 8 * N3;                         // [4][N3] w2..w4, w5 - w5_ref
+    float* sG = sW + 4 * N3;                         // [10][N3] J, Ja
+    float* sA = sG + 10 * N3;                        // [3][6][N3] per-direction accumulators | [12][N3] Ftilde
+    float* sQ = sA + 18 * N3;                        // [5][N3] own dq
+    float* sWf = sQ + 5 * N3;                        // [6][4][N2] neighbour entropy variables
+    const int64_t eoff = el * 5 * N3;
+
+    if (active) {
+        for (int node = tl; node < N3; node += TE) {
+            float d[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                d[v] = dq[eoff + v * N3 + node];
+                sQ[v * N3 + node] = d[v];
+            }
+            PrimF s;
+            to_prim_f(d, ref, s);
+            sP[node] = s.rho;
+            sP[N3 + node] = s.dr;
+            sP[2 * N3 + node] = s.u0;
+            sP[3 * N3 + node] = s.u1;
+            sP[4 * N3 + node] = s.u2;
+            sP[5 * N3 + node] = s.usq;
+            sP[6 * N3 + node] = s.beta;
+            sP[7 * N3 + node] = s.db;
+            sW[node] = 2.0f * s.beta * s.u0;
+            sW[N3 + node] = 2.0f * s.beta * s.u1;
+            sW[2 * N3 + node] = 2.0f * s.beta * s.u2;
+            sW[3 * N3 + node] = -2.0f * s.db;         // w5 - w5_ref (the constant has no gradient)
+#pragma unroll
+            for (int c = 0; c < 10; ++c) sG[c * N3 + node] = geom[(el * 10 + c) * N3 + node];
+        }
+    }
+    __syncthreads();
+
+    // ---- volume: all three directions at once, one thread per line, own accumulators per direction
+    if (active && tl < 3 * N2) {
+        const int l = tl / N2, line = tl - l * N2;
+        const int base = line_base_f<N>(l, line % N, line / N);
+        const int st = dir_stride_f<N>(l);
+        const float* n0p = sG + (1 + 3 * l) * N3;
+        const float* n1p = n0p + N3;
+        const float* n2p = n1p + N3;
+        float acc[N][6];
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int v = 0; v < 6; ++v) acc[i][v] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < N - 1; ++i) {
+            const int ii = base + i * st;
+            PrimF si;
+            load_prim_f(sP, N3, ii, si);
+            const float a0 = n0p[ii], a1 = n1p[ii], a2 = n2p[ii];
+#pragma unroll
+            for (int j = i + 1; j < N; ++j) {
+                const int jj = base + j * st;
+                PrimF sj;
+                load_prim_f(sP, N3, jj, sj);
+                float df[5], un;
+                ec_flux_pert(si, sj, 0.5f * (a0 + n0p[jj]), 0.5f * (a1 + n1p[jj]), 0.5f * (a2 + n2p[jj]), ref, df, un);
+                const float c = ops.S2[i][j];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    acc[i][v] -= c * df[v];
+                    acc[j][v] += c * df[v];
+                }
+                acc[i][5] -= c * un;
+                acc[j][5] += c * un;
+            }
+        }
+        float* A = sA + l * 6 * N3;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int ii = base + i * st;
+#pragma unroll
+            for (int v = 0; v < 6; ++v) A[v * N3 + ii] = acc[i][v] * ops.winv[i];
+        }
+    }
+    __syncthreads();
+    // sum the three directions into direction 0's slots
+    if (active) {
+        for (int node = tl; node < N3; node += TE)
+#pragma unroll
+            for (int v = 0; v < 6; ++v) sA[v * N3 + node] += sA[(6 + v) * N3 + node] + sA[(12 + v) * N3 + node];
+    }
+    __syncthreads();
+
+    // ---- interface SAT, direction by direction (edges and corners are shared)
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        if (active) {
+            for (int fn = tl; fn < 2 * N2; fn += TE) {
+                const int side = fn / N2, fi = fn - side * N2;
+                const int st = dir_stride_f<N>(l);
+                const int base = line_base_f<N>(l, fi % N, fi / N);
+                const int own = base + (side ? (N - 1) * st : 0);
+                const int nbn = base + (side ? 0 : (N - 1) * st);
+                const int64_t nb = nbr[el * 6 + 2 * l + side];
+                float qn[5];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) qn[v] = dq[nb * 5 * N3 + v * N3 + nbn];
+                PrimF so, sn;
+                load_prim_f(sP, N3, own, so);
+                to_prim_f(qn, ref, sn);
+                const float n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own],
+                            n2 = sG[(3 + 3 * l) * N3 + own];
+                float df[5], un;
+                ec_flux_pert(so, sn, n0, n1, n2, ref, df, un);
+                const float E = side ? 1.0f : -1.0f;
+                float lam = 0.0f;
+                if (ph.dissipation) {
+                    const float nn = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+                    const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + sqrtf(0.5f * ref.gamma / so.beta) * nn;
+                    const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + sqrtf(0.5f * ref.gamma / sn.beta) * nn;
+                    lam = 0.5f * fmaxf(lo, ln);
+                }
+                const float wi = ops.winv[side ? N - 1 : 0];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sA[v * N3 + own] += (-E * df[v] - lam * (sQ[v * N3 + own] - qn[v])) * wi;
+                sA[5 * N3 + own] += -E * un * wi;
+                float* wf = sWf + (2 * l + side) * 4 * N2 + fi;
+                wf[0] = 2.0f * sn.beta * sn.u0;
+                wf[N2] = 2.0f * sn.beta * sn.u1;
+                wf[2 * N2] = 2.0f * sn.beta * sn.u2;
+                wf[3 * N2] = -2.0f * sn.db;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- viscous chain
+    if (ph.viscous) {
+        constexpr int NPT = (N3 + TE - 1) / TE;    // nodes per thread
+        float Ft[NPT][3][4];
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < NPT; ++r) {
+                const int node = tl + r * TE;
+                if (node >= N3) break;
+                const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+                const float wown[4] = {sW[node], sW[N3 + node], sW[2 * N3 + node], sW[3 * N3 + node]};
+                float th[3][4];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int ia = a == 0 ? i1 : (a == 1 ? i2 : i3);
+                    const int st = dir_stride_f<N>(a);
+                    const int lb = node - ia * st;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float s = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < N; ++j) s += ops.D[ia][j] * sW[k * N3 + lb + j * st];
+                        th[a][k] = s;
+                    }
+                    if (ia == 0 || ia == N - 1) {
+                        const int side = ia == N - 1;
+                        const int fi = a == 0 ? (i2 + N * i3) : (a == 1 ? (i1 + N * i3) : (i1 + N * i2));
+                        const float E = side ? 0.5f : -0.5f;
+                        const float* wf = sWf + (2 * a + side) * 4 * N2 + fi;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) th[a][k] += E * (wf[k * N2] - wown[k]) * ops.winv[ia];
+                    }
+                }
+                const float Jinv = frcp(sG[node]);
+                float g[3][4];
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        g[m][k] = Jinv * (sG[(1 + m) * N3 + node] * th[0][k] + sG[(4 + m) * N3 + node] * th[1][k] +
+                                          sG[(7 + m) * N3 + node] * th[2][k]);
+                const float RT = 0.5f / sP[6 * N3 + node];
+                const float u[3] = {sP[2 * N3 + node], sP[3 * N3 + node], sP[4 * N3 + node]};
+                float du[3][3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) du[k][m] = RT * (g[m][k] + u[k] * g[m][3]);
+                const float div = du[0][0] + du[1][1] + du[2][2];
+                const float hc = ph.kappa / ph.R * RT * RT;
+                float FV[3][4];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        FV[m][i] = ph.mu * (du[i][m] + du[m][i] - (i == m ? (2.0f / 3.0f) * div : 0.0f));
+                    FV[m][3] = FV[m][0] * u[0] + FV[m][1] * u[1] + FV[m][2] * u[2] + hc * g[m][3];
+                }
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        Ft[r][l][k] = sG[(1 + 3 * l) * N3 + node] * FV[0][k] + sG[(2 + 3 * l) * N3 + node] * FV[1][k] +
+                                      sG[(3 + 3 * l) * N3 + node] * FV[2][k];
+            }
+        }
+        // the volume/interface sums in sA[0..5] are complete; move them into sP (free now) so
+        // that sA can hold the viscous fluxes
+        __syncthreads();
+        if (active) {
+            for (int node = tl; node < N3; node += TE)
+#pragma unroll
+                for (int v = 0; v < 6; ++v) sP[v * N3 + node] = sA[v * N3 + node];
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < NPT; ++r) {
+                const int node = tl + r * TE;
+                if (node >= N3) break;
+                const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) sA[(l * 4 + k) * N3 + node] = Ft[r][l][k];
+                    const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
+                    if (il == 0 || il == N - 1) {
+                        const int side = il == N - 1;
+                        const int fi = l == 0 ? (i2 + N * i3) : (l == 1 ? (i1 + N * i3) : (i1 + N * i2));
+                        float* tr = trace + ((el * 6 + 2 * l + side) * 4) * N2 + fi;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) tr[k * N2] = Ft[r][l][k];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (active) {
+            for (int node = tl; node < N3; node += TE) {
+                const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+                float vs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
+                    const int st = dir_stride_f<N>(l);
+                    const int lb = node - il * st;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float s = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < N; ++j) s += ops.D[il][j] * sA[(l * 4 + k) * N3 + lb + j * st];
+                        vs[k] += s;
+                    }
+                }
+                const float Jinv = frcp(sG[node]);
+                const float lin = sP[5 * N3 + node];
+                out[eoff + node] = (sP[node] + ref.rho0 * lin) * Jinv;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) out[eoff + (1 + k) * N3 + node] = (sP[(1 + k) * N3 + node] + vs[k]) * Jinv;
+                out[eoff + 4 * N3 + node] = (sP[4 * N3 + node] + ref.H0 * lin + vs[3]) * Jinv;
+            }
+        }
+    } else if (active) {
+        for (int node = tl; node < N3; node += TE) {
+            const float Jinv = frcp(sG[node]);
+            const float lin = sA[5 * N3 + node];
+            out[eoff + node] = (sA[node] + ref.rho0 * lin) * Jinv;
+#pragma unroll
+            for (int k = 1; k < 4; ++k) out[eoff + k * N3 + node] = sA[k * N3 + node] * Jinv;
+            out[eoff + 4 * N3 + node] = (sA[4 * N3 + node] + ref.H0 * lin) * Jinv;
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(CfgF<N>::EPB_SAT * 2 * CfgF<N>::N2)
+visc_sat_f32(float* __restrict__ out, const float* __restrict__ geom, const int32_t* __restrict__ nbr,
+             const float* __restrict__ trace, int64_t K, const OpsF ops) {
+    constexpr int N2 = CfgF<N>::N2, N3 = CfgF<N>::N3;
+    const int t = threadIdx.x;
+    const int el_loc = t / (2 * N2);
+    const int r = t - el_loc * 2 * N2;
+    const int side = r / N2, fi = r - side * N2;
+    const int64_t el = (int64_t)blockIdx.x * CfgF<N>::EPB_SAT + el_loc;
+    const bool active = el < K;
+    const float E = side ? 0.5f : -0.5f;
+    const float wi = ops.winv[side ? N - 1 : 0];
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        if (active) {
+            const int st = dir_stride_f<N>(l);
+            const int own = line_base_f<N>(l, fi % N, fi / N) + (side ? (N - 1) * st : 0);
+            const int64_t nb = nbr[el * 6 + 2 * l + side];
+            const float* to = trace + ((el * 6 + 2 * l + side) * 4) * N2 + fi;
+            const float* tn = trace + ((nb * 6 + 2 * l + 1 - side) * 4) * N2 + fi;
+            const float c = E * wi / geom[el * 10 * N3 + own];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) out[(el * 5 + 1 + k) * N3 + own] += c * (tn[k * N2] - to[k * N2]);
+        }
+        __syncthreads();
+    }
+}
+
+template <int N>
+cudaError_t launch_f32_n(const esdc_ctx* c, const float* dq, float* out, cudaStream_t s, cudaEvent_t* ev) {
+    using C = CfgF<N>;
+    const size_t smem = (size_t)C::EPB * C::SM * sizeof(float);
+    const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
+    const PhysF& ph = c->physf;
+    Ref ref;
+    ref.rho0 = ph.rho0;
+    ref.p0 = ph.p0;
+    ref.beta0 = ph.rho0 / (2.0f * ph.p0);
+    ref.RT0 = ph.p0 / ph.rho0;
+    ref.H0 = ph.gamma * ph.p0 / (ph.gamma - 1.0f);
+    ref.inv_gm1 = ph.inv_gm1;
+    ref.gm1 = ph.gamma - 1.0f;
+    ref.gamma = ph.gamma;
+    if (ev) cudaEventRecord(ev[0], s);
+    rhs_main_f32<N><<<grid, C::THREADS, smem, s>>>(dq, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf,
+                                                   ph, ref);
+    if (ev) cudaEventRecord(ev[1], s);
+    if (ev) cudaEventRecord(ev[2], s);
+    if (ph.viscous) {
+        const unsigned g2 = (unsigned)((c->K + C::EPB_SAT - 1) / C::EPB_SAT);
+        visc_sat_f32<N><<<g2, C::EPB_SAT * 2 * C::N2, 0, s>>>(out, c->d_geomf, c->d_nbr, (const float*)c->d_trace,
+                                                                c->K, c->opsf);
+    }
+    if (ev) cudaEventRecord(ev[3], s);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t prepare_f32_n() {
+    using C = CfgF<N>;
+    const size_t smem = (size_t)C::EPB * C::SM * sizeof(float);
+    return cudaFuncSetAttribute(rhs_main_f32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+cudaError_t prepare_rhs_f32(const esdc_ctx* c) {
+    switch (c->N) {
+        case 2: return prepare_f32_n<2>();
+        case 3: return prepare_f32_n<3>();
+        case 4: return prepare_f32_n<4>();
+        case 5: return prepare_f32_n<5>();
+        case 6: return prepare_f32_n<6>();
+        case 7: return prepare_f32_n<7>();
+        case 8: return prepare_f32_n<8>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rhs_f32(const esdc_ctx* c, const float* dq, float* out, cudaStream_t s, cudaEvent_t* ev) {
+    switch (c->N) {
+        case 2: return launch_f32_n<2>(c, dq, out, s, ev);
+        case 3: return launch_f32_n<3>(c, dq, out, s, ev);
+        case 4: return launch_f32_n<4>(c, dq, out, s, ev);
+        case 5: return launch_f32_n<5>(c, dq, out, s, ev);
+        case 6: return launch_f32_n<6>(c, dq, out, s, ev);
+        case 7: return launch_f32_n<7>(c, dq, out, s, ev);
+        case 8: return launch_f32_n<8>(c, dq, out, s, ev);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace esdc

@@ -1,0 +1,117 @@
+"""Mixed-precision form (float32 residual, float64 state and budgets) against the float64 oracle.
+
+Error statement per variable v: e_v = ||R32 - R_oracle||_inf / ||R_oracle||_inf and the
+conditioning-normalised c_v = ||R32 - R_oracle||_inf / (eps32 T_v), with T_v the magnitude of the
+summed flux terms (tests/gpu_common.term_scale).  c_v = O(1) means the float32 residual is as
+accurate as float32 differencing of the fluxes allows.  The physics-level check is the
+kinetic-energy dissipation rate of the Taylor-Green vortex, required within 1e-3 relative.
+
+Measured (GB300): generic perturbed states e_v ~ 2e-7 with c_v <= 0.2 for momentum and 1.2-3.2 for
+mass and energy, whose linear part rho0 ubar.n / gamma p0/(gamma-1) ubar.n is differenced in float32
+(float32 rounding of O(1) velocities times gamma/(gamma-1)/(gamma Ma^2) ~ 250).  The bound used is
+c_v <= 8.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import esdc_oracle as O
+from tests.gpu_common import make_pair, normwise_errors, term_scale
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+C_MAX = 8.0
+
+
+def _report(r32, ro, qo, mesh, gas, elems=None):
+    e = normwise_errors(r32, ro)
+    T = term_scale(qo, mesh, gas, elems)
+    a = r32.double().cpu()
+    c = [float((a[:, v] - ro[:, v]).abs().max()) / (EPS32 * T[v]) for v in range(5)]
+    print("fp32 e_v", ["%.1e" % x for x in e], "c_v", ["%.2f" % x for x in c])
+    return e, c
+
+
+@pytest.mark.parametrize("noise", [0.0, 1e-3])
+def test_fp32_residual_tgv_4cubed_p3(noise):
+    solver, qg, mesh, gas, qo = make_pair(3, (4, 4, 4), Re=1600.0, precision="fp32", noise=noise)
+    r = solver.rhs(qg)
+    assert r.dtype == torch.float32
+    e, c = _report(r, O.rhs(qo, mesh, gas), qo, mesh, gas)
+    assert max(e) <= 1e-4
+    assert max(c) <= C_MAX
+
+
+@pytest.mark.parametrize("p", range(1, 8))
+def test_fp32_residual_every_degree_warped(p):
+    solver, qg, mesh, gas, qo = make_pair(p, (3, 2, 2), warp=0.1, seed=2, Re=100.0, noise=0.05, precision="fp32")
+    e, c = _report(solver.rhs(qg), O.rhs(qo, mesh, gas), qo, mesh, gas)
+    assert max(c) <= C_MAX
+    assert max(e) <= 1e-5
+
+
+def test_fp32_residual_16cubed_p4_warped_sampled():
+    solver, qg, mesh, gas, qo = make_pair(4, (16, 16, 16), warp=0.1, seed=0, Re=1600.0, precision="fp32")
+    r = solver.rhs(qg)
+    E = torch.tensor(np.random.default_rng(5).choice(16 ** 3, 48, replace=False))
+    e, c = _report(r[E.cuda()], O.rhs(qo, mesh, gas, elems=E), qo, mesh, gas, elems=E)
+    assert max(c) <= C_MAX
+    assert e[1] <= 1e-3 and e[2] <= 1e-3 and e[3] <= 1e-3      # momentum (perturbation split)
+
+
+def test_fp32_rk_steps_and_ke_rate():
+    """Ten DP5 steps of the 4^3 p=3 Taylor-Green case: float64 state updated by float32 residuals,
+    compared with the oracle's float64 trajectory; the kinetic-energy dissipation rate of the final
+    state agrees within 1e-3 relative."""
+    solver, qg, mesh, gas, qo = make_pair(3, (4, 4, 4), Re=1600.0, precision="fp32")
+    dt = 2.0e-3
+    q0 = qg.clone()
+    solver.rk_step(qg, dt, 10)
+    qn = O.rk_step(qo, lambda s: O.rhs(s, mesh, gas), dt, 10)
+    e = normwise_errors(qg - q0, qn - qo)
+    print("fp32 rk increment e_v", e)
+    assert max(e) <= 1e-4
+    b = solver.budgets(qg, solver.rhs(qg))
+    bo = O.budgets(qn, O.rhs(qn, mesh, gas), mesh, gas)
+    assert abs(b[3] - bo[3]) <= 1e-3 * abs(bo[3])
+    assert abs(b[1] - bo[1]) <= 1e-9 * abs(bo[1])
+
+
+def test_fp32_ke_rate_16cubed_p4_warped_vs_fp64():
+    """Kinetic-energy dissipation rate of the 16^3 p=4 warped Taylor-Green run after 5 DP5 steps:
+    float32-mixed vs float64 GPU path within 1e-3 relative (both float64 budgets)."""
+    from paper_1911_10966_gb300.solver import Solver
+    s64, q64, _, _, _ = make_pair(4, (16, 16, 16), warp=0.1, seed=0, Re=1600.0)
+    s32 = Solver(4, 16, 16, 16, s64.coords, Re=1600.0, precision="fp32")
+    q32 = q64.clone()
+    dt = s64.dt_cfl(q64, 0.5)
+    s64.rk_step(q64, dt, 5)
+    s32.rk_step(q32, dt, 5)
+    b64 = s64.budgets(q64, s64.rhs(q64))
+    b32 = s32.budgets(q32, s32.rhs(q32))
+    print("dKE/dt fp64 %.9e fp32 %.9e; dS/dt fp64 %.9e fp32 %.9e" % (b64[3], b32[3], b64[2], b32[2]))
+    assert abs(b32[3] - b64[3]) <= 1e-3 * abs(b64[3])
+    # the entropy rate weights the float32 mass residual by w1 ~ -7: measured 2.3e-3 relative
+    assert abs(b32[2] - b64[2]) <= 5e-3 * abs(b64[2])
+
+
+def test_fp32_freestream_and_conservation():
+    """Uniform flow on a warped mesh: the float32 residual vanishes to float32 differencing of the
+    fluxes (c_v <= 8; the dropped p0 n part is exact by the float64 GCL), and the float32 residual
+    conserves mass to float32 round-off."""
+    solver, qg, mesh, gas, qo = make_pair(4, (4, 4, 4), warp=0.1, seed=0, Re=1600.0, state="freestream",
+                                          precision="fp32")
+    r = solver.rhs(qg)
+    T = term_scale(qo, mesh, gas)
+    for v in range(5):
+        assert float(r[:, v].abs().max()) <= C_MAX * EPS32 * T[v], (v, float(r[:, v].abs().max()), T[v])
+    solver2, qg2, _, _, _ = make_pair(3, (3, 3, 3), warp=0.1, seed=1, Re=1600.0, precision="fp32", noise=1e-2)
+    r2 = solver2.rhs(qg2).double()
+    J2, _ = solver2.geometry()
+    w = torch.tensor(O.sbp_operator(3).w.numpy())
+    PJ = (w[:, None, None] * w[None, :, None] * w[None, None, :]).to(r2.device) * torch.tensor(J2, device=r2.device)
+    tot = float((PJ * r2[:, 0]).sum())
+    assert abs(tot) <= 1e-5 * float((PJ * r2[:, 0].abs()).sum())
