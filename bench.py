@@ -306,6 +306,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms_rhs = a.elapsed_time(b) / reps
 
+    adj = _adjoint_leg(solver, solver.to_device(q_init), dt, ms_rhs, flush)
     fp32 = _fp32_leg(args, solver, q_init, dt, flush, barrier, dist, ws) if not args.no_fp32 else None
     if fp32 is not None:
         fp32["speedup_vs_f64_rhs"] = (ms_main / max(nres, 1)) / fp32["roofline"]["kernel_ms"]
@@ -338,6 +339,7 @@ def run_ours(args):
         "rhs_only": {"value": n / (ms_rhs * 1e-3), "unit": "node-RHS/s", "ms": ms_rhs,
                      "face_kernel_ms": ms_face / max(nres, 1)},
         "fp32_mixed": fp32,
+        "adjoint": adj,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -405,6 +407,46 @@ def _fp32_leg(args, s64, q_init, dt, flush, barrier, dist, ws):
             "ke_rate_rel_error_5_steps": abs(k32 - k64) / abs(k64),
             "gpu_launches": steps * (RHS_PER_STEP * 2 + RHS_PER_STEP + 1 + 2),
             "speedup_vs_f64_rhs": None}
+
+
+def _adjoint_leg(solver, q, dt, ms_rhs, flush):
+    """Cost of the hand-written adjoint on the same workload: one vector-Jacobian product against one
+    residual, and the gradient of the final kinetic energy through 5 DP5 steps (checkpointed
+    forward + reverse sweep with stage recomputation) against the 5 forward steps alone."""
+    stream = torch.cuda.current_stream()
+    lam = torch.randn(q.shape, dtype=torch.float64, device=q.device, generator=torch.Generator(q.device).manual_seed(3))
+    g = solver.rhs_vjp(q, lam)
+    reps = 10
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1.0)
+    a.record(stream)
+    for _ in range(reps):
+        g = solver.rhs_vjp(q, lam)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_vjp = a.elapsed_time(b) / reps
+    nsteps = 5
+    qa = q.clone()
+    flush.fill_(2.0)
+    a.record(stream)
+    solver.rk_step(qa, dt, nsteps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = a.elapsed_time(b)
+    qb = q.clone()
+    flush.fill_(3.0)
+    a.record(stream)
+    ck = solver.rk_step_ckpt(qb, dt, nsteps)
+    lamN = solver.ke_gradient(qb)
+    _, gmu = solver.rk_adjoint(ck, dt, lamN)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_grad = a.elapsed_time(b)
+    return {"vjp_ms": ms_vjp, "rhs_ms": ms_rhs, "vjp_over_rhs": ms_vjp / ms_rhs,
+            "trajectory_steps": nsteps, "forward_ms": ms_fwd, "gradient_ms": ms_grad,
+            "gradient_over_forward": ms_grad / ms_fwd, "dtype": "f64",
+            "what": "d KE(q_5)/d(q_0, mu): checkpointed forward + reverse sweep (6 residual recomputations "
+                    "+ 6 VJPs per step)"}
 
 
 def main():

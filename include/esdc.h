@@ -158,6 +158,47 @@ int esdc_budgets(esdc_ctx* ctx, const double* q_dev, const void* dqdt_dev, doubl
 int esdc_dt_cfl(esdc_ctx* ctx, const double* q_dev, double cfl, double* dt_host, void* stream);
 
 /*
+ * esdc_rhs_vjp -- the adjoint of esdc_rhs (no counterpart in the paper, whose method this
+ * differentiates): grad = (dR/dq)^T lambda for the float64 residual R(q) = dq/dt of eq. NSL,
+ * through the Chandrashekar flux and its log means, the interface dissipation, the BR1 viscous
+ * chain and the metric terms.  At non-smooth points it uses d|x| = sign(x), sign(0) = 0, and splits
+ * the cotangent of max(a, b) in half at a tie.  If grad_mu_host is not NULL it also returns
+ * lambda . dR/dmu (R is linear in mu through mu and kappa = mu cp/Pr) and synchronises stream.
+ * q_dev, lambda_dev, grad_dev: [K][5][N^3] float64 device arrays (grad_dev must not alias the
+ * others).  ESDC_PREC_FP64 contexts only (ESDC_ERR_UNSUPPORTED otherwise).  The first call
+ * allocates the adjoint face buffers (K*6*9*N^2 float64), kept until esdc_destroy.
+ */
+int esdc_rhs_vjp(esdc_ctx* ctx, const double* q_dev, const double* lambda_dev, double* grad_dev,
+                 double* grad_mu_host, void* stream);
+
+/*
+ * esdc_ke_gradient -- grad = d/dq of the integrated kinetic energy sum P J rho|u|^2/2
+ * (= P J (-|u|^2/2, u, 0) per node): the seed of the kinetic-energy adjoint.  Asynchronous.
+ */
+int esdc_ke_gradient(esdc_ctx* ctx, const double* q_dev, double* grad_dev, void* stream);
+
+/*
+ * esdc_rk_step_ckpt -- esdc_rk_step that first stores the state of every step:
+ * ckpt_dev[n] = q before step n, n = 0..nsteps-1 (ckpt_dev: nsteps*K*5*N^3 float64, caller owned).
+ */
+int esdc_rk_step_ckpt(esdc_ctx* ctx, double* q_dev, double dt, int nsteps, double* ckpt_dev, void* workspace_dev,
+                      size_t workspace_bytes, void* stream);
+
+/* esdc_rk_adjoint_workspace_bytes -- workspace of esdc_rk_adjoint: 12 state-sized float64 buffers. */
+int esdc_rk_adjoint_workspace_bytes(const esdc_ctx* ctx, size_t* bytes);
+
+/*
+ * esdc_rk_adjoint -- discrete adjoint of nsteps DP5 steps (reverse sweep with stage
+ * recomputation from the per-step checkpoints of esdc_rk_step_ckpt).  On entry lambda_dev holds
+ * dL/dq_N; on exit dL/dq_0.  grad_mu_host (nullable) receives dL/dmu.  Per step: six residuals to
+ * rebuild the stage states, then for t = 6..1 psi_t = J(q_t)^T kappa_t with
+ * kappa_t = dt b_t lambda_{n+1} + sum_{s>t} dt a_st psi_s, and lambda_n = lambda_{n+1} + sum_t psi_t.
+ * ESDC_PREC_FP64 contexts only.  Synchronises stream when grad_mu_host is not NULL.
+ */
+int esdc_rk_adjoint(esdc_ctx* ctx, const double* ckpt_dev, double dt, int nsteps, double* lambda_dev,
+                    double* grad_mu_host, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/*
  * esdc_profile -- enable (on = 1) or disable CUDA-event timing of the residual kernels of this
  * context: every esdc_rhs (also inside esdc_rk_step) then records an event pair around the fused
  * element kernel and another around the viscous interface kernel on the call's stream.

@@ -125,6 +125,10 @@ void free_ctx(esdc_ctx* c) {
     cudaFree(c->d_red);
     cudaFree(c->d_red_out);
     cudaFree(c->d_stage_q);
+    cudaFree(c->d_adj_g);
+    cudaFree(c->d_adj_t);
+    cudaFree(c->d_adj_mu);
+    cudaFree(c->d_adj_acc);
     cudaFree(c->d_stage_r);
     delete c;
 }
@@ -427,6 +431,132 @@ int esdc_dt_cfl(esdc_ctx* c, const double* q, double cfl, double* dt, void* stre
         d = std::fmin(d, c->h_min * c->h_min / (N2 * N2 * nu));
     }
     *dt = cfl * d;
+    return ESDC_OK;
+}
+
+static int ensure_adjoint(esdc_ctx* c) {
+    if (c->setup.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for ESDC_PREC_FP64 contexts");
+    if (c->d_adj_g) return ESDC_OK;
+    const size_t N2 = (size_t)c->N * c->N;
+    CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&c->d_adj_t, (size_t)c->K * 6 * 4 * N2 * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&c->d_adj_mu, esdc::adjoint_mu_blocks(c) * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&c->d_adj_acc, 8 * sizeof(double)));
+    CUDA_TRY(esdc::prepare_adjoint(c));
+    return ESDC_OK;
+}
+
+int esdc_rhs_vjp(esdc_ctx* c, const double* q, const double* lam, double* grad, double* grad_mu, void* stream) {
+    if (!c || !q || !lam || !grad) return fail(ESDC_ERR_ARG, "null argument");
+    int st = ensure_adjoint(c);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (grad_mu) CUDA_TRY(cudaMemsetAsync(c->d_adj_acc, 0, sizeof(double), s));
+    cudaError_t e = esdc::launch_rhs_vjp(c, q, lam, grad, grad_mu ? c->d_adj_acc : nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "esdc_rhs_vjp launch");
+    if (grad_mu) {
+        CUDA_TRY(cudaMemcpyAsync(grad_mu, c->d_adj_acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return ESDC_OK;
+}
+
+int esdc_ke_gradient(esdc_ctx* c, const double* q, double* grad, void* stream) {
+    if (!c || !q || !grad) return fail(ESDC_ERR_ARG, "null argument");
+    cudaError_t e = esdc::launch_ke_gradient(c, q, grad, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "esdc_ke_gradient");
+    return ESDC_OK;
+}
+
+int esdc_rk_step_ckpt(esdc_ctx* c, double* q, double dt, int nsteps, double* ckpt, void* ws, size_t ws_bytes,
+                      void* stream) {
+    if (!c || !q || !ckpt) return fail(ESDC_ERR_ARG, "null argument");
+    const size_t n5 = (size_t)c->n_nodes * 5;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int step = 0; step < nsteps; ++step) {
+        CUDA_TRY(cudaMemcpyAsync(ckpt + step * n5, q, n5 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        int st = esdc_rk_step(c, q, dt, 1, ws, ws_bytes, stream);
+        if (st) return st;
+    }
+    return ESDC_OK;
+}
+
+int esdc_rk_adjoint_workspace_bytes(const esdc_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(ESDC_ERR_ARG, "null argument");
+    *bytes = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
+    return ESDC_OK;
+}
+
+int esdc_rk_adjoint(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, double* grad_mu, void* ws,
+                    size_t ws_bytes, void* stream) {
+    if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
+    if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
+    size_t need = 0;
+    esdc_rk_adjoint_workspace_bytes(c, &need);
+    if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");
+    if (!aligned(ws, 256) || !aligned(lam, 16) || !aligned(ckpt, 16))
+        return fail(ESDC_ERR_ARG, "lam/ckpt must be 16-byte and workspace 256-byte aligned");
+    int st = ensure_adjoint(c);
+    if (st) return st;
+    const int64_t n = c->n_nodes * 5;
+    const size_t sub = round256((size_t)n * sizeof(double));
+    double* K6[6];
+    double* Qs[6];
+    for (int j = 0; j < 6; ++j) K6[j] = (double*)((char*)ws + j * sub);
+    Qs[0] = nullptr;
+    for (int j = 1; j < 6; ++j) Qs[j] = (double*)((char*)ws + (5 + j) * sub);
+    double* psi = (double*)((char*)ws + 11 * sub);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(c->d_adj_acc, 0, sizeof(double), s));
+    cudaError_t e;
+    for (int step = nsteps - 1; step >= 0; --step) {
+        const double* qn = ckpt + (size_t)step * n;
+        // recompute the stage states of this step from its checkpoint
+        for (int t = 0; t < 6; ++t) {
+            const double* qs = qn;
+            if (t > 0) {
+                esdc::Combine cb{};
+                cb.nk = t;
+                for (int j = 0; j < t; ++j) {
+                    cb.k[j] = K6[j];
+                    cb.coef[j] = dt * kA[t][j];
+                }
+                e = esdc::launch_combine(Qs[t], qn, cb, n, s);
+                if (e != cudaSuccess) return cuda_fail(e, "adjoint stage recompute");
+                qs = Qs[t];
+            }
+            st = rhs_impl(c, qs, K6[t], s);
+            if (st) return st;
+        }
+        // kappa_t = dt b_t lam_{n+1}; then t = 5..0: psi_t = J(q_t)^T kappa_t, lam += psi_t,
+        // kappa_s += dt a_ts psi_t for s < t
+        for (int t = 0; t < 6; ++t) {
+            e = esdc::launch_scale(K6[t], lam, dt * kB[t], n, s);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint init");
+        }
+        for (int t = 5; t >= 0; --t) {
+            const double* qt = t == 0 ? qn : Qs[t];
+            e = esdc::launch_rhs_vjp(c, qt, K6[t], psi, c->d_adj_acc, s);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint vjp");
+            esdc::Combine cb{};
+            cb.nk = 1;
+            cb.k[0] = psi;
+            cb.coef[0] = 1.0;
+            e = esdc::launch_combine(lam, lam, cb, n, s);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint accumulate");
+            for (int u = 0; u < t; ++u) {
+                if (kA[t][u] == 0.0) continue;
+                cb.coef[0] = dt * kA[t][u];
+                e = esdc::launch_combine(K6[u], K6[u], cb, n, s);
+                if (e != cudaSuccess) return cuda_fail(e, "adjoint stage cotangent");
+            }
+        }
+    }
+    if (grad_mu) {
+        CUDA_TRY(cudaMemcpyAsync(grad_mu, c->d_adj_acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
     return ESDC_OK;
 }
 

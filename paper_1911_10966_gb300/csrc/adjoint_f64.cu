@@ -1,0 +1,664 @@
+// Vector-Jacobian product of the float64 residual: grad = (dR/dq)^T lambda and
+// grad_mu = lambda . dR/dmu, for R = dq/dt of rhs_f64.cu (same discretization, same readings).
+//
+// The forward residual is a sum of terms, each local to one element except the face couplings:
+//   volume   r_i -= 2 S_ij f(q_i,q_j)/w_i, r_j += 2 S_ij f(q_i,q_j)/w_j     (pairs on xi_l lines)
+//   inviscid r_o += (-E f(q_o,q_n) - lam/2 (q_o - q_n))/w_end               (face nodes)
+//   viscous  r += sum_l D_l Ft_l + (E/2)(Ft_l,nbr - Ft_l,own)/w_end, Ft built from theta_a =
+//            D_a w + (E/2)(w_nbr - w_own)/w_end
+//   dq/dt = r / J.
+// With lt = lambda / J the transposes are: pair cotangent mu = 2 S_ij (lt_j/w_j - lt_i/w_i) pulled
+// back through the two-point flux to both nodes; the interface cotangent lt_o/w_end pulled back to
+// the own node and (through the face buffer gbuf) to the neighbour; the viscous chain reversed
+// node by node with the transposed derivative D_l^T along lines, the lifted-gradient cotangent on
+// faces written to tbuf for the neighbour.  Kernel adj_main does everything inside an element,
+// kernel adj_face adds what the neighbours wrote for this element's face nodes.
+// Non-smooth points follow the convention of reverse-mode differentiation: d|x| = sign(x) with
+// sign(0) = 0, and max(a, b) splits its cotangent in half at a tie.
+#include <cuda_runtime.h>
+
+#include "esdc_internal.h"
+#include "kernels.h"
+
+namespace esdc {
+namespace {
+
+constexpr int kAdjRed = 256;
+
+template <int N>
+struct CfgA {
+    static constexpr int N2 = N * N, N3 = N * N * N;
+    static constexpr int EPB = N3 >= 96 ? 1 : (N3 >= 48 ? 2 : (N3 >= 24 ? 4 : 16));
+    static constexpr int THREADS = EPB * N3;
+    // shared doubles per element: prim/w 10 | lt 5 | geometry 10 | prim-bar 6 | q-bar 5 | theta-bar 12
+    // | neighbour face w 24 N2
+    static constexpr int SM = 48 * N3 + 24 * N2;
+    static constexpr int EPB_F = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
+};
+
+struct Prim {
+    double rho, u0, u1, u2, beta, usq;
+};
+struct PBar {   // cotangents of (rho, u0, u1, u2, beta, usq)
+    double rho, u0, u1, u2, beta, usq;
+};
+
+__device__ __forceinline__ void to_prim(const double* q, const Phys& ph, Prim& s) {
+    const double ri = 1.0 / q[0];
+    s.rho = q[0];
+    s.u0 = q[1] * ri;
+    s.u1 = q[2] * ri;
+    s.u2 = q[3] * ri;
+    s.usq = s.u0 * s.u0 + s.u1 * s.u1 + s.u2 * s.u2;
+    const double p = (ph.gamma - 1.0) * (q[4] - 0.5 * q[0] * s.usq);
+    s.beta = 0.5 * q[0] / p;
+}
+
+// pull a primitive cotangent back to the conserved variables at state s
+__device__ __forceinline__ void pbar_to_q(const Prim& s, const PBar& b, const Phys& ph, double qb[5]) {
+    const double gm1 = ph.gamma - 1.0;
+    const double ut0 = b.u0 + 2.0 * s.u0 * b.usq, ut1 = b.u1 + 2.0 * s.u1 * b.usq, ut2 = b.u2 + 2.0 * s.u2 * b.usq;
+    const double ri = 1.0 / s.rho;
+    // beta = rho/(2p): d beta = beta/rho d rho - beta/p d p, and beta/p = 2 beta^2/rho
+    const double pb = -b.beta * 2.0 * s.beta * s.beta * ri;
+    qb[0] = b.rho + b.beta * s.beta * ri + pb * gm1 * 0.5 * s.usq - (ut0 * s.u0 + ut1 * s.u1 + ut2 * s.u2) * ri;
+    qb[1] = ut0 * ri - pb * gm1 * s.u0;
+    qb[2] = ut1 * ri - pb * gm1 * s.u1;
+    qb[3] = ut2 * ri - pb * gm1 * s.u2;
+    qb[4] = pb * gm1;
+}
+
+// Logarithmic mean and its partial derivatives.  Series branch (u = ((a-b)/(a+b))^2 < 1e-4):
+// L = (a+b)/(2F(u)), F = artanh(f)/f = 1 + u/3 + u^2/5 + ..., dL/da = G/2 - 2 f b F'(u) G^2/(a+b)
+// with G = 1/F; otherwise L = (a-b)/l, l = log(a/b), dL/da = (1 - L/a)/l, dL/db = (L/b - 1)/l.
+__device__ __forceinline__ void ln_mean_d(double a, double b, double& L, double& La, double& Lb) {
+    const double d = a - b, s = a + b;
+    const double f = d / s;
+    const double u = f * f;
+    if (u < 1.0e-4) {
+        const double G = 1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0)));
+        const double Fp = 1.0 / 3.0 + u * (2.0 / 5.0 + u * (3.0 / 7.0 + u * (4.0 / 9.0)));
+        L = 0.5 * s * G;
+        const double t = 2.0 * f * Fp * G * G / s;
+        La = 0.5 * G - t * b;
+        Lb = 0.5 * G + t * a;
+    } else {
+        const double l = log(a / b);
+        L = d / l;
+        La = (1.0 - L / a) / l;
+        Lb = (L / b - 1.0) / l;
+    }
+}
+
+// Reverse of the contracted Chandrashekar flux: given the cotangent mu[5] of f(a, b; n), add the
+// primitive cotangents of both states to ab, bb.
+__device__ __forceinline__ void ec_flux_vjp(const Prim& a, const Prim& b, double n0, double n1, double n2,
+                                            const double mu[5], const Phys& ph, PBar& ab, PBar& bb) {
+    double Lr, Lra, Lrb, Lb, Lba, Lbb;
+    ln_mean_d(a.rho, b.rho, Lr, Lra, Lrb);
+    ln_mean_d(a.beta, b.beta, Lb, Lba, Lbb);
+    const double IBL = 1.0 / Lb;
+    const double rsb = 1.0 / (a.beta + b.beta);
+    const double ub0 = 0.5 * (a.u0 + b.u0), ub1 = 0.5 * (a.u1 + b.u1), ub2 = 0.5 * (a.u2 + b.u2);
+    const double un = ub0 * n0 + ub1 * n1 + ub2 * n2;
+    const double pt = 0.5 * (a.rho + b.rho) * rsb;
+    const double f1 = Lr * un;
+    const double fm0 = f1 * ub0 + pt * n0, fm1 = f1 * ub1 + pt * n1, fm2 = f1 * ub2 + pt * n2;
+    const double c5 = 0.5 * ph.inv_gm1 * IBL - 0.25 * (a.usq + b.usq);
+    // reverse
+    const double fmb0 = mu[1] + mu[4] * ub0, fmb1 = mu[2] + mu[4] * ub1, fmb2 = mu[3] + mu[4] * ub2;
+    const double f1b = mu[0] + mu[4] * c5 + fmb0 * ub0 + fmb1 * ub1 + fmb2 * ub2;
+    const double c5b = mu[4] * f1;
+    const double ptb = fmb0 * n0 + fmb1 * n1 + fmb2 * n2;
+    const double unb = f1b * Lr;
+    const double ubb0 = mu[4] * fm0 + fmb0 * f1 + unb * n0;
+    const double ubb1 = mu[4] * fm1 + fmb1 * f1 + unb * n1;
+    const double ubb2 = mu[4] * fm2 + fmb2 * f1 + unb * n2;
+    const double Lrb_ = f1b * un;
+    const double IBLb = c5b * 0.5 * ph.inv_gm1;
+    const double rsbb = ptb * 0.5 * (a.rho + b.rho);
+    const double bsum = -rsbb * rsb * rsb;
+    const double ibl2 = -IBLb * IBL * IBL;
+    ab.rho += 0.5 * ptb * rsb + Lrb_ * Lra;
+    bb.rho += 0.5 * ptb * rsb + Lrb_ * Lrb;
+    ab.beta += bsum + ibl2 * Lba;
+    bb.beta += bsum + ibl2 * Lbb;
+    ab.usq += -0.25 * c5b;
+    bb.usq += -0.25 * c5b;
+    ab.u0 += 0.5 * ubb0;
+    ab.u1 += 0.5 * ubb1;
+    ab.u2 += 0.5 * ubb2;
+    bb.u0 += 0.5 * ubb0;
+    bb.u1 += 0.5 * ubb1;
+    bb.u2 += 0.5 * ubb2;
+}
+
+template <int N>
+__device__ __forceinline__ int line_base(int l, int t1, int t2) {
+    return l == 0 ? (t1 * N + t2 * N * N) : (l == 1 ? (t1 + t2 * N * N) : (t1 + t2 * N));
+}
+template <int N>
+__device__ __forceinline__ int dir_stride(int l) {
+    return l == 0 ? 1 : (l == 1 ? N : N * N);
+}
+
+__device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Prim& s) {
+    s.rho = sP[idx];
+    s.u0 = sP[N3 + idx];
+    s.u1 = sP[2 * N3 + idx];
+    s.u2 = sP[3 * N3 + idx];
+    s.beta = sP[4 * N3 + idx];
+    s.usq = sP[5 * N3 + idx];
+}
+
+__device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+template <int N>
+__global__ void __launch_bounds__(CfgA<N>::THREADS)
+adj_main(const double* __restrict__ q, const double* __restrict__ lam, const double* __restrict__ geom,
+         const int32_t* __restrict__ nbr, double* __restrict__ grad, double* __restrict__ gbuf,
+         double* __restrict__ tbuf, double* __restrict__ mupart, int64_t K, const Ops ops, const Phys ph) {
+    constexpr int N2 = CfgA<N>::N2, N3 = CfgA<N>::N3, EPB = CfgA<N>::EPB;
+    extern __shared__ double smem[];
+    __shared__ double red[CfgA<N>::THREADS];
+    const int t = threadIdx.x;
+    const int el_loc = t / N3;
+    const int node = t - el_loc * N3;
+    const int64_t el = (int64_t)blockIdx.x * EPB + el_loc;
+    const bool active = el < K;
+    double* sP = smem + (size_t)el_loc * CfgA<N>::SM;   // [10][N3] rho,u0,u1,u2,beta,usq,w2..w5
+    double* sL = sP + 10 * N3;                          // [5][N3] lt = lambda / J
+    double* sG = sL + 5 * N3;                           // [10][N3]
+    double* sB = sG + 10 * N3;                          // [6][N3] primitive cotangents
+    double* sQ = sB + 6 * N3;                           // [5][N3] direct conserved cotangents
+    double* sT = sQ + 5 * N3;                           // [12][N3] theta-bar
+    double* sWf = sT + 12 * N3;                         // [6][4][N2]
+    const int64_t eoff = el * 5 * N3;
+    double mu_acc = 0.0;
+
+    if (active) {
+        double qv[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qv[v] = q[eoff + v * N3 + node];
+        Prim s;
+        to_prim(qv, ph, s);
+        sP[node] = s.rho;
+        sP[N3 + node] = s.u0;
+        sP[2 * N3 + node] = s.u1;
+        sP[3 * N3 + node] = s.u2;
+        sP[4 * N3 + node] = s.beta;
+        sP[5 * N3 + node] = s.usq;
+        sP[6 * N3 + node] = 2.0 * s.beta * s.u0;
+        sP[7 * N3 + node] = 2.0 * s.beta * s.u1;
+        sP[8 * N3 + node] = 2.0 * s.beta * s.u2;
+        sP[9 * N3 + node] = -2.0 * s.beta;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) sG[c * N3 + node] = geom[(el * 10 + c) * N3 + node];
+        const double Jinv = 1.0 / sG[node];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            sL[v * N3 + node] = lam[eoff + v * N3 + node] * Jinv;
+            sQ[v * N3 + node] = 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sB[c * N3 + node] = 0.0;
+    }
+    __syncthreads();
+
+    // ---- volume term, one xi_l line per thread, direction by direction
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        if (active && node < N2) {
+            const int base = line_base<N>(l, node % N, node / N);
+            const int st = dir_stride<N>(l);
+            const double* n0p = sG + (1 + 3 * l) * N3;
+            const double* n1p = n0p + N3;
+            const double* n2p = n1p + N3;
+            PBar acc[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) acc[i] = PBar{0, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int i = 0; i < N - 1; ++i) {
+                const int ii = base + i * st;
+                Prim si;
+                load_prim(sP, N3, ii, si);
+                const double a0 = n0p[ii], a1 = n1p[ii], a2 = n2p[ii];
+                double li[5];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) li[v] = sL[v * N3 + ii] * ops.winv[i];
+#pragma unroll
+                for (int j = i + 1; j < N; ++j) {
+                    const int jj = base + j * st;
+                    Prim sj;
+                    load_prim(sP, N3, jj, sj);
+                    const double c = ops.S2[i][j];
+                    double mu[5];
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) mu[v] = c * (sL[v * N3 + jj] * ops.winv[j] - li[v]);
+                    ec_flux_vjp(si, sj, 0.5 * (a0 + n0p[jj]), 0.5 * (a1 + n1p[jj]), 0.5 * (a2 + n2p[jj]), mu, ph,
+                                acc[i], acc[j]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int ii = base + i * st;
+                sB[ii] += acc[i].rho;
+                sB[N3 + ii] += acc[i].u0;
+                sB[2 * N3 + ii] += acc[i].u1;
+                sB[3 * N3 + ii] += acc[i].u2;
+                sB[4 * N3 + ii] += acc[i].beta;
+                sB[5 * N3 + ii] += acc[i].usq;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- inviscid interface term: own cotangents here, neighbour cotangents to gbuf
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        if (active && node < 2 * N2) {
+            const int side = node / N2, fi = node - side * N2;
+            const int st = dir_stride<N>(l);
+            const int base = line_base<N>(l, fi % N, fi / N);
+            const int own = base + (side ? (N - 1) * st : 0);
+            const int nbn = base + (side ? 0 : (N - 1) * st);
+            const int64_t nb = nbr[el * 6 + 2 * l + side];
+            double qo[5], qn[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                qo[v] = q[eoff + v * N3 + own];
+                qn[v] = q[nb * 5 * N3 + v * N3 + nbn];
+            }
+            Prim so, sn;
+            load_prim(sP, N3, own, so);
+            to_prim(qn, ph, sn);
+            const double n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own],
+                         n2 = sG[(3 + 3 * l) * N3 + own];
+            const double E = side ? 1.0 : -1.0;
+            const double wi = ops.winv[side ? N - 1 : 0];
+            double nu[5], muf[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                nu[v] = sL[v * N3 + own] * wi;
+                muf[v] = -E * nu[v];
+            }
+            PBar bo{0, 0, 0, 0, 0, 0}, bn{0, 0, 0, 0, 0, 0};
+            ec_flux_vjp(so, sn, n0, n1, n2, muf, ph, bo, bn);
+            double qbo[5] = {0, 0, 0, 0, 0}, qbn[5] = {0, 0, 0, 0, 0};
+            if (ph.dissipation) {
+                const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+                const double uo = so.u0 * n0 + so.u1 * n1 + so.u2 * n2;
+                const double un_ = sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2;
+                const double co = sqrt(0.5 * ph.gamma / so.beta), cn = sqrt(0.5 * ph.gamma / sn.beta);
+                const double lo = fabs(uo) + co * nn, ln = fabs(un_) + cn * nn;
+                const double lam2 = 0.5 * fmax(lo, ln);
+                double lb = 0.0;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    qbo[v] -= lam2 * nu[v];
+                    qbn[v] += lam2 * nu[v];
+                    lb -= nu[v] * (qo[v] - qn[v]);
+                }
+                const double lob = lo > ln ? 0.5 * lb : (lo < ln ? 0.0 : 0.25 * lb);
+                const double lnb = ln > lo ? 0.5 * lb : (ln < lo ? 0.0 : 0.25 * lb);
+                const double so_ = sgn(uo) * lob, sn_ = sgn(un_) * lnb;
+                bo.u0 += so_ * n0;
+                bo.u1 += so_ * n1;
+                bo.u2 += so_ * n2;
+                bn.u0 += sn_ * n0;
+                bn.u1 += sn_ * n1;
+                bn.u2 += sn_ * n2;
+                bo.beta += lob * nn * (-0.5 * co / so.beta);
+                bn.beta += lnb * nn * (-0.5 * cn / sn.beta);
+            }
+            sB[own] += bo.rho;
+            sB[N3 + own] += bo.u0;
+            sB[2 * N3 + own] += bo.u1;
+            sB[3 * N3 + own] += bo.u2;
+            sB[4 * N3 + own] += bo.beta;
+            sB[5 * N3 + own] += bo.usq;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sQ[v * N3 + own] += qbo[v];
+            double qb[5];
+            pbar_to_q(sn, bn, ph, qb);
+            double* gb = gbuf + ((el * 6 + 2 * l + side) * 5) * N2 + fi;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) gb[v * N2] = qb[v] + qbn[v];
+            double* wf = sWf + (2 * l + side) * 4 * N2 + fi;
+            wf[0] = 2.0 * sn.beta * sn.u0;
+            wf[N2] = 2.0 * sn.beta * sn.u1;
+            wf[2 * N2] = 2.0 * sn.beta * sn.u2;
+            wf[3 * N2] = -2.0 * sn.beta;
+        }
+        __syncthreads();
+    }
+
+    // ---- viscous chain, reversed node by node
+    if (ph.viscous) {
+        const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+        double ub[3] = {0, 0, 0}, bb = 0.0;
+        if (active) {
+            // forward recompute: theta, g, du, FV
+            const double wown[4] = {sP[6 * N3 + node], sP[7 * N3 + node], sP[8 * N3 + node], sP[9 * N3 + node]};
+            double th[3][4];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int ia = a == 0 ? i1 : (a == 1 ? i2 : i3);
+                const int st = dir_stride<N>(a);
+                const int lb = node - ia * st;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int j = 0; j < N; ++j) s += ops.D[ia][j] * sP[(6 + k) * N3 + lb + j * st];
+                    th[a][k] = s;
+                }
+                if (ia == 0 || ia == N - 1) {
+                    const int side = ia == N - 1;
+                    const int fi = a == 0 ? (i2 + N * i3) : (a == 1 ? (i1 + N * i3) : (i1 + N * i2));
+                    const double E = side ? 0.5 : -0.5;
+                    const double* wf = sWf + (2 * a + side) * 4 * N2 + fi;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) th[a][k] += E * (wf[k * N2] - wown[k]) * ops.winv[ia];
+                }
+            }
+            const double Jinv = 1.0 / sG[node];
+            double g[3][4];
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    g[m][k] = Jinv * (sG[(1 + m) * N3 + node] * th[0][k] + sG[(4 + m) * N3 + node] * th[1][k] +
+                                      sG[(7 + m) * N3 + node] * th[2][k]);
+            const double beta = sP[4 * N3 + node];
+            const double RT = 0.5 / beta;
+            const double u[3] = {sP[N3 + node], sP[2 * N3 + node], sP[3 * N3 + node]};
+            double du[3][3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) du[k][m] = RT * (g[m][k] + u[k] * g[m][3]);
+            const double div = du[0][0] + du[1][1] + du[2][2];
+            const double hc = ph.kappa / ph.R * RT * RT;
+            double FV[3][4];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    FV[m][i] = ph.mu * (du[i][m] + du[m][i] - (i == m ? (2.0 / 3.0) * div : 0.0));
+                FV[m][3] = FV[m][0] * u[0] + FV[m][1] * u[1] + FV[m][2] * u[2] + hc * g[m][3];
+            }
+            // Phi_l = D_l^T lt (momentum, energy) plus the interface terms -(E/2)(lt_own + lt_nbr)/w_end
+            double Phi[3][4];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
+                const int st = dir_stride<N>(l);
+                const int lb = node - il * st;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int i = 0; i < N; ++i) s += ops.D[i][il] * sL[(1 + k) * N3 + lb + i * st];
+                    Phi[l][k] = s;
+                }
+                if (il == 0 || il == N - 1) {
+                    const int side = il == N - 1;
+                    const int st2 = dir_stride<N>(l);
+                    const int nbn = node + (side ? -(N - 1) * st2 : (N - 1) * st2);   // matching node in nb
+                    const int64_t nb = nbr[el * 6 + 2 * l + side];
+                    const double Jn = 1.0 / geom[nb * 10 * N3 + nbn];
+                    const double E = side ? 0.5 : -0.5;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        Phi[l][k] -= E * ops.winv[il] * (sL[(1 + k) * N3 + node] + lam[(nb * 5 + 1 + k) * N3 + nbn] * Jn);
+                }
+            }
+            double Psi[3][4];
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    Psi[m][k] = sG[(1 + m) * N3 + node] * Phi[0][k] + sG[(4 + m) * N3 + node] * Phi[1][k] +
+                                sG[(7 + m) * N3 + node] * Phi[2][k];
+            // lambda . R_visc is linear in mu (kappa proportional to mu)
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mu_acc += Psi[m][k] * FV[m][k];
+            // reverse FV -> tau, u, hc, g
+            double gb[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+            double dub[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            double hcb = 0.0, divb = 0.0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double Tb = Psi[m][i] + Psi[m][3] * u[i];
+                    ub[i] += Psi[m][3] * FV[m][i];
+                    dub[i][m] += ph.mu * Tb;
+                    dub[m][i] += ph.mu * Tb;
+                    if (i == m) divb -= (2.0 / 3.0) * ph.mu * Tb;
+                }
+                hcb += Psi[m][3] * g[m][3];
+                gb[m][3] += Psi[m][3] * hc;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dub[k][k] += divb;
+            double RTb = hcb * ph.kappa / ph.R * 2.0 * RT;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    gb[m][k] += RT * dub[k][m];
+                    gb[m][3] += RT * u[k] * dub[k][m];
+                    ub[k] += RT * g[m][3] * dub[k][m];
+                    RTb += (g[m][k] + u[k] * g[m][3]) * dub[k][m];
+                }
+            bb += RTb * (-0.5 / (beta * beta));
+            // g = J^-1 sum_a Ja_am theta_a  ->  theta-bar
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    sT[(a * 4 + k) * N3 + node] =
+                        Jinv * (sG[(1 + 3 * a) * N3 + node] * gb[0][k] + sG[(2 + 3 * a) * N3 + node] * gb[1][k] +
+                                sG[(3 + 3 * a) * N3 + node] * gb[2][k]);
+        }
+        __syncthreads();
+        if (active) {
+            // w-bar: D_a^T theta-bar_a along lines and the own part of the lift; faces to tbuf
+            double wb[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int ia = a == 0 ? i1 : (a == 1 ? i2 : i3);
+                const int st = dir_stride<N>(a);
+                const int lb = node - ia * st;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int i = 0; i < N; ++i) s += ops.D[i][ia] * sT[(a * 4 + k) * N3 + lb + i * st];
+                    wb[k] += s;
+                }
+                if (ia == 0 || ia == N - 1) {
+                    const int side = ia == N - 1;
+                    const int fi = a == 0 ? (i2 + N * i3) : (a == 1 ? (i1 + N * i3) : (i1 + N * i2));
+                    const double E = side ? 0.5 : -0.5;
+                    double* tb = tbuf + ((el * 6 + 2 * a + side) * 4) * N2 + fi;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const double thb = sT[(a * 4 + k) * N3 + node];
+                        wb[k] -= E * ops.winv[ia] * thb;
+                        tb[k * N2] = thb;
+                    }
+                }
+            }
+            const double beta = sP[4 * N3 + node];
+            const double u[3] = {sP[N3 + node], sP[2 * N3 + node], sP[3 * N3 + node]};
+            // w = (2 beta u, -2 beta)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ub[k] += 2.0 * beta * wb[k];
+                bb += 2.0 * u[k] * wb[k];
+            }
+            bb -= 2.0 * wb[3];
+            sB[N3 + node] += ub[0];
+            sB[2 * N3 + node] += ub[1];
+            sB[3 * N3 + node] += ub[2];
+            sB[4 * N3 + node] += bb;
+        }
+    }
+    __syncthreads();
+    if (active) {
+        Prim s;
+        load_prim(sP, N3, node, s);
+        PBar b{sB[node], sB[N3 + node], sB[2 * N3 + node], sB[3 * N3 + node], sB[4 * N3 + node], sB[5 * N3 + node]};
+        double qb[5];
+        pbar_to_q(s, b, ph, qb);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) grad[eoff + v * N3 + node] = qb[v] + sQ[v * N3 + node];
+    }
+    // deterministic block sum of the mu cotangent (lambda . R_visc)
+    red[t] = mu_acc;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int i = 0; i < CfgA<N>::THREADS; ++i) s += red[i];
+        mupart[blockIdx.x] = s;
+    }
+}
+
+// Add the neighbours' contributions on this element's face nodes: the inviscid interface
+// cotangent they computed for our state (gbuf) and the lift part of their gradient cotangent
+// (tbuf), pulled back through w(q).
+template <int N>
+__global__ void __launch_bounds__(CfgA<N>::EPB_F * 2 * CfgA<N>::N2)
+adj_face(const double* __restrict__ q, const int32_t* __restrict__ nbr, const double* __restrict__ gbuf,
+         const double* __restrict__ tbuf, double* __restrict__ grad, int64_t K, const Ops ops, const Phys ph) {
+    constexpr int N2 = CfgA<N>::N2, N3 = CfgA<N>::N3;
+    const int t = threadIdx.x;
+    const int el_loc = t / (2 * N2);
+    const int r = t - el_loc * 2 * N2;
+    const int side = r / N2, fi = r - side * N2;
+    const int64_t el = (int64_t)blockIdx.x * CfgA<N>::EPB_F + el_loc;
+    const bool active = el < K;
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        if (active) {
+            const int st = dir_stride<N>(l);
+            const int own = line_base<N>(l, fi % N, fi / N) + (side ? (N - 1) * st : 0);
+            const int64_t nb = nbr[el * 6 + 2 * l + side];
+            const int nside = 1 - side;
+            const double* gb = gbuf + ((nb * 6 + 2 * l + nside) * 5) * N2 + fi;
+            double add[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) add[v] = gb[v * N2];
+            if (ph.viscous) {
+                const double* tb = tbuf + ((nb * 6 + 2 * l + nside) * 4) * N2 + fi;
+                const double En = nside ? 0.5 : -0.5;
+                const double wi = ops.winv[nside ? N - 1 : 0];
+                double wb[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) wb[k] = En * wi * tb[k * N2];
+                double qv[5];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) qv[v] = q[(el * 5 + v) * N3 + own];
+                Prim s;
+                to_prim(qv, ph, s);
+                PBar b{0.0, 2.0 * s.beta * wb[0], 2.0 * s.beta * wb[1], 2.0 * s.beta * wb[2],
+                       2.0 * (s.u0 * wb[0] + s.u1 * wb[1] + s.u2 * wb[2]) - 2.0 * wb[3], 0.0};
+                double qb[5];
+                pbar_to_q(s, b, ph, qb);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) add[v] += qb[v];
+            }
+#pragma unroll
+            for (int v = 0; v < 5; ++v) grad[(el * 5 + v) * N3 + own] += add[v];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kAdjRed) finish_mu(const double* __restrict__ part, int64_t n, double scale,
+                                                     double* __restrict__ acc) {
+    __shared__ double sh[kAdjRed];
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kAdjRed) a += part[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = kAdjRed / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) acc[0] += sh[0] * scale;
+}
+
+template <int N>
+cudaError_t launch_adj_n(const esdc_ctx* c, const double* q, const double* lam, double* grad, double* mu_acc,
+                         cudaStream_t s) {
+    using C = CfgA<N>;
+    const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
+    const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
+    adj_main<N><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
+                                               c->d_adj_mu, c->K, c->ops, c->phys);
+    const unsigned g2 = (unsigned)((c->K + C::EPB_F - 1) / C::EPB_F);
+    adj_face<N><<<g2, C::EPB_F * 2 * C::N2, 0, s>>>(q, c->d_nbr, c->d_adj_g, c->d_adj_t, grad, c->K, c->ops, c->phys);
+    if (mu_acc) {
+        const double scale = c->phys.mu > 0.0 ? 1.0 / c->phys.mu : 0.0;
+        finish_mu<<<1, kAdjRed, 0, s>>>(c->d_adj_mu, grid, scale, mu_acc);
+    }
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t prepare_adj_n() {
+    using C = CfgA<N>;
+    const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
+    return cudaFuncSetAttribute(adj_main<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+size_t adjoint_mu_blocks(const esdc_ctx* c) {
+    int epb = 1;
+    switch (c->N) {
+        case 2: epb = CfgA<2>::EPB; break;
+        case 3: epb = CfgA<3>::EPB; break;
+        case 4: epb = CfgA<4>::EPB; break;
+        case 5: epb = CfgA<5>::EPB; break;
+        case 6: epb = CfgA<6>::EPB; break;
+        case 7: epb = CfgA<7>::EPB; break;
+        default: epb = CfgA<8>::EPB; break;
+    }
+    return (size_t)((c->K + epb - 1) / epb);
+}
+
+cudaError_t prepare_adjoint(const esdc_ctx* c) {
+    switch (c->N) {
+        case 2: return prepare_adj_n<2>();
+        case 3: return prepare_adj_n<3>();
+        case 4: return prepare_adj_n<4>();
+        case 5: return prepare_adj_n<5>();
+        case 6: return prepare_adj_n<6>();
+        case 7: return prepare_adj_n<7>();
+        case 8: return prepare_adj_n<8>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rhs_vjp(const esdc_ctx* c, const double* q, const double* lam, double* grad, double* mu_acc,
+                           cudaStream_t s) {
+    switch (c->N) {
+        case 2: return launch_adj_n<2>(c, q, lam, grad, mu_acc, s);
+        case 3: return launch_adj_n<3>(c, q, lam, grad, mu_acc, s);
+        case 4: return launch_adj_n<4>(c, q, lam, grad, mu_acc, s);
+        case 5: return launch_adj_n<5>(c, q, lam, grad, mu_acc, s);
+        case 6: return launch_adj_n<6>(c, q, lam, grad, mu_acc, s);
+        case 7: return launch_adj_n<7>(c, q, lam, grad, mu_acc, s);
+        case 8: return launch_adj_n<8>(c, q, lam, grad, mu_acc, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace esdc

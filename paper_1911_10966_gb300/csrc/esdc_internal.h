@@ -81,6 +81,11 @@ struct esdc_ctx {
     double* d_red = nullptr;         // reduction partials
     double* d_red_out = nullptr;     // reduction results
     int red_blocks = 0;
+    // adjoint buffers, allocated on the first vector-Jacobian product
+    double* d_adj_g = nullptr;       // [K][6][5][N2] interface cotangents for the neighbour
+    double* d_adj_t = nullptr;       // [K][6][4][N2] lifted-gradient cotangents for the neighbour
+    double* d_adj_mu = nullptr;      // per-block partial sums of lambda . R_visc
+    double* d_adj_acc = nullptr;     // accumulated d/dmu
     // CUDA-event profiling of the residual kernels (esdc_profile)
     int profiling = 0;
     std::vector<void*> prof_events;  // cudaEvent_t quadruples: main start/stop, face start/stop

@@ -25,6 +25,15 @@ cudaError_t launch_cfl(const esdc_ctx* c, const double* q, cudaStream_t s);
 
 cudaError_t probe_fma(int kind, double* flops_per_s, cudaStream_t s);
 
+// adjoint (float64)
+size_t adjoint_mu_blocks(const esdc_ctx* c);
+cudaError_t prepare_adjoint(const esdc_ctx* c);
+// grad = (dR/dq)^T lam; if mu_acc != NULL, *mu_acc += lam . dR/dmu (device scalar)
+cudaError_t launch_rhs_vjp(const esdc_ctx* c, const double* q, const double* lam, double* grad, double* mu_acc,
+                           cudaStream_t s);
+cudaError_t launch_scale(double* out, const double* x, double a, int64_t n, cudaStream_t s);
+cudaError_t launch_ke_gradient(const esdc_ctx* c, const double* q, double* grad, cudaStream_t s);
+
 // mixed-precision form
 cudaError_t prepare_rhs_f32(const esdc_ctx* c);
 cudaError_t launch_rhs_f32(const esdc_ctx* c, const float* dq, float* out, cudaStream_t s, cudaEvent_t* ev);

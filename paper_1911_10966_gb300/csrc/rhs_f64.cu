@@ -32,60 +32,82 @@ struct Cfg {
     // shared doubles per element: prim/w/Ftilde 12 x N3 | r 5 x N3 | geometry 10 x N3 | face w 24 x N2
     static constexpr int SM = 27 * N3 + 24 * N2;
     static constexpr int EPB_SAT = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
+    // resident CTAs per SM the register allocation is sized for (the float64 pipe needs few warps)
+    static constexpr int MINB = N >= 6 ? 1 : (N >= 4 ? 3 : 4);
 };
 
+// Per-node primitives in the form the pair loop consumes: half density and half velocity (so that
+// averages are single additions), beta = rho/(2p) and a quarter of |u|^2.
 struct Prim {
-    double rho, u0, u1, u2, beta, usq;
+    double hr, hu0, hu1, hu2, beta, qq;
 };
 
 __device__ __forceinline__ void to_prim(const double* q, const Phys& ph, Prim& s) {
     const double ri = 1.0 / q[0];
-    s.rho = q[0];
-    s.u0 = q[1] * ri;
-    s.u1 = q[2] * ri;
-    s.u2 = q[3] * ri;
-    s.usq = s.u0 * s.u0 + s.u1 * s.u1 + s.u2 * s.u2;
-    const double p = (ph.gamma - 1.0) * (q[4] - 0.5 * q[0] * s.usq);
-    s.beta = 0.5 * q[0] / p;
+    const double u0 = q[1] * ri, u1 = q[2] * ri, u2 = q[3] * ri;
+    const double usq = u0 * u0 + u1 * u1 + u2 * u2;
+    const double p = (ph.gamma - 1.0) * (q[4] - 0.5 * q[0] * usq);
+    s.hr = 0.5 * q[0];
+    s.hu0 = 0.5 * u0;
+    s.hu1 = 0.5 * u1;
+    s.hu2 = 0.5 * u2;
+    s.beta = s.hr / p;
+    s.qq = 0.25 * usq;
 }
 
-// Logarithmic mean by the artanh series in f = (a-b)/(a+b), u = f^2 (Ismail-Roe style):
-// L = (a+b)/2 * G(u), G = 1/(1 + u/3 + u^2/5 + u^3/7 + ...) = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
-// for u < 1e-4 (truncation below 1e-17), else (a-b)/log(a/b).
-__device__ __forceinline__ double ln_mean(double a, double b) {
-    const double d = a - b, s = a + b;
-    const double f = d / s;
-    const double u = f * f;
-    if (u < 1.0e-4) return 0.5 * s * (1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0))));
-    return d / log(a / b);
+// Reciprocal by Newton-Raphson on g(r) = 1/r - x from the hardware approximation (about 23 bits):
+// each step r <- r + r (1 - x r) doubles the number of correct bits.
+__device__ __forceinline__ double rcp_approx(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_newton1(double x) {     // ~46 bits
+    const double r = rcp_approx(x);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ __forceinline__ double rcp_newton2(double x) {     // full double precision (within an ulp)
+    double r = rcp_newton1(x);
+    return fma(r, fma(-x, r, 1.0), r);
 }
 
-// Reciprocal logarithmic mean given rs = 1/(a+b): 2 rs (1 + u/3 + u^2/5 + u^3/7) or log(a/b)/(a-b).
-__device__ __forceinline__ double inv_ln_mean(double a, double b, double rs) {
-    const double d = a - b;
-    const double f = d * rs;
-    const double u = f * f;
-    if (u < 1.0e-4) return 2.0 * rs * (1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0))));
-    return log(a / b) / d;
-}
+// u = ((a-b)/(a+b))^2 < 1e-4, tested on the high word (integer pipe): the threshold moves by less
+// than 1e-6 relative, and both branches are accurate to float64 round-off around it.
+__device__ __forceinline__ bool small_jump(double u) { return __double2hiint(u) < 0x3F1A36E2; }
 
-// Chandrashekar two-point flux contracted with n (Sec. 4):
+// Chandrashekar two-point flux contracted with a direction vector n (Sec. 4):
 // f1 = rho_ln ubar.n, f_m = f1 ubar + p_t n, f5 = f1 (1/(2(g-1) beta_ln) - avg|u|^2/2) + ubar.f_m,
-// p_t = avg(rho)/(2 avg(beta)) = (rho_a + rho_b)/(2 (beta_a + beta_b)).
+// p_t = avg(rho)/(2 avg(beta)).  Log means by the artanh series in u = f^2, f = (a-b)/(a+b)
+// (Ismail-Roe style): L = (a+b)/2 G(u), G = 1 - u/3 - 4u^2/45 - 44u^3/945, and
+// 1/L = 2/(a+b) (1 + u/3 + u^2/5 + u^3/7) for u < 1e-4 (truncation below 1e-17), else the
+// logarithmic form.  The flux is linear in n: the volume loop passes n_i + n_j (twice the averaged
+// metric) and halves the pair coefficient instead.
 __device__ __forceinline__ void ec_flux(const Prim& a, const Prim& b, double n0, double n1, double n2,
                                         const Phys& ph, double f[5]) {
-    const double rho_ln = ln_mean(a.rho, b.rho);
-    const double rsb = 1.0 / (a.beta + b.beta);
-    const double ibeta_ln = inv_ln_mean(a.beta, b.beta, rsb);
-    const double ub0 = 0.5 * (a.u0 + b.u0), ub1 = 0.5 * (a.u1 + b.u1), ub2 = 0.5 * (a.u2 + b.u2);
-    const double un = ub0 * n0 + ub1 * n1 + ub2 * n2;
-    const double pt = 0.5 * (a.rho + b.rho) * rsb;
+    // density log mean from half densities: L = (hr_a + hr_b) G(u)
+    const double sh = a.hr + b.hr;
+    const double fr = (a.hr - b.hr) * rcp_newton1(sh);
+    const double ur = fr * fr;
+    double rho_ln;
+    if (small_jump(ur)) rho_ln = sh * fma(ur, fma(ur, fma(ur, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
+    else rho_ln = 2.0 * (a.hr - b.hr) / log(a.hr / b.hr);
+    // 1/beta_ln and p_t share 1/(beta_a + beta_b)
+    const double rsb = rcp_newton2(a.beta + b.beta);
+    const double fb = (a.beta - b.beta) * rsb;
+    const double ub = fb * fb;
+    double ibeta_ln;
+    if (small_jump(ub)) ibeta_ln = rsb * fma(ub, fma(ub, fma(ub, 2.0 / 7.0, 2.0 / 5.0), 2.0 / 3.0), 2.0);
+    else ibeta_ln = log(a.beta / b.beta) / (a.beta - b.beta);
+    const double ub0 = a.hu0 + b.hu0, ub1 = a.hu1 + b.hu1, ub2 = a.hu2 + b.hu2;
+    const double un = fma(ub2, n2, fma(ub1, n1, ub0 * n0));
+    const double pt = sh * rsb;
     const double f1 = rho_ln * un;
     f[0] = f1;
-    f[1] = f1 * ub0 + pt * n0;
-    f[2] = f1 * ub1 + pt * n1;
-    f[3] = f1 * ub2 + pt * n2;
-    f[4] = f1 * (0.5 * ph.inv_gm1 * ibeta_ln - 0.25 * (a.usq + b.usq)) + ub0 * f[1] + ub1 * f[2] + ub2 * f[3];
+    f[1] = fma(f1, ub0, pt * n0);
+    f[2] = fma(f1, ub1, pt * n1);
+    f[3] = fma(f1, ub2, pt * n2);
+    const double c5 = fma(0.5 * ph.inv_gm1, ibeta_ln, -(a.qq + b.qq));
+    f[4] = fma(ub2, f[3], fma(ub1, f[2], fma(ub0, f[1], f1 * c5)));
 }
 
 template <int N>
@@ -99,16 +121,16 @@ __device__ __forceinline__ int dir_stride(int l) {
 }
 
 __device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Prim& s) {
-    s.rho = sP[idx];
-    s.u0 = sP[N3 + idx];
-    s.u1 = sP[2 * N3 + idx];
-    s.u2 = sP[3 * N3 + idx];
+    s.hr = sP[idx];
+    s.hu0 = sP[N3 + idx];
+    s.hu1 = sP[2 * N3 + idx];
+    s.hu2 = sP[3 * N3 + idx];
     s.beta = sP[4 * N3 + idx];
-    s.usq = sP[5 * N3 + idx];
+    s.qq = sP[5 * N3 + idx];
 }
 
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
+__global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::MINB)
 rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const double* __restrict__ geom,
              const int32_t* __restrict__ nbr, double* __restrict__ trace, int64_t K, const Ops ops,
              const Phys ph) {
@@ -119,7 +141,7 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
     const int node = t - el_loc * N3;
     const int64_t el = (int64_t)blockIdx.x * EPB + el_loc;
     const bool active = el < K;
-    double* sP = smem + (size_t)el_loc * Cfg<N>::SM;   // [12][N3]: rho,u0,u1,u2,beta,usq,w2..w5 | Ftilde
+    double* sP = smem + (size_t)el_loc * Cfg<N>::SM;   // [12][N3]: rho/2,u/2 (3),beta,|u|^2/4,w2..w5 | Ftilde
     double* sR = sP + 12 * N3;                          // [5][N3]
     double* sG = sP + 17 * N3;                          // [10][N3]: J, Ja_lm
     double* sWf = sP + 27 * N3;                         // [6][4][N2]
@@ -132,15 +154,15 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
         for (int v = 0; v < 5; ++v) qv[v] = q[eoff + v * N3 + node];
         Prim s;
         to_prim(qv, ph, s);
-        sP[node] = s.rho;
-        sP[N3 + node] = s.u0;
-        sP[2 * N3 + node] = s.u1;
-        sP[3 * N3 + node] = s.u2;
+        sP[node] = s.hr;
+        sP[N3 + node] = s.hu0;
+        sP[2 * N3 + node] = s.hu1;
+        sP[3 * N3 + node] = s.hu2;
         sP[4 * N3 + node] = s.beta;
-        sP[5 * N3 + node] = s.usq;
-        sP[6 * N3 + node] = 2.0 * s.beta * s.u0;
-        sP[7 * N3 + node] = 2.0 * s.beta * s.u1;
-        sP[8 * N3 + node] = 2.0 * s.beta * s.u2;
+        sP[5 * N3 + node] = s.qq;
+        sP[6 * N3 + node] = 4.0 * s.beta * s.hu0;     // w2..w4 = 2 beta u
+        sP[7 * N3 + node] = 4.0 * s.beta * s.hu1;
+        sP[8 * N3 + node] = 4.0 * s.beta * s.hu2;
         sP[9 * N3 + node] = -2.0 * s.beta;
 #pragma unroll
         for (int c = 0; c < 10; ++c) sG[c * N3 + node] = geom[(el * 10 + c) * N3 + node];
@@ -175,12 +197,12 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
                     Prim sj;
                     load_prim(sP, N3, jj, sj);
                     double f[5];
-                    ec_flux(si, sj, 0.5 * (a0 + n0p[jj]), 0.5 * (a1 + n1p[jj]), 0.5 * (a2 + n2p[jj]), ph, f);
-                    const double c = ops.S2[i][j];
+                    ec_flux(si, sj, a0 + n0p[jj], a1 + n1p[jj], a2 + n2p[jj], ph, f);   // 2 x averaged metric
+                    const double c = 0.5 * ops.S2[i][j];
 #pragma unroll
                     for (int v = 0; v < 5; ++v) {
-                        acc[i][v] -= c * f[v];
-                        acc[j][v] += c * f[v];
+                        acc[i][v] = fma(-c, f[v], acc[i][v]);
+                        acc[j][v] = fma(c, f[v], acc[j][v]);
                     }
                 }
             }
@@ -221,17 +243,17 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             double lam = 0.0;
             if (ph.dissipation) {
                 const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
-                const double lo = fabs(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + sqrt(0.5 * ph.gamma / so.beta) * nn;
-                const double ln = fabs(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + sqrt(0.5 * ph.gamma / sn.beta) * nn;
+                const double lo = 2.0 * fabs(so.hu0 * n0 + so.hu1 * n1 + so.hu2 * n2) + sqrt(0.5 * ph.gamma / so.beta) * nn;
+                const double ln = 2.0 * fabs(sn.hu0 * n0 + sn.hu1 * n1 + sn.hu2 * n2) + sqrt(0.5 * ph.gamma / sn.beta) * nn;
                 lam = 0.5 * fmax(lo, ln);
             }
             const double wi = ops.winv[side ? N - 1 : 0];
 #pragma unroll
             for (int v = 0; v < 5; ++v) sR[v * N3 + own] += (-E * f[v] - lam * (qo[v] - qn[v])) * wi;
             double* wf = sWf + (2 * l + side) * 4 * N2 + fi;
-            wf[0] = 2.0 * sn.beta * sn.u0;
-            wf[N2] = 2.0 * sn.beta * sn.u1;
-            wf[2 * N2] = 2.0 * sn.beta * sn.u2;
+            wf[0] = 4.0 * sn.beta * sn.hu0;
+            wf[N2] = 4.0 * sn.beta * sn.hu1;
+            wf[2 * N2] = 4.0 * sn.beta * sn.hu2;
             wf[3 * N2] = -2.0 * sn.beta;
         }
         __syncthreads();
@@ -275,7 +297,7 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
                                       + sG[(7 + m) * N3 + node] * th[2][k]);
             const double beta = sP[4 * N3 + node];
             const double RT = 0.5 / beta;
-            const double u[3] = {sP[N3 + node], sP[2 * N3 + node], sP[3 * N3 + node]};
+            const double u[3] = {2.0 * sP[N3 + node], 2.0 * sP[2 * N3 + node], 2.0 * sP[3 * N3 + node]};
             // du_k/dx_m = RT (g_m[k] + u_k g_m[3]); dT/dx_m = (RT)^2/R g_m[3]
             double du[3][3];
 #pragma unroll

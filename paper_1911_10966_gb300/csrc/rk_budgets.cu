@@ -158,7 +158,52 @@ __global__ void __launch_bounds__(kRedThreads) finish_max(const double* __restri
     }
 }
 
+__global__ void __launch_bounds__(256) scale_kernel(double* __restrict__ out, const double* __restrict__ x, double a,
+                                                    int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = a * x[i];
+}
+
+// d/dq of sum P J rho|u|^2/2: P J (-|u|^2/2, u, 0)
+__global__ void __launch_bounds__(256) ke_grad_kernel(const double* __restrict__ q, const double* __restrict__ geom,
+                                                      int64_t K, int N, const Ops ops, double* __restrict__ g) {
+    const int N3 = N * N * N;
+    const int64_t n = K * N3;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t e = i / N3;
+        const int node = (int)(i - e * N3);
+        const int i1 = node % N, i2 = (node / N) % N, i3 = node / (N * N);
+        const double PJ = ops.w[i1] * ops.w[i2] * ops.w[i3] * geom[e * 10 * N3 + node];
+        const double* qe = q + e * 5 * N3 + node;
+        const double ri = 1.0 / qe[0];
+        const double u0 = qe[N3] * ri, u1 = qe[2 * N3] * ri, u2 = qe[3 * N3] * ri;
+        double* ge = g + e * 5 * N3 + node;
+        ge[0] = -0.5 * PJ * (u0 * u0 + u1 * u1 + u2 * u2);
+        ge[N3] = PJ * u0;
+        ge[2 * N3] = PJ * u1;
+        ge[3 * N3] = PJ * u2;
+        ge[4 * N3] = 0.0;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_scale(double* out, const double* x, double a, int64_t n, cudaStream_t s) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    scale_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, x, a, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ke_gradient(const esdc_ctx* c, const double* q, double* grad, cudaStream_t s) {
+    int64_t blocks = (c->n_nodes + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    ke_grad_kernel<<<(unsigned)blocks, 256, 0, s>>>(q, c->d_geom, c->K, c->N, c->ops, grad);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int64_t n, cudaStream_t s) {
     int64_t blocks = (n / 2 + 255) / 256;

@@ -158,6 +158,57 @@ class Solver:
             nat.check(code, "esdc_budgets")
         return tuple(out)
 
+    # -- adjoint (float64 contexts)
+    def rhs_vjp(self, q, lam, want_mu=False):
+        """(dR/dq)^T lam and, if want_mu, lam . dR/dmu."""
+        self._check_state(q)
+        self._check_state(lam)
+        g = torch.empty_like(q)
+        gm = ctypes.c_double()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_rhs_vjp(self._ctx, q.data_ptr(), lam.data_ptr(), g.data_ptr(),
+                                             ctypes.byref(gm) if want_mu else None, _stream_ptr()), "esdc_rhs_vjp")
+        return (g, gm.value) if want_mu else g
+
+    def ke_gradient(self, q):
+        self._check_state(q)
+        g = torch.empty_like(q)
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_ke_gradient(self._ctx, q.data_ptr(), g.data_ptr(), _stream_ptr()),
+                      "esdc_ke_gradient")
+        return g
+
+    def rk_step_ckpt(self, q, dt, nsteps):
+        """Advance q in place; return the [nsteps, K, 5, N, N, N] checkpoints (state before each step)."""
+        self._check_state(q)
+        ck = torch.empty((nsteps,) + self.state_shape, dtype=torch.float64, device=self.device)
+        nb = self.workspace_bytes()
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_rk_step_ckpt(self._ctx, q.data_ptr(), float(dt), int(nsteps), ck.data_ptr(),
+                                                  self._ws.data_ptr(), self._ws.numel(), _stream_ptr()),
+                      "esdc_rk_step_ckpt")
+        return ck
+
+    def rk_adjoint(self, ckpt, dt, lam):
+        """Reverse sweep: lam (dL/dq_N) is replaced by dL/dq_0; returns (lam, dL/dmu)."""
+        self._check_state(lam)
+        nsteps = ckpt.shape[0]
+        b = ctypes.c_size_t()
+        nat.check(nat.lib().esdc_rk_adjoint_workspace_bytes(self._ctx, ctypes.byref(b)), "workspace")
+        ws = torch.empty(b.value, dtype=torch.uint8, device=self.device)
+        gm = ctypes.c_double()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_rk_adjoint(self._ctx, ckpt.data_ptr(), float(dt), int(nsteps), lam.data_ptr(),
+                                                ctypes.byref(gm), ws.data_ptr(), ws.numel(), _stream_ptr()),
+                      "esdc_rk_adjoint")
+        return lam, gm.value
+
+    @property
+    def mu(self):
+        return 1.0 / self.Re if self.Re > 0 else 0.0
+
     def profile(self, on=True):
         """Record CUDA events around the residual kernels of every following evaluation."""
         nat.check(nat.lib().esdc_profile(self._ctx, 1 if on else 0), "esdc_profile")
