@@ -31,10 +31,11 @@ struct CfgF {
     static constexpr int TE = (N3 <= 256) ? (N3 > LINES ? N3 : LINES) : LINES;   // threads per element
     static constexpr int EPB = TE >= 128 ? 1 : (128 + TE - 1) / TE;
     static constexpr int THREADS = EPB * TE;
-    // shared floats per element: prim 8 | w 4 | geometry 10 | accumulators 3 x 6 (aliased by the
-    // 12 viscous fluxes) | own dq 5 | face w 24 N^2/N3
-    static constexpr int SM = (8 + 4 + 10 + 18 + 5) * N3 + 24 * N2;
+    // shared floats per element: prim 2 x float4 | w 4 | geometry 3 x float4 | accumulators 3 x 6
+    // (aliased by the 12 viscous fluxes) | own dq 5 | face w 24 N^2 (rounded to whole float4)
+    static constexpr int SM = ((8 + 4 + 12 + 18 + 5) * N3 + 24 * N2 + 3) / 4 * 4;
     static constexpr int EPB_SAT = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
+    static constexpr int MINB = N <= 4 ? 4 : (N == 5 ? 3 : 2);   // resident CTAs the registers are sized for
 };
 
 struct PrimF {
@@ -42,10 +43,21 @@ struct PrimF {
 };
 
 struct Ref {
-    float rho0, p0, beta0, RT0, H0, inv_gm1, gm1, gamma;
+    float rho0, p0, beta0, RT0, H0, inv_gm1, gm1, gamma, inv_p0;
 };
 
-__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+// approximate reciprocal and square root (about 1 ulp): the float32 residual's rounding is
+// dominated by the flux differencing, not by these
+__device__ __forceinline__ float frcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float fsqrt(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // primitives from the float32 perturbation state
 __device__ __forceinline__ void to_prim_f(const float dq[5], const Ref& r, PrimF& s) {
@@ -59,7 +71,7 @@ __device__ __forceinline__ void to_prim_f(const float dq[5], const Ref& r, PrimF
     const float dp = r.gm1 * (dq[4] - 0.5f * s.rho * s.usq);
     const float h = 0.5f * frcp(r.p0 + dp);          // 1/(2p)
     s.beta = s.rho * h;
-    s.db = (s.dr * r.p0 - r.rho0 * dp) * h / r.p0;   // beta - beta0 = (drho p0 - rho0 dp)/(2 p p0)
+    s.db = (s.dr * r.p0 - r.rho0 * dp) * h * r.inv_p0;   // beta - beta0 = (drho p0 - rho0 dp)/(2 p p0)
 }
 
 // perturbation part of the two-point flux (df[0..4]) and ubar.n (the linear reference part)
@@ -73,7 +85,7 @@ __device__ __forceinline__ void ec_flux_pert(const PrimF& a, const PrimF& b, flo
     if (uu < 1.0e-2f) {
         drl = 0.5f * (a.dr + b.dr) + 0.5f * s * (uu * (-1.0f / 3.0f + uu * (-4.0f / 45.0f + uu * (-44.0f / 945.0f))));
     } else {
-        drl = (a.rho - b.rho) / logf(a.rho / b.rho) - r.rho0;
+        drl = (a.rho - b.rho) * frcp(logf(a.rho * frcp(b.rho))) - r.rho0;
     }
     // beta: 1/(2 beta_ln) - RT0 and p_t - p0 from the perturbations
     const float sb = a.beta + b.beta;
@@ -86,7 +98,7 @@ __device__ __forceinline__ void ec_flux_pert(const PrimF& a, const PrimF& b, flo
         const float Fm1 = ub * (1.0f / 3.0f + ub * (1.0f / 5.0f + ub * (1.0f / 7.0f)));
         dI = (2.0f * r.beta0 * Fm1 - dbs) * rsb * r.RT0;
     } else {
-        dI = 0.5f * logf(a.beta / b.beta) / (a.beta - b.beta) - r.RT0;
+        dI = 0.5f * logf(a.beta * frcp(b.beta)) * frcp(a.beta - b.beta) - r.RT0;
     }
     const float dpt = (r.beta0 * (a.dr + b.dr) - r.rho0 * dbs) * rsb * r.RT0;
     const float ub0 = 0.5f * (a.u0 + b.u0), ub1 = 0.5f * (a.u1 + b.u1), ub2 = 0.5f * (a.u2 + b.u2);
@@ -110,19 +122,21 @@ __device__ __forceinline__ int dir_stride_f(int l) {
     return l == 0 ? 1 : (l == 1 ? N : N * N);
 }
 
-__device__ __forceinline__ void load_prim_f(const float* sP, int N3, int idx, PrimF& s) {
-    s.rho = sP[idx];
-    s.dr = sP[N3 + idx];
-    s.u0 = sP[2 * N3 + idx];
-    s.u1 = sP[3 * N3 + idx];
-    s.u2 = sP[4 * N3 + idx];
-    s.usq = sP[5 * N3 + idx];
-    s.beta = sP[6 * N3 + idx];
-    s.db = sP[7 * N3 + idx];
+// node primitives stored as two float4 per node: (rho, drho, u0, u1), (u2, |u|^2, beta, dbeta)
+__device__ __forceinline__ void load_prim_f(const float4* sP4, int N3, int idx, PrimF& s) {
+    const float4 a = sP4[idx], b = sP4[N3 + idx];
+    s.rho = a.x;
+    s.dr = a.y;
+    s.u0 = a.z;
+    s.u1 = a.w;
+    s.u2 = b.x;
+    s.usq = b.y;
+    s.beta = b.z;
+    s.db = b.w;
 }
 
 template <int N>
-__global__ void __launch_bounds__(CfgF<N>::THREADS)
+__global__ void __launch_bounds__(CfgF<N>::THREADS, CfgF<N>::MINB)
 rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float* __restrict__ geom,
              const int32_t* __restrict__ nbr, float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph,
              const Ref ref) {
@@ -134,10 +148,11 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
     const int tl = t - el_loc * TE;
     const int64_t el = (int64_t)blockIdx.x * C::EPB + el_loc;
     const bool active = el < K;
-    float* sP = smf + (size_t)el_loc * C::SM;       // [8][N3] rho, dr, u0, u1, u2, usq, beta, db
+    float* sP = smf + (size_t)el_loc * C::SM;       // [2][N3] float4 primitives | later [8][N3] floats
+    float4* sP4 = reinterpret_cast<float4*>(sP);
     float* sW = sP + 8 * N3;                         // [4][N3] w2..w4, w5 - w5_ref
-    float* sG = sW + 4 * N3;                         // [10][N3] J, Ja
-    float* sA = sG + 10 * N3;                        // [3][6][N3] per-direction accumulators | [12][N3] Ftilde
+    float4* sG4 = reinterpret_cast<float4*>(sW + 4 * N3);   // [3][N3] (Ja_l0, Ja_l1, Ja_l2, 1/J)
+    float* sA = sW + 16 * N3;                        // [3][6][N3] per-direction accumulators | [12][N3] Ftilde
     float* sQ = sA + 18 * N3;                        // [5][N3] own dq
     float* sWf = sQ + 5 * N3;                        // [6][4][N2] neighbour entropy variables
     const int64_t eoff = el * 5 * N3;
@@ -152,20 +167,18 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
             }
             PrimF s;
             to_prim_f(d, ref, s);
-            sP[node] = s.rho;
-            sP[N3 + node] = s.dr;
-            sP[2 * N3 + node] = s.u0;
-            sP[3 * N3 + node] = s.u1;
-            sP[4 * N3 + node] = s.u2;
-            sP[5 * N3 + node] = s.usq;
-            sP[6 * N3 + node] = s.beta;
-            sP[7 * N3 + node] = s.db;
+            sP4[node] = make_float4(s.rho, s.dr, s.u0, s.u1);
+            sP4[N3 + node] = make_float4(s.u2, s.usq, s.beta, s.db);
             sW[node] = 2.0f * s.beta * s.u0;
             sW[N3 + node] = 2.0f * s.beta * s.u1;
             sW[2 * N3 + node] = 2.0f * s.beta * s.u2;
             sW[3 * N3 + node] = -2.0f * s.db;         // w5 - w5_ref (the constant has no gradient)
+            float gv[10];
 #pragma unroll
-            for (int c = 0; c < 10; ++c) sG[c * N3 + node] = geom[(el * 10 + c) * N3 + node];
+            for (int c = 0; c < 10; ++c) gv[c] = geom[(el * 10 + c) * N3 + node];
+            const float Ji = frcp(gv[0]);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) sG4[l * N3 + node] = make_float4(gv[1 + 3 * l], gv[2 + 3 * l], gv[3 + 3 * l], Ji);
         }
     }
     __syncthreads();
@@ -175,9 +188,7 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
         const int l = tl / N2, line = tl - l * N2;
         const int base = line_base_f<N>(l, line % N, line / N);
         const int st = dir_stride_f<N>(l);
-        const float* n0p = sG + (1 + 3 * l) * N3;
-        const float* n1p = n0p + N3;
-        const float* n2p = n1p + N3;
+        const float4* nl = sG4 + l * N3;
         float acc[N][6];
 #pragma unroll
         for (int i = 0; i < N; ++i)
@@ -187,16 +198,18 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
         for (int i = 0; i < N - 1; ++i) {
             const int ii = base + i * st;
             PrimF si;
-            load_prim_f(sP, N3, ii, si);
-            const float a0 = n0p[ii], a1 = n1p[ii], a2 = n2p[ii];
+            load_prim_f(sP4, N3, ii, si);
+            const float4 ni = nl[ii];
 #pragma unroll
             for (int j = i + 1; j < N; ++j) {
                 const int jj = base + j * st;
                 PrimF sj;
-                load_prim_f(sP, N3, jj, sj);
+                load_prim_f(sP4, N3, jj, sj);
+                const float4 nj = nl[jj];
                 float df[5], un;
-                ec_flux_pert(si, sj, 0.5f * (a0 + n0p[jj]), 0.5f * (a1 + n1p[jj]), 0.5f * (a2 + n2p[jj]), ref, df, un);
-                const float c = ops.S2[i][j];
+                // the flux is linear in n: pass n_i + n_j and halve the pair coefficient
+                ec_flux_pert(si, sj, ni.x + nj.x, ni.y + nj.y, ni.z + nj.z, ref, df, un);
+                const float c = 0.5f * ops.S2[i][j];
 #pragma unroll
                 for (int v = 0; v < 5; ++v) {
                     acc[i][v] -= c * df[v];
@@ -238,18 +251,18 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
 #pragma unroll
                 for (int v = 0; v < 5; ++v) qn[v] = dq[nb * 5 * N3 + v * N3 + nbn];
                 PrimF so, sn;
-                load_prim_f(sP, N3, own, so);
+                load_prim_f(sP4, N3, own, so);
                 to_prim_f(qn, ref, sn);
-                const float n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own],
-                            n2 = sG[(3 + 3 * l) * N3 + own];
+                const float4 nv = sG4[l * N3 + own];
+                const float n0 = nv.x, n1 = nv.y, n2 = nv.z;
                 float df[5], un;
                 ec_flux_pert(so, sn, n0, n1, n2, ref, df, un);
                 const float E = side ? 1.0f : -1.0f;
                 float lam = 0.0f;
                 if (ph.dissipation) {
-                    const float nn = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
-                    const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + sqrtf(0.5f * ref.gamma / so.beta) * nn;
-                    const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + sqrtf(0.5f * ref.gamma / sn.beta) * nn;
+                    const float nn = fsqrt(n0 * n0 + n1 * n1 + n2 * n2);
+                    const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + fsqrt(0.5f * ref.gamma * frcp(so.beta)) * nn;
+                    const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + fsqrt(0.5f * ref.gamma * frcp(sn.beta)) * nn;
                     lam = 0.5f * fmaxf(lo, ln);
                 }
                 const float wi = ops.winv[side ? N - 1 : 0];
@@ -299,16 +312,18 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
                         for (int k = 0; k < 4; ++k) th[a][k] += E * (wf[k * N2] - wown[k]) * ops.winv[ia];
                     }
                 }
-                const float Jinv = frcp(sG[node]);
+                const float4 G0 = sG4[node], G1 = sG4[N3 + node], G2 = sG4[2 * N3 + node];
+                const float Jinv = G0.w;
+                const float Ja[3][3] = {{G0.x, G0.y, G0.z}, {G1.x, G1.y, G1.z}, {G2.x, G2.y, G2.z}};
                 float g[3][4];
 #pragma unroll
                 for (int m = 0; m < 3; ++m)
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        g[m][k] = Jinv * (sG[(1 + m) * N3 + node] * th[0][k] + sG[(4 + m) * N3 + node] * th[1][k] +
-                                          sG[(7 + m) * N3 + node] * th[2][k]);
-                const float RT = 0.5f / sP[6 * N3 + node];
-                const float u[3] = {sP[2 * N3 + node], sP[3 * N3 + node], sP[4 * N3 + node]};
+                        g[m][k] = Jinv * (Ja[0][m] * th[0][k] + Ja[1][m] * th[1][k] + Ja[2][m] * th[2][k]);
+                const float4 P0 = sP4[node], P1 = sP4[N3 + node];
+                const float RT = 0.5f * frcp(P1.z);
+                const float u[3] = {P0.z, P0.w, P1.x};
                 float du[3][3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
@@ -328,8 +343,7 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
                 for (int l = 0; l < 3; ++l)
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        Ft[r][l][k] = sG[(1 + 3 * l) * N3 + node] * FV[0][k] + sG[(2 + 3 * l) * N3 + node] * FV[1][k] +
-                                      sG[(3 + 3 * l) * N3 + node] * FV[2][k];
+                        Ft[r][l][k] = Ja[l][0] * FV[0][k] + Ja[l][1] * FV[1][k] + Ja[l][2] * FV[2][k];
             }
         }
         // the volume/interface sums in sA[0..5] are complete; move them into sP (free now) so
@@ -380,7 +394,7 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
                         vs[k] += s;
                     }
                 }
-                const float Jinv = frcp(sG[node]);
+                const float Jinv = sG4[node].w;
                 const float lin = sP[5 * N3 + node];
                 out[eoff + node] = (sP[node] + ref.rho0 * lin) * Jinv;
 #pragma unroll
@@ -390,7 +404,7 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
         }
     } else if (active) {
         for (int node = tl; node < N3; node += TE) {
-            const float Jinv = frcp(sG[node]);
+            const float Jinv = sG4[node].w;
             const float lin = sA[5 * N3 + node];
             out[eoff + node] = (sA[node] + ref.rho0 * lin) * Jinv;
 #pragma unroll
@@ -444,6 +458,7 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const float* dq, float* out, cudaStr
     ref.inv_gm1 = ph.inv_gm1;
     ref.gm1 = ph.gamma - 1.0f;
     ref.gamma = ph.gamma;
+    ref.inv_p0 = 1.0f / ph.p0;
     if (ev) cudaEventRecord(ev[0], s);
     rhs_main_f32<N><<<grid, C::THREADS, smem, s>>>(dq, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf,
                                                    ph, ref);
