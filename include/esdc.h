@@ -122,7 +122,7 @@ int esdc_rhs_host(esdc_ctx* ctx, const double* q_host, void* dqdt_host, void* st
 /*
  * esdc_workspace_bytes -- device workspace needed by esdc_rk_step (what = 0): for ESDC_PREC_FP64
  * six stage derivatives and one stage state, each K*5*N^3 float64; for ESDC_PREC_FP32 six float32
- * stage derivatives and two float32 perturbation states (each sub-buffer 256-byte aligned).
+ * stage derivatives and one float32 perturbation state (each sub-buffer 256-byte aligned).
  */
 int esdc_workspace_bytes(const esdc_ctx* ctx, int what, size_t* bytes);
 

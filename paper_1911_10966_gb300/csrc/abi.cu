@@ -67,36 +67,34 @@ int rhs_impl(esdc_ctx* c, const double* q, void* dqdt, cudaStream_t s) {
         e = esdc::launch_rhs_f64(c, q, (double*)dqdt, s, next_events(c));
     } else {
         e = esdc::launch_shadow(c, q, c->d_shadow, s);
-        if (e == cudaSuccess) e = esdc::launch_rhs_f32(c, c->d_shadow, (float*)dqdt, s, next_events(c));
+        esdc::StageF in{};
+        in.base = c->d_shadow;
+        if (e == cudaSuccess) e = esdc::launch_rhs_f32(c, in, (float*)dqdt, s, next_events(c));
     }
     if (e != cudaSuccess) return cuda_fail(e, "esdc_rhs launch");
     return ESDC_OK;
 }
 
-// Mixed precision: nsteps DP5 steps with float32 residuals on float32 perturbation stage states and
-// the float64 solution update q += dt sum_j b_j k_j (accumulated in float64).
+// Mixed precision: nsteps DP5 steps with float32 residuals on float32 perturbation stage states
+// (formed inside the residual kernel from the step's shadow state and the earlier stage
+// derivatives) and the float64 solution update q += dt sum_j b_j k_j (accumulated in float64).
 int rk_step_f32(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s) {
     const int64_t n = c->n_nodes * 5;
     const size_t sub = round256((size_t)n * sizeof(float));
     float* k[6];
     for (int j = 0; j < 6; ++j) k[j] = (float*)((char*)ws + j * sub);
-    float* stage = (float*)((char*)ws + 6 * sub);
-    float* base = (float*)((char*)ws + 7 * sub);
+    float* base = (float*)((char*)ws + 6 * sub);
     cudaError_t e = esdc::launch_shadow(c, q, base, s);
     if (e != cudaSuccess) return cuda_fail(e, "shadow");
     for (int step = 0; step < nsteps; ++step) {
         for (int st = 0; st < 6; ++st) {
-            const float* in = base;
-            if (st > 0) {
-                esdc::CombineF cb{};
-                cb.nk = st;
-                for (int j = 0; j < st; ++j) {
-                    cb.k[j] = k[j];
-                    cb.coef[j] = (float)(dt * kA[st][j]);
-                }
-                e = esdc::launch_stage_f32(base, cb, stage, n, s);
-                if (e != cudaSuccess) return cuda_fail(e, "stage combine (float32)");
-                in = stage;
+            esdc::StageF in{};
+            in.base = base;
+            for (int j = 0; j < st; ++j) {
+                if (kA[st][j] == 0.0) continue;
+                in.k[in.nk] = k[j];
+                in.c[in.nk] = (float)(dt * kA[st][j]);
+                ++in.nk;
             }
             e = esdc::launch_rhs_f32(c, in, k[st], s, next_events(c));
             if (e != cudaSuccess) return cuda_fail(e, "residual (float32)");
@@ -350,7 +348,7 @@ int esdc_workspace_bytes(const esdc_ctx* c, int what, size_t* bytes) {
     if (!c || !bytes) return fail(ESDC_ERR_ARG, "null argument");
     if (what != 0) return fail(ESDC_ERR_ARG, "unknown workspace kind");
     if (c->setup.precision == ESDC_PREC_FP64) *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(double));
-    else *bytes = 8 * round256((size_t)c->n_nodes * 5 * sizeof(float));
+    else *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(float));
     return ESDC_OK;
 }
 

@@ -200,16 +200,17 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
             sL[v * N3 + node] = lam[eoff + v * N3 + node] * Jinv;
             sQ[v * N3 + node] = 0.0;
         }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) sB[c * N3 + node] = 0.0;
     }
     __syncthreads();
 
-    // ---- volume term, one xi_l line per thread, direction by direction
-#pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-        if (active && node < N2) {
-            const int base = line_base<N>(l, node % N, node / N);
+    // ---- volume term: the 3 N^2 lines of all directions at once, one per thread; direction l
+    // assigns its primitive cotangents to its own array (sB for l = 0, the two halves of the
+    // theta-bar buffer sT for l = 1, 2, which is free until the viscous part)
+    if (active) {
+        for (int lt = node; lt < 3 * N2; lt += N3) {
+            const int l = lt / N2, line = lt - l * N2;
+            double* Bl = l == 0 ? sB : sT + (l - 1) * 6 * N3;
+            const int base = line_base<N>(l, line % N, line / N);
             const int st = dir_stride<N>(l);
             const double* n0p = sG + (1 + 3 * l) * N3;
             const double* n1p = n0p + N3;
@@ -242,16 +243,21 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 const int ii = base + i * st;
-                sB[ii] += acc[i].rho;
-                sB[N3 + ii] += acc[i].u0;
-                sB[2 * N3 + ii] += acc[i].u1;
-                sB[3 * N3 + ii] += acc[i].u2;
-                sB[4 * N3 + ii] += acc[i].beta;
-                sB[5 * N3 + ii] += acc[i].usq;
+                Bl[ii] = acc[i].rho;
+                Bl[N3 + ii] = acc[i].u0;
+                Bl[2 * N3 + ii] = acc[i].u1;
+                Bl[3 * N3 + ii] = acc[i].u2;
+                Bl[4 * N3 + ii] = acc[i].beta;
+                Bl[5 * N3 + ii] = acc[i].usq;
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sB[c * N3 + node] += sT[c * N3 + node] + sT[(6 + c) * N3 + node];
+    }
+    __syncthreads();
 
     // ---- inviscid interface term: own cotangents here, neighbour cotangents to gbuf
 #pragma unroll 1

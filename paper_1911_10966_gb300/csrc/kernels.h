@@ -35,20 +35,20 @@ cudaError_t launch_scale(double* out, const double* x, double a, int64_t n, cuda
 cudaError_t launch_ke_gradient(const esdc_ctx* c, const double* q, double* grad, cudaStream_t s);
 
 // mixed-precision form
-cudaError_t prepare_rhs_f32(const esdc_ctx* c);
-cudaError_t launch_rhs_f32(const esdc_ctx* c, const float* dq, float* out, cudaStream_t s, cudaEvent_t* ev);
-struct CombineF {           // float32 stage combination: out = base + sum_j coef_j k_j
+struct StageF {             // residual input base + sum_j c_j k_j (float32 perturbation state)
+    const float* base;
     const float* k[6];
-    float coef[6];
+    float c[6];
     int nk;
 };
+cudaError_t prepare_rhs_f32(const esdc_ctx* c);
+cudaError_t launch_rhs_f32(const esdc_ctx* c, const StageF& in, float* out, cudaStream_t s, cudaEvent_t* ev);
 struct Combine64F {         // float64 accumulation of float32 stage derivatives
     const float* k[6];
     double coef[6];
     int nk;
 };
 cudaError_t launch_shadow(const esdc_ctx* c, const double* q, float* dq, cudaStream_t s);
-cudaError_t launch_stage_f32(const float* base, const CombineF& cb, float* out, int64_t n, cudaStream_t s);
 cudaError_t launch_final_f32(const esdc_ctx* c, double* q, float* dq_new, const Combine64F& cb, cudaStream_t s);
 
 }  // namespace esdc

@@ -4,7 +4,8 @@
 // pressure and enthalpy.
 //
 // Input: the shadow state dq = (rho - rho0, rho u, rho E - E0) in float32 (written by a float64
-// kernel from the float64 state), float32 geometry, neighbour table.  Reference state rho0 = 1,
+// kernel from the float64 state), optionally plus float32 Runge-Kutta stage increments
+// sum_j c_j k_j added on load, float32 geometry, neighbour table.  Reference state rho0 = 1,
 // p0 = R (T0 = 1), beta0 = 1/(2R), E0 = p0/(gamma-1).
 //
 // The Chandrashekar flux is split exactly as f = f_ref + df with
@@ -135,9 +136,22 @@ __device__ __forceinline__ void load_prim_f(const float4* sP4, int N3, int idx, 
     s.db = b.w;
 }
 
+// The residual's input state value at flat index i: base[i] + sum_j c_j k_j[i] (a Runge-Kutta stage
+// formed on the fly; nk = 0 for a plain state).
+__device__ __forceinline__ float stage_value(const StageF& in, int64_t i) {
+    // all loads independent and issued together (predicated on nk), read-only path
+    float kv[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) kv[j] = j < in.nk ? __ldg(in.k[j] + i) : 0.0f;
+    float a = __ldg(in.base + i);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a = fmaf(in.c[j], kv[j], a);
+    return a;
+}
+
 template <int N>
 __global__ void __launch_bounds__(CfgF<N>::THREADS, CfgF<N>::MINB)
-rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float* __restrict__ geom,
+rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom,
              const int32_t* __restrict__ nbr, float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph,
              const Ref ref) {
     using C = CfgF<N>;
@@ -162,7 +176,7 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
             float d[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-                d[v] = dq[eoff + v * N3 + node];
+                d[v] = stage_value(in, eoff + v * N3 + node);
                 sQ[v * N3 + node] = d[v];
             }
             PrimF s;
@@ -228,6 +242,50 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
         }
     }
     __syncthreads();
+
+    // ---- interface SAT, all six faces at once: face nodes of direction l add into the direction-l
+    // accumulators, so edges and corners shared by several directions never collide
+    if (active) {
+        for (int fn = tl; fn < 6 * N2; fn += TE) {
+            const int l = fn / (2 * N2);
+            const int rem = fn - l * 2 * N2;
+            const int side = rem / N2, fi = rem - side * N2;
+            const int st = dir_stride_f<N>(l);
+            const int base = line_base_f<N>(l, fi % N, fi / N);
+            const int own = base + (side ? (N - 1) * st : 0);
+            const int nbn = base + (side ? 0 : (N - 1) * st);
+            const int64_t nb = nbr[el * 6 + 2 * l + side];
+            float qn[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) qn[v] = stage_value(in, nb * 5 * N3 + v * N3 + nbn);
+            PrimF so, sn;
+            load_prim_f(sP4, N3, own, so);
+            to_prim_f(qn, ref, sn);
+            const float4 nv = sG4[l * N3 + own];
+            const float n0 = nv.x, n1 = nv.y, n2 = nv.z;
+            float df[5], un;
+            ec_flux_pert(so, sn, n0, n1, n2, ref, df, un);
+            const float E = side ? 1.0f : -1.0f;
+            float lam = 0.0f;
+            if (ph.dissipation) {
+                const float nn = fsqrt(n0 * n0 + n1 * n1 + n2 * n2);
+                const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + fsqrt(0.5f * ref.gamma * frcp(so.beta)) * nn;
+                const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + fsqrt(0.5f * ref.gamma * frcp(sn.beta)) * nn;
+                lam = 0.5f * fmaxf(lo, ln);
+            }
+            const float wi = ops.winv[side ? N - 1 : 0];
+            float* A = sA + l * 6 * N3;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) A[v * N3 + own] += (-E * df[v] - lam * (sQ[v * N3 + own] - qn[v])) * wi;
+            A[5 * N3 + own] += -E * un * wi;
+            float* wf = sWf + (2 * l + side) * 4 * N2 + fi;
+            wf[0] = 2.0f * sn.beta * sn.u0;
+            wf[N2] = 2.0f * sn.beta * sn.u1;
+            wf[2 * N2] = 2.0f * sn.beta * sn.u2;
+            wf[3 * N2] = -2.0f * sn.db;
+        }
+    }
+    __syncthreads();
     // sum the three directions into direction 0's slots
     if (active) {
         for (int node = tl; node < N3; node += TE)
@@ -235,49 +293,6 @@ rhs_main_f32(const float* __restrict__ dq, float* __restrict__ out, const float*
             for (int v = 0; v < 6; ++v) sA[v * N3 + node] += sA[(6 + v) * N3 + node] + sA[(12 + v) * N3 + node];
     }
     __syncthreads();
-
-    // ---- interface SAT, direction by direction (edges and corners are shared)
-#pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-        if (active) {
-            for (int fn = tl; fn < 2 * N2; fn += TE) {
-                const int side = fn / N2, fi = fn - side * N2;
-                const int st = dir_stride_f<N>(l);
-                const int base = line_base_f<N>(l, fi % N, fi / N);
-                const int own = base + (side ? (N - 1) * st : 0);
-                const int nbn = base + (side ? 0 : (N - 1) * st);
-                const int64_t nb = nbr[el * 6 + 2 * l + side];
-                float qn[5];
-#pragma unroll
-                for (int v = 0; v < 5; ++v) qn[v] = dq[nb * 5 * N3 + v * N3 + nbn];
-                PrimF so, sn;
-                load_prim_f(sP4, N3, own, so);
-                to_prim_f(qn, ref, sn);
-                const float4 nv = sG4[l * N3 + own];
-                const float n0 = nv.x, n1 = nv.y, n2 = nv.z;
-                float df[5], un;
-                ec_flux_pert(so, sn, n0, n1, n2, ref, df, un);
-                const float E = side ? 1.0f : -1.0f;
-                float lam = 0.0f;
-                if (ph.dissipation) {
-                    const float nn = fsqrt(n0 * n0 + n1 * n1 + n2 * n2);
-                    const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + fsqrt(0.5f * ref.gamma * frcp(so.beta)) * nn;
-                    const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + fsqrt(0.5f * ref.gamma * frcp(sn.beta)) * nn;
-                    lam = 0.5f * fmaxf(lo, ln);
-                }
-                const float wi = ops.winv[side ? N - 1 : 0];
-#pragma unroll
-                for (int v = 0; v < 5; ++v) sA[v * N3 + own] += (-E * df[v] - lam * (sQ[v * N3 + own] - qn[v])) * wi;
-                sA[5 * N3 + own] += -E * un * wi;
-                float* wf = sWf + (2 * l + side) * 4 * N2 + fi;
-                wf[0] = 2.0f * sn.beta * sn.u0;
-                wf[N2] = 2.0f * sn.beta * sn.u1;
-                wf[2 * N2] = 2.0f * sn.beta * sn.u2;
-                wf[3 * N2] = -2.0f * sn.db;
-            }
-        }
-        __syncthreads();
-    }
 
     // ---- viscous chain
     if (ph.viscous) {
@@ -444,7 +459,7 @@ visc_sat_f32(float* __restrict__ out, const float* __restrict__ geom, const int3
 }
 
 template <int N>
-cudaError_t launch_f32_n(const esdc_ctx* c, const float* dq, float* out, cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaStream_t s, cudaEvent_t* ev) {
     using C = CfgF<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(float);
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
@@ -460,7 +475,7 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const float* dq, float* out, cudaStr
     ref.gamma = ph.gamma;
     ref.inv_p0 = 1.0f / ph.p0;
     if (ev) cudaEventRecord(ev[0], s);
-    rhs_main_f32<N><<<grid, C::THREADS, smem, s>>>(dq, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf,
+    rhs_main_f32<N><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf,
                                                    ph, ref);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
@@ -495,15 +510,15 @@ cudaError_t prepare_rhs_f32(const esdc_ctx* c) {
     }
 }
 
-cudaError_t launch_rhs_f32(const esdc_ctx* c, const float* dq, float* out, cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t launch_rhs_f32(const esdc_ctx* c, const StageF& in, float* out, cudaStream_t s, cudaEvent_t* ev) {
     switch (c->N) {
-        case 2: return launch_f32_n<2>(c, dq, out, s, ev);
-        case 3: return launch_f32_n<3>(c, dq, out, s, ev);
-        case 4: return launch_f32_n<4>(c, dq, out, s, ev);
-        case 5: return launch_f32_n<5>(c, dq, out, s, ev);
-        case 6: return launch_f32_n<6>(c, dq, out, s, ev);
-        case 7: return launch_f32_n<7>(c, dq, out, s, ev);
-        case 8: return launch_f32_n<8>(c, dq, out, s, ev);
+        case 2: return launch_f32_n<2>(c, in, out, s, ev);
+        case 3: return launch_f32_n<3>(c, in, out, s, ev);
+        case 4: return launch_f32_n<4>(c, in, out, s, ev);
+        case 5: return launch_f32_n<5>(c, in, out, s, ev);
+        case 6: return launch_f32_n<6>(c, in, out, s, ev);
+        case 7: return launch_f32_n<7>(c, in, out, s, ev);
+        case 8: return launch_f32_n<8>(c, in, out, s, ev);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -29,8 +29,9 @@ struct Cfg {
     static constexpr int N2 = N * N, N3 = N * N * N;
     static constexpr int EPB = N3 >= 96 ? 1 : (N3 >= 48 ? 2 : (N3 >= 24 ? 4 : 16));
     static constexpr int THREADS = EPB * N3;
-    // shared doubles per element: prim/w/Ftilde 12 x N3 | r 5 x N3 | geometry 10 x N3 | face w 24 x N2
-    static constexpr int SM = 27 * N3 + 24 * N2;
+    // shared doubles per element: prim/w/Ftilde 12 x N3 | r 3 x 5 x N3 (one per line direction) |
+    // geometry 10 x N3 | face w 24 x N2
+    static constexpr int SM = 37 * N3 + 24 * N2;
     static constexpr int EPB_SAT = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
     // resident CTAs per SM the register allocation is sized for (the float64 pipe needs few warps)
     static constexpr int MINB = N >= 6 ? 1 : (N >= 4 ? 3 : 4);
@@ -42,8 +43,12 @@ struct Prim {
     double hr, hu0, hu1, hu2, beta, qq;
 };
 
-__device__ __forceinline__ void to_prim(const double* q, const Phys& ph, Prim& s) {
-    const double ri = 1.0 / q[0];
+// forward declarations of the reciprocal helpers defined below
+__device__ __forceinline__ double rcp_newton2(double x);
+
+// Primitives of a conserved state, plus RT = p/rho and the sound speed c = sqrt(gamma p/rho).
+__device__ __forceinline__ void to_prim(const double* q, const Phys& ph, Prim& s, double& RT, double& c) {
+    const double ri = rcp_newton2(q[0]);
     const double u0 = q[1] * ri, u1 = q[2] * ri, u2 = q[3] * ri;
     const double usq = u0 * u0 + u1 * u1 + u2 * u2;
     const double p = (ph.gamma - 1.0) * (q[4] - 0.5 * q[0] * usq);
@@ -51,8 +56,10 @@ __device__ __forceinline__ void to_prim(const double* q, const Phys& ph, Prim& s
     s.hu0 = 0.5 * u0;
     s.hu1 = 0.5 * u1;
     s.hu2 = 0.5 * u2;
-    s.beta = s.hr / p;
+    s.beta = s.hr * rcp_newton2(p);
     s.qq = 0.25 * usq;
+    RT = p * ri;
+    c = sqrt(ph.gamma * RT);
 }
 
 // Reciprocal by Newton-Raphson on g(r) = 1/r - x from the hardware approximation (about 23 bits):
@@ -141,10 +148,10 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
     const int node = t - el_loc * N3;
     const int64_t el = (int64_t)blockIdx.x * EPB + el_loc;
     const bool active = el < K;
-    double* sP = smem + (size_t)el_loc * Cfg<N>::SM;   // [12][N3]: rho/2,u/2 (3),beta,|u|^2/4,w2..w5 | Ftilde
-    double* sR = sP + 12 * N3;                          // [5][N3]
-    double* sG = sP + 17 * N3;                          // [10][N3]: J, Ja_lm
-    double* sWf = sP + 27 * N3;                         // [6][4][N2]
+    double* sP = smem + (size_t)el_loc * Cfg<N>::SM;   // [12][N3]: rho/2,u/2 (3),beta,|u|^2/4,w2..w5,RT,c | Ftilde
+    double* sR = sP + 12 * N3;                          // [3][5][N3] per-direction accumulators
+    double* sG = sP + 27 * N3;                          // [10][N3]: J, Ja_lm
+    double* sWf = sP + 37 * N3;                         // [6][4][N2]
     const int64_t eoff = el * 5 * N3;
 
     // ---- node-local precompute
@@ -153,7 +160,10 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
 #pragma unroll
         for (int v = 0; v < 5; ++v) qv[v] = q[eoff + v * N3 + node];
         Prim s;
-        to_prim(qv, ph, s);
+        double RT, cs;
+        to_prim(qv, ph, s, RT, cs);
+        sP[10 * N3 + node] = RT;
+        sP[11 * N3 + node] = cs;
         sP[node] = s.hr;
         sP[N3 + node] = s.hu0;
         sP[2 * N3 + node] = s.hu1;
@@ -166,16 +176,15 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
         sP[9 * N3 + node] = -2.0 * s.beta;
 #pragma unroll
         for (int c = 0; c < 10; ++c) sG[c * N3 + node] = geom[(el * 10 + c) * N3 + node];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sR[v * N3 + node] = 0.0;
     }
     __syncthreads();
 
-    // ---- volume flux differencing, one xi_l line per thread
-#pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-        if (active && node < N2) {
-            const int base = line_base<N>(l, node % N, node / N);
+    // ---- volume flux differencing: the 3 N^2 lines of all directions at once, one per thread, each
+    // direction into its own accumulator (assigned, so no clearing is needed)
+    if (active) {
+        for (int lt = node; lt < 3 * N2; lt += N3) {
+            const int l = lt / N2, line = lt - l * N2;
+            const int base = line_base<N>(l, line % N, line / N);
             const int st = dir_stride<N>(l);
             const double* n0p = sG + (1 + 3 * l) * N3;
             const double* n1p = n0p + N3;
@@ -206,21 +215,24 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
                     }
                 }
             }
+            double* R = sR + l * 5 * N3;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 const int ii = base + i * st;
 #pragma unroll
-                for (int v = 0; v < 5; ++v) sR[v * N3 + ii] += acc[i][v] * ops.winv[i];
+                for (int v = 0; v < 5; ++v) R[v * N3 + ii] = acc[i][v] * ops.winv[i];
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
 
-    // ---- inviscid interface SAT (and neighbour entropy variables for the gradient lift)
-#pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-        if (active && node < 2 * N2) {
-            const int side = node / N2, fi = node - side * N2;
+    // ---- inviscid interface SAT on all six faces at once (face nodes of direction l add into the
+    // direction-l accumulator); neighbour entropy variables recorded for the gradient lift
+    if (active) {
+        for (int fn = node; fn < 6 * N2; fn += N3) {
+            const int l = fn / (2 * N2);
+            const int rem = fn - l * 2 * N2;
+            const int side = rem / N2, fi = rem - side * N2;
             const int st = dir_stride<N>(l);
             const int base = line_base<N>(l, fi % N, fi / N);
             const int own = base + (side ? (N - 1) * st : 0);
@@ -233,8 +245,9 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
                 qn[v] = q[nb * 5 * N3 + v * N3 + nbn];
             }
             Prim so, sn;
+            double RTn, cn;
             load_prim(sP, N3, own, so);
-            to_prim(qn, ph, sn);
+            to_prim(qn, ph, sn, RTn, cn);
             const double n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own],
                          n2 = sG[(3 + 3 * l) * N3 + own];
             double f[5];
@@ -243,21 +256,28 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             double lam = 0.0;
             if (ph.dissipation) {
                 const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
-                const double lo = 2.0 * fabs(so.hu0 * n0 + so.hu1 * n1 + so.hu2 * n2) + sqrt(0.5 * ph.gamma / so.beta) * nn;
-                const double ln = 2.0 * fabs(sn.hu0 * n0 + sn.hu1 * n1 + sn.hu2 * n2) + sqrt(0.5 * ph.gamma / sn.beta) * nn;
+                const double lo = 2.0 * fabs(so.hu0 * n0 + so.hu1 * n1 + so.hu2 * n2) + sP[11 * N3 + own] * nn;
+                const double ln = 2.0 * fabs(sn.hu0 * n0 + sn.hu1 * n1 + sn.hu2 * n2) + cn * nn;
                 lam = 0.5 * fmax(lo, ln);
             }
             const double wi = ops.winv[side ? N - 1 : 0];
+            double* R = sR + l * 5 * N3;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) sR[v * N3 + own] += (-E * f[v] - lam * (qo[v] - qn[v])) * wi;
+            for (int v = 0; v < 5; ++v) R[v * N3 + own] += (-E * f[v] - lam * (qo[v] - qn[v])) * wi;
             double* wf = sWf + (2 * l + side) * 4 * N2 + fi;
             wf[0] = 4.0 * sn.beta * sn.hu0;
             wf[N2] = 4.0 * sn.beta * sn.hu1;
             wf[2 * N2] = 4.0 * sn.beta * sn.hu2;
             wf[3 * N2] = -2.0 * sn.beta;
         }
-        __syncthreads();
     }
+    __syncthreads();
+    // sum the three directions into the first accumulator
+    if (active) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sR[v * N3 + node] += sR[(5 + v) * N3 + node] + sR[(10 + v) * N3 + node];
+    }
+    __syncthreads();
 
     const double Jinv = active ? 1.0 / sG[node] : 0.0;
     if (ph.viscous) {
@@ -295,8 +315,7 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
                 for (int k = 0; k < 4; ++k)
                     g[m][k] = Jinv * (sG[(1 + m) * N3 + node] * th[0][k] + sG[(4 + m) * N3 + node] * th[1][k]
                                       + sG[(7 + m) * N3 + node] * th[2][k]);
-            const double beta = sP[4 * N3 + node];
-            const double RT = 0.5 / beta;
+            const double RT = sP[10 * N3 + node];
             const double u[3] = {2.0 * sP[N3 + node], 2.0 * sP[2 * N3 + node], 2.0 * sP[3 * N3 + node]};
             // du_k/dx_m = RT (g_m[k] + u_k g_m[3]); dT/dx_m = (RT)^2/R g_m[3]
             double du[3][3];

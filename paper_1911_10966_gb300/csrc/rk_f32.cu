@@ -1,7 +1,6 @@
 // Float64 <-> float32 state kernels of the mixed-precision form.
 //   shadow:  dq = float(q - q_ref) with q_ref = (rho0, 0, 0, 0, E0): the float32 perturbation state
 //            the float32 residual reads (float64 subtraction before rounding).
-//   stage:   dq_s = dq_n + sum_j c_j k_j, all float32 (stage states only feed the float32 residual).
 //   final:   q += sum_j c_j k_j accumulated in float64 (the Runge-Kutta solution update), then the
 //            new shadow of q is written.
 #include <cuda_runtime.h>
@@ -20,16 +19,6 @@ __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ 
         const int v = (int)((i / N3) % 5);
         const double off = v == 0 ? rho0 : (v == 4 ? E0 : 0.0);
         dq[i] = (float)(q[i] - off);
-    }
-}
-
-__global__ void __launch_bounds__(256) stage_kernel(const float* __restrict__ base, const CombineF cb,
-                                                    float* __restrict__ out, int64_t n) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        float a = base[i];
-        for (int j = 0; j < cb.nk; ++j) a += cb.coef[j] * cb.k[j][i];
-        out[i] = a;
     }
 }
 
@@ -61,11 +50,6 @@ unsigned grid_for(int64_t n) {
 cudaError_t launch_shadow(const esdc_ctx* c, const double* q, float* dq, cudaStream_t s) {
     const double E0 = c->phys.R / (c->phys.gamma - 1.0);
     shadow_kernel<<<grid_for(c->n_nodes * 5), 256, 0, s>>>(q, dq, c->n_nodes, c->N3, 1.0, E0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_stage_f32(const float* base, const CombineF& cb, float* out, int64_t n, cudaStream_t s) {
-    stage_kernel<<<grid_for(n), 256, 0, s>>>(base, cb, out, n);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,45 @@
+"""bench.py's multi-rank logic on CPU with two gloo ranks: each rank reports its own step time,
+the job reports the maximum and counts every rank's replica (weak scaling, no data-path
+collective)."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = 10.0 + 5.0 * rank
+    m = bench.max_over_ranks(ms, dist, torch.device("cpu"))
+    out[rank] = (m, bench.replica_throughput(1000, world, m))
+    dist.destroy_process_group()
+
+
+def test_two_rank_max_and_replica_throughput():
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    for r in range(world):
+        m, v = out[r]
+        assert m == 15.0
+        assert v == pytest.approx(world * 1000 * 6 / 15e-3)
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.replica_throughput(10, 1, 1.0) == pytest.approx(60000.0)
