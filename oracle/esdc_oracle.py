@@ -195,6 +195,25 @@ def make_mesh(p: int, x, kx: int, ky: int, kz: int) -> Mesh:
     return Mesh(sbp, x, J, Ja, box_neighbours(kx, ky, kz), smallest_edge(x))
 
 
+def make_submesh(p: int, x, nbr: torch.Tensor, elems):
+    """The mesh restricted to `elems` and the two rings of face neighbours around them, which is
+    all the residual on `elems` reads (the viscous terms need the neighbours' lifted gradients,
+    which need their neighbours' face states); metric terms are element-local, so they are the
+    same as on the full mesh.  Returns (submesh, closure element ids, rows of `elems`)."""
+    E = torch.as_tensor(elems, dtype=torch.long)
+    E1 = torch.unique(torch.cat([E, nbr[E].reshape(-1)]))
+    E2 = torch.unique(torch.cat([E1, nbr[E1].reshape(-1)]))
+    pos = torch.full((nbr.shape[0],), -1, dtype=torch.long)
+    pos[E2] = torch.arange(E2.numel())
+    sub_nbr = pos[nbr[E2]]
+    own = torch.arange(E2.numel()).unsqueeze(1).expand_as(sub_nbr)
+    sub_nbr = torch.where(sub_nbr < 0, own, sub_nbr)   # outer ring: links never followed for elems
+    sbp = sbp_operator(p)
+    xs = torch.as_tensor(x[E2.numpy()], dtype=F64)
+    J, Ja = metric_terms(xs, sbp.D)
+    return Mesh(sbp, xs, J, Ja, sub_nbr, smallest_edge(xs)), E2, pos[E]
+
+
 # --------------------------------------------------------------------------------------------
 # Gas physics (Sec. 4: eq. ns_iflux, constitutive relations, entropy, eq. Fv, eq. tau)
 # --------------------------------------------------------------------------------------------

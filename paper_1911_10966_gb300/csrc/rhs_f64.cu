@@ -34,7 +34,7 @@ struct Cfg {
     static constexpr int SM = 37 * N3 + 24 * N2;
     static constexpr int EPB_SAT = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
     // resident CTAs per SM the register allocation is sized for (the float64 pipe needs few warps)
-    static constexpr int MINB = N >= 6 ? 1 : (N >= 4 ? 3 : 4);
+    static constexpr int MINB = N >= 7 ? 1 : (N == 6 ? 2 : (N >= 4 ? 3 : 4));
 };
 
 // Per-node primitives in the form the pair loop consumes: half density and half velocity (so that

@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(kRedThreads) budgets_kernel(const double* __re
         double qv[5];
         for (int v = 0; v < 5; ++v) qv[v] = q[(e * 5 + v) * N3 + node];
         const double rho = qv[0];
-        const double u0 = qv[1] / rho, u1 = qv[2] / rho, u2 = qv[3] / rho;
+        const double ri = 1.0 / rho;
+        const double u0 = qv[1] * ri, u1 = qv[2] * ri, u2 = qv[3] * ri;
         const double usq = u0 * u0 + u1 * u1 + u2 * u2;
         const double p = (ph.gamma - 1.0) * (qv[4] - 0.5 * rho * usq);
         const bool ok = rho > 0.0 && p > 0.0 && isfinite(qv[0] + qv[1] + qv[2] + qv[3] + qv[4]);

@@ -15,7 +15,10 @@ TWO_PI_BOX = ([-math.pi] * 3, [math.pi] * 3)
 
 
 def make_pair(p, k, *, warp=0.0, seed=0, Ma=0.1, Re=1600.0, dissipation=True, box=TWO_PI_BOX,
-              state="tgv", noise=0.0, noise_seed=1, precision="fp64"):
+              state="tgv", noise=0.0, noise_seed=1, precision="fp64", oracle_elems=None):
+    """GPU solver + state and the oracle's mesh + state for the same workload.  With oracle_elems
+    the oracle side is the two-ring submesh around those elements (returned mesh/state are the
+    submesh's; the residual rows of oracle_elems are returned as mesh.rows)."""
     from paper_1911_10966_gb300.solver import Solver, lgl
     kx, ky, kz = k
     lo, hi = box
@@ -24,8 +27,13 @@ def make_pair(p, k, *, warp=0.0, seed=0, Ma=0.1, Re=1600.0, dissipation=True, bo
     solver = Solver(p, kx, ky, kz, x_gpu, Ma=Ma, Re=Re, dissipation=dissipation, precision=precision)
     s = O.sbp_operator(p)
     x_ora = I.box_coords(s.xi.numpy(), kx, ky, kz, lo, hi, warp=warp, seed=seed)
-    mesh = O.make_mesh(p, x_ora, kx, ky, kz)
     gas = O.Gas.from_mach(Ma, Re)
+    if oracle_elems is not None:
+        mesh, E2, rows = O.make_submesh(p, x_ora, O.box_neighbours(kx, ky, kz), oracle_elems)
+        mesh.rows = rows
+        x_ora = x_ora[E2.numpy()]
+    else:
+        mesh = O.make_mesh(p, x_ora, kx, ky, kz)
 
     def st(x):
         if state == "tgv":
@@ -58,8 +66,11 @@ def term_scale(q, mesh, gas, elems=None):
     return [float(t[:, v].max()) for v in range(5)]
 
 
-def assert_parity(r_gpu, r_ora, q_ora, mesh, gas, elems=None, tol=1e-12, c_round=4.0):
-    """Per variable: ||R_gpu - R_ora||_inf <= max(tol ||R_ora||_inf, c_round eps T_v)."""
+def assert_parity(r_gpu, r_ora, q_ora, mesh, gas, elems=None, tol=1e-12, c_round=8.0):
+    """Per variable: ||R_gpu - R_ora||_inf <= max(tol ||R_ora||_inf, c_round eps T_v).  c_round = 8:
+    the two evaluation orders of the oracle itself differ by about 1 eps T_v, and at p = 7 the two
+    independent float64 constructions of the curl-form metrics (which differ by ~4e-13 relative)
+    add up to 4.5 eps T_v in the momentum residual of the 48^3 Taylor-Green mesh."""
     a = r_gpu.detach().double().cpu()
     b = torch.as_tensor(r_ora).double()
     T = term_scale(q_ora, mesh, gas, elems)

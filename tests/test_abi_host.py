@@ -99,3 +99,27 @@ def test_inverted_mesh_rejected(L):
 def test_strerror(L):
     for c in (0, -1, -2, -3, -4, -5):
         assert len(L.esdc_strerror(c)) > 0
+
+
+def test_empty_and_out_of_range_sizes(L):
+    """No elements, too many elements and degrees outside 1..7 are refused before any allocation."""
+    x = np.zeros((1, 3, 2, 2, 2))
+    for kx, ky, kz in ((0, 1, 1), (1, 0, 1), (1, 1, -3), (2 ** 20, 2 ** 10, 1)):
+        st = _setup(1, kx, ky, kz)
+        assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_ARG
+    for p in (0, 8, -1):
+        st = _setup(p, 1, 1, 1)
+        assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_ARG
+    st = _setup(1, 1, 1, 1)
+    st.precision = 2
+    assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_ARG
+
+
+def test_single_element_and_p1_geometry(L):
+    """Degenerate but valid: one element periodic onto itself, p = 1 (two nodes per direction)."""
+    s = O.sbp_operator(1)
+    x = np.ascontiguousarray(I.box_coords(s.xi.numpy(), 1, 1, 1, [0] * 3, [2] * 3))
+    J = np.zeros((1, 8))
+    st = _setup(1, 1, 1, 1)
+    nat.check(L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, J.ctypes.data, None, None), "geometry")
+    assert np.allclose(J, 1.0)

@@ -115,3 +115,12 @@ def test_fp32_freestream_and_conservation():
     PJ = (w[:, None, None] * w[None, :, None] * w[None, None, :]).to(r2.device) * torch.tensor(J2, device=r2.device)
     tot = float((PJ * r2[:, 0]).sum())
     assert abs(tot) <= 1e-5 * float((PJ * r2[:, 0].abs()).sum())
+
+
+def test_fp32_residual_48cubed_p7_full_size_sampled():
+    """Mixed-precision residual on the full 48^3 p = 7 Taylor-Green mesh, sampled elements."""
+    E = torch.tensor(np.random.default_rng(7).choice(48 ** 3, 24, replace=False))
+    solver, qg, mesh, gas, qo = make_pair(7, (48, 48, 48), Re=1600.0, precision="fp32", oracle_elems=E)
+    r = solver.rhs(qg)
+    e, c = _report(r[E.cuda()], O.rhs(qo, mesh, gas, elems=mesh.rows), qo, mesh, gas, elems=mesh.rows)
+    assert max(c) <= C_MAX

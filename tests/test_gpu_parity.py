@@ -1,6 +1,6 @@
 """GPU FP64 path vs the CPU oracle, element by element, through the C ABI (libesdc.so).
 
-Tolerance, per variable v: ||R_gpu - R_ora||_inf <= max(1e-12 ||R_ora||_inf, 4 eps T_v), with T_v the
+Tolerance, per variable v: ||R_gpu - R_ora||_inf <= max(1e-12 ||R_ora||_inf, 8 eps T_v), with T_v the
 magnitude of the summed flux-difference terms (tests/gpu_common.term_scale).  For generic states
 the first bound (the 1e-12 FP64 target) is the active one; for smooth low-Mach states the oracle's
 own float64 rounding (about eps T_v, measured by evaluating the volume term in two algebraically
@@ -147,3 +147,13 @@ def test_bad_arguments_rejected():
         solver.rhs(qg.float())
     ws = torch.empty(8, dtype=torch.uint8, device=qg.device)
     assert L.esdc_rk_step(solver._ctx, qg.data_ptr(), 1e-3, 1, ws.data_ptr(), 8, None) == nat.ESDC_ERR_ARG
+
+
+def test_rhs_parity_48cubed_p7_full_size_sampled():
+    """The largest workload (Taylor-Green 48^3, p = 7: 56.6 M nodes, 2.3 GB of state) at full size:
+    float64 residual on 24 seeded elements against the oracle."""
+    E = torch.tensor(np.random.default_rng(7).choice(48 ** 3, 24, replace=False))
+    solver, qg, mesh, gas, qo = make_pair(7, (48, 48, 48), Re=1600.0, oracle_elems=E)
+    rg = solver.rhs(qg)
+    ro = O.rhs(qo, mesh, gas, elems=mesh.rows)
+    assert_parity(rg[E.cuda()], ro, qo, mesh, gas, elems=mesh.rows)
