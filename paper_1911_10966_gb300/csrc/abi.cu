@@ -261,7 +261,7 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     cudaError_t e = cudaGetDevice(&c->device);
     const size_t N2 = (size_t)hs.N * hs.N;
     const size_t geom_bytes = (size_t)c->K * 10 * c->N3 * sizeof(double);
-    c->red_blocks = 1024;
+    c->red_blocks = 608;             // 4 blocks of 256 threads per SM on 152 SMs
     if (e == cudaSuccess) e = cudaMalloc(&c->d_geom, geom_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_nbr, (size_t)c->K * 6 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_trace, (size_t)c->K * 6 * 4 * N2 * sizeof(double));

@@ -7,6 +7,16 @@
 
 namespace esdc {
 
+// Quotient by a run-time invariant divisor d >= 2 as the high 64 bits of x * M with M = ceil(2^64 / d)
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994).  Writing
+// M d = 2^64 + delta, 0 <= delta < d, the product over 2^64 is x/d + x delta / (d 2^64), which keeps
+// the floor of x/d for every x < 2^64 / d.
+struct DivU64 {
+    unsigned long long m;
+    static DivU64 make(unsigned long long d) { return DivU64{~0ull / d + 1ull}; }
+    __device__ __forceinline__ unsigned long long operator()(unsigned long long x) const { return __umul64hi(x, m); }
+};
+
 cudaError_t prepare_rhs_f64(const esdc_ctx* c);
 // ev: NULL, or four events recorded around the element kernel and the face kernel
 cudaError_t launch_rhs_f64(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev);

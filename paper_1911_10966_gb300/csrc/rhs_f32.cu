@@ -21,6 +21,7 @@
 
 #include "esdc_internal.h"
 #include "kernels.h"
+#include "visc_sat.cuh"
 
 namespace esdc {
 namespace {
@@ -32,10 +33,9 @@ struct CfgF {
     static constexpr int TE = (N3 <= 256) ? (N3 > LINES ? N3 : LINES) : LINES;   // threads per element
     static constexpr int EPB = TE >= 128 ? 1 : (128 + TE - 1) / TE;
     static constexpr int THREADS = EPB * TE;
-    // shared floats per element: prim 2 x float4 | w 4 | geometry 3 x float4 | accumulators 3 x 6
-    // (aliased by the 12 viscous fluxes) | own dq 5 | face w 24 N^2 (rounded to whole float4)
+    // shared floats per element: prim 2 x float4 | w float4 | geometry 3 x float4 | accumulators 3 x 6
+    // (aliased by the 3 x float4 viscous fluxes) | own dq 5 | face w 24 N^2 (rounded to whole float4)
     static constexpr int SM = ((8 + 4 + 12 + 18 + 5) * N3 + 24 * N2 + 3) / 4 * 4;
-    static constexpr int EPB_SAT = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
     static constexpr int MINB = N <= 4 ? 4 : (N == 5 ? 3 : 2);   // resident CTAs the registers are sized for
 };
 
@@ -164,9 +164,10 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
     const bool active = el < K;
     float* sP = smf + (size_t)el_loc * C::SM;       // [2][N3] float4 primitives | later [8][N3] floats
     float4* sP4 = reinterpret_cast<float4*>(sP);
-    float* sW = sP + 8 * N3;                         // [4][N3] w2..w4, w5 - w5_ref
-    float4* sG4 = reinterpret_cast<float4*>(sW + 4 * N3);   // [3][N3] (Ja_l0, Ja_l1, Ja_l2, 1/J)
-    float* sA = sW + 16 * N3;                        // [3][6][N3] per-direction accumulators | [12][N3] Ftilde
+    float4* sW4 = reinterpret_cast<float4*>(sP + 8 * N3);   // [N3] (w2, w3, w4, w5 - w5_ref)
+    float4* sG4 = sW4 + N3;                          // [3][N3] (Ja_l0, Ja_l1, Ja_l2, 1/J)
+    float* sA = sP + 24 * N3;                        // [3][6][N3] per-direction accumulators | float4 [3][N3] Ftilde
+    float4* sF4 = reinterpret_cast<float4*>(sA);
     float* sQ = sA + 18 * N3;                        // [5][N3] own dq
     float* sWf = sQ + 5 * N3;                        // [6][4][N2] neighbour entropy variables
     const int64_t eoff = el * 5 * N3;
@@ -183,10 +184,8 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             to_prim_f(d, ref, s);
             sP4[node] = make_float4(s.rho, s.dr, s.u0, s.u1);
             sP4[N3 + node] = make_float4(s.u2, s.usq, s.beta, s.db);
-            sW[node] = 2.0f * s.beta * s.u0;
-            sW[N3 + node] = 2.0f * s.beta * s.u1;
-            sW[2 * N3 + node] = 2.0f * s.beta * s.u2;
-            sW[3 * N3 + node] = -2.0f * s.db;         // w5 - w5_ref (the constant has no gradient)
+            // w5 - w5_ref: the constant has no gradient
+            sW4[node] = make_float4(2.0f * s.beta * s.u0, 2.0f * s.beta * s.u1, 2.0f * s.beta * s.u2, -2.0f * s.db);
             float gv[10];
 #pragma unroll
             for (int c = 0; c < 10; ++c) gv[c] = geom[(el * 10 + c) * N3 + node];
@@ -304,20 +303,28 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                 const int node = tl + r * TE;
                 if (node >= N3) break;
                 const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
-                const float wown[4] = {sW[node], sW[N3 + node], sW[2 * N3 + node], sW[3 * N3 + node]};
+                const float4 w4 = sW4[node];
+                const float wown[4] = {w4.x, w4.y, w4.z, w4.w};
                 float th[3][4];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     const int ia = a == 0 ? i1 : (a == 1 ? i2 : i3);
                     const int st = dir_stride_f<N>(a);
                     const int lb = node - ia * st;
+                    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        float s = 0.0f;
-#pragma unroll
-                        for (int j = 0; j < N; ++j) s += ops.D[ia][j] * sW[k * N3 + lb + j * st];
-                        th[a][k] = s;
+                    for (int j = 0; j < N; ++j) {
+                        const float d = ops.D[ia][j];
+                        const float4 wj = sW4[lb + j * st];
+                        s.x += d * wj.x;
+                        s.y += d * wj.y;
+                        s.z += d * wj.z;
+                        s.w += d * wj.w;
                     }
+                    th[a][0] = s.x;
+                    th[a][1] = s.y;
+                    th[a][2] = s.z;
+                    th[a][3] = s.w;
                     if (ia == 0 || ia == N - 1) {
                         const int side = ia == N - 1;
                         const int fi = a == 0 ? (i2 + N * i3) : (a == 1 ? (i1 + N * i3) : (i1 + N * i2));
@@ -378,8 +385,7 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                 const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
 #pragma unroll
                 for (int l = 0; l < 3; ++l) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) sA[(l * 4 + k) * N3 + node] = Ft[r][l][k];
+                    sF4[l * N3 + node] = make_float4(Ft[r][l][0], Ft[r][l][1], Ft[r][l][2], Ft[r][l][3]);
                     const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
                     if (il == 0 || il == N - 1) {
                         const int side = il == N - 1;
@@ -402,11 +408,13 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                     const int st = dir_stride_f<N>(l);
                     const int lb = node - il * st;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        float s = 0.0f;
-#pragma unroll
-                        for (int j = 0; j < N; ++j) s += ops.D[il][j] * sA[(l * 4 + k) * N3 + lb + j * st];
-                        vs[k] += s;
+                    for (int j = 0; j < N; ++j) {
+                        const float d = ops.D[il][j];
+                        const float4 f = sF4[l * N3 + lb + j * st];
+                        vs[0] += d * f.x;
+                        vs[1] += d * f.y;
+                        vs[2] += d * f.z;
+                        vs[3] += d * f.w;
                     }
                 }
                 const float Jinv = sG4[node].w;
@@ -426,35 +434,6 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             for (int k = 1; k < 4; ++k) out[eoff + k * N3 + node] = sA[k * N3 + node] * Jinv;
             out[eoff + 4 * N3 + node] = (sA[4 * N3 + node] + ref.H0 * lin) * Jinv;
         }
-    }
-}
-
-template <int N>
-__global__ void __launch_bounds__(CfgF<N>::EPB_SAT * 2 * CfgF<N>::N2)
-visc_sat_f32(float* __restrict__ out, const float* __restrict__ geom, const int32_t* __restrict__ nbr,
-             const float* __restrict__ trace, int64_t K, const OpsF ops) {
-    constexpr int N2 = CfgF<N>::N2, N3 = CfgF<N>::N3;
-    const int t = threadIdx.x;
-    const int el_loc = t / (2 * N2);
-    const int r = t - el_loc * 2 * N2;
-    const int side = r / N2, fi = r - side * N2;
-    const int64_t el = (int64_t)blockIdx.x * CfgF<N>::EPB_SAT + el_loc;
-    const bool active = el < K;
-    const float E = side ? 0.5f : -0.5f;
-    const float wi = ops.winv[side ? N - 1 : 0];
-#pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-        if (active) {
-            const int st = dir_stride_f<N>(l);
-            const int own = line_base_f<N>(l, fi % N, fi / N) + (side ? (N - 1) * st : 0);
-            const int64_t nb = nbr[el * 6 + 2 * l + side];
-            const float* to = trace + ((el * 6 + 2 * l + side) * 4) * N2 + fi;
-            const float* tn = trace + ((nb * 6 + 2 * l + 1 - side) * 4) * N2 + fi;
-            const float c = E * wi / geom[el * 10 * N3 + own];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) out[(el * 5 + 1 + k) * N3 + own] += c * (tn[k * N2] - to[k * N2]);
-        }
-        __syncthreads();
     }
 }
 
@@ -480,9 +459,9 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaSt
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (ph.viscous) {
-        const unsigned g2 = (unsigned)((c->K + C::EPB_SAT - 1) / C::EPB_SAT);
-        visc_sat_f32<N><<<g2, C::EPB_SAT * 2 * C::N2, 0, s>>>(out, c->d_geomf, c->d_nbr, (const float*)c->d_trace,
-                                                                c->K, c->opsf);
+        const cudaError_t e = launch_visc_sat<float, N>(out, c->d_geomf, c->d_nbr, (const float*)c->d_trace, c->K,
+                                                          c->opsf.winv[0], s);
+        if (e != cudaSuccess) return e;
     }
     if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();

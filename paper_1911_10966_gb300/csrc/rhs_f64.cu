@@ -14,12 +14,13 @@
 //      tau and the heat flux, and the contravariant viscous flux Ftilde_l = sum_m Ja_lm F^V_m;
 //      the normal component on each face is written to the trace buffer.
 //   4. divergence sum_l D_l Ftilde_l; dq/dt = r / J is written.
-// Kernel visc_sat then adds the BR1 interface term (E_ii/2)(Ftilde_nbr - Ftilde_own)/(w_i J) on
-// face nodes once every element's traces exist.
+// visc_sat_kernel (visc_sat.cuh) then adds the BR1 interface term (E_ii/2)(Ftilde_nbr - Ftilde_own)
+// / (w_i J) on face nodes once every element's traces exist.
 #include <cuda_runtime.h>
 
 #include "esdc_internal.h"
 #include "kernels.h"
+#include "visc_sat.cuh"
 
 namespace esdc {
 namespace {
@@ -32,7 +33,6 @@ struct Cfg {
     // shared doubles per element: prim/w/Ftilde 12 x N3 | r 3 x 5 x N3 (one per line direction) |
     // geometry 10 x N3 | face w 24 x N2
     static constexpr int SM = 37 * N3 + 24 * N2;
-    static constexpr int EPB_SAT = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
     // resident CTAs per SM the register allocation is sized for (the float64 pipe needs few warps)
     static constexpr int MINB = N >= 7 ? 1 : (N == 6 ? 2 : (N >= 4 ? 3 : 4));
 };
@@ -381,35 +381,6 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
 
 // BR1 viscous interface term on face nodes, direction by direction (edge nodes see up to 3 faces).
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::EPB_SAT * 2 * Cfg<N>::N2)
-visc_sat_f64(double* __restrict__ dqdt, const double* __restrict__ geom, const int32_t* __restrict__ nbr,
-             const double* __restrict__ trace, int64_t K, const Ops ops) {
-    constexpr int N2 = Cfg<N>::N2, N3 = Cfg<N>::N3;
-    const int t = threadIdx.x;
-    const int el_loc = t / (2 * N2);
-    const int r = t - el_loc * 2 * N2;
-    const int side = r / N2, fi = r - side * N2;
-    const int64_t el = (int64_t)blockIdx.x * Cfg<N>::EPB_SAT + el_loc;
-    const bool active = el < K;
-    const double E = side ? 0.5 : -0.5;
-    const double wi = ops.winv[side ? N - 1 : 0];
-#pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-        if (active) {
-            const int st = dir_stride<N>(l);
-            const int own = line_base<N>(l, fi % N, fi / N) + (side ? (N - 1) * st : 0);
-            const int64_t nb = nbr[el * 6 + 2 * l + side];
-            const double* to = trace + ((el * 6 + 2 * l + side) * 4) * N2 + fi;
-            const double* tn = trace + ((nb * 6 + 2 * l + 1 - side) * 4) * N2 + fi;
-            const double c = E * wi / geom[el * 10 * N3 + own];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) dqdt[(el * 5 + 1 + k) * N3 + own] += c * (tn[k * N2] - to[k * N2]);
-        }
-        __syncthreads();
-    }
-}
-
-template <int N>
 cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev) {
     using C = Cfg<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
@@ -420,9 +391,9 @@ cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaS
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (c->phys.viscous) {
-        const unsigned g2 = (unsigned)((c->K + C::EPB_SAT - 1) / C::EPB_SAT);
-        visc_sat_f64<N><<<g2, C::EPB_SAT * 2 * C::N2, 0, s>>>(dqdt, c->d_geom, c->d_nbr, (const double*)c->d_trace,
-                                                                c->K, c->ops);
+        const cudaError_t e = launch_visc_sat<double, N>(dqdt, c->d_geom, c->d_nbr, (const double*)c->d_trace, c->K,
+                                                           c->ops.winv[0], s);
+        if (e != cudaSuccess) return e;
     }
     if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();

@@ -2,6 +2,9 @@
 // CFL reduction.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstring>
+
 #include "esdc_internal.h"
 #include "kernels.h"
 
@@ -10,23 +13,32 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-// out[i] = q0[i] + sum_j coef_j k_j[i]; two doubles per thread per iteration (16-byte accesses)
+// out[i] = q0[i] + sum_j coef_j k_j[i]; two doubles per thread per iteration (16-byte accesses).  The
+// stage loop has a fixed trip count with predicated terms, so the stage pointers stay in parameter
+// space and all loads of an iteration are issued together; terms are summed in stage order.
 __global__ void __launch_bounds__(256) combine_kernel(double* __restrict__ out, const double* __restrict__ q0,
                                                       const Combine cb, int64_t n) {
     const int64_t n2 = n / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+        double2 kv[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            kv[j] = j < cb.nk ? reinterpret_cast<const double2*>(cb.k[j])[i] : make_double2(0.0, 0.0);
         double2 acc = reinterpret_cast<const double2*>(q0)[i];
-        for (int j = 0; j < cb.nk; ++j) {
-            const double2 kv = reinterpret_cast<const double2*>(cb.k[j])[i];
-            acc.x += cb.coef[j] * kv.x;
-            acc.y += cb.coef[j] * kv.y;
-        }
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (j < cb.nk) {
+                acc.x += cb.coef[j] * kv[j].x;
+                acc.y += cb.coef[j] * kv[j].y;
+            }
         reinterpret_cast<double2*>(out)[i] = acc;
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         double acc = q0[n - 1];
-        for (int j = 0; j < cb.nk; ++j) acc += cb.coef[j] * cb.k[j][n - 1];
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (j < cb.nk) acc += cb.coef[j] * cb.k[j][n - 1];
         out[n - 1] = acc;
     }
 }
@@ -45,40 +57,90 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
+__device__ __forceinline__ double rcp_nr(double x) {
+    // hardware reciprocal estimate refined by two Newton steps y <- y + y (1 - x y)
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    y = fma(y, fma(-x, y, 1.0), y);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+
+// ln x for a positive finite double.  With x = m 2^e, m in [sqrt(1/2), sqrt(2)):
+// ln m = 2 artanh t, t = (m - 1)/(m + 1), |t| <= 3 - 2 sqrt(2) ~ 0.1716, summed as the artanh Taylor
+// series 2 t (1 + t^2/3 + t^4/5 + ... + t^18/19) (the first omitted term, t^20/21, is below 3e-17
+// relative), and ln x = e ln2_hi + (ln m + e ln2_lo) with ln 2 split into a head and a tail.
+__device__ __forceinline__ double ln_pos(double x, double ln2_hi, double ln2_lo) {
+    long long b = __double_as_longlong(x);
+    int e = 0;
+    if (b < 0x0010000000000000LL) {            // subnormal: scale by 2^54 first
+        x *= 18014398509481984.0;
+        b = __double_as_longlong(x);
+        e = -54;
+    }
+    e += (int)(b >> 52) - 1023;
+    double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);   // [1, 2)
+    if (m > 1.4142135623730951) {
+        m *= 0.5;
+        e += 1;
+    }
+    const double a = m - 1.0, d = m + 1.0;
+    const double r = rcp_nr(d);
+    double t = a * r;
+    t = fma(fma(-t, d, a), r, t);               // one residual correction of the quotient
+    const double t2 = t * t;
+    double sr = 1.0 / 19.0;
+    sr = fma(sr, t2, 1.0 / 17.0);
+    sr = fma(sr, t2, 1.0 / 15.0);
+    sr = fma(sr, t2, 1.0 / 13.0);
+    sr = fma(sr, t2, 1.0 / 11.0);
+    sr = fma(sr, t2, 1.0 / 9.0);
+    sr = fma(sr, t2, 1.0 / 7.0);
+    sr = fma(sr, t2, 1.0 / 5.0);
+    sr = fma(sr, t2, 1.0 / 3.0);
+    const double lm = 2.0 * fma(t * t2, sr, t);
+    const double ed = (double)e;
+    return fma(ed, ln2_hi, fma(ed, ln2_lo, lm));
+}
+
+struct Ln2 {
+    double hi, lo;
+};
+
 // Per block: sums of P J S, P J KE, P J w.dq, P J dKE.dq and the count of non-physical nodes.
 template <typename TD>
 __global__ void __launch_bounds__(kRedThreads) budgets_kernel(const double* __restrict__ q, const TD* __restrict__ dq,
-                                                               const double* __restrict__ geom, int64_t K, int N,
-                                                               const Ops ops, const Phys ph, double* __restrict__ part) {
+                                                              const double* __restrict__ geom, int64_t K, int N,
+                                                              DivU64 div_n3, const Ops ops, const Phys ph, Ln2 ln2,
+                                                              double* __restrict__ part) {
     __shared__ double sh[kRedThreads];
     const int N3 = N * N * N;
     const int64_t n = K * N3;
     double aS = 0.0, aK = 0.0, aW = 0.0, aE = 0.0, bad = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
-        const int64_t e = g / N3;
+        const int64_t e = (int64_t)div_n3((unsigned long long)g);
         const int node = (int)(g - e * N3);
         const int i1 = node % N, i2 = (node / N) % N, i3 = node / (N * N);
         const double PJ = ops.w[i1] * ops.w[i2] * ops.w[i3] * geom[e * 10 * N3 + node];
         double qv[5];
         for (int v = 0; v < 5; ++v) qv[v] = q[(e * 5 + v) * N3 + node];
         const double rho = qv[0];
-        const double ri = 1.0 / rho;
+        const bool pos = rho > 0.0 && isfinite(qv[0] + qv[1] + qv[2] + qv[3] + qv[4]);
+        const double ri = rcp_nr(pos ? rho : 1.0);
         const double u0 = qv[1] * ri, u1 = qv[2] * ri, u2 = qv[3] * ri;
         const double usq = u0 * u0 + u1 * u1 + u2 * u2;
         const double p = (ph.gamma - 1.0) * (qv[4] - 0.5 * rho * usq);
-        const bool ok = rho > 0.0 && p > 0.0 && isfinite(qv[0] + qv[1] + qv[2] + qv[3] + qv[4]);
-        if (!ok) {
+        if (!(pos && p > 0.0)) {
             bad += 1.0;
             continue;
         }
-        const double s = log(p) - ph.gamma * log(rho);
+        const double s = ln_pos(p, ln2.hi, ln2.lo) - ph.gamma * ln_pos(rho, ln2.hi, ln2.lo);
         aS += PJ * (-rho * s * ph.inv_gm1);
         aK += PJ * 0.5 * rho * usq;
         if (dq) {
             double d[5];
             for (int v = 0; v < 5; ++v) d[v] = (double)dq[(e * 5 + v) * N3 + node];
-            const double rp = rho / p;
+            const double rp = rho * rcp_nr(p);
             const double w1 = (ph.gamma - s) * ph.inv_gm1 - 0.5 * rp * usq;
             aW += PJ * (w1 * d[0] + rp * (u0 * d[1] + u1 * d[2] + u2 * d[3]) - rp * d[4]);
             aE += PJ * (-0.5 * usq * d[0] + u0 * d[1] + u1 * d[2] + u2 * d[3]);
@@ -214,13 +276,26 @@ cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int
     return cudaGetLastError();
 }
 
+Ln2 ln2_split() {
+    // ln 2 as a head with the low 20 bits of its significand cleared and the tail ln 2 - head
+    const double l = std::log(2.0);
+    unsigned long long bits;
+    std::memcpy(&bits, &l, sizeof bits);
+    bits &= ~0xFFFFFull;
+    double hi;
+    std::memcpy(&hi, &bits, sizeof hi);
+    return Ln2{hi, (double)(std::log(2.0L) - (long double)hi)};
+}
+
 cudaError_t launch_budgets(const esdc_ctx* c, const double* q, const void* dqdt, int dq_f32, cudaStream_t s) {
+    static const Ln2 ln2 = ln2_split();
+    const DivU64 dn3 = DivU64::make((unsigned long long)c->N3);
     if (dq_f32)
-        budgets_kernel<float><<<c->red_blocks, kRedThreads, 0, s>>>(q, (const float*)dqdt, c->d_geom, c->K, c->N,
-                                                                     c->ops, c->phys, c->d_red);
+        budgets_kernel<float><<<c->red_blocks, kRedThreads, 0, s>>>(q, (const float*)dqdt, c->d_geom, c->K, c->N, dn3,
+                                                                     c->ops, c->phys, ln2, c->d_red);
     else
         budgets_kernel<double><<<c->red_blocks, kRedThreads, 0, s>>>(q, (const double*)dqdt, c->d_geom, c->K, c->N,
-                                                                      c->ops, c->phys, c->d_red);
+                                                                      dn3, c->ops, c->phys, ln2, c->d_red);
     finish_sum<<<1, kRedThreads, 0, s>>>(c->d_red, c->red_blocks, 5, c->d_red_out);
     return cudaGetLastError();
 }

@@ -11,28 +11,42 @@
 namespace esdc {
 namespace {
 
+// Variable index (0..4) of entry i of a [K][5][N3] array: (i / N3) mod 5 by invariant division.
+__device__ __forceinline__ int var_of(int64_t i, DivU64 div_n3, DivU64 div_5) {
+    const unsigned long long row = div_n3((unsigned long long)i);
+    return (int)(row - 5ull * div_5(row));
+}
+
 __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ q, float* __restrict__ dq,
-                                                     int64_t n_nodes, int N3, double rho0, double E0) {
+                                                     int64_t n_nodes, DivU64 div_n3, DivU64 div_5, double rho0,
+                                                     double E0) {
     const int64_t n = n_nodes * 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int v = (int)((i / N3) % 5);
+        const int v = var_of(i, div_n3, div_5);
         const double off = v == 0 ? rho0 : (v == 4 ? E0 : 0.0);
         dq[i] = (float)(q[i] - off);
     }
 }
 
 __global__ void __launch_bounds__(256) final_kernel(double* __restrict__ q, float* __restrict__ dq_new,
-                                                    const Combine64F cb, int64_t n_nodes, int N3, double rho0,
-                                                    double E0) {
+                                                    const Combine64F cb, int64_t n_nodes, DivU64 div_n3,
+                                                    DivU64 div_5, double rho0, double E0) {
     const int64_t n = n_nodes * 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        // all stage loads issued together (fixed trip count, predicated), summed in stage order
+        float kv[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) kv[j] = j < cb.nk ? __ldg(cb.k[j] + i) : 0.0f;
+        const double q0 = q[i];
         double inc = 0.0;
-        for (int j = 0; j < cb.nk; ++j) inc += cb.coef[j] * (double)cb.k[j][i];
-        const double qn = q[i] + inc;
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (j < cb.nk) inc += cb.coef[j] * (double)kv[j];
+        const double qn = q0 + inc;
         q[i] = qn;
-        const int v = (int)((i / N3) % 5);
+        const int v = var_of(i, div_n3, div_5);
         const double off = v == 0 ? rho0 : (v == 4 ? E0 : 0.0);
         dq_new[i] = (float)(qn - off);
     }
@@ -49,13 +63,15 @@ unsigned grid_for(int64_t n) {
 
 cudaError_t launch_shadow(const esdc_ctx* c, const double* q, float* dq, cudaStream_t s) {
     const double E0 = c->phys.R / (c->phys.gamma - 1.0);
-    shadow_kernel<<<grid_for(c->n_nodes * 5), 256, 0, s>>>(q, dq, c->n_nodes, c->N3, 1.0, E0);
+    shadow_kernel<<<grid_for(c->n_nodes * 5), 256, 0, s>>>(q, dq, c->n_nodes, DivU64::make(c->N3), DivU64::make(5),
+                                                           1.0, E0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_final_f32(const esdc_ctx* c, double* q, float* dq_new, const Combine64F& cb, cudaStream_t s) {
     const double E0 = c->phys.R / (c->phys.gamma - 1.0);
-    final_kernel<<<grid_for(c->n_nodes * 5), 256, 0, s>>>(q, dq_new, cb, c->n_nodes, c->N3, 1.0, E0);
+    final_kernel<<<grid_for(c->n_nodes * 5), 256, 0, s>>>(q, dq_new, cb, c->n_nodes, DivU64::make(c->N3),
+                                                          DivU64::make(5), 1.0, E0);
     return cudaGetLastError();
 }
 
