@@ -174,8 +174,8 @@ def replica_throughput(n_nodes: int, world: int, ms_max: float, rhs_per_step: in
 def _config(args, extra=None):
     c = {"workload": WORKLOAD["name"], "mesh": f"{WORKLOAD['k']}^3 hexahedra, sinusoidal warp 0.1h",
          "p": WORKLOAD["p"], "nodes": WORKLOAD["k"] ** 3 * (WORKLOAD["p"] + 1) ** 3, "Re": WORKLOAD["Re"],
-         "Ma": WORKLOAD["Ma"], "step": "DP5 step (6 residuals) + float64 budgets", "replicas": args.gpus,
-         "l2": "flushed between timed steps (256 MiB write)"}
+         "Ma": WORKLOAD["Ma"], "step": "DP5 step (6 residuals) + float64 budgets recorded on the device",
+         "replicas": args.gpus, "l2": "flushed between timed steps (256 MiB write)"}
     if extra:
         c.update(extra)
     return c
@@ -270,6 +270,8 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # float64 budgets of every step, recorded on the device and read back after the timed region
+    hist = torch.zeros((args.steps, 5), dtype=torch.float64, device=q.device)
     solver.profile(True)
     with ClockSampler(local) as clk:
         time.sleep(0.6)          # let the sampler start before the timed region
@@ -278,11 +280,12 @@ def run_ours(args):
             flush.fill_(float(i))
             evs[i][0].record(stream)
             solver.rk_step(q, dt, 1)
-            solver.budgets(q)
+            solver.budgets_async(q, hist[i])
             evs[i][1].record(stream)
         barrier()
     ms_main, ms_face, nres = solver.profile_read()
     solver.profile(False)
+    _check_budgets(hist)
     ms_step = sum(a.elapsed_time(b) for a, b in evs) / args.steps
     ms_max = max_over_ranks(ms_step, dist, q.device)
     value = replica_throughput(n, ws, ms_max)
@@ -356,6 +359,13 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _check_budgets(hist):
+    """The per-step budgets recorded on the device: every state physical, every sum finite."""
+    h = hist.cpu()
+    if float(h[:, 4].abs().sum()) != 0.0 or not bool(torch.isfinite(h).all()):
+        raise RuntimeError("non-physical state during the timed steps")
+
+
 def _fp32_leg(args, s64, q_init, dt, flush, barrier, dist, ws):
     """The mixed-precision form on the same workload: float32 residual, float64 state and budgets."""
     from paper_1911_10966_gb300.solver import Solver, probe_fma
@@ -374,17 +384,19 @@ def _fp32_leg(args, s64, q_init, dt, flush, barrier, dist, ws):
     peak32 = probe_fma("f32")
     steps = args.steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    hist = torch.zeros((steps, 5), dtype=torch.float64, device=q.device)
     s32.profile(True)
     barrier()
     for i in range(steps):
         flush.fill_(float(i))
         evs[i][0].record(stream)
         s32.rk_step(q, dt, 1)
-        s32.budgets(q)
+        s32.budgets_async(q, hist[i])
         evs[i][1].record(stream)
     barrier()
     ms_main, ms_face, nres = s32.profile_read()
     s32.profile(False)
+    _check_budgets(hist)
     ms_step = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, dist, q.device)
     # kinetic-energy dissipation rate after the same number of steps in both precisions
     qa = s64.to_device(q_init)

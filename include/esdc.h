@@ -151,6 +151,17 @@ int esdc_budgets(esdc_ctx* ctx, const double* q_dev, const void* dqdt_dev, doubl
                  void* stream);
 
 /*
+ * esdc_budgets_async -- the same reductions as esdc_budgets, written to device memory without
+ * synchronising, so that a time loop can record the budgets of every step and read them back
+ * later: out_dev[5] (caller-owned float64 device memory) receives (sum P J S, sum P J rho|u|^2/2,
+ * sum P J w.dq/dt, sum P J (dKE/dq).dq/dt, number of non-finite or non-physical nodes); out_dev[2..3]
+ * are 0 when dqdt_dev is NULL.  A non-physical state is reported only through out_dev[4].  Uses the
+ * context's reduction scratch: calls on one context must not overlap on the GPU (same stream, or
+ * ordered).  Errors: ESDC_ERR_ARG, ESDC_ERR_CUDA (launch).
+ */
+int esdc_budgets_async(esdc_ctx* ctx, const double* q_dev, const void* dqdt_dev, double* out_dev, void* stream);
+
+/*
  * esdc_dt_cfl -- dt = cfl * min(h/(N^2 max(|u|+c)), h^2/(N^4 nu)), nu = max(4/3, gamma/Pr) mu/rho_min,
  * h = smallest element edge (the paper integrates adaptively; this fixed-step rule is the
  * library's).  Synchronises stream.  ESDC_ERR_STATE on a non-physical state.

@@ -57,6 +57,7 @@ def lib() -> ctypes.CDLL:
         "esdc_workspace_bytes": (I, [P, I, ctypes.POINTER(S)]),
         "esdc_rk_step": (I, [P, P, D, I, P, S, P]),
         "esdc_budgets": (I, [P, P, P, ctypes.POINTER(D), P]),
+        "esdc_budgets_async": (I, [P, P, P, P, P]),
         "esdc_dt_cfl": (I, [P, P, D, ctypes.POINTER(D), P]),
         "esdc_profile": (I, [P, I]),
         "esdc_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)]),

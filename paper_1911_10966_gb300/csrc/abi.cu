@@ -122,6 +122,7 @@ void free_ctx(esdc_ctx* c) {
     cudaFree(c->d_shadow);
     cudaFree(c->d_red);
     cudaFree(c->d_red_out);
+    cudaFree(c->d_lntab);
     cudaFree(c->d_stage_q);
     cudaFree(c->d_adj_g);
     cudaFree(c->d_adj_t);
@@ -267,6 +268,12 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->d_trace, (size_t)c->K * 6 * 4 * N2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_red, (size_t)c->red_blocks * 5 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_red_out, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_lntab, esdc::kLnTab * 3 * sizeof(double));
+    if (e == cudaSuccess) {
+        std::vector<double> tab(esdc::kLnTab * 3);
+        esdc::fill_ln_table(tab.data());
+        e = cudaMemcpy(c->d_lntab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemcpy(c->d_geom, hs.geom.data(), geom_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_nbr, hs.nbr.data(), hs.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -400,7 +407,7 @@ int esdc_rk_step(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, size_t
 int esdc_budgets(esdc_ctx* c, const double* q, const void* dqdt, double out[4], void* stream) {
     if (!c || !q || !out) return fail(ESDC_ERR_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = esdc::launch_budgets(c, q, dqdt, c->setup.precision == ESDC_PREC_FP32, s);
+    cudaError_t e = esdc::launch_budgets(c, q, dqdt, c->setup.precision == ESDC_PREC_FP32, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "budgets launch");
     double r[5];
     CUDA_TRY(cudaMemcpyAsync(r, c->d_red_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -408,6 +415,14 @@ int esdc_budgets(esdc_ctx* c, const double* q, const void* dqdt, double out[4], 
     for (int i = 0; i < 4; ++i) out[i] = r[i];
     if (!dqdt) out[2] = out[3] = 0.0;
     if (r[4] > 0.0) return fail(ESDC_ERR_STATE, "non-finite or non-physical values at " + std::to_string((long long)r[4]) + " nodes");
+    return ESDC_OK;
+}
+
+int esdc_budgets_async(esdc_ctx* c, const double* q, const void* dqdt, double* out_dev, void* stream) {
+    if (!c || !q || !out_dev) return fail(ESDC_ERR_ARG, "null argument");
+    cudaError_t e = esdc::launch_budgets(c, q, dqdt, c->setup.precision == ESDC_PREC_FP32, out_dev,
+                                         (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "budgets launch");
     return ESDC_OK;
 }
 

@@ -30,7 +30,13 @@ struct Combine {
 cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int64_t n, cudaStream_t s);
 
 // Reductions: budgets (4 sums + non-physical count) and CFL inputs (max |u|+c, min rho).
-cudaError_t launch_budgets(const esdc_ctx* c, const double* q, const void* dqdt, int dq_f32, cudaStream_t s);
+// Table of the budgets' logarithm: entry k (0 <= k < kLnTab) holds T_k = 1/c_k rounded to double,
+// c_k = 1 + (k + 1/2)/kLnTab, and -ln T_k as a head and a tail double (host, long double).
+constexpr int kLnTab = 128;
+void fill_ln_table(double* tab);
+// out: 5 doubles of device memory (NULL: the context's d_red_out)
+cudaError_t launch_budgets(const esdc_ctx* c, const double* q, const void* dqdt, int dq_f32, double* out,
+                           cudaStream_t s);
 cudaError_t launch_cfl(const esdc_ctx* c, const double* q, cudaStream_t s);
 
 cudaError_t probe_fma(int kind, double* flops_per_s, cudaStream_t s);

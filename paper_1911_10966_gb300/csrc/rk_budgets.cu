@@ -65,11 +65,15 @@ __device__ __forceinline__ double rcp_nr(double x) {
     return fma(y, fma(-x, y, 1.0), y);
 }
 
-// ln x for a positive finite double.  With x = m 2^e, m in [sqrt(1/2), sqrt(2)):
-// ln m = 2 artanh t, t = (m - 1)/(m + 1), |t| <= 3 - 2 sqrt(2) ~ 0.1716, summed as the artanh Taylor
-// series 2 t (1 + t^2/3 + t^4/5 + ... + t^18/19) (the first omitted term, t^20/21, is below 3e-17
-// relative), and ln x = e ln2_hi + (ln m + e ln2_lo) with ln 2 split into a head and a tail.
-__device__ __forceinline__ double ln_pos(double x, double ln2_hi, double ln2_lo) {
+// ln x for a positive finite double by table reduction (Tang's method, ACM TOMS 15, 1989): with
+// x = m 2^e, m in [1, 2), and k the top 7 bits of m's fraction, r = m T_k - 1 (one FMA, |r| <= 2^-8
+// since m lies within 1/256 of c_k), and
+//   ln x = e ln 2 - ln T_k + ln(1 + r),  ln(1 + r) = r - r^2/2 + r^3/3 - ... + r^7/7,
+// the first omitted term r^8/8 being below 2^-67.  The error is about one unit in the last place of
+// the larger of e ln 2 and ln c_k; near x = 1 from below the two nearly cancel, so the error there is
+// absolute (~1e-16), which is what the entropy sums need.  tab: shared-memory copy of the table
+// (T_k, head, tail of -ln T_k).
+__device__ __forceinline__ double ln_pos(double x, const double* __restrict__ tab, double ln2_hi, double ln2_lo) {
     long long b = __double_as_longlong(x);
     int e = 0;
     if (b < 0x0010000000000000LL) {            // subnormal: scale by 2^54 first
@@ -78,54 +82,52 @@ __device__ __forceinline__ double ln_pos(double x, double ln2_hi, double ln2_lo)
         e = -54;
     }
     e += (int)(b >> 52) - 1023;
-    double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);   // [1, 2)
-    if (m > 1.4142135623730951) {
-        m *= 0.5;
-        e += 1;
-    }
-    const double a = m - 1.0, d = m + 1.0;
-    const double r = rcp_nr(d);
-    double t = a * r;
-    t = fma(fma(-t, d, a), r, t);               // one residual correction of the quotient
-    const double t2 = t * t;
-    double sr = 1.0 / 19.0;
-    sr = fma(sr, t2, 1.0 / 17.0);
-    sr = fma(sr, t2, 1.0 / 15.0);
-    sr = fma(sr, t2, 1.0 / 13.0);
-    sr = fma(sr, t2, 1.0 / 11.0);
-    sr = fma(sr, t2, 1.0 / 9.0);
-    sr = fma(sr, t2, 1.0 / 7.0);
-    sr = fma(sr, t2, 1.0 / 5.0);
-    sr = fma(sr, t2, 1.0 / 3.0);
-    const double lm = 2.0 * fma(t * t2, sr, t);
+    const int k = (int)((b >> 45) & (kLnTab - 1));
+    const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);   // [1, 2)
+    const double r = fma(m, tab[3 * k], -1.0);
+    double c = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+    c = fma(r, c, 1.0 / 5.0);
+    c = fma(r, c, -1.0 / 4.0);
+    c = fma(r, c, 1.0 / 3.0);
+    c = fma(r, c, -1.0 / 2.0);
+    const double p = fma(r * r, c, r);
     const double ed = (double)e;
-    return fma(ed, ln2_hi, fma(ed, ln2_lo, lm));
+    return fma(ed, ln2_hi, tab[3 * k + 1]) + (fma(ed, ln2_lo, tab[3 * k + 2]) + p);
 }
 
 struct Ln2 {
     double hi, lo;
 };
 
+// true when x is neither infinite nor NaN (exponent field not all ones), tested on the integer pipe
+__device__ __forceinline__ bool finite_bits(double x) { return (__double2hiint(x) & 0x7FF00000) != 0x7FF00000; }
+
 // Per block: sums of P J S, P J KE, P J w.dq, P J dKE.dq and the count of non-physical nodes.
 template <typename TD>
 __global__ void __launch_bounds__(kRedThreads) budgets_kernel(const double* __restrict__ q, const TD* __restrict__ dq,
                                                               const double* __restrict__ geom, int64_t K, int N,
                                                               DivU64 div_n3, const Ops ops, const Phys ph, Ln2 ln2,
-                                                              double* __restrict__ part) {
+                                                              const double* __restrict__ lntab, double* __restrict__ part) {
     __shared__ double sh[kRedThreads];
+    __shared__ double sw[kMaxN * kMaxN * kMaxN];     // tensor-product LGL weights w_i1 w_i2 w_i3
+    __shared__ double stab[3 * kLnTab];
     const int N3 = N * N * N;
+    for (int node = threadIdx.x; node < N3; node += blockDim.x)
+        sw[node] = ops.w[node % N] * ops.w[(node / N) % N] * ops.w[node / (N * N)];
+    for (int i = threadIdx.x; i < 3 * kLnTab; i += blockDim.x) stab[i] = lntab[i];
+    __syncthreads();
     const int64_t n = K * N3;
     double aS = 0.0, aK = 0.0, aW = 0.0, aE = 0.0, bad = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
         const int64_t e = (int64_t)div_n3((unsigned long long)g);
         const int node = (int)(g - e * N3);
-        const int i1 = node % N, i2 = (node / N) % N, i3 = node / (N * N);
-        const double PJ = ops.w[i1] * ops.w[i2] * ops.w[i3] * geom[e * 10 * N3 + node];
+        const double PJ = sw[node] * geom[e * 10 * N3 + node];
         double qv[5];
         for (int v = 0; v < 5; ++v) qv[v] = q[(e * 5 + v) * N3 + node];
         const double rho = qv[0];
-        const bool pos = rho > 0.0 && isfinite(qv[0] + qv[1] + qv[2] + qv[3] + qv[4]);
+        const bool pos = rho > 0.0 && finite_bits(qv[0]) && finite_bits(qv[1]) && finite_bits(qv[2]) &&
+                         finite_bits(qv[3]) && finite_bits(qv[4]);
         const double ri = rcp_nr(pos ? rho : 1.0);
         const double u0 = qv[1] * ri, u1 = qv[2] * ri, u2 = qv[3] * ri;
         const double usq = u0 * u0 + u1 * u1 + u2 * u2;
@@ -134,17 +136,21 @@ __global__ void __launch_bounds__(kRedThreads) budgets_kernel(const double* __re
             bad += 1.0;
             continue;
         }
-        const double s = ln_pos(p, ln2.hi, ln2.lo) - ph.gamma * ln_pos(rho, ln2.hi, ln2.lo);
+        const double s = ln_pos(p, stab, ln2.hi, ln2.lo) - ph.gamma * ln_pos(rho, stab, ln2.hi, ln2.lo);
         aS += PJ * (-rho * s * ph.inv_gm1);
         aK += PJ * 0.5 * rho * usq;
         if (dq) {
             double d[5];
-            for (int v = 0; v < 5; ++v) d[v] = (double)dq[(e * 5 + v) * N3 + node];
+            bool fin = true;
+            for (int v = 0; v < 5; ++v) {
+                d[v] = (double)dq[(e * 5 + v) * N3 + node];
+                fin = fin && finite_bits(d[v]);
+            }
             const double rp = rho * rcp_nr(p);
             const double w1 = (ph.gamma - s) * ph.inv_gm1 - 0.5 * rp * usq;
             aW += PJ * (w1 * d[0] + rp * (u0 * d[1] + u1 * d[2] + u2 * d[3]) - rp * d[4]);
             aE += PJ * (-0.5 * usq * d[0] + u0 * d[1] + u1 * d[2] + u2 * d[3]);
-            if (!isfinite(d[0] + d[1] + d[2] + d[3] + d[4])) bad += 1.0;
+            if (!fin) bad += 1.0;
         }
     }
     const double r0 = block_sum(aS, sh), r1 = block_sum(aK, sh), r2 = block_sum(aW, sh), r3 = block_sum(aE, sh),
@@ -155,15 +161,17 @@ __global__ void __launch_bounds__(kRedThreads) budgets_kernel(const double* __re
     }
 }
 
-// Sum nparts rows of width `width` in a fixed order (one block).
+// Sum nparts rows of width `width` in a fixed order (one block): warp w sums columns w, w + 8, ...;
+// each lane adds rows lane, lane + 32, ... in order, then a fixed butterfly combines the lanes.
 __global__ void __launch_bounds__(kRedThreads) finish_sum(const double* __restrict__ part, int nparts, int width,
                                                           double* __restrict__ out) {
-    __shared__ double sh[kRedThreads];
-    for (int c = 0; c < width; ++c) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = warp; c < width; c += kRedThreads / 32) {
         double a = 0.0;
-        for (int i = threadIdx.x; i < nparts; i += blockDim.x) a += part[i * width + c];
-        const double r = block_sum(a, sh);
-        if (threadIdx.x == 0) out[c] = r;
+        for (int i = lane; i < nparts; i += 32) a += part[i * width + c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) out[c] = a;
     }
 }
 
@@ -276,6 +284,18 @@ cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int
     return cudaGetLastError();
 }
 
+void fill_ln_table(double* tab) {
+    for (int k = 0; k < kLnTab; ++k) {
+        const double c = 1.0 + (k + 0.5) / kLnTab;
+        const double T = 1.0 / c;
+        const long double L = -std::log((long double)T);
+        const double hi = (double)L;
+        tab[3 * k] = T;
+        tab[3 * k + 1] = hi;
+        tab[3 * k + 2] = (double)(L - (long double)hi);
+    }
+}
+
 Ln2 ln2_split() {
     // ln 2 as a head with the low 20 bits of its significand cleared and the tail ln 2 - head
     const double l = std::log(2.0);
@@ -287,16 +307,17 @@ Ln2 ln2_split() {
     return Ln2{hi, (double)(std::log(2.0L) - (long double)hi)};
 }
 
-cudaError_t launch_budgets(const esdc_ctx* c, const double* q, const void* dqdt, int dq_f32, cudaStream_t s) {
+cudaError_t launch_budgets(const esdc_ctx* c, const double* q, const void* dqdt, int dq_f32, double* out,
+                           cudaStream_t s) {
     static const Ln2 ln2 = ln2_split();
     const DivU64 dn3 = DivU64::make((unsigned long long)c->N3);
     if (dq_f32)
         budgets_kernel<float><<<c->red_blocks, kRedThreads, 0, s>>>(q, (const float*)dqdt, c->d_geom, c->K, c->N, dn3,
-                                                                     c->ops, c->phys, ln2, c->d_red);
+                                                                     c->ops, c->phys, ln2, c->d_lntab, c->d_red);
     else
         budgets_kernel<double><<<c->red_blocks, kRedThreads, 0, s>>>(q, (const double*)dqdt, c->d_geom, c->K, c->N,
-                                                                      dn3, c->ops, c->phys, ln2, c->d_red);
-    finish_sum<<<1, kRedThreads, 0, s>>>(c->d_red, c->red_blocks, 5, c->d_red_out);
+                                                                      dn3, c->ops, c->phys, ln2, c->d_lntab, c->d_red);
+    finish_sum<<<1, kRedThreads, 0, s>>>(c->d_red, c->red_blocks, 5, out ? out : c->d_red_out);
     return cudaGetLastError();
 }
 

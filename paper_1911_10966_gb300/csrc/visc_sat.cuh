@@ -66,23 +66,42 @@ visc_sat_kernel(T* __restrict__ out, const T* __restrict__ geom, const int32_t* 
     int ix[3];
     boundary_node<N>(r, ix[0], ix[1], ix[2]);
     const int node = ix[0] + N * ix[1] + N2 * ix[2];
+    // issue every independent load first: the neighbour indices, this element's traces, the
+    // Jacobian and the residual being updated; only the neighbour traces wait on a load
+    bool on[3];
+    int side[3], fi[3];
+    int32_t nb[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        on[l] = ix[l] == 0 || ix[l] == N - 1;
+        side[l] = ix[l] == N - 1;
+        fi[l] = l == 0 ? ix[1] + N * ix[2] : (l == 1 ? ix[0] + N * ix[2] : ix[0] + N * ix[1]);
+        nb[l] = on[l] ? nbr[el * 6 + 2 * l + side[l]] : 0;
+    }
+    T own[3][4];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        const T* to = trace + ((el * 6 + 2 * l + side[l]) * 4) * N2 + fi[l];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) own[l][k] = on[l] ? to[k * N2] : T(0);
+    }
+    const T J = geom[el * 10 * N3 + node];
+    T* o = out + el * 5 * N3 + node;
+    T res[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) res[k] = o[(1 + k) * N3];
     T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        const int il = ix[l];
-        if (il != 0 && il != N - 1) continue;
-        const int side = il == N - 1;
-        const int fi = l == 0 ? ix[1] + N * ix[2] : (l == 1 ? ix[0] + N * ix[2] : ix[0] + N * ix[1]);
-        const int64_t nb = nbr[el * 6 + 2 * l + side];
-        const T* to = trace + ((el * 6 + 2 * l + side) * 4) * N2 + fi;
-        const T* tn = trace + ((nb * 6 + 2 * l + 1 - side) * 4) * N2 + fi;
-        const T hs = side ? T(0.5) : T(-0.5);
+        if (!on[l]) continue;
+        const T* tn = trace + (((int64_t)nb[l] * 6 + 2 * l + 1 - side[l]) * 4) * N2 + fi[l];
+        const T hs = side[l] ? T(0.5) : T(-0.5);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] += hs * (tn[k * N2] - to[k * N2]);
+        for (int k = 0; k < 4; ++k) acc[k] += hs * (tn[k * N2] - own[l][k]);
     }
-    const T c = w_end / geom[el * 10 * N3 + node];
+    const T c = w_end / J;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) out[(el * 5 + 1 + k) * N3 + node] += c * acc[k];
+    for (int k = 0; k < 4; ++k) o[(1 + k) * N3] = res[k] + c * acc[k];
 }
 
 template <typename T, int N>

@@ -158,6 +158,20 @@ class Solver:
             nat.check(code, "esdc_budgets")
         return tuple(out)
 
+    def budgets_async(self, q, out, dqdt=None):
+        """Write (sum PJ S, KE, sum PJ w.dq/dt, dKE/dt, non-physical node count) into the float64
+        CUDA tensor `out` (5 contiguous elements) without synchronising."""
+        self._check_state(q)
+        if dqdt is not None:
+            self._check_state(dqdt, self.dtype_r)
+        if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+                and out.numel() >= 5 and out.device == self.device):
+            raise ValueError("out must be a contiguous float64 CUDA tensor of at least 5 elements on the solver's device")
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_budgets_async(self._ctx, q.data_ptr(), dqdt.data_ptr() if dqdt is not None else None,
+                                                   out.data_ptr(), _stream_ptr()), "esdc_budgets_async")
+        return out
+
     # -- adjoint (float64 contexts)
     def rhs_vjp(self, q, lam, want_mu=False):
         """(dR/dq)^T lam and, if want_mu, lam . dR/dmu."""

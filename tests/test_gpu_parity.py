@@ -138,6 +138,28 @@ def test_nonphysical_state_reported_without_fault():
     assert solver.budgets(qg)[1] > 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_budgets_async_equals_budgets(precision):
+    """esdc_budgets_async writes the same bits as esdc_budgets into device memory (same kernel and
+    summation order), with and without dq/dt; a non-physical node is counted in out[4]."""
+    from paper_1911_10966_gb300.solver import Solver
+    solver, qg, mesh, gas, qo = make_pair(3, (3, 2, 2), warp=0.1, seed=5, Re=800.0, noise=1e-2)
+    if precision == "fp32":
+        solver = Solver(3, 3, 2, 2, solver.coords, Re=800.0, precision="fp32")
+    r = solver.rhs(qg)
+    hist = torch.full((3, 5), float("nan"), dtype=torch.float64, device=qg.device)
+    solver.budgets_async(qg, hist[0], r)
+    solver.budgets_async(qg, hist[1])
+    bad = qg.clone()
+    bad[1, 0, 1, 1, 1] = -1.0
+    bad[2, 3, 0, 0, 0] = float("inf")
+    solver.budgets_async(bad, hist[2])
+    h = hist.cpu()
+    assert tuple(h[0, :4].tolist()) == solver.budgets(qg, r) and h[0, 4] == 0
+    assert tuple(h[1, :4].tolist()) == solver.budgets(qg) and h[1, 4] == 0 and h[1, 2] == 0 and h[1, 3] == 0
+    assert h[2, 4] == 2
+
+
 def test_bad_arguments_rejected():
     from paper_1911_10966_gb300 import _native as nat
     solver, qg, mesh, gas, qo = make_pair(2, (2, 2, 2), Re=0.0)
