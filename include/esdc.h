@@ -202,12 +202,31 @@ int esdc_rk_adjoint_workspace_bytes(const esdc_ctx* ctx, size_t* bytes);
  * esdc_rk_adjoint -- discrete adjoint of nsteps DP5 steps (reverse sweep with stage
  * recomputation from the per-step checkpoints of esdc_rk_step_ckpt).  On entry lambda_dev holds
  * dL/dq_N; on exit dL/dq_0.  grad_mu_host (nullable) receives dL/dmu.  Per step: six residuals to
- * rebuild the stage states, then for t = 6..1 psi_t = J(q_t)^T kappa_t with
+ * rebuild the stage states Y_t, then for t = 6..1 psi_t = J(Y_t)^T kappa_t with
  * kappa_t = dt b_t lambda_{n+1} + sum_{s>t} dt a_st psi_s, and lambda_n = lambda_{n+1} + sum_t psi_t.
  * ESDC_PREC_FP64 contexts only.  Synchronises stream when grad_mu_host is not NULL.
  */
 int esdc_rk_adjoint(esdc_ctx* ctx, const double* ckpt_dev, double dt, int nsteps, double* lambda_dev,
                     double* grad_mu_host, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/*
+ * esdc_rk_step_stages -- esdc_rk_step that stores the six stage states of every step, the stage
+ * checkpoints of the adjoint (no counterpart in the paper, whose method this differentiates):
+ * stages_dev[(n*6 + t)] = Y_t of step n, each K*5*N^3 float64 (Y_0 = q before step n; Y_t the
+ * state at which the t-th residual of the step is evaluated).  stages_dev: nsteps*6*K*5*N^3 float64,
+ * caller owned, 16-byte aligned.  The stage combinations write there directly, so storing costs one
+ * copy of q per step.  ESDC_PREC_FP64 contexts only (ESDC_ERR_UNSUPPORTED otherwise).  Asynchronous.
+ */
+int esdc_rk_step_stages(esdc_ctx* ctx, double* q_dev, double dt, int nsteps, double* stages_dev,
+                        void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/*
+ * esdc_rk_adjoint_stages -- the reverse sweep of esdc_rk_adjoint from stored stage states
+ * (esdc_rk_step_stages): per step six vector-Jacobian products and no residual recomputation.
+ * Same arguments, workspace (esdc_rk_adjoint_workspace_bytes) and results as esdc_rk_adjoint.
+ */
+int esdc_rk_adjoint_stages(esdc_ctx* ctx, const double* stages_dev, double dt, int nsteps, double* lambda_dev,
+                           double* grad_mu_host, void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /*
  * esdc_profile -- enable (on = 1) or disable CUDA-event timing of the residual kernels of this

@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
         "esdc_ke_gradient": (I, [P, P, P, P]),
         "esdc_rk_step_ckpt": (I, [P, P, D, I, P, P, S, P]),
         "esdc_rk_adjoint_workspace_bytes": (I, [P, ctypes.POINTER(S)]),
+        "esdc_rk_step_stages": (I, [P, P, D, I, P, P, S, P]),
+        "esdc_rk_adjoint_stages": (I, [P, P, D, I, P, ctypes.POINTER(D), P, S, P]),
         "esdc_rk_adjoint": (I, [P, P, D, I, P, ctypes.POINTER(D), P, S, P]),
         "esdc_strerror": (ctypes.c_char_p, [I]),
         "esdc_last_error": (ctypes.c_char_p, []),

@@ -1,8 +1,9 @@
 """torch.autograd.Function wrappers of the residual, the DP5 trajectory and the kinetic energy.
 
 Forward passes call the library's float64 kernels; backward passes call its hand-written adjoint
-kernels (esdc_rhs_vjp, esdc_rk_adjoint with per-step checkpoints and stage recomputation,
-esdc_ke_gradient).  Nothing here differentiates through torch operations.
+kernels (esdc_rhs_vjp; esdc_rk_adjoint_stages from stored stage states, or esdc_rk_adjoint from
+per-step checkpoints with stage recomputation; esdc_ke_gradient).  Nothing here differentiates
+through torch operations.
 """
 from __future__ import annotations
 
@@ -26,14 +27,22 @@ class Residual(torch.autograd.Function):
 
 class Trajectory(torch.autograd.Function):
     """q_N after nsteps fixed DP5 steps from q_0, as a function of (q_0, mu).  mu must equal the
-    solver's viscosity (it is an input only so that dL/dmu can flow back)."""
+    solver's viscosity (it is an input only so that dL/dmu can flow back).
+
+    stages: checkpoint granularity of the reverse sweep.  True stores the six stage states of every
+    step (6 x nsteps states, no recomputation); False stores the state before each step and
+    recomputes the stage states in the reverse sweep (six residuals per step); None picks True when
+    the stage states take at most half of the free device memory."""
 
     @staticmethod
-    def forward(ctx, q0, mu, solver, dt, nsteps):
+    def forward(ctx, q0, mu, solver, dt, nsteps, stages=None):
         if abs(float(mu) - solver.mu) > 1e-15 * max(1.0, abs(solver.mu)):
             raise ValueError("mu must equal the solver's viscosity 1/Re")
+        if stages is None:
+            free, _ = torch.cuda.mem_get_info(q0.device)
+            stages = 6 * nsteps * q0.numel() * 8 <= free // 2
         q = q0.detach().clone().contiguous()
-        ck = solver.rk_step_ckpt(q, dt, nsteps)
+        ck = solver.rk_step_ckpt(q, dt, nsteps, stages=bool(stages))
         ctx.solver, ctx.dt = solver, dt
         ctx.save_for_backward(ck)
         return q
@@ -43,7 +52,7 @@ class Trajectory(torch.autograd.Function):
         (ck,) = ctx.saved_tensors
         lam = g.detach().clone().contiguous()
         lam, gmu = ctx.solver.rk_adjoint(ck, ctx.dt, lam)
-        return lam, torch.tensor(gmu, dtype=torch.float64, device=lam.device), None, None, None
+        return lam, torch.tensor(gmu, dtype=torch.float64, device=lam.device), None, None, None, None
 
 
 class KineticEnergy(torch.autograd.Function):

@@ -112,10 +112,123 @@ int rk_step_f32(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStr
     return ESDC_OK;
 }
 
+// nsteps float64 DP5 steps.  stages (nullable): the six stage states of every step are written to
+// stages + (step * 6 + t) * K*5*N^3, t = 0 being the state at the start of the step; the stage
+// combinations then write there instead of the workspace buffer, so storing them costs one copy of q
+// per step.
+int rk_step_f64(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s, double* stages) {
+    const int64_t n = c->n_nodes * 5;
+    const size_t sub = round256((size_t)n * sizeof(double));
+    double* k[6];
+    for (int j = 0; j < 6; ++j) k[j] = (double*)((char*)ws + j * sub);
+    double* stage_ws = (double*)((char*)ws + 6 * sub);
+    for (int step = 0; step < nsteps; ++step) {
+        for (int st = 0; st < 6; ++st) {
+            double* dst = stages ? stages + ((size_t)step * 6 + st) * n : stage_ws;
+            const double* qs = q;
+            if (st == 0) {
+                if (stages) CUDA_TRY(cudaMemcpyAsync(dst, q, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            } else {
+                esdc::Combine cb{};
+                cb.nk = st;
+                for (int j = 0; j < st; ++j) {
+                    cb.k[j] = k[j];
+                    cb.coef[j] = dt * kA[st][j];
+                }
+                cudaError_t e = esdc::launch_combine(dst, q, cb, n, s);
+                if (e != cudaSuccess) return cuda_fail(e, "stage combine");
+                qs = dst;
+            }
+            int r = rhs_impl(c, qs, k[st], s);
+            if (r) return r;
+        }
+        esdc::Combine cb{};
+        cb.nk = 0;
+        for (int j = 0; j < 6; ++j)
+            if (kB[j] != 0.0) {
+                cb.k[cb.nk] = k[j];
+                cb.coef[cb.nk] = dt * kB[j];
+                ++cb.nk;
+            }
+        cudaError_t e = esdc::launch_combine(q, q, cb, n, s);
+        if (e != cudaSuccess) return cuda_fail(e, "step combine");
+    }
+    return ESDC_OK;
+}
+
+// Reverse sweep over one DP5 step from its six stage states Y[0..5] (float64 contexts).  On entry
+// lam = dL/dq_{n+1}; on exit dL/dq_n.  For t = 5..0:
+//   kappa_t = dt b_t lam + sum_{s>t} dt a_st psi_s,   psi_t = J(Y_t)^T kappa_t,
+// then lam += sum_t psi_t; lambda . dR/dmu of every VJP accumulates into d_adj_acc.  psi[6] and kappa
+// are state-sized buffers; psi may alias buffers whose contents are no longer needed.
+int adjoint_step(esdc_ctx* c, const double* const Y[6], double dt, double* lam, double* const psi[6], double* kappa,
+                 cudaStream_t s) {
+    const int64_t n = c->n_nodes * 5;
+    for (int t = 5; t >= 0; --t) {
+        esdc::LinComb lc{};
+        if (kB[t] != 0.0) {
+            lc.x[lc.n] = lam;
+            lc.c[lc.n++] = dt * kB[t];
+        }
+        for (int u = 5; u > t; --u)
+            if (kA[u][t] != 0.0) {
+                lc.x[lc.n] = psi[u];
+                lc.c[lc.n++] = dt * kA[u][t];
+            }
+        cudaError_t e = esdc::launch_lincomb(kappa, lc, n, s);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint stage cotangent");
+        e = esdc::launch_rhs_vjp(c, Y[t], kappa, psi[t], c->d_adj_acc, s);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint vjp");
+    }
+    esdc::LinComb lc{};
+    lc.x[lc.n] = lam;
+    lc.c[lc.n++] = 1.0;
+    for (int t = 5; t >= 0; --t) {
+        lc.x[lc.n] = psi[t];
+        lc.c[lc.n++] = 1.0;
+    }
+    cudaError_t e = esdc::launch_lincomb(lam, lc, n, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint accumulate");
+    return ESDC_OK;
+}
+
+int ensure_adjoint(esdc_ctx* c) {
+    if (c->setup.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for ESDC_PREC_FP64 contexts");
+    if (c->d_adj_g) return ESDC_OK;
+    const size_t N2 = (size_t)c->N * c->N;
+    CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&c->d_adj_t, (size_t)c->K * 6 * 4 * N2 * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&c->d_adj_mu, esdc::adjoint_mu_blocks(c) * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&c->d_adj_acc, 8 * sizeof(double)));
+    CUDA_TRY(esdc::prepare_adjoint(c));
+    return ESDC_OK;
+}
+
+int adjoint_checks(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, void* ws, size_t ws_bytes) {
+    if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
+    if (c->setup.precision != ESDC_PREC_FP64) return fail(ESDC_ERR_UNSUPPORTED, "the adjoint needs a float64 context");
+    if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
+    const size_t need = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
+    if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");
+    if (!aligned(ws, 256) || !aligned(lam, 16) || !aligned(ckpt, 16))
+        return fail(ESDC_ERR_ARG, "lam/ckpt must be 16-byte and workspace 256-byte aligned");
+    return ensure_adjoint(c);
+}
+
+int adjoint_finish(esdc_ctx* c, double* grad_mu, cudaStream_t s) {
+    if (grad_mu) {
+        CUDA_TRY(cudaMemcpyAsync(grad_mu, c->d_adj_acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return ESDC_OK;
+}
+
 void free_ctx(esdc_ctx* c) {
     if (!c) return;
     for (void* ev : c->prof_events) cudaEventDestroy((cudaEvent_t)ev);
     cudaFree(c->d_geom);
+    cudaFree(c->d_jinv);
     cudaFree(c->d_geomf);
     cudaFree(c->d_nbr);
     cudaFree(c->d_trace);
@@ -275,6 +388,13 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
         e = cudaMemcpy(c->d_lntab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemcpy(c->d_geom, hs.geom.data(), geom_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        std::vector<double> jinv((size_t)c->K * c->N3);
+        for (int64_t el = 0; el < c->K; ++el)
+            for (int i = 0; i < c->N3; ++i) jinv[el * c->N3 + i] = 1.0 / hs.geom[(el * 10) * c->N3 + i];
+        e = cudaMalloc(&c->d_jinv, jinv.size() * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_jinv, jinv.data(), jinv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_nbr, hs.nbr.data(), hs.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = esdc::prepare_rhs_f64(c);
@@ -367,41 +487,7 @@ int esdc_rk_step(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, size_t
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "workspace too small");
     if (!aligned(ws, 256) || !aligned(q, 16)) return fail(ESDC_ERR_ARG, "q must be 16-byte and workspace 256-byte aligned");
     if (c->setup.precision == ESDC_PREC_FP32) return rk_step_f32(c, q, dt, nsteps, ws, (cudaStream_t)stream);
-    const int64_t n = c->n_nodes * 5;
-    const size_t sub = round256((size_t)n * sizeof(double));
-    double* k[6];
-    for (int j = 0; j < 6; ++j) k[j] = (double*)((char*)ws + j * sub);
-    double* stage = (double*)((char*)ws + 6 * sub);
-    cudaStream_t s = (cudaStream_t)stream;
-    for (int step = 0; step < nsteps; ++step) {
-        for (int st = 0; st < 6; ++st) {
-            const double* qs = q;
-            if (st > 0) {
-                esdc::Combine cb{};
-                cb.nk = st;
-                for (int j = 0; j < st; ++j) {
-                    cb.k[j] = k[j];
-                    cb.coef[j] = dt * kA[st][j];
-                }
-                cudaError_t e = esdc::launch_combine(stage, q, cb, n, s);
-                if (e != cudaSuccess) return cuda_fail(e, "stage combine");
-                qs = stage;
-            }
-            int r = rhs_impl(c, qs, k[st], s);
-            if (r) return r;
-        }
-        esdc::Combine cb{};
-        cb.nk = 0;
-        for (int j = 0; j < 6; ++j)
-            if (kB[j] != 0.0) {
-                cb.k[cb.nk] = k[j];
-                cb.coef[cb.nk] = dt * kB[j];
-                ++cb.nk;
-            }
-        cudaError_t e = esdc::launch_combine(q, q, cb, n, s);
-        if (e != cudaSuccess) return cuda_fail(e, "step combine");
-    }
-    return ESDC_OK;
+    return rk_step_f64(c, q, dt, nsteps, ws, (cudaStream_t)stream, nullptr);
 }
 
 int esdc_budgets(esdc_ctx* c, const double* q, const void* dqdt, double out[4], void* stream) {
@@ -444,19 +530,6 @@ int esdc_dt_cfl(esdc_ctx* c, const double* q, double cfl, double* dt, void* stre
         d = std::fmin(d, c->h_min * c->h_min / (N2 * N2 * nu));
     }
     *dt = cfl * d;
-    return ESDC_OK;
-}
-
-static int ensure_adjoint(esdc_ctx* c) {
-    if (c->setup.precision != ESDC_PREC_FP64)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for ESDC_PREC_FP64 contexts");
-    if (c->d_adj_g) return ESDC_OK;
-    const size_t N2 = (size_t)c->N * c->N;
-    CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
-    CUDA_TRY(cudaMalloc(&c->d_adj_t, (size_t)c->K * 6 * 4 * N2 * sizeof(double)));
-    CUDA_TRY(cudaMalloc(&c->d_adj_mu, esdc::adjoint_mu_blocks(c) * sizeof(double)));
-    CUDA_TRY(cudaMalloc(&c->d_adj_acc, 8 * sizeof(double)));
-    CUDA_TRY(esdc::prepare_adjoint(c));
     return ESDC_OK;
 }
 
@@ -503,26 +576,18 @@ int esdc_rk_adjoint_workspace_bytes(const esdc_ctx* c, size_t* bytes) {
 
 int esdc_rk_adjoint(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, double* grad_mu, void* ws,
                     size_t ws_bytes, void* stream) {
-    if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
-    if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
-    size_t need = 0;
-    esdc_rk_adjoint_workspace_bytes(c, &need);
-    if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");
-    if (!aligned(ws, 256) || !aligned(lam, 16) || !aligned(ckpt, 16))
-        return fail(ESDC_ERR_ARG, "lam/ckpt must be 16-byte and workspace 256-byte aligned");
-    int st = ensure_adjoint(c);
+    int st = adjoint_checks(c, ckpt, dt, nsteps, lam, ws, ws_bytes);
     if (st) return st;
     const int64_t n = c->n_nodes * 5;
     const size_t sub = round256((size_t)n * sizeof(double));
-    double* K6[6];
+    double* K6[6];            // stage derivatives of the recomputation, then the stage cotangents psi_t
     double* Qs[6];
     for (int j = 0; j < 6; ++j) K6[j] = (double*)((char*)ws + j * sub);
     Qs[0] = nullptr;
     for (int j = 1; j < 6; ++j) Qs[j] = (double*)((char*)ws + (5 + j) * sub);
-    double* psi = (double*)((char*)ws + 11 * sub);
+    double* kappa = (double*)((char*)ws + 11 * sub);
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaMemsetAsync(c->d_adj_acc, 0, sizeof(double), s));
-    cudaError_t e;
     for (int step = nsteps - 1; step >= 0; --step) {
         const double* qn = ckpt + (size_t)step * n;
         // recompute the stage states of this step from its checkpoint
@@ -535,42 +600,51 @@ int esdc_rk_adjoint(esdc_ctx* c, const double* ckpt, double dt, int nsteps, doub
                     cb.k[j] = K6[j];
                     cb.coef[j] = dt * kA[t][j];
                 }
-                e = esdc::launch_combine(Qs[t], qn, cb, n, s);
+                cudaError_t e = esdc::launch_combine(Qs[t], qn, cb, n, s);
                 if (e != cudaSuccess) return cuda_fail(e, "adjoint stage recompute");
                 qs = Qs[t];
             }
             st = rhs_impl(c, qs, K6[t], s);
             if (st) return st;
         }
-        // kappa_t = dt b_t lam_{n+1}; then t = 5..0: psi_t = J(q_t)^T kappa_t, lam += psi_t,
-        // kappa_s += dt a_ts psi_t for s < t
-        for (int t = 0; t < 6; ++t) {
-            e = esdc::launch_scale(K6[t], lam, dt * kB[t], n, s);
-            if (e != cudaSuccess) return cuda_fail(e, "adjoint init");
-        }
-        for (int t = 5; t >= 0; --t) {
-            const double* qt = t == 0 ? qn : Qs[t];
-            e = esdc::launch_rhs_vjp(c, qt, K6[t], psi, c->d_adj_acc, s);
-            if (e != cudaSuccess) return cuda_fail(e, "adjoint vjp");
-            esdc::Combine cb{};
-            cb.nk = 1;
-            cb.k[0] = psi;
-            cb.coef[0] = 1.0;
-            e = esdc::launch_combine(lam, lam, cb, n, s);
-            if (e != cudaSuccess) return cuda_fail(e, "adjoint accumulate");
-            for (int u = 0; u < t; ++u) {
-                if (kA[t][u] == 0.0) continue;
-                cb.coef[0] = dt * kA[t][u];
-                e = esdc::launch_combine(K6[u], K6[u], cb, n, s);
-                if (e != cudaSuccess) return cuda_fail(e, "adjoint stage cotangent");
-            }
-        }
+        const double* Y[6] = {qn, Qs[1], Qs[2], Qs[3], Qs[4], Qs[5]};
+        st = adjoint_step(c, Y, dt, lam, K6, kappa, s);
+        if (st) return st;
     }
-    if (grad_mu) {
-        CUDA_TRY(cudaMemcpyAsync(grad_mu, c->d_adj_acc, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
+    return adjoint_finish(c, grad_mu, s);
+}
+
+int esdc_rk_step_stages(esdc_ctx* c, double* q, double dt, int nsteps, double* stages, void* ws, size_t ws_bytes,
+                        void* stream) {
+    if (!c || !q || !ws || !stages) return fail(ESDC_ERR_ARG, "null argument");
+    if (c->setup.precision != ESDC_PREC_FP64) return fail(ESDC_ERR_UNSUPPORTED, "stage storage needs a float64 context");
+    if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
+    size_t need = 0;
+    esdc_workspace_bytes(c, 0, &need);
+    if (ws_bytes < need) return fail(ESDC_ERR_ARG, "workspace too small");
+    if (!aligned(ws, 256) || !aligned(q, 16) || !aligned(stages, 16))
+        return fail(ESDC_ERR_ARG, "q/stages must be 16-byte and workspace 256-byte aligned");
+    return rk_step_f64(c, q, dt, nsteps, ws, (cudaStream_t)stream, stages);
+}
+
+int esdc_rk_adjoint_stages(esdc_ctx* c, const double* stages, double dt, int nsteps, double* lam, double* grad_mu,
+                           void* ws, size_t ws_bytes, void* stream) {
+    int st = adjoint_checks(c, stages, dt, nsteps, lam, ws, ws_bytes);
+    if (st) return st;
+    const int64_t n = c->n_nodes * 5;
+    const size_t sub = round256((size_t)n * sizeof(double));
+    double* psi[6];
+    for (int j = 0; j < 6; ++j) psi[j] = (double*)((char*)ws + j * sub);
+    double* kappa = (double*)((char*)ws + 6 * sub);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(c->d_adj_acc, 0, sizeof(double), s));
+    for (int step = nsteps - 1; step >= 0; --step) {
+        const double* Y[6];
+        for (int t = 0; t < 6; ++t) Y[t] = stages + ((size_t)step * 6 + t) * n;
+        st = adjoint_step(c, Y, dt, lam, psi, kappa, s);
+        if (st) return st;
     }
-    return ESDC_OK;
+    return adjoint_finish(c, grad_mu, s);
 }
 
 int esdc_profile(esdc_ctx* c, int on) {

@@ -34,6 +34,8 @@ struct CfgA {
     // | neighbour face w 24 N2
     static constexpr int SM = 48 * N3 + 24 * N2;
     static constexpr int EPB_F = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
+    // resident CTAs the register allocation is sized for (3 at N = 4, 5 measured faster than 2)
+    static constexpr int MINB = (N == 4 || N == 5) ? 3 : 1;
 };
 
 struct Prim {
@@ -154,7 +156,7 @@ __device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Pri
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
 template <int N>
-__global__ void __launch_bounds__(CfgA<N>::THREADS)
+__global__ void __launch_bounds__(CfgA<N>::THREADS, CfgA<N>::MINB)
 adj_main(const double* __restrict__ q, const double* __restrict__ lam, const double* __restrict__ geom,
          const int32_t* __restrict__ nbr, double* __restrict__ grad, double* __restrict__ gbuf,
          double* __restrict__ tbuf, double* __restrict__ mupart, int64_t K, const Ops ops, const Phys ph) {

@@ -74,6 +74,7 @@ struct esdc_ctx {
     double h_min = 0.0;
     // device buffers owned by the library
     double* d_geom = nullptr;        // [K][10][N3]
+    double* d_jinv = nullptr;        // [K][N3] 1/J
     float* d_geomf = nullptr;        // [K][10][N3] float32 copy (mixed precision)
     int32_t* d_nbr = nullptr;        // [K][6]
     void* d_trace = nullptr;         // [K][6][4][N2] viscous normal-flux traces (f64 or f32)

@@ -29,6 +29,14 @@ struct Combine {
 };
 cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int64_t n, cudaStream_t s);
 
+// out = sum_j c[j] * x[j] (n doubles, up to 7 terms, summed in j order; out may alias an x[j])
+struct LinComb {
+    const double* x[7];
+    double c[7];
+    int n;
+};
+cudaError_t launch_lincomb(double* out, const LinComb& lc, int64_t n, cudaStream_t s);
+
 // Reductions: budgets (4 sums + non-physical count) and CFL inputs (max |u|+c, min rho).
 // Table of the budgets' logarithm: entry k (0 <= k < kLnTab) holds T_k = 1/c_k rounded to double,
 // c_k = 1 + (k + 1/2)/kLnTab, and -ln T_k as a head and a tail double (host, long double).

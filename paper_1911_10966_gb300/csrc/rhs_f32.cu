@@ -459,8 +459,8 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaSt
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (ph.viscous) {
-        const cudaError_t e = launch_visc_sat<float, N>(out, c->d_geomf, c->d_nbr, (const float*)c->d_trace, c->K,
-                                                          c->opsf.winv[0], s);
+        const cudaError_t e = launch_visc_sat<float, N, false>(out, c->d_geomf, c->d_nbr, (const float*)c->d_trace,
+                                                               c->K, c->opsf.winv[0], s);
         if (e != cudaSuccess) return e;
     }
     if (ev) cudaEventRecord(ev[3], s);

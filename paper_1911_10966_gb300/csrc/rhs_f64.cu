@@ -380,6 +380,8 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
 }
 
 // BR1 viscous interface term on face nodes, direction by direction (edge nodes see up to 3 faces).
+// ---- host-side launchers
+
 template <int N>
 cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev) {
     using C = Cfg<N>;
@@ -391,8 +393,8 @@ cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaS
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (c->phys.viscous) {
-        const cudaError_t e = launch_visc_sat<double, N>(dqdt, c->d_geom, c->d_nbr, (const double*)c->d_trace, c->K,
-                                                           c->ops.winv[0], s);
+        const cudaError_t e = launch_visc_sat<double, N, true>(dqdt, c->d_jinv, c->d_nbr, (const double*)c->d_trace,
+                                                               c->K, c->ops.winv[0], s);
         if (e != cudaSuccess) return e;
     }
     if (ev) cudaEventRecord(ev[3], s);

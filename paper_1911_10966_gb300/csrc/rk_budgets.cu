@@ -13,32 +13,58 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-// out[i] = q0[i] + sum_j coef_j k_j[i]; two doubles per thread per iteration (16-byte accesses).  The
-// stage loop has a fixed trip count with predicated terms, so the stage pointers stay in parameter
-// space and all loads of an iteration are issued together; terms are summed in stage order.
+// out[i] = q0[i] + sum_j coef_j k_j[i]; two doubles per thread per iteration (16-byte accesses).  NK,
+// the number of terms, is a template parameter so that the stage pointers stay in parameter space,
+// all loads of an iteration are issued together and no float64 work is spent on absent terms;
+// terms are summed in stage order.
+template <int NK>
 __global__ void __launch_bounds__(256) combine_kernel(double* __restrict__ out, const double* __restrict__ q0,
                                                       const Combine cb, int64_t n) {
     const int64_t n2 = n / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-        double2 kv[6];
+        double2 kv[NK];
 #pragma unroll
-        for (int j = 0; j < 6; ++j)
-            kv[j] = j < cb.nk ? reinterpret_cast<const double2*>(cb.k[j])[i] : make_double2(0.0, 0.0);
+        for (int j = 0; j < NK; ++j) kv[j] = reinterpret_cast<const double2*>(cb.k[j])[i];
         double2 acc = reinterpret_cast<const double2*>(q0)[i];
 #pragma unroll
-        for (int j = 0; j < 6; ++j)
-            if (j < cb.nk) {
-                acc.x += cb.coef[j] * kv[j].x;
-                acc.y += cb.coef[j] * kv[j].y;
-            }
+        for (int j = 0; j < NK; ++j) {
+            acc.x = fma(cb.coef[j], kv[j].x, acc.x);
+            acc.y = fma(cb.coef[j], kv[j].y, acc.y);
+        }
         reinterpret_cast<double2*>(out)[i] = acc;
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         double acc = q0[n - 1];
 #pragma unroll
-        for (int j = 0; j < 6; ++j)
-            if (j < cb.nk) acc += cb.coef[j] * cb.k[j][n - 1];
+        for (int j = 0; j < NK; ++j) acc = fma(cb.coef[j], cb.k[j][n - 1], acc);
+        out[n - 1] = acc;
+    }
+}
+
+// out[i] = sum_j c_j x_j[i] over NT terms, two doubles per thread and iteration, terms in j order
+// (the first one a product, the rest fused multiply-adds).  Each thread reads all its terms before
+// writing, so out may alias an input.
+template <int NT>
+__global__ void __launch_bounds__(256) lincomb_kernel(double* __restrict__ out, const LinComb lc, int64_t n) {
+    const int64_t n2 = n / 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+        double2 xv[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) xv[j] = reinterpret_cast<const double2*>(lc.x[j])[i];
+        double2 acc = make_double2(lc.c[0] * xv[0].x, lc.c[0] * xv[0].y);
+#pragma unroll
+        for (int j = 1; j < NT; ++j) {
+            acc.x = fma(lc.c[j], xv[j].x, acc.x);
+            acc.y = fma(lc.c[j], xv[j].y, acc.y);
+        }
+        reinterpret_cast<double2*>(out)[i] = acc;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        double acc = lc.c[0] * lc.x[0][n - 1];
+#pragma unroll
+        for (int j = 1; j < NT; ++j) acc = fma(lc.c[j], lc.x[j][n - 1], acc);
         out[n - 1] = acc;
     }
 }
@@ -280,7 +306,16 @@ cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int
     int64_t blocks = (n / 2 + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    combine_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, q0, cb, n);
+    const unsigned g = (unsigned)blocks;
+    switch (cb.nk) {
+        case 1: combine_kernel<1><<<g, 256, 0, s>>>(out, q0, cb, n); break;
+        case 2: combine_kernel<2><<<g, 256, 0, s>>>(out, q0, cb, n); break;
+        case 3: combine_kernel<3><<<g, 256, 0, s>>>(out, q0, cb, n); break;
+        case 4: combine_kernel<4><<<g, 256, 0, s>>>(out, q0, cb, n); break;
+        case 5: combine_kernel<5><<<g, 256, 0, s>>>(out, q0, cb, n); break;
+        case 6: combine_kernel<6><<<g, 256, 0, s>>>(out, q0, cb, n); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -305,6 +340,24 @@ Ln2 ln2_split() {
     double hi;
     std::memcpy(&hi, &bits, sizeof hi);
     return Ln2{hi, (double)(std::log(2.0L) - (long double)hi)};
+}
+
+cudaError_t launch_lincomb(double* out, const LinComb& lc, int64_t n, cudaStream_t s) {
+    int64_t blocks = (n / 2 + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    const unsigned g = (unsigned)blocks;
+    switch (lc.n) {
+        case 1: lincomb_kernel<1><<<g, 256, 0, s>>>(out, lc, n); break;
+        case 2: lincomb_kernel<2><<<g, 256, 0, s>>>(out, lc, n); break;
+        case 3: lincomb_kernel<3><<<g, 256, 0, s>>>(out, lc, n); break;
+        case 4: lincomb_kernel<4><<<g, 256, 0, s>>>(out, lc, n); break;
+        case 5: lincomb_kernel<5><<<g, 256, 0, s>>>(out, lc, n); break;
+        case 6: lincomb_kernel<6><<<g, 256, 0, s>>>(out, lc, n); break;
+        case 7: lincomb_kernel<7><<<g, 256, 0, s>>>(out, lc, n); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_budgets(const esdc_ctx* c, const double* q, const void* dqdt, int dq_f32, double* out,

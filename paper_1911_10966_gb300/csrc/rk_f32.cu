@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "esdc_internal.h"
+#include "fpconv.cuh"
 #include "kernels.h"
 
 namespace esdc {
@@ -24,8 +25,10 @@ __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int v = var_of(i, div_n3, div_5);
-        const double off = v == 0 ? rho0 : (v == 4 ? E0 : 0.0);
-        dq[i] = (float)(q[i] - off);
+        double x = q[i];
+        if (v == 0) x -= rho0;
+        else if (v == 4) x -= E0;
+        dq[i] = d2f_int(x);
     }
 }
 
@@ -43,12 +46,14 @@ __global__ void __launch_bounds__(256) final_kernel(double* __restrict__ q, floa
         double inc = 0.0;
 #pragma unroll
         for (int j = 0; j < 6; ++j)
-            if (j < cb.nk) inc += cb.coef[j] * (double)kv[j];
+            if (j < cb.nk) inc = fma(cb.coef[j], f2d_int(kv[j]), inc);
         const double qn = q0 + inc;
         q[i] = qn;
         const int v = var_of(i, div_n3, div_5);
-        const double off = v == 0 ? rho0 : (v == 4 ? E0 : 0.0);
-        dq_new[i] = (float)(qn - off);
+        double x = qn;
+        if (v == 0) x -= rho0;
+        else if (v == 4) x -= E0;
+        dq_new[i] = d2f_int(x);
     }
 }
 

@@ -50,11 +50,12 @@ __device__ __forceinline__ void boundary_node(int r, int& i1, int& i2, int& i3) 
     }
 }
 
-// out, geom (J at component 0 of [K][10][N3]) and trace in the residual's precision T; w_end is the
-// inverse LGL end weight 1/w_0 = 1/w_{N-1}.
-template <typename T, int N>
+// out and trace in the residual's precision T; w_end is the inverse LGL end weight
+// 1/w_0 = 1/w_{N-1}.  jac: with JINV, 1/J as [K][N3]; otherwise the geometry [K][10][N3] with J at
+// component 0 (the float64 path passes the reciprocal to keep a division off its float64 pipe).
+template <typename T, int N, bool JINV>
 __global__ void __launch_bounds__(VSat<N>::THREADS)
-visc_sat_kernel(T* __restrict__ out, const T* __restrict__ geom, const int32_t* __restrict__ nbr,
+visc_sat_kernel(T* __restrict__ out, const T* __restrict__ jac, const int32_t* __restrict__ nbr,
                 const T* __restrict__ trace, int64_t K, T w_end) {
     using C = VSat<N>;
     constexpr int N2 = C::N2, N3 = C::N3;
@@ -85,7 +86,7 @@ visc_sat_kernel(T* __restrict__ out, const T* __restrict__ geom, const int32_t* 
 #pragma unroll
         for (int k = 0; k < 4; ++k) own[l][k] = on[l] ? to[k * N2] : T(0);
     }
-    const T J = geom[el * 10 * N3 + node];
+    const T Jf = JINV ? jac[el * N3 + node] : jac[el * 10 * N3 + node];
     T* o = out + el * 5 * N3 + node;
     T res[4];
 #pragma unroll
@@ -99,17 +100,17 @@ visc_sat_kernel(T* __restrict__ out, const T* __restrict__ geom, const int32_t* 
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[k] += hs * (tn[k * N2] - own[l][k]);
     }
-    const T c = w_end / J;
+    const T c = JINV ? w_end * Jf : w_end / Jf;
 #pragma unroll
     for (int k = 0; k < 4; ++k) o[(1 + k) * N3] = res[k] + c * acc[k];
 }
 
-template <typename T, int N>
-cudaError_t launch_visc_sat(T* out, const T* geom, const int32_t* nbr, const T* trace, int64_t K, T w_end,
+template <typename T, int N, bool JINV>
+cudaError_t launch_visc_sat(T* out, const T* jac, const int32_t* nbr, const T* trace, int64_t K, T w_end,
                             cudaStream_t s) {
     using C = VSat<N>;
     const unsigned grid = (unsigned)((K + C::EPB - 1) / C::EPB);
-    visc_sat_kernel<T, N><<<grid, C::THREADS, 0, s>>>(out, geom, nbr, trace, K, w_end);
+    visc_sat_kernel<T, N, JINV><<<grid, C::THREADS, 0, s>>>(out, jac, nbr, trace, K, w_end);
     return cudaGetLastError();
 }
 

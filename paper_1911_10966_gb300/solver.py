@@ -63,6 +63,7 @@ class Solver:
             nat.check(nat.lib().esdc_create(ctypes.byref(st), coords.ctypes.data, ctypes.byref(self._ctx)),
                       "esdc_create")
         self._ws = None
+        self._adj_ws = None
 
     @classmethod
     def box(cls, p, kx, ky, kz, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, warp=0.0, seed=0, **kw):
@@ -192,31 +193,41 @@ class Solver:
                       "esdc_ke_gradient")
         return g
 
-    def rk_step_ckpt(self, q, dt, nsteps):
-        """Advance q in place; return the [nsteps, K, 5, N, N, N] checkpoints (state before each step)."""
+    def rk_step_ckpt(self, q, dt, nsteps, stages=False):
+        """Advance q in place and return the checkpoints of the adjoint: the state before each step,
+        [nsteps, K, 5, N, N, N], or with stages=True the six stage states of every step,
+        [nsteps, 6, K, 5, N, N, N] (six times the memory, no recomputation in the reverse sweep)."""
         self._check_state(q)
-        ck = torch.empty((nsteps,) + self.state_shape, dtype=torch.float64, device=self.device)
+        shape = (nsteps, 6) + self.state_shape if stages else (nsteps,) + self.state_shape
+        ck = torch.empty(shape, dtype=torch.float64, device=self.device)
         nb = self.workspace_bytes()
         if self._ws is None or self._ws.numel() < nb:
             self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        fn = "esdc_rk_step_stages" if stages else "esdc_rk_step_ckpt"
         with torch.cuda.device(self.device):
-            nat.check(nat.lib().esdc_rk_step_ckpt(self._ctx, q.data_ptr(), float(dt), int(nsteps), ck.data_ptr(),
-                                                  self._ws.data_ptr(), self._ws.numel(), _stream_ptr()),
-                      "esdc_rk_step_ckpt")
+            nat.check(getattr(nat.lib(), fn)(self._ctx, q.data_ptr(), float(dt), int(nsteps), ck.data_ptr(),
+                                             self._ws.data_ptr(), self._ws.numel(), _stream_ptr()), fn)
         return ck
 
     def rk_adjoint(self, ckpt, dt, lam):
-        """Reverse sweep: lam (dL/dq_N) is replaced by dL/dq_0; returns (lam, dL/dmu)."""
+        """Reverse sweep from the checkpoints of rk_step_ckpt (per-step states: stage recomputation;
+        stage states: none): lam (dL/dq_N) is replaced by dL/dq_0; returns (lam, dL/dmu)."""
         self._check_state(lam)
+        stages = ckpt.dim() == len(self.state_shape) + 2
+        if not (ckpt.is_cuda and ckpt.dtype == torch.float64 and ckpt.is_contiguous() and ckpt.device == self.device
+                and tuple(ckpt.shape[2 if stages else 1:]) == self.state_shape and (not stages or ckpt.shape[1] == 6)):
+            raise ValueError("ckpt must come from rk_step_ckpt of this solver")
         nsteps = ckpt.shape[0]
         b = ctypes.c_size_t()
         nat.check(nat.lib().esdc_rk_adjoint_workspace_bytes(self._ctx, ctypes.byref(b)), "workspace")
-        ws = torch.empty(b.value, dtype=torch.uint8, device=self.device)
+        if self._adj_ws is None or self._adj_ws.numel() < b.value:
+            self._adj_ws = torch.empty(b.value, dtype=torch.uint8, device=self.device)
         gm = ctypes.c_double()
+        fn = "esdc_rk_adjoint_stages" if stages else "esdc_rk_adjoint"
         with torch.cuda.device(self.device):
-            nat.check(nat.lib().esdc_rk_adjoint(self._ctx, ckpt.data_ptr(), float(dt), int(nsteps), lam.data_ptr(),
-                                                ctypes.byref(gm), ws.data_ptr(), ws.numel(), _stream_ptr()),
-                      "esdc_rk_adjoint")
+            nat.check(getattr(nat.lib(), fn)(self._ctx, ckpt.data_ptr(), float(dt), int(nsteps), lam.data_ptr(),
+                                             ctypes.byref(gm), self._adj_ws.data_ptr(), self._adj_ws.numel(),
+                                             _stream_ptr()), fn)
         return lam, gm.value
 
     @property

@@ -137,6 +137,29 @@ def test_trajectory_gradient_vortex_8cubed_p4_50_steps():
     assert abs(gold["dke_dmu"] - gmu) <= 1e-9 * abs(gmu)
 
 
+def test_stage_checkpoints_equal_recomputation():
+    """The reverse sweep from stored stage states (esdc_rk_step_stages / esdc_rk_adjoint_stages) and
+    the one that recomputes them from per-step checkpoints evaluate the same VJPs at stage states
+    that agree bit for bit, so the gradients agree to rounding of the stage combinations (<= 1e-13)."""
+    from paper_1911_10966_gb300.autograd import KineticEnergy, Trajectory
+    solver, qg, mesh, gas, qo = make_pair(3, (3, 3, 2), warp=0.1, seed=6, Re=300.0, Ma=0.5, state="vortex",
+                                          box=([-5.0] * 3, [5.0] * 3))
+    dt = 0.5 * solver.dt_cfl(qg, 0.5)
+    grads = []
+    for stages in (True, False):
+        q0 = qg.clone().requires_grad_(True)
+        mu = torch.tensor(solver.mu, dtype=torch.float64, requires_grad=True)
+        qN = Trajectory.apply(q0, mu, solver, dt, 4, stages)
+        KineticEnergy.apply(qN, solver).backward()
+        grads.append((q0.grad.clone(), float(mu.grad), qN.detach().clone()))
+    (ga, ma, qa), (gb, mb, qb) = grads
+    assert torch.equal(qa, qb)
+    e = normwise_errors(ga, gb.cpu())
+    print("stage checkpoints vs recomputation", ["%.1e" % x for x in e], ma, mb)
+    assert max(e) <= 1e-13, e
+    assert abs(ma - mb) <= 1e-13 * abs(mb)
+
+
 def test_trajectory_gradient_matches_oracle_autograd():
     """Three DP5 steps on a 2^3 warped p=3 vortex box: the GPU adjoint gradient of the final kinetic
     energy w.r.t. q_0 and mu equals the oracle's autograd gradient."""
