@@ -326,6 +326,8 @@ def run_ours(args):
     ms_rhs = a.elapsed_time(b) / reps
 
     adj = _adjoint_leg(solver, solver.to_device(q_init), dt, ms_rhs, flush)
+    ada = _adaptive_leg(solver, q_init, dt)
+    var = _variants_leg(solver, q_init, ms_rhs)
     fp32 = _fp32_leg(args, solver, q_init, dt, flush, barrier, dist, ws) if not args.no_fp32 else None
     if fp32 is not None:
         fp32["speedup_vs_f64_rhs"] = (ms_main / max(nres, 1)) / fp32["roofline"]["kernel_ms"]
@@ -359,6 +361,8 @@ def run_ours(args):
                      "face_kernel_ms": ms_face / max(nres, 1)},
         "fp32_mixed": fp32,
         "adjoint": adj,
+        "adaptive_dp54": ada,
+        "volume_flux_variants": var,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -484,6 +488,47 @@ def _adjoint_leg(solver, q, dt, ms_rhs, flush):
             "what": "d KE(q_5)/d(q_0, mu): forward storing the stage states + reverse sweep (6 VJPs per "
                     "step); recompute variant: per-step checkpoints, 6 residual recomputations + 6 VJPs "
                     "per step"}
+
+
+def _variants_leg(solver, q_init, ms_rhs):
+    """Residual cost of the paper's comparison discretisations on the same workload (float64): the
+    Kennedy-Gruber split form (SF-KG) and standard collocation (DC) beside ES-C."""
+    from paper_1911_10966_gb300.solver import Solver
+    W = WORKLOAD
+    out = {"esc": {"rhs_ms": ms_rhs, "node_rhs_per_s": solver.n_nodes / (ms_rhs * 1e-3)}}
+    for vf in ("kg", "dc"):
+        s = Solver(W["p"], W["k"], W["k"], W["k"], solver.coords, Ma=W["Ma"], Re=W["Re"], volume_flux=vf)
+        q = s.to_device(q_init)
+        r = s.rhs(q)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            s.rhs(q, out=r)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 10
+        out[vf] = {"rhs_ms": ms, "node_rhs_per_s": s.n_nodes / (ms * 1e-3)}
+        s.close()
+    return out
+
+
+def _adaptive_leg(solver, q_init, dt):
+    """Adaptive DP5(4) (esdc_rk_adaptive) on the same workload over 200 CFL steps of physical time,
+    rtol = atol = 1e-8, first trial step 4 CFL steps: residual throughput including the error
+    estimate and the per-step host decision."""
+    tol, span = 1e-8, 200.0
+    q = solver.to_device(q_init)
+    solver.rk_adaptive(q, 0.0, 2.0 * dt, dt, rtol=tol, atol=tol)        # warm-up: workspace
+    q = solver.to_device(q_init)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = solver.rk_adaptive(q, 0.0, span * dt, 4.0 * dt, rtol=tol, atol=tol)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"t_end_over_cfl_dt": span, "rtol": tol, "atol": tol, "accepted": st["accepted"],
+            "rejected": st["rejected"], "rhs": st["rhs"], "wall_ms": wall * 1e3,
+            "node_rhs_per_s": solver.n_nodes * st["rhs"] / wall, "mean_dt_over_cfl_dt": span / st["accepted"]}
 
 
 def main():

@@ -40,6 +40,16 @@ extern "C" {
 #define ESDC_PREC_FP64 0          /* whole residual in float64                                  */
 #define ESDC_PREC_FP32 1          /* residual arithmetic in float32, state/RK/budgets float64   */
 
+/* Volume-flux variants (Sec. 4).  ESDC_FLUX_ESC: the entropy-stable collocation of the paper
+ * (Chandrashekar two-point flux, eq. discEL).  ESDC_FLUX_KG: the same Hadamard flux differencing with
+ * the Kennedy-Gruber two-point flux (the paper's SF-KG).  ESDC_FLUX_DC: standard collocation, D
+ * applied to the nodal contravariant Euler fluxes (the paper's DC), with the central interface flux.
+ * All three use the same interface dissipation, viscous terms and metrics; KG and DC are float64
+ * only and have no adjoint (ESDC_ERR_UNSUPPORTED). */
+#define ESDC_FLUX_ESC 0
+#define ESDC_FLUX_KG 1
+#define ESDC_FLUX_DC 2
+
 typedef struct esdc_ctx esdc_ctx; /* opaque, library owned */
 
 /* Problem description.  Only fully periodic structured boxes are connected by this build. */
@@ -52,6 +62,7 @@ typedef struct esdc_setup {
     double Re;              /* Reynolds number; Re <= 0 means inviscid (mu = 0)                   */
     int dissipation;        /* 1: entropy-stable interface dissipation; 0: entropy conservative   */
     int precision;          /* ESDC_PREC_FP64 or ESDC_PREC_FP32                                   */
+    int volume_flux;        /* ESDC_FLUX_ESC (the method), ESDC_FLUX_KG or ESDC_FLUX_DC           */
 } esdc_setup_t;
 
 /*
@@ -123,8 +134,36 @@ int esdc_rhs_host(esdc_ctx* ctx, const double* q_host, void* dqdt_host, void* st
  * esdc_workspace_bytes -- device workspace needed by esdc_rk_step (what = 0): for ESDC_PREC_FP64
  * six stage derivatives and one stage state, each K*5*N^3 float64; for ESDC_PREC_FP32 six float32
  * stage derivatives and one float32 perturbation state (each sub-buffer 256-byte aligned).
+ * what = 1: esdc_rk_adaptive's workspace, nine K*5*N^3 float64 buffers.
  */
 int esdc_workspace_bytes(const esdc_ctx* ctx, int what, size_t* bytes);
+
+/*
+ * esdc_rk_adaptive -- integrate q from t0 to t_end with the Dormand-Prince 5(4) pair and adaptive
+ * step sizes (Sec. 5: DP5 with "adaptive time-stepping based on signal processing", Soderlind 2003,
+ * Soderlind & Wang 2006; the paper states neither the filter nor the norm, so the library's choice
+ * is fixed here):
+ *   error estimate  e = dt sum_j (b_j - bhat_j) k_j with the embedded 4th-order weights and the
+ *                   seventh stage evaluated at the new solution (first same as last);
+ *   error norm      err = sqrt(mean over all K*5*N^3 values of (e / (atol + rtol max(|q_n|,
+ *                   |q_n+1|)))^2), accepted when err <= 1;
+ *   step control    H211b filter, b = 4: dt_n+1 = dt_n L(rho_n), rho_n = (0.8/err_n)^(1/20)
+ *                   (0.8/err_n-1)^(1/20) (dt_n/dt_n-1)^(-1/4) over accepted steps (first step:
+ *                   err_n-1 = err_n, ratio 1); a rejected step is retried with dt L((0.8/err)^(1/5)),
+ *                   or dt L(0) when err is not finite (an unphysical stage state);
+ *                   limiter L(rho) = 1 + atan(rho - 1); the last step lands on t_end.
+ * q_dev: [K][5][N^3] float64, advanced in place.  dt_inout: first trial step on entry (> 0), the
+ * proposed next step on exit.  rtol, atol > 0.  max_steps: bound on attempted (accepted + rejected)
+ * steps; the call returns ESDC_OK when it is reached, with stats_host[3] < t_end.  workspace_dev:
+ * esdc_workspace_bytes(ctx, 1) bytes, 256-byte aligned.  stats_host[4] (nullable): accepted steps,
+ * rejected steps, residual evaluations, time reached.  dt_history_host (nullable): the first
+ * history_capacity accepted step sizes.  The accept/reject decision runs on the host: the call
+ * synchronises stream once per attempted step.  ESDC_PREC_FP64 contexts only
+ * (ESDC_ERR_UNSUPPORTED otherwise).
+ */
+int esdc_rk_adaptive(esdc_ctx* ctx, double* q_dev, double t0, double t_end, double* dt_inout, double rtol,
+                     double atol, int max_steps, void* workspace_dev, size_t workspace_bytes, double* stats_host,
+                     double* dt_history_host, int history_capacity, void* stream);
 
 /*
  * esdc_rk_step -- nsteps fixed steps of size dt of the 5th-order Dormand-Prince solution

@@ -331,6 +331,28 @@ def ec_flux_n(qa: torch.Tensor, qb: torch.Tensor, n, gas: Gas) -> torch.Tensor:
     return torch.stack([f1, fm[0], fm[1], fm[2], f5], dim=1)
 
 
+def kg_flux_n(qa: torch.Tensor, qb: torch.Tensor, n, gas: Gas) -> torch.Tensor:
+    """Kennedy-Gruber two-point flux contracted with n (the SF-KG variant, Sec. 4):
+    f1 = rho_bar ubar_n, f_{2..4} = f1 ubar + p_bar n, f5 = f1 e_bar + p_bar ubar_n, with arithmetic
+    means of rho, u, p and the specific total energy e = rho E / rho."""
+    ra, ua, pa, _ = primitives(qa, gas)
+    rb, ub, pb, _ = primitives(qb, gas)
+    rbar = 0.5 * (ra + rb)
+    ubar = [0.5 * (ua[d] + ub[d]) for d in range(3)]
+    pbar = 0.5 * (pa + pb)
+    ebar = 0.5 * (qa[:, 4] / ra + qb[:, 4] / rb)
+    ubar_n = ubar[0] * n[0] + ubar[1] * n[1] + ubar[2] * n[2]
+    f1 = rbar * ubar_n
+    return torch.stack([f1, f1 * ubar[0] + pbar * n[0], f1 * ubar[1] + pbar * n[1], f1 * ubar[2] + pbar * n[2],
+                        f1 * ebar + pbar * ubar_n], dim=1)
+
+
+def central_flux_n(qa: torch.Tensor, qb: torch.Tensor, n, gas: Gas) -> torch.Tensor:
+    """Arithmetic mean of the two Euler fluxes contracted with n: the interface flux read for the DC
+    variant, whose volume term uses no two-point flux."""
+    return 0.5 * (euler_flux_n(qa, n, gas) + euler_flux_n(qb, n, gas))
+
+
 def sound_speed(q: torch.Tensor, gas: Gas) -> torch.Tensor:
     rho, _, p, _ = primitives(q, gas)
     return torch.sqrt(gas.gamma * p / rho)
@@ -385,6 +407,16 @@ def volume_term(q: torch.Tensor, Ja: torch.Tensor, sbp: SBP, gas: Gas, flux=None
         nbar = [0.5 * (nt[:, m].unsqueeze(-1) + nt[:, m].unsqueeze(-2)) for m in range(3)]
         F = flux(qi, qj, nbar, gas)
         out = out + (-2.0 * torch.einsum("ij,...ij->...i", sbp.D, F)).movedim(-1, a)
+    return out
+
+
+def dc_volume_term(q: torch.Tensor, Ja: torch.Tensor, sbp: SBP, gas: Gas) -> torch.Tensor:
+    """-sum_l D_l Ftilde_l, Ftilde_l = sum_m Ja_lm F_m(q) at each node: the standard collocation (DC)
+    divergence of the inviscid flux (Sec. 4), D applied to the nodal contravariant fluxes."""
+    out = torch.zeros_like(q)
+    for l in range(3):
+        Ft = euler_flux_n(q, [Ja[:, l, m] for m in range(3)], gas)
+        out = out - dxi(Ft, l, sbp.D)
     return out
 
 
@@ -474,12 +506,25 @@ def viscous_term(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor) -> torc
     return out
 
 
-def rhs(q, mesh: Mesh, gas: Gas, dissipation=True, elems=None, flux=None) -> torch.Tensor:
-    """dq/dt = J^-1 [-volume + SAT^(I) + viscous + SAT^(V)] on elements `elems` (default all)."""
+SCHEMES = ("esc", "kg", "dc")
+
+
+def rhs(q, mesh: Mesh, gas: Gas, dissipation=True, elems=None, flux=None, scheme="esc") -> torch.Tensor:
+    """dq/dt = J^-1 [-volume + SAT^(I) + viscous + SAT^(V)] on elements `elems` (default all).
+    scheme: "esc" (Chandrashekar two-point flux, the paper's ES-C), "kg" (Kennedy-Gruber two-point
+    flux, SF-KG) or "dc" (nodal fluxes differentiated by D, with the central interface flux)."""
     q = torch.as_tensor(q, dtype=F64)
     K = q.shape[0]
     E = torch.arange(K) if elems is None else torch.as_tensor(elems, dtype=torch.long)
-    r = volume_term(q[E], mesh.Ja[E], mesh.sbp, gas, flux) + inviscid_sat(q, mesh, gas, E, dissipation, flux)
+    if scheme == "dc":
+        r = dc_volume_term(q[E], mesh.Ja[E], mesh.sbp, gas) + inviscid_sat(q, mesh, gas, E, dissipation,
+                                                                           central_flux_n)
+    else:
+        if scheme == "kg":
+            flux = kg_flux_n
+        elif scheme != "esc":
+            raise ValueError(scheme)
+        r = volume_term(q[E], mesh.Ja[E], mesh.sbp, gas, flux) + inviscid_sat(q, mesh, gas, E, dissipation, flux)
     if gas.mu > 0.0:
         r = r + viscous_term(q, mesh, gas, E)
     return r / mesh.J[E].unsqueeze(1)
@@ -514,6 +559,99 @@ def rk_step(q, f, dt: float, nsteps: int = 1):
             if b != 0.0:
                 q = q + (dt * b) * k[j]
     return q
+
+
+# Adaptive Dormand-Prince 5(4) with a digital-filter step controller (Sec. 5: the paper integrates
+# with DP5 and "adaptive time-stepping based on signal processing", citing Soderlind 2003 and
+# Soderlind & Wang 2006, without stating the filter, the error norm or the tolerances).  Readings:
+#   * error estimate: the embedded 4th-order solution of Dormand & Prince (1980); the 7th stage is
+#     the residual at the new solution (first same as last), err_vec = dt sum_j (b_j - bhat_j) k_j;
+#   * error norm: weighted RMS over all nodes and variables (Hairer, Norsett & Wanner, Solving ODEs
+#     I, eq. II.4.11): sc = atol + rtol max(|q_n|, |q_n+1|), err = sqrt(mean((err_vec/sc)^2));
+#   * filter: H211b with b = 4 (Soderlind 2003): the next step is dt_n rho_n with
+#     rho_n = (theta/err_n)^(1/(b k)) (theta/err_n-1)^(1/(b k)) (dt_n/dt_n-1)^(-1/b) over accepted
+#     steps, k = 5 (the estimate is O(dt^5)), setpoint theta = 0.8; on the first step
+#     err_n-1 = err_n and dt_n-1 = dt_n;
+#   * limiter: rho_hat = 1 + atan(rho - 1) (Soderlind & Wang 2006, kappa = 1);
+#   * a step is accepted when err <= 1; a rejected step is retried with
+#     dt rho_hat((theta/err)^(1/k)) and leaves the filter's history unchanged; a non-finite err (a
+#     trial step so large that a stage state is unphysical) counts as rho = 0, i.e. dt rho_hat(0);
+#   * the last step is shortened to land on t_end.
+
+DP5_BHAT = [5179 / 57600, 0.0, 7571 / 16695, 393 / 640, -92097 / 339200, 187 / 2100, 1 / 40]
+DP54_K = 5
+H211B_B = 4.0
+CTRL_THETA = 0.8
+
+
+def dp54_error_norm(q0, q1, err_vec, rtol: float, atol: float) -> float:
+    """Weighted RMS norm of the embedded error estimate (reading above)."""
+    sc = atol + rtol * torch.maximum(q0.abs(), q1.abs())
+    return float(torch.sqrt(((err_vec / sc) ** 2).mean()))
+
+
+def step_limiter(rho: float) -> float:
+    """Smooth step-ratio limiter 1 + atan(rho - 1)."""
+    return 1.0 + math.atan(rho - 1.0)
+
+
+def h211b_ratio(err: float, err_prev: float, rho_prev: float) -> float:
+    """Unlimited H211b step-size ratio from the current and previous error norms and the previous
+    accepted step-size ratio."""
+    e = 1.0 / (H211B_B * DP54_K)
+    return (CTRL_THETA / err) ** e * (CTRL_THETA / err_prev) ** e * rho_prev ** (-1.0 / H211B_B)
+
+
+def dp54_step(q, k1, f, dt: float):
+    """One Dormand-Prince step from q with first stage k1 = f(q): returns (q_new, k7 = f(q_new),
+    err_vec) with the 5th-order solution and the embedded error estimate."""
+    k = [k1]
+    for s in range(1, 6):
+        qs = q
+        for j, a in enumerate(DP5_A[s]):
+            qs = qs + (dt * a) * k[j]
+        k.append(f(qs))
+    q_new = q
+    for j, b in enumerate(DP5_B):
+        if b != 0.0:
+            q_new = q_new + (dt * b) * k[j]
+    k.append(f(q_new))
+    err_vec = torch.zeros_like(q)
+    for j in range(7):
+        d = (DP5_B[j] if j < 6 else 0.0) - DP5_BHAT[j]
+        if d != 0.0:
+            err_vec = err_vec + (dt * d) * k[j]
+    return q_new, k[6], err_vec
+
+
+def rk_adaptive(q, f, t0: float, t_end: float, dt0: float, rtol: float, atol: float, max_steps: int = 1000):
+    """Integrate q from t0 to t_end with adaptive DP5(4) (readings above).  Returns (q, stats) with
+    stats = {"accepted": [dt of each accepted step], "rejected": count, "rhs": evaluations,
+    "dt_next": the proposed next step}."""
+    t = t0
+    dt = dt0
+    k1 = f(q) if t < t_end else None
+    nrhs = 1 if t < t_end else 0
+    err_prev, h_prev = None, None
+    accepted, rejected = [], 0
+    while t < t_end and len(accepted) + rejected < max_steps:
+        last = t + dt >= t_end
+        h = t_end - t if last else dt
+        q_new, k7, ev = dp54_step(q, k1, f, h)
+        nrhs += 6
+        err = dp54_error_norm(q, q_new, ev, rtol, atol)
+        if err <= 1.0:
+            rho = h211b_ratio(err, err if err_prev is None else err_prev, 1.0 if h_prev is None else h / h_prev)
+            q, k1 = q_new, k7
+            t = t_end if last else t + h
+            accepted.append(h)
+            err_prev, h_prev = err, h
+            dt = h * step_limiter(rho)
+        else:
+            rejected += 1
+            rho = (CTRL_THETA / err) ** (1.0 / DP54_K) if math.isfinite(err) else 0.0
+            dt = h * step_limiter(rho)
+    return q, {"accepted": accepted, "rejected": rejected, "rhs": nrhs, "dt_next": dt}
 
 
 # --------------------------------------------------------------------------------------------

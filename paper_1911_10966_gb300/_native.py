@@ -17,6 +17,7 @@ ESDC_ERR_MESH = -2
 ESDC_ERR_CUDA = -3
 ESDC_ERR_STATE = -4
 ESDC_ERR_UNSUPPORTED = -5
+FLUX = {"esc": 0, "kg": 1, "dc": 2}
 PREC_FP64 = 0
 PREC_FP32 = 1
 
@@ -24,7 +25,8 @@ PREC_FP32 = 1
 class Setup(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("kx", ctypes.c_int), ("ky", ctypes.c_int), ("kz", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Ma", ctypes.c_double),
-                ("Re", ctypes.c_double), ("dissipation", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("Re", ctypes.c_double), ("dissipation", ctypes.c_int), ("precision", ctypes.c_int),
+                ("volume_flux", ctypes.c_int)]
 
 
 class EsdcError(RuntimeError):
@@ -57,6 +59,7 @@ def lib() -> ctypes.CDLL:
         "esdc_workspace_bytes": (I, [P, I, ctypes.POINTER(S)]),
         "esdc_rk_step": (I, [P, P, D, I, P, S, P]),
         "esdc_budgets": (I, [P, P, P, ctypes.POINTER(D), P]),
+        "esdc_rk_adaptive": (I, [P, P, D, D, ctypes.POINTER(D), D, D, I, P, S, P, P, I, P]),
         "esdc_budgets_async": (I, [P, P, P, P, P]),
         "esdc_dt_cfl": (I, [P, P, D, ctypes.POINTER(D), P]),
         "esdc_profile": (I, [P, I]),

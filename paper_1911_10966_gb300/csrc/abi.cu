@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <utility>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -45,6 +46,13 @@ const double kA[6][5] = {
     {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0},
     {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0}};
 const double kB[6] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0};
+// embedded 4th-order weights of the pair (Dormand & Prince 1980); stage 7 is the residual at the new
+// solution (its row of A is b)
+const double kBhat[7] = {5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0,
+                         187.0 / 2100.0, 1.0 / 40.0};
+// digital-filter step control: H211b (Soderlind 2003) with b = 4 on an O(dt^5) estimate, setpoint
+// 0.8, ratio limiter 1 + atan(rho - 1) (Soderlind & Wang 2006)
+const double kCtrlB = 4.0, kCtrlK = 5.0, kCtrlTheta = 0.8;
 
 // Four profiling events for the next residual evaluation (NULL when profiling is off).
 cudaEvent_t* next_events(esdc_ctx* c) {
@@ -192,9 +200,103 @@ int adjoint_step(esdc_ctx* c, const double* const Y[6], double dt, double* lam, 
     return ESDC_OK;
 }
 
+double step_limiter(double rho) { return 1.0 + std::atan(rho - 1.0); }
+
+double h211b_ratio(double err, double err_prev, double rho_prev) {
+    const double e = 1.0 / (kCtrlB * kCtrlK);
+    return std::pow(kCtrlTheta / err, e) * std::pow(kCtrlTheta / err_prev, e) * std::pow(rho_prev, -1.0 / kCtrlB);
+}
+
+// Adaptive DP5(4) on a float64 context; see esdc_rk_adaptive.  Workspace: 7 stage derivatives, one
+// stage state, one candidate solution.
+int rk_adaptive_f64(esdc_ctx* c, double* q, double t0, double t_end, double* dt_io, double rtol, double atol,
+                    int max_steps, void* ws, double* stats, double* hist, int hist_cap, cudaStream_t s) {
+    const int64_t n = c->n_nodes * 5;
+    const size_t sub = round256((size_t)n * sizeof(double));
+    double* k[7];
+    for (int j = 0; j < 7; ++j) k[j] = (double*)((char*)ws + j * sub);
+    double* stage = (double*)((char*)ws + 7 * sub);
+    double* qn = (double*)((char*)ws + 8 * sub);
+    double t = t0, dt = *dt_io;
+    int acc = 0, rej = 0;
+    int64_t nrhs = 0;
+    double err_prev = -1.0, h_prev = -1.0;
+    int r;
+    if (t < t_end) {
+        r = rhs_impl(c, q, k[0], s);
+        if (r) return r;
+        ++nrhs;
+    }
+    while (t < t_end && acc + rej < max_steps) {
+        const bool last = t + dt >= t_end;
+        const double h = last ? t_end - t : dt;
+        for (int st = 1; st < 6; ++st) {
+            esdc::Combine cb{};
+            cb.nk = st;
+            for (int j = 0; j < st; ++j) {
+                cb.k[j] = k[j];
+                cb.coef[j] = h * kA[st][j];
+            }
+            cudaError_t e = esdc::launch_combine(stage, q, cb, n, s);
+            if (e != cudaSuccess) return cuda_fail(e, "stage combine");
+            r = rhs_impl(c, stage, k[st], s);
+            if (r) return r;
+        }
+        esdc::Combine cb{};
+        for (int j = 0; j < 6; ++j)
+            if (kB[j] != 0.0) {
+                cb.k[cb.nk] = k[j];
+                cb.coef[cb.nk] = h * kB[j];
+                ++cb.nk;
+            }
+        cudaError_t e = esdc::launch_combine(qn, q, cb, n, s);
+        if (e != cudaSuccess) return cuda_fail(e, "candidate solution");
+        r = rhs_impl(c, qn, k[6], s);
+        if (r) return r;
+        nrhs += 6;
+        esdc::LinComb lc{};
+        for (int j = 0; j < 7; ++j) {
+            const double d = (j < 6 ? kB[j] : 0.0) - kBhat[j];
+            if (d != 0.0) {
+                lc.x[lc.n] = k[j];
+                lc.c[lc.n++] = h * d;
+            }
+        }
+        e = esdc::launch_dp54_error(c, q, qn, lc, rtol, atol, s);
+        if (e != cudaSuccess) return cuda_fail(e, "error estimate");
+        double sum = 0.0;
+        CUDA_TRY(cudaMemcpyAsync(&sum, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        const double err = std::sqrt(sum / (double)n);
+        if (err <= 1.0) {
+            const double rho = h211b_ratio(err, err_prev < 0.0 ? err : err_prev, h_prev < 0.0 ? 1.0 : h / h_prev);
+            CUDA_TRY(cudaMemcpyAsync(q, qn, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            std::swap(k[0], k[6]);          // first same as last
+            t = last ? t_end : t + h;
+            if (hist && acc < hist_cap) hist[acc] = h;
+            ++acc;
+            err_prev = err;
+            h_prev = h;
+            dt = h * step_limiter(rho);
+        } else {
+            // a non-finite estimate (a stage state gone unphysical) counts as rho = 0
+            ++rej;
+            dt = h * step_limiter(std::isfinite(err) ? std::pow(kCtrlTheta / err, 1.0 / kCtrlK) : 0.0);
+        }
+    }
+    *dt_io = dt;
+    if (stats) {
+        stats[0] = acc;
+        stats[1] = rej;
+        stats[2] = (double)nrhs;
+        stats[3] = t;
+    }
+    return ESDC_OK;
+}
+
 int ensure_adjoint(esdc_ctx* c) {
-    if (c->setup.precision != ESDC_PREC_FP64)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for ESDC_PREC_FP64 contexts");
+    if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 ES-C contexts");
     if (c->d_adj_g) return ESDC_OK;
     const size_t N2 = (size_t)c->N * c->N;
     CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
@@ -207,7 +309,8 @@ int ensure_adjoint(esdc_ctx* c) {
 
 int adjoint_checks(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, void* ws, size_t ws_bytes) {
     if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
-    if (c->setup.precision != ESDC_PREC_FP64) return fail(ESDC_ERR_UNSUPPORTED, "the adjoint needs a float64 context");
+    if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 ES-C contexts");
     if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
     const size_t need = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");
@@ -292,6 +395,10 @@ static int check_setup(const esdc_setup_t& s) {
     if (s.dissipation != 0 && s.dissipation != 1) return fail(ESDC_ERR_ARG, "dissipation must be 0 or 1");
     if (s.precision != ESDC_PREC_FP64 && s.precision != ESDC_PREC_FP32)
         return fail(ESDC_ERR_ARG, "precision must be ESDC_PREC_FP64 or ESDC_PREC_FP32");
+    if (s.volume_flux != ESDC_FLUX_ESC && s.volume_flux != ESDC_FLUX_KG && s.volume_flux != ESDC_FLUX_DC)
+        return fail(ESDC_ERR_ARG, "volume_flux must be ESDC_FLUX_ESC, ESDC_FLUX_KG or ESDC_FLUX_DC");
+    if (s.volume_flux != ESDC_FLUX_ESC && s.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "the KG and DC volume fluxes are built for float64 only");
     return ESDC_OK;
 }
 
@@ -473,8 +580,9 @@ int esdc_rhs_host(esdc_ctx* c, const double* q_host, void* dqdt_host, void* stre
 
 int esdc_workspace_bytes(const esdc_ctx* c, int what, size_t* bytes) {
     if (!c || !bytes) return fail(ESDC_ERR_ARG, "null argument");
-    if (what != 0) return fail(ESDC_ERR_ARG, "unknown workspace kind");
-    if (c->setup.precision == ESDC_PREC_FP64) *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(double));
+    if (what != 0 && what != 1) return fail(ESDC_ERR_ARG, "unknown workspace kind");
+    if (what == 1) *bytes = 9 * round256((size_t)c->n_nodes * 5 * sizeof(double));
+    else if (c->setup.precision == ESDC_PREC_FP64) *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     else *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(float));
     return ESDC_OK;
 }
@@ -553,6 +661,24 @@ int esdc_ke_gradient(esdc_ctx* c, const double* q, double* grad, void* stream) {
     cudaError_t e = esdc::launch_ke_gradient(c, q, grad, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "esdc_ke_gradient");
     return ESDC_OK;
+}
+
+int esdc_rk_adaptive(esdc_ctx* c, double* q, double t0, double t_end, double* dt_inout, double rtol, double atol,
+                     int max_steps, void* ws, size_t ws_bytes, double* stats, double* dt_history, int history_capacity,
+                     void* stream) {
+    if (!c || !q || !ws || !dt_inout) return fail(ESDC_ERR_ARG, "null argument");
+    if (c->setup.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "adaptive stepping needs a float64 context");
+    if (!std::isfinite(t0) || !std::isfinite(t_end) || t_end < t0 || !(*dt_inout > 0.0) ||
+        !std::isfinite(*dt_inout) || !(rtol > 0.0) || !(atol > 0.0) || max_steps < 0 || history_capacity < 0)
+        return fail(ESDC_ERR_ARG, "need t0 <= t_end, dt > 0, rtol > 0, atol > 0, max_steps >= 0");
+    size_t need = 0;
+    esdc_workspace_bytes(c, 1, &need);
+    if (ws_bytes < need) return fail(ESDC_ERR_ARG, "workspace too small");
+    if (!aligned(ws, 256) || !aligned(q, 16))
+        return fail(ESDC_ERR_ARG, "q must be 16-byte and workspace 256-byte aligned");
+    return rk_adaptive_f64(c, q, t0, t_end, dt_inout, rtol, atol, max_steps, ws, stats, dt_history, history_capacity,
+                           (cudaStream_t)stream);
 }
 
 int esdc_rk_step_ckpt(esdc_ctx* c, double* q, double dt, int nsteps, double* ckpt, void* ws, size_t ws_bytes,

@@ -36,6 +36,10 @@ struct LinComb {
     int n;
 };
 cudaError_t launch_lincomb(double* out, const LinComb& lc, int64_t n, cudaStream_t s);
+// sum over all elements of ((sum_j c_j x_j) / (atol + rtol max(|q0|, |q1|)))^2 into c->d_red_out[0]
+// (5 to 7 terms)
+cudaError_t launch_dp54_error(const esdc_ctx* c, const double* q0, const double* q1, const LinComb& lc, double rtol,
+                              double atol, cudaStream_t s);
 
 // Reductions: budgets (4 sums + non-physical count) and CFL inputs (max |u|+c, min rho).
 // Table of the budgets' logarithm: entry k (0 <= k < kLnTab) holds T_k = 1/c_k rounded to double,

@@ -136,7 +136,45 @@ __device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Pri
     s.qq = sP[5 * N3 + idx];
 }
 
-template <int N>
+// Volume-flux variants of the kernel (the paper's comparison, Sec. 4): the entropy-stable
+// Chandrashekar flux (ES-C), the Kennedy-Gruber split form (SF-KG) and standard collocation (DC).
+enum : int { kFluxESC = 0, kFluxKG = 1, kFluxDC = 2 };
+
+// Kennedy-Gruber two-point flux contracted with n: f1 = rho_bar ubar.n, f_m = f1 ubar_m + p_bar n_m,
+// f5 = f1 e_bar + p_bar ubar.n with arithmetic means of rho, u, p = rho RT and the specific total
+// energy e = RT/(gamma-1) + |u|^2/2 (halved primitives: rho_bar = hr_a + hr_b, ubar = hu_a + hu_b).
+__device__ __forceinline__ void kg_flux(const Prim& a, const Prim& b, double RTa, double RTb, double n0, double n1,
+                                        double n2, const Phys& ph, double f[5]) {
+    const double rb = a.hr + b.hr;
+    const double ub0 = a.hu0 + b.hu0, ub1 = a.hu1 + b.hu1, ub2 = a.hu2 + b.hu2;
+    const double pb = fma(a.hr, RTa, b.hr * RTb);
+    const double eb = fma(0.5 * ph.inv_gm1, RTa + RTb, a.qq + b.qq);
+    const double un = fma(ub2, n2, fma(ub1, n1, ub0 * n0));
+    const double f1 = rb * un;
+    f[0] = f1;
+    f[1] = fma(f1, ub0, pb * n0);
+    f[2] = fma(f1, ub1, pb * n1);
+    f[3] = fma(f1, ub2, pb * n2);
+    f[4] = fma(f1, eb, pb * un);
+}
+
+// Euler flux of one state contracted with n, from the halved primitives and RT = p/rho:
+// f1 = rho u.n, f_m = f1 u_m + p n_m, f5 = f1 H with H = gamma/(gamma-1) RT + |u|^2/2.
+__device__ __forceinline__ void euler_flux_prim(const Prim& s, double RT, double n0, double n1, double n2,
+                                                const Phys& ph, double f[5]) {
+    const double rho = 2.0 * s.hr;
+    const double u0 = 2.0 * s.hu0, u1 = 2.0 * s.hu1, u2 = 2.0 * s.hu2;
+    const double p = rho * RT;
+    const double un = fma(u2, n2, fma(u1, n1, u0 * n0));
+    const double f1 = rho * un;
+    f[0] = f1;
+    f[1] = fma(f1, u0, p * n0);
+    f[2] = fma(f1, u1, p * n1);
+    f[3] = fma(f1, u2, p * n2);
+    f[4] = f1 * fma(ph.gamma * ph.inv_gm1, RT, 2.0 * s.qq);
+}
+
+template <int N, int VF>
 __global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::MINB)
 rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const double* __restrict__ geom,
              const int32_t* __restrict__ nbr, double* __restrict__ trace, int64_t K, const Ops ops,
@@ -176,6 +214,18 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
         sP[9 * N3 + node] = -2.0 * s.beta;
 #pragma unroll
         for (int c = 0; c < 10; ++c) sG[c * N3 + node] = geom[(el * 10 + c) * N3 + node];
+        if constexpr (VF == kFluxDC) {
+            // nodal contravariant fluxes Ftilde_l = sum_m Ja_lm F_m(q), held in the direction-l
+            // accumulator until the line through the node reads them
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                double f[5];
+                euler_flux_prim(s, RT, sG[(1 + 3 * l) * N3 + node], sG[(2 + 3 * l) * N3 + node],
+                                sG[(3 + 3 * l) * N3 + node], ph, f);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sR[(l * 5 + v) * N3 + node] = f[v];
+            }
+        }
     }
     __syncthreads();
 
@@ -194,19 +244,38 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             for (int i = 0; i < N; ++i)
 #pragma unroll
                 for (int v = 0; v < 5; ++v) acc[i][v] = 0.0;
+            double* R = sR + l * 5 * N3;
+            [[maybe_unused]] double Fl[N][5];
+            if constexpr (VF == kFluxDC) {
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) Fl[i][v] = R[v * N3 + base + i * st];
+            }
 #pragma unroll
             for (int i = 0; i < N - 1; ++i) {
                 const int ii = base + i * st;
                 Prim si;
-                load_prim(sP, N3, ii, si);
+                if constexpr (VF != kFluxDC) load_prim(sP, N3, ii, si);
                 const double a0 = n0p[ii], a1 = n1p[ii], a2 = n2p[ii];
 #pragma unroll
                 for (int j = i + 1; j < N; ++j) {
                     const int jj = base + j * st;
-                    Prim sj;
-                    load_prim(sP, N3, jj, sj);
                     double f[5];
-                    ec_flux(si, sj, a0 + n0p[jj], a1 + n1p[jj], a2 + n2p[jj], ph, f);   // 2 x averaged metric
+                    if constexpr (VF == kFluxESC) {
+                        Prim sj;
+                        load_prim(sP, N3, jj, sj);
+                        ec_flux(si, sj, a0 + n0p[jj], a1 + n1p[jj], a2 + n2p[jj], ph, f);   // 2 x averaged metric
+                    } else if constexpr (VF == kFluxKG) {
+                        Prim sj;
+                        load_prim(sP, N3, jj, sj);
+                        kg_flux(si, sj, sP[10 * N3 + ii], sP[10 * N3 + jj], a0 + n0p[jj], a1 + n1p[jj], a2 + n2p[jj],
+                                ph, f);
+                    } else {
+                        // twice the central flux of the nodal contravariant fluxes
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) f[v] = Fl[i][v] + Fl[j][v];
+                    }
                     const double c = 0.5 * ops.S2[i][j];
 #pragma unroll
                     for (int v = 0; v < 5; ++v) {
@@ -215,7 +284,6 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
                     }
                 }
             }
-            double* R = sR + l * 5 * N3;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 const int ii = base + i * st;
@@ -251,7 +319,17 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             const double n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own],
                          n2 = sG[(3 + 3 * l) * N3 + own];
             double f[5];
-            ec_flux(so, sn, n0, n1, n2, ph, f);
+            if constexpr (VF == kFluxESC) {
+                ec_flux(so, sn, n0, n1, n2, ph, f);
+            } else if constexpr (VF == kFluxKG) {
+                kg_flux(so, sn, sP[10 * N3 + own], RTn, n0, n1, n2, ph, f);
+            } else {
+                double fo[5];
+                euler_flux_prim(so, sP[10 * N3 + own], n0, n1, n2, ph, fo);
+                euler_flux_prim(sn, RTn, n0, n1, n2, ph, f);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) f[v] = 0.5 * (fo[v] + f[v]);
+            }
             const double E = side ? 1.0 : -1.0;
             double lam = 0.0;
             if (ph.dissipation) {
@@ -382,14 +460,15 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
 // BR1 viscous interface term on face nodes, direction by direction (edge nodes see up to 3 faces).
 // ---- host-side launchers
 
-template <int N>
-cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev) {
+template <int N, int VF>
+cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s,
+                         cudaEvent_t* ev) {
     using C = Cfg<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     if (ev) cudaEventRecord(ev[0], s);
-    rhs_main_f64<N><<<grid, C::THREADS, smem, s>>>(q, dqdt, c->d_geom, c->d_nbr, (double*)c->d_trace, c->K,
-                                                   c->ops, c->phys);
+    rhs_main_f64<N, VF><<<grid, C::THREADS, smem, s>>>(q, dqdt, c->d_geom, c->d_nbr, (double*)c->d_trace, c->K,
+                                                       c->ops, c->phys);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (c->phys.viscous) {
@@ -402,10 +481,26 @@ cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaS
 }
 
 template <int N>
-cudaError_t prepare_n() {
+cudaError_t prepare_n(int vf) {
     using C = Cfg<N>;
-    const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
-    return cudaFuncSetAttribute(rhs_main_f64<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int smem = (int)(C::EPB * C::SM * sizeof(double));
+    constexpr cudaFuncAttribute kAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    switch (vf) {
+        case kFluxESC: return cudaFuncSetAttribute(rhs_main_f64<N, kFluxESC>, kAttr, smem);
+        case kFluxKG: return cudaFuncSetAttribute(rhs_main_f64<N, kFluxKG>, kAttr, smem);
+        case kFluxDC: return cudaFuncSetAttribute(rhs_main_f64<N, kFluxDC>, kAttr, smem);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int N>
+cudaError_t launch_vf(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev) {
+    switch (c->setup.volume_flux) {
+        case kFluxESC: return launch_rhs_n<N, kFluxESC>(c, q, dqdt, s, ev);
+        case kFluxKG: return launch_rhs_n<N, kFluxKG>(c, q, dqdt, s, ev);
+        case kFluxDC: return launch_rhs_n<N, kFluxDC>(c, q, dqdt, s, ev);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -413,26 +508,26 @@ cudaError_t prepare_n() {
 // Opt the fused kernel into more than 48 KB of dynamic shared memory (on the current device).
 cudaError_t prepare_rhs_f64(const esdc_ctx* c) {
     switch (c->N) {
-        case 2: return prepare_n<2>();
-        case 3: return prepare_n<3>();
-        case 4: return prepare_n<4>();
-        case 5: return prepare_n<5>();
-        case 6: return prepare_n<6>();
-        case 7: return prepare_n<7>();
-        case 8: return prepare_n<8>();
+        case 2: return prepare_n<2>(c->setup.volume_flux);
+        case 3: return prepare_n<3>(c->setup.volume_flux);
+        case 4: return prepare_n<4>(c->setup.volume_flux);
+        case 5: return prepare_n<5>(c->setup.volume_flux);
+        case 6: return prepare_n<6>(c->setup.volume_flux);
+        case 7: return prepare_n<7>(c->setup.volume_flux);
+        case 8: return prepare_n<8>(c->setup.volume_flux);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_rhs_f64(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev) {
     switch (c->N) {
-        case 2: return launch_rhs_n<2>(c, q, dqdt, s, ev);
-        case 3: return launch_rhs_n<3>(c, q, dqdt, s, ev);
-        case 4: return launch_rhs_n<4>(c, q, dqdt, s, ev);
-        case 5: return launch_rhs_n<5>(c, q, dqdt, s, ev);
-        case 6: return launch_rhs_n<6>(c, q, dqdt, s, ev);
-        case 7: return launch_rhs_n<7>(c, q, dqdt, s, ev);
-        case 8: return launch_rhs_n<8>(c, q, dqdt, s, ev);
+        case 2: return launch_vf<2>(c, q, dqdt, s, ev);
+        case 3: return launch_vf<3>(c, q, dqdt, s, ev);
+        case 4: return launch_vf<4>(c, q, dqdt, s, ev);
+        case 5: return launch_vf<5>(c, q, dqdt, s, ev);
+        case 6: return launch_vf<6>(c, q, dqdt, s, ev);
+        case 7: return launch_vf<7>(c, q, dqdt, s, ev);
+        case 8: return launch_vf<8>(c, q, dqdt, s, ev);
         default: return cudaErrorInvalidValue;
     }
 }

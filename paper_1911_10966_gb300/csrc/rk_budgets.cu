@@ -187,6 +187,34 @@ __global__ void __launch_bounds__(kRedThreads) budgets_kernel(const double* __re
     }
 }
 
+// Embedded error estimate of one Dormand-Prince 5(4) step (Dormand & Prince 1980): per element
+// e = sum_j d_j k_j (d_j = dt (b_j - bhat_j), NT nonzero terms), sc = atol + rtol max(|q0|, |q1|),
+// and the block sums of (e/sc)^2 (the weighted RMS norm of Hairer, Norsett & Wanner, eq. II.4.11,
+// before the mean and square root).
+template <int NT>
+__global__ void __launch_bounds__(kRedThreads) dp54_err_kernel(const double* __restrict__ q0,
+                                                               const double* __restrict__ q1, const LinComb lc,
+                                                               double rtol, double atol, int64_t n,
+                                                               double* __restrict__ part) {
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double kv[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) kv[j] = lc.x[j][i];
+        const double a = q0[i], b = q1[i];
+        double e = lc.c[0] * kv[0];
+#pragma unroll
+        for (int j = 1; j < NT; ++j) e = fma(lc.c[j], kv[j], e);
+        const double sc = fma(rtol, fmax(fabs(a), fabs(b)), atol);
+        const double r = e * rcp_nr(sc);
+        acc = fma(r, r, acc);
+    }
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
 // Sum nparts rows of width `width` in a fixed order (one block): warp w sums columns w, w + 8, ...;
 // each lane adds rows lane, lane + 32, ... in order, then a fixed butterfly combines the lanes.
 __global__ void __launch_bounds__(kRedThreads) finish_sum(const double* __restrict__ part, int nparts, int width,
@@ -357,6 +385,19 @@ cudaError_t launch_lincomb(double* out, const LinComb& lc, int64_t n, cudaStream
         case 7: lincomb_kernel<7><<<g, 256, 0, s>>>(out, lc, n); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dp54_error(const esdc_ctx* c, const double* q0, const double* q1, const LinComb& lc, double rtol,
+                              double atol, cudaStream_t s) {
+    const int64_t n = c->n_nodes * 5;
+    switch (lc.n) {
+        case 5: dp54_err_kernel<5><<<c->red_blocks, kRedThreads, 0, s>>>(q0, q1, lc, rtol, atol, n, c->d_red); break;
+        case 6: dp54_err_kernel<6><<<c->red_blocks, kRedThreads, 0, s>>>(q0, q1, lc, rtol, atol, n, c->d_red); break;
+        case 7: dp54_err_kernel<7><<<c->red_blocks, kRedThreads, 0, s>>>(q0, q1, lc, rtol, atol, n, c->d_red); break;
+        default: return cudaErrorInvalidValue;
+    }
+    finish_sum<<<1, kRedThreads, 0, s>>>(c->d_red, c->red_blocks, 1, c->d_red_out);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ class Solver:
     """
 
     def __init__(self, p, kx, ky, kz, coords, *, gamma=1.4, Pr=0.72, Ma=0.1, Re=0.0, dissipation=True,
-                 precision="fp64", device=None):
+                 precision="fp64", volume_flux="esc", device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU implementation exists)")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
@@ -51,19 +51,23 @@ class Solver:
         self.K = kx * ky * kz
         self.gamma, self.Pr, self.Ma, self.Re = gamma, Pr, Ma, Re
         self.precision = precision
+        if volume_flux not in nat.FLUX:
+            raise ValueError("volume_flux must be 'esc', 'kg' or 'dc'")
+        self.volume_flux = volume_flux
         self.dtype_r = torch.float64 if precision == "fp64" else torch.float32
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         if coords.shape != (self.K, 3, self.N, self.N, self.N):
             raise ValueError(f"coords must have shape {(self.K, 3, self.N, self.N, self.N)}, got {coords.shape}")
         self.coords = coords
         st = nat.Setup(p, kx, ky, kz, gamma, Pr, Ma, Re, 1 if dissipation else 0,
-                       nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32)
+                       nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32, nat.FLUX[volume_flux])
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             nat.check(nat.lib().esdc_create(ctypes.byref(st), coords.ctypes.data, ctypes.byref(self._ctx)),
                       "esdc_create")
         self._ws = None
         self._adj_ws = None
+        self._ada_ws = None
 
     @classmethod
     def box(cls, p, kx, ky, kz, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, warp=0.0, seed=0, **kw):
@@ -192,6 +196,29 @@ class Solver:
             nat.check(nat.lib().esdc_ke_gradient(self._ctx, q.data_ptr(), g.data_ptr(), _stream_ptr()),
                       "esdc_ke_gradient")
         return g
+
+    def rk_adaptive(self, q, t0, t_end, dt0, rtol=1e-6, atol=1e-6, max_steps=100000, history=0):
+        """Advance q in place from t0 to t_end with adaptive DP5(4) (float64 contexts).  Returns a
+        dict: accepted, rejected, rhs (residual evaluations), t (time reached), dt_next and, if
+        history > 0, dt_history (the first `history` accepted step sizes)."""
+        self._check_state(q)
+        b = ctypes.c_size_t()
+        nat.check(nat.lib().esdc_workspace_bytes(self._ctx, 1, ctypes.byref(b)), "esdc_workspace_bytes")
+        if self._ada_ws is None or self._ada_ws.numel() < b.value:
+            self._ada_ws = torch.empty(b.value, dtype=torch.uint8, device=self.device)
+        dt = ctypes.c_double(float(dt0))
+        stats = (ctypes.c_double * 4)()
+        hist = (ctypes.c_double * max(int(history), 1))()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_rk_adaptive(self._ctx, q.data_ptr(), float(t0), float(t_end), ctypes.byref(dt),
+                                                 float(rtol), float(atol), int(max_steps), self._ada_ws.data_ptr(),
+                                                 self._ada_ws.numel(), stats, hist if history else None,
+                                                 int(history), _stream_ptr()), "esdc_rk_adaptive")
+        out = {"accepted": int(stats[0]), "rejected": int(stats[1]), "rhs": int(stats[2]), "t": stats[3],
+               "dt_next": dt.value}
+        if history:
+            out["dt_history"] = list(hist)[:min(int(history), out["accepted"])]
+        return out
 
     def rk_step_ckpt(self, q, dt, nsteps, stages=False):
         """Advance q in place and return the checkpoints of the adjoint: the state before each step,

@@ -4,6 +4,7 @@
   python -m paper_1911_10966_gb300.studies psweep      # p = 2..7 at ~16M nodes (+ the 256^3-node meshes
                                                         #   of the paper's cost study, Sec. 5.2, p = 1, 3, 7)
   python -m paper_1911_10966_gb300.studies hconv       # isentropic vortex L2 error, p = 3, 4, 5, 4^3..32^3
+  python -m paper_1911_10966_gb300.studies variants    # ES-C / SF-KG / DC DP5 step time, 256^3 nodes, p = 1, 3, 7
 
 All arithmetic runs in libesdc.so; this module only sets up meshes and states, times calls with CUDA
 events and computes error norms of the returned fields.
@@ -141,6 +142,27 @@ def psweep():
     return rows
 
 
+def variants():
+    """The paper's cost comparison (Sec. 5.2, "Error vs. cost" figure): Taylor-Green at Ma 0.05,
+    Re 1600, 256^3 nodes at p = 1, 3, 7, time per fixed DP5 step (six residuals) with the ES-C,
+    SF-KG and DC volume fluxes in float64 (p = 15 needs more than the 8 nodes per direction the
+    kernels are built for)."""
+    rows = []
+    for p, k in PAPER_E3.items():
+        for vf in ("esc", "kg", "dc"):
+            s = Solver.box(p, k, k, k, Re=1600.0, Ma=0.05, volume_flux=vf)
+            q = s.to_device(I.taylor_green(s.coords, Ma=0.05))
+            dt = s.dt_cfl(q, 0.5)
+            ms = _time_step(s, q, dt)
+            row = {"study": "variants", "p": p, "k": k, "nodes": s.n_nodes, "volume_flux": vf, "dp5_step_ms": ms,
+                   "node_rhs_per_s": s.n_nodes * 6 / (ms * 1e-3), "rhs_ms": _time_rhs(s, q)}
+            print(json.dumps(row), flush=True)
+            rows.append(row)
+            del q, s
+            torch.cuda.empty_cache()
+    return rows
+
+
 def _vortex(x, t, u_inf, Ma=0.5):
     """Exact translating isentropic vortex (axis along x3) at time t, periodic images ignored."""
     c = (u_inf[0] * t, u_inf[1] * t, 0.0)
@@ -180,4 +202,4 @@ def hconv(t_final=0.5):
 
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "psweep"
-    {"precision": precision, "psweep": psweep, "hconv": hconv}[which]()
+    {"precision": precision, "psweep": psweep, "hconv": hconv, "variants": variants}[which]()
