@@ -492,25 +492,32 @@ def _adjoint_leg(solver, q, dt, ms_rhs, flush):
 
 def _variants_leg(solver, q_init, ms_rhs):
     """Residual cost of the paper's comparison discretisations on the same workload (float64): the
-    Kennedy-Gruber split form (SF-KG) and standard collocation (DC) beside ES-C."""
+    Kennedy-Gruber split form (SF-KG) and standard collocation (DC) beside ES-C, and ES-C with the
+    Roe-type matrix interface dissipation instead of local Lax-Friedrichs."""
     from paper_1911_10966_gb300.solver import Solver
     W = WORKLOAD
     out = {"esc": {"rhs_ms": ms_rhs, "node_rhs_per_s": solver.n_nodes / (ms_rhs * 1e-3)}}
-    for vf in ("kg", "dc"):
-        s = Solver(W["p"], W["k"], W["k"], W["k"], solver.coords, Ma=W["Ma"], Re=W["Re"], volume_flux=vf)
-        q = s.to_device(q_init)
-        r = s.rhs(q)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(10):
-            s.rhs(q, out=r)
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / 10
-        out[vf] = {"rhs_ms": ms, "node_rhs_per_s": s.n_nodes / (ms * 1e-3)}
+    for vf, diss in (("kg", True), ("dc", True), ("esc", "matrix")):
+        s = Solver(W["p"], W["k"], W["k"], W["k"], solver.coords, Ma=W["Ma"], Re=W["Re"], volume_flux=vf,
+                   dissipation=diss)
+        ms = _time_rhs_ms(s, q_init)
+        out[vf if diss is True else "esc_matrix_dissipation"] = {"rhs_ms": ms,
+                                                                 "node_rhs_per_s": s.n_nodes / (ms * 1e-3)}
         s.close()
     return out
+
+
+def _time_rhs_ms(s, q_init, reps=10):
+    q = s.to_device(q_init)
+    r = s.rhs(q)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        s.rhs(q, out=r)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
 
 
 def _adaptive_leg(solver, q_init, dt):

@@ -46,6 +46,16 @@ extern "C" {
  * applied to the nodal contravariant Euler fluxes (the paper's DC), with the central interface flux.
  * All three use the same interface dissipation, viscous terms and metrics; KG and DC are float64
  * only and have no adjoint (ESDC_ERR_UNSUPPORTED). */
+/* Interface dissipation of SAT^(I) (the paper defers the SAT to its references).  ESDC_DISS_NONE:
+ * entropy conservative.  ESDC_DISS_LLF: local Lax-Friedrichs, lambda/2 (q_own - q_nbr) with
+ * lambda = max over both sides of |u.n_J| + c |n_J|.  ESDC_DISS_MATRIX: Roe-type entropy-stable
+ * matrix dissipation D (w_own - w_nbr)/2, D = R |Lambda| R^T at the averaged state (log-mean
+ * density, mean velocity, p = rho_bar/(2 beta_bar)) with eigenvectors scaled so that R R^T = dq/dw;
+ * float64 only, no adjoint (ESDC_ERR_UNSUPPORTED). */
+#define ESDC_DISS_NONE 0
+#define ESDC_DISS_LLF 1
+#define ESDC_DISS_MATRIX 2
+
 #define ESDC_FLUX_ESC 0
 #define ESDC_FLUX_KG 1
 #define ESDC_FLUX_DC 2
@@ -60,7 +70,7 @@ typedef struct esdc_setup {
     double Pr;              /* Prandtl number (> 0)                                               */
     double Ma;              /* reference Mach number (> 0): sets R = 1/(gamma Ma^2)                */
     double Re;              /* Reynolds number; Re <= 0 means inviscid (mu = 0)                   */
-    int dissipation;        /* 1: entropy-stable interface dissipation; 0: entropy conservative   */
+    int dissipation;        /* ESDC_DISS_NONE, ESDC_DISS_LLF or ESDC_DISS_MATRIX (below)          */
     int precision;          /* ESDC_PREC_FP64 or ESDC_PREC_FP32                                   */
     int volume_flux;        /* ESDC_FLUX_ESC (the method), ESDC_FLUX_KG or ESDC_FLUX_DC           */
 } esdc_setup_t;

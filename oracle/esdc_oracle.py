@@ -353,6 +353,44 @@ def central_flux_n(qa: torch.Tensor, qb: torch.Tensor, n, gas: Gas) -> torch.Ten
     return 0.5 * (euler_flux_n(qa, n, gas) + euler_flux_n(qb, n, gas))
 
 
+def dq_dw(rho, u, p, gas: Gas) -> torch.Tensor:
+    """The symmetric matrix dq/dw (inverse Hessian of the entropy function in conserved variables)
+    at the state (rho, u, p), shape [..., 5, 5]: rows (rho, rho u, rho E) differentiated by w."""
+    E = p / (gas.gamma - 1.0) + 0.5 * rho * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
+    H = (E + p) / rho
+    a2 = gas.gamma * p / rho
+    m = [rho * u[d] for d in range(3)]
+    rows = [[rho, m[0], m[1], m[2], E]]
+    for i in range(3):
+        rows.append([m[i]] + [m[i] * u[j] + (p if i == j else torch.zeros_like(p)) for j in range(3)]
+                    + [rho * H * u[i]])
+    rows.append([E, rho * H * u[0], rho * H * u[1], rho * H * u[2], rho * H * H - a2 * p / (gas.gamma - 1.0)])
+    return torch.stack([torch.stack(r, dim=-1) for r in rows], dim=-2)
+
+
+def matrix_dissipation(rho, u, p, n, gas: Gas) -> torch.Tensor:
+    """Roe-type entropy-stable dissipation matrix D = R |Lambda| R^T for the direction n (not
+    normalised) at the state (rho, u, p), shape [..., 5, 5].  R are the right eigenvectors of the
+    flux Jacobian in n scaled so that R R^T = dq/dw (Barth's scaling); the three eigenvalues u.n share
+    one eigenspace, so D = |u.n| dq/dw + s (|u.n - a|n|| - |u.n|) r1 r1^T + s (|u.n + a|n|| - |u.n|)
+    r5 r5^T with the acoustic eigenvectors r1,5 = (1, u -+ a nhat, H -+ a u.nhat) and s = rho/(2 gamma)."""
+    nn = torch.sqrt(n[0] ** 2 + n[1] ** 2 + n[2] ** 2)
+    nh = [n[d] / nn for d in range(3)]
+    a = torch.sqrt(gas.gamma * p / rho)
+    usq = u[0] ** 2 + u[1] ** 2 + u[2] ** 2
+    H = a * a / (gas.gamma - 1.0) + 0.5 * usq
+    un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2]
+    unh = un / nn
+    l1, l2, l5 = (un - a * nn).abs(), un.abs(), (un + a * nn).abs()
+    one = torch.ones_like(rho)
+    r1 = torch.stack([one, u[0] - a * nh[0], u[1] - a * nh[1], u[2] - a * nh[2], H - a * unh], dim=-1)
+    r5 = torch.stack([one, u[0] + a * nh[0], u[1] + a * nh[1], u[2] + a * nh[2], H + a * unh], dim=-1)
+    sc = rho / (2.0 * gas.gamma)
+    outer = lambda r: r.unsqueeze(-1) * r.unsqueeze(-2)
+    return (l2[..., None, None] * dq_dw(rho, u, p, gas) + (sc * (l1 - l2))[..., None, None] * outer(r1)
+            + (sc * (l5 - l2))[..., None, None] * outer(r5))
+
+
 def sound_speed(q: torch.Tensor, gas: Gas) -> torch.Tensor:
     rho, _, p, _ = primitives(q, gas)
     return torch.sqrt(gas.gamma * p / rho)
@@ -423,7 +461,8 @@ def dc_volume_term(q: torch.Tensor, Ja: torch.Tensor, sbp: SBP, gas: Gas) -> tor
 def inviscid_sat(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, dissipation=True,
                  flux=None) -> torch.Tensor:
     """SAT^(I) on elements E at every face node: -(1/P_ii) E_ii [f*(own, nbr) - f(own)].n_J minus
-    (1/P_ii) lambda/2 (q_own - q_nbr) when dissipation is on (local Lax-Friedrichs reading)."""
+    (1/P_ii) lambda/2 (q_own - q_nbr) when dissipation is True (local Lax-Friedrichs reading), or
+    minus (1/P_ii) D (w_own - w_nbr)/2 with the Roe-type matrix D when dissipation == "matrix"."""
     flux = flux or ec_flux_n
     sbp = mesh.sbp
     qE = q[E]
@@ -438,7 +477,19 @@ def inviscid_sat(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, dissipa
             n = [nJ[:, m] for m in range(3)]
             sgn = -1.0 if side == 0 else 1.0
             val = -sgn * (flux(qo, qn, n, gas) - euler_flux_n(qo, n, gas))
-            if dissipation:
+            if dissipation == "matrix":
+                # reading: D at the averaged state (rho_ln, ubar, p = rho_bar/(2 beta_bar)) applied to
+                # the jump of the entropy variables
+                ro, uo, po, To = primitives(qo, gas)
+                rn, un_, pn, Tn = primitives(qn, gas)
+                bo, bn = 1.0 / (2.0 * gas.R * To), 1.0 / (2.0 * gas.R * Tn)
+                rh = logmean(ro, rn)
+                uh = [0.5 * (uo[d] + un_[d]) for d in range(3)]
+                ph = 0.5 * (ro + rn) / (bo + bn)
+                Dm = matrix_dissipation(rh, uh, ph, n, gas)
+                jw = entropy_variables(qo, gas) - entropy_variables(qn, gas)
+                val = val - 0.5 * torch.einsum("k...ij,kj...->ki...", Dm, jw)
+            elif dissipation:
                 _, uo, _, _ = primitives(qo, gas)
                 _, un_, _, _ = primitives(qn, gas)
                 nn = torch.sqrt(n[0] ** 2 + n[1] ** 2 + n[2] ** 2)

@@ -295,8 +295,9 @@ int rk_adaptive_f64(esdc_ctx* c, double* q, double t0, double t_end, double* dt_
 }
 
 int ensure_adjoint(esdc_ctx* c) {
-    if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 ES-C contexts");
+    if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
+        c->setup.dissipation == ESDC_DISS_MATRIX)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 ES-C contexts with scalar dissipation");
     if (c->d_adj_g) return ESDC_OK;
     const size_t N2 = (size_t)c->N * c->N;
     CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
@@ -309,8 +310,9 @@ int ensure_adjoint(esdc_ctx* c) {
 
 int adjoint_checks(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, void* ws, size_t ws_bytes) {
     if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
-    if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 ES-C contexts");
+    if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
+        c->setup.dissipation == ESDC_DISS_MATRIX)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 ES-C contexts with scalar dissipation");
     if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
     const size_t need = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");
@@ -392,7 +394,10 @@ static int check_setup(const esdc_setup_t& s) {
     if ((int64_t)s.kx * s.ky * s.kz > (int64_t)INT32_MAX / 6) return fail(ESDC_ERR_ARG, "too many elements");
     if (!(s.gamma > 1.0) || !(s.Pr > 0.0) || !(s.Ma > 0.0) || !std::isfinite(s.Re))
         return fail(ESDC_ERR_ARG, "gamma > 1, Pr > 0, Ma > 0 and finite Re required");
-    if (s.dissipation != 0 && s.dissipation != 1) return fail(ESDC_ERR_ARG, "dissipation must be 0 or 1");
+    if (s.dissipation != ESDC_DISS_NONE && s.dissipation != ESDC_DISS_LLF && s.dissipation != ESDC_DISS_MATRIX)
+        return fail(ESDC_ERR_ARG, "dissipation must be ESDC_DISS_NONE, ESDC_DISS_LLF or ESDC_DISS_MATRIX");
+    if (s.dissipation == ESDC_DISS_MATRIX && s.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "the matrix dissipation is built for float64 only");
     if (s.precision != ESDC_PREC_FP64 && s.precision != ESDC_PREC_FP32)
         return fail(ESDC_ERR_ARG, "precision must be ESDC_PREC_FP64 or ESDC_PREC_FP32");
     if (s.volume_flux != ESDC_FLUX_ESC && s.volume_flux != ESDC_FLUX_KG && s.volume_flux != ESDC_FLUX_DC)

@@ -136,6 +136,67 @@ __device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Pri
     s.qq = sP[5 * N3 + idx];
 }
 
+// Roe-type entropy-stable interface dissipation D (w_a - w_b) (the matrix alternative to local
+// Lax-Friedrichs).  D = R |Lambda| R^T in the direction n at the averaged state (rho_ln, ubar,
+// p = rho_bar/(2 beta_bar)), with R the eigenvectors of the flux Jacobian scaled so that R R^T = dq/dw.
+// The three eigenvalues u.n share an eigenspace, so D = |u.n| dq/dw + s (|u.n - a|n|| - |u.n|) r1 r1^T
+// + s (|u.n + a|n|| - |u.n|) r5 r5^T, r1,5 = (1, u -+ a nhat, H -+ a u.nhat), s = rho/(2 gamma).
+// The entropy-variable jump takes its logarithms as log(p_a/p_b) and log(rho_a/rho_b).
+__device__ __forceinline__ void matrix_dissipation(const Prim& a, double RTa, const Prim& b, double RTb, double n0,
+                                                   double n1, double n2, const Phys& ph, double dm[5]) {
+    const double ra = 2.0 * a.hr, rb = 2.0 * b.hr;
+    const double pa = ra * RTa, pb = rb * RTb;
+    // jump of the entropy variables w = ((gamma - s)/(gamma - 1) - beta |u|^2, 2 beta u, -2 beta)
+    const double ds = log(pa / pb) - ph.gamma * log(ra / rb);
+    double jw[5];
+    jw[0] = -ds * ph.inv_gm1 - 4.0 * (a.beta * a.qq - b.beta * b.qq);
+    jw[1] = 4.0 * (a.beta * a.hu0 - b.beta * b.hu0);
+    jw[2] = 4.0 * (a.beta * a.hu1 - b.beta * b.hu1);
+    jw[3] = 4.0 * (a.beta * a.hu2 - b.beta * b.hu2);
+    jw[4] = -2.0 * (a.beta - b.beta);
+    // averaged state
+    const double sh = a.hr + b.hr;
+    const double fr = (a.hr - b.hr) * rcp_newton1(sh);
+    const double ur = fr * fr;
+    double rho;
+    if (small_jump(ur)) rho = sh * fma(ur, fma(ur, fma(ur, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
+    else rho = 2.0 * (a.hr - b.hr) / log(a.hr / b.hr);
+    const double p = sh * rcp_newton2(a.beta + b.beta);
+    const double u0 = a.hu0 + b.hu0, u1 = a.hu1 + b.hu1, u2 = a.hu2 + b.hu2;
+    const double usq = u0 * u0 + u1 * u1 + u2 * u2;
+    const double c2 = ph.gamma * p / rho;
+    const double c = sqrt(c2);
+    const double H = fma(c2, ph.inv_gm1, 0.5 * usq);
+    const double E = fma(p, ph.inv_gm1, 0.5 * rho * usq);
+    const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    const double inn = 1.0 / nn;
+    const double un = u0 * n0 + u1 * n1 + u2 * n2;
+    const double unh = un * inn;
+    const double l2 = fabs(un), l1 = fabs(un - c * nn), l5 = fabs(un + c * nn);
+    // dq/dw jw
+    const double m0 = rho * u0, m1 = rho * u1, m2 = rho * u2;
+    const double ujw = u0 * jw[1] + u1 * jw[2] + u2 * jw[3];
+    const double t = jw[0] + ujw + H * jw[4];
+    double r[5];
+    r[0] = rho * jw[0] + m0 * jw[1] + m1 * jw[2] + m2 * jw[3] + E * jw[4];
+    r[1] = fma(m0, t, p * jw[1]);
+    r[2] = fma(m1, t, p * jw[2]);
+    r[3] = fma(m2, t, p * jw[3]);
+    r[4] = E * jw[0] + rho * H * ujw + (rho * H * H - c2 * p * ph.inv_gm1) * jw[4];
+    // acoustic eigenvector corrections
+    const double cn0 = c * n0 * inn, cn1 = c * n1 * inn, cn2 = c * n2 * inn;
+    const double njw = cn0 * jw[1] + cn1 * jw[2] + cn2 * jw[3];
+    const double c1 = jw[0] + ujw - njw + (H - c * unh) * jw[4];
+    const double c5 = jw[0] + ujw + njw + (H + c * unh) * jw[4];
+    const double sc = rho / (2.0 * ph.gamma);
+    const double k1 = sc * (l1 - l2) * c1, k5 = sc * (l5 - l2) * c5;
+    dm[0] = l2 * r[0] + k1 + k5;
+    dm[1] = l2 * r[1] + k1 * (u0 - cn0) + k5 * (u0 + cn0);
+    dm[2] = l2 * r[2] + k1 * (u1 - cn1) + k5 * (u1 + cn1);
+    dm[3] = l2 * r[3] + k1 * (u2 - cn2) + k5 * (u2 + cn2);
+    dm[4] = l2 * r[4] + k1 * (H - c * unh) + k5 * (H + c * unh);
+}
+
 // Volume-flux variants of the kernel (the paper's comparison, Sec. 4): the entropy-stable
 // Chandrashekar flux (ES-C), the Kennedy-Gruber split form (SF-KG) and standard collocation (DC).
 enum : int { kFluxESC = 0, kFluxKG = 1, kFluxDC = 2 };
@@ -332,7 +393,10 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             }
             const double E = side ? 1.0 : -1.0;
             double lam = 0.0;
-            if (ph.dissipation) {
+            double dm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            if (ph.dissipation == 2) {
+                matrix_dissipation(so, sP[10 * N3 + own], sn, RTn, n0, n1, n2, ph, dm);
+            } else if (ph.dissipation) {
                 const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
                 const double lo = 2.0 * fabs(so.hu0 * n0 + so.hu1 * n1 + so.hu2 * n2) + sP[11 * N3 + own] * nn;
                 const double ln = 2.0 * fabs(sn.hu0 * n0 + sn.hu1 * n1 + sn.hu2 * n2) + cn * nn;
@@ -341,7 +405,7 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             const double wi = ops.winv[side ? N - 1 : 0];
             double* R = sR + l * 5 * N3;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) R[v * N3 + own] += (-E * f[v] - lam * (qo[v] - qn[v])) * wi;
+            for (int v = 0; v < 5; ++v) R[v * N3 + own] += (-E * f[v] - lam * (qo[v] - qn[v]) - 0.5 * dm[v]) * wi;
             double* wf = sWf + (2 * l + side) * 4 * N2 + fi;
             wf[0] = 4.0 * sn.beta * sn.hu0;
             wf[N2] = 4.0 * sn.beta * sn.hu1;

@@ -39,6 +39,9 @@ class Solver:
 
     coords: numpy [K, 3, N, N, N] node coordinates (degree-p mapping at the LGL nodes).
     precision: "fp64" (whole residual in float64) or "fp32" (float32 residual, float64 state).
+    dissipation: True (local Lax-Friedrichs), False (entropy conservative) or "matrix" (Roe-type
+    entropy-stable matrix dissipation; float64 only).
+    volume_flux: "esc" (the paper's ES-C), "kg" (SF-KG) or "dc" (DC); the last two float64 only.
     """
 
     def __init__(self, p, kx, ky, kz, coords, *, gamma=1.4, Pr=0.72, Ma=0.1, Re=0.0, dissipation=True,
@@ -59,7 +62,8 @@ class Solver:
         if coords.shape != (self.K, 3, self.N, self.N, self.N):
             raise ValueError(f"coords must have shape {(self.K, 3, self.N, self.N, self.N)}, got {coords.shape}")
         self.coords = coords
-        st = nat.Setup(p, kx, ky, kz, gamma, Pr, Ma, Re, 1 if dissipation else 0,
+        diss = 2 if dissipation == "matrix" else (1 if dissipation else 0)
+        st = nat.Setup(p, kx, ky, kz, gamma, Pr, Ma, Re, diss,
                        nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32, nat.FLUX[volume_flux])
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
