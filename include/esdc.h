@@ -73,7 +73,13 @@ typedef struct esdc_setup {
     int dissipation;        /* ESDC_DISS_NONE, ESDC_DISS_LLF or ESDC_DISS_MATRIX (below)          */
     int precision;          /* ESDC_PREC_FP64 or ESDC_PREC_FP32                                   */
     int volume_flux;        /* ESDC_FLUX_ESC (the method), ESDC_FLUX_KG or ESDC_FLUX_DC           */
+    double ip_coef;         /* interior-penalty coefficient sigma >= 0 (0: off; below)             */
 } esdc_setup_t;
+
+/* Interior penalty (the IP term of eq. NSL; its constants are in the paper's references).  With
+ * ip_coef = sigma > 0 and mu > 0, every face node adds -(1/P_ii) sigma mu |n_J| / h dq/dw (w_own -
+ * w_nbr), with dq/dw at the averaged state of ESDC_DISS_MATRIX and h = (J_own + J_nbr)/|n_J|; the
+ * term is symmetric in the two sides, conserves, and produces entropy.  Float64 only, no adjoint. */
 
 /*
  * esdc_lgl -- the N = p+1 LGL nodes xi[N] (ascending on [-1, 1]) and quadrature weights w[N]

@@ -18,7 +18,7 @@ Readings of points the paper leaves open (each one is repeated where it is used)
   * inviscid interface term: EC two-point flux plus local Lax-Friedrichs dissipation in the
     conserved variables, lambda = max over both sides of |u.n_J| + c |n_J|.
   * viscous interface terms: BR1 (central) lifting of the entropy-variable jump into the gradient
-    and central viscous interface flux; no interior penalty.
+    and central viscous interface flux; interior penalty optional (default off).
 Parity status: every function below is pinned by tests in tests/test_oracle_*.py except the
 numerical values of the interface-dissipation and viscous-interface readings (only their
 conservation and entropy properties are pinned: "parity unpinned" for those constants).
@@ -557,13 +557,43 @@ def viscous_term(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor) -> torc
     return out
 
 
+
+def interior_penalty(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, coef: float) -> torch.Tensor:
+    """Interior-penalty term IP (eq. NSL; its constants are in the paper's references).  Reading: at
+    every face node -(1/P_ii) coef mu |n_J| / h dq/dw (w_own - w_nbr), with dq/dw at the averaged state
+    of the matrix dissipation and h = (J_own + J_nbr)/|n_J| (the sum of the two elements' normal
+    half-widths), symmetric in the two sides so that the term conserves and produces entropy."""
+    sbp = mesh.sbp
+    qE = q[E]
+    out = torch.zeros_like(qE)
+    wend = float(sbp.w[0])
+    for l in range(3):
+        for side in (0, 1):
+            f = 2 * l + side
+            nbE = mesh.nbr[E, f]
+            qo = face(qE, l, side)
+            qn = face(q[nbE], l, 1 - side)
+            nJ = face(mesh.Ja[E, l], l, side)
+            nn = torch.sqrt(nJ[:, 0] ** 2 + nJ[:, 1] ** 2 + nJ[:, 2] ** 2)
+            h = (face(mesh.J[E].unsqueeze(1), l, side)[:, 0] + face(mesh.J[nbE].unsqueeze(1), l, 1 - side)[:, 0]) / nn
+            ro, uo, po, To = primitives(qo, gas)
+            rn, un_, pn, Tn = primitives(qn, gas)
+            bo, bn = 1.0 / (2.0 * gas.R * To), 1.0 / (2.0 * gas.R * Tn)
+            M = dq_dw(logmean(ro, rn), [0.5 * (uo[d] + un_[d]) for d in range(3)], 0.5 * (ro + rn) / (bo + bn), gas)
+            jw = entropy_variables(qo, gas) - entropy_variables(qn, gas)
+            val = -(coef * gas.mu * nn / h).unsqueeze(1) * torch.einsum("k...ij,kj...->ki...", M, jw)
+            out = _on_face(out, val / wend, l, side)
+    return out
+
 SCHEMES = ("esc", "kg", "dc")
 
 
-def rhs(q, mesh: Mesh, gas: Gas, dissipation=True, elems=None, flux=None, scheme="esc") -> torch.Tensor:
+def rhs(q, mesh: Mesh, gas: Gas, dissipation=True, elems=None, flux=None, scheme="esc",
+        ip_coef: float = 0.0) -> torch.Tensor:
     """dq/dt = J^-1 [-volume + SAT^(I) + viscous + SAT^(V)] on elements `elems` (default all).
     scheme: "esc" (Chandrashekar two-point flux, the paper's ES-C), "kg" (Kennedy-Gruber two-point
-    flux, SF-KG) or "dc" (nodal fluxes differentiated by D, with the central interface flux)."""
+    flux, SF-KG) or "dc" (nodal fluxes differentiated by D, with the central interface flux).
+    ip_coef > 0 adds the interior-penalty term (viscous runs only)."""
     q = torch.as_tensor(q, dtype=F64)
     K = q.shape[0]
     E = torch.arange(K) if elems is None else torch.as_tensor(elems, dtype=torch.long)
@@ -578,6 +608,8 @@ def rhs(q, mesh: Mesh, gas: Gas, dissipation=True, elems=None, flux=None, scheme
         r = volume_term(q[E], mesh.Ja[E], mesh.sbp, gas, flux) + inviscid_sat(q, mesh, gas, E, dissipation, flux)
     if gas.mu > 0.0:
         r = r + viscous_term(q, mesh, gas, E)
+        if ip_coef > 0.0:
+            r = r + interior_penalty(q, mesh, gas, E, ip_coef)
     return r / mesh.J[E].unsqueeze(1)
 
 

@@ -26,7 +26,7 @@ class Setup(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("kx", ctypes.c_int), ("ky", ctypes.c_int), ("kz", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Ma", ctypes.c_double),
                 ("Re", ctypes.c_double), ("dissipation", ctypes.c_int), ("precision", ctypes.c_int),
-                ("volume_flux", ctypes.c_int)]
+                ("volume_flux", ctypes.c_int), ("ip_coef", ctypes.c_double)]
 
 
 class EsdcError(RuntimeError):

@@ -296,8 +296,9 @@ int rk_adaptive_f64(esdc_ctx* c, double* q, double t0, double t_end, double* dt_
 
 int ensure_adjoint(esdc_ctx* c) {
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
-        c->setup.dissipation == ESDC_DISS_MATRIX)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 ES-C contexts with scalar dissipation");
+        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0)
+        return fail(ESDC_ERR_UNSUPPORTED,
+                    "the adjoint is built for float64 ES-C contexts with scalar dissipation and no interior penalty");
     if (c->d_adj_g) return ESDC_OK;
     const size_t N2 = (size_t)c->N * c->N;
     CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
@@ -311,8 +312,9 @@ int ensure_adjoint(esdc_ctx* c) {
 int adjoint_checks(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, void* ws, size_t ws_bytes) {
     if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
-        c->setup.dissipation == ESDC_DISS_MATRIX)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 ES-C contexts with scalar dissipation");
+        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0)
+        return fail(ESDC_ERR_UNSUPPORTED,
+                    "the adjoint is built for float64 ES-C contexts with scalar dissipation and no interior penalty");
     if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
     const size_t need = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");
@@ -398,6 +400,9 @@ static int check_setup(const esdc_setup_t& s) {
         return fail(ESDC_ERR_ARG, "dissipation must be ESDC_DISS_NONE, ESDC_DISS_LLF or ESDC_DISS_MATRIX");
     if (s.dissipation == ESDC_DISS_MATRIX && s.precision != ESDC_PREC_FP64)
         return fail(ESDC_ERR_UNSUPPORTED, "the matrix dissipation is built for float64 only");
+    if (!(s.ip_coef >= 0.0) || !std::isfinite(s.ip_coef)) return fail(ESDC_ERR_ARG, "ip_coef must be finite and >= 0");
+    if (s.ip_coef > 0.0 && s.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "the interior penalty is built for float64 only");
     if (s.precision != ESDC_PREC_FP64 && s.precision != ESDC_PREC_FP32)
         return fail(ESDC_ERR_ARG, "precision must be ESDC_PREC_FP64 or ESDC_PREC_FP32");
     if (s.volume_flux != ESDC_FLUX_ESC && s.volume_flux != ESDC_FLUX_KG && s.volume_flux != ESDC_FLUX_DC)
@@ -474,6 +479,7 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     c->phys.inv_gm1 = 1.0 / (s.gamma - 1.0);
     c->phys.dissipation = s.dissipation;
     c->phys.viscous = mu > 0.0;
+    c->phys.ip_coef = mu > 0.0 ? s.ip_coef : 0.0;
     c->physf.gamma = (float)s.gamma;
     c->physf.R = (float)R;
     c->physf.mu = (float)mu;

@@ -24,7 +24,8 @@ struct Ops {
 struct Phys {
     double gamma, R, mu, kappa;
     double inv_gm1;            // 1/(gamma-1)
-    int dissipation;           // 1: LLF interface dissipation on
+    double ip_coef;            // interior-penalty coefficient (0: off)
+    int dissipation;           // 0 none, 1 local Lax-Friedrichs, 2 matrix
     int viscous;               // mu > 0
 };
 

@@ -136,65 +136,72 @@ __device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Pri
     s.qq = sP[5 * N3 + idx];
 }
 
-// Roe-type entropy-stable interface dissipation D (w_a - w_b) (the matrix alternative to local
-// Lax-Friedrichs).  D = R |Lambda| R^T in the direction n at the averaged state (rho_ln, ubar,
-// p = rho_bar/(2 beta_bar)), with R the eigenvectors of the flux Jacobian scaled so that R R^T = dq/dw.
-// The three eigenvalues u.n share an eigenspace, so D = |u.n| dq/dw + s (|u.n - a|n|| - |u.n|) r1 r1^T
-// + s (|u.n + a|n|| - |u.n|) r5 r5^T, r1,5 = (1, u -+ a nhat, H -+ a u.nhat), s = rho/(2 gamma).
-// The entropy-variable jump takes its logarithms as log(p_a/p_b) and log(rho_a/rho_b).
-__device__ __forceinline__ void matrix_dissipation(const Prim& a, double RTa, const Prim& b, double RTb, double n0,
-                                                   double n1, double n2, const Phys& ph, double dm[5]) {
+// Face quantities shared by the matrix dissipation and the interior penalty: the jump of the entropy
+// variables w = ((gamma - s)/(gamma - 1) - beta |u|^2, 2 beta u, -2 beta) across the face (its
+// logarithms taken as log(p_a/p_b) and log(rho_a/rho_b)), and dq/dw times that jump at the averaged
+// state (rho_ln, ubar, p = rho_bar/(2 beta_bar)), from which a, H and rho E follow.
+struct FaceAvg {
+    double rho, u0, u1, u2, p, c2, H, E, ujw;
+};
+
+__device__ __forceinline__ void face_jump_avg(const Prim& a, double RTa, const Prim& b, double RTb, const Phys& ph,
+                                              double jw[5], double r[5], FaceAvg& st) {
     const double ra = 2.0 * a.hr, rb = 2.0 * b.hr;
     const double pa = ra * RTa, pb = rb * RTb;
-    // jump of the entropy variables w = ((gamma - s)/(gamma - 1) - beta |u|^2, 2 beta u, -2 beta)
     const double ds = log(pa / pb) - ph.gamma * log(ra / rb);
-    double jw[5];
     jw[0] = -ds * ph.inv_gm1 - 4.0 * (a.beta * a.qq - b.beta * b.qq);
     jw[1] = 4.0 * (a.beta * a.hu0 - b.beta * b.hu0);
     jw[2] = 4.0 * (a.beta * a.hu1 - b.beta * b.hu1);
     jw[3] = 4.0 * (a.beta * a.hu2 - b.beta * b.hu2);
     jw[4] = -2.0 * (a.beta - b.beta);
-    // averaged state
     const double sh = a.hr + b.hr;
     const double fr = (a.hr - b.hr) * rcp_newton1(sh);
     const double ur = fr * fr;
-    double rho;
-    if (small_jump(ur)) rho = sh * fma(ur, fma(ur, fma(ur, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
-    else rho = 2.0 * (a.hr - b.hr) / log(a.hr / b.hr);
-    const double p = sh * rcp_newton2(a.beta + b.beta);
-    const double u0 = a.hu0 + b.hu0, u1 = a.hu1 + b.hu1, u2 = a.hu2 + b.hu2;
-    const double usq = u0 * u0 + u1 * u1 + u2 * u2;
-    const double c2 = ph.gamma * p / rho;
-    const double c = sqrt(c2);
-    const double H = fma(c2, ph.inv_gm1, 0.5 * usq);
-    const double E = fma(p, ph.inv_gm1, 0.5 * rho * usq);
+    if (small_jump(ur)) st.rho = sh * fma(ur, fma(ur, fma(ur, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
+    else st.rho = 2.0 * (a.hr - b.hr) / log(a.hr / b.hr);
+    st.p = sh * rcp_newton2(a.beta + b.beta);
+    st.u0 = a.hu0 + b.hu0;
+    st.u1 = a.hu1 + b.hu1;
+    st.u2 = a.hu2 + b.hu2;
+    const double usq = st.u0 * st.u0 + st.u1 * st.u1 + st.u2 * st.u2;
+    st.c2 = ph.gamma * st.p / st.rho;
+    st.H = fma(st.c2, ph.inv_gm1, 0.5 * usq);
+    st.E = fma(st.p, ph.inv_gm1, 0.5 * st.rho * usq);
+    // dq/dw jw
+    const double m0 = st.rho * st.u0, m1 = st.rho * st.u1, m2 = st.rho * st.u2;
+    st.ujw = st.u0 * jw[1] + st.u1 * jw[2] + st.u2 * jw[3];
+    const double t = jw[0] + st.ujw + st.H * jw[4];
+    r[0] = st.rho * jw[0] + m0 * jw[1] + m1 * jw[2] + m2 * jw[3] + st.E * jw[4];
+    r[1] = fma(m0, t, st.p * jw[1]);
+    r[2] = fma(m1, t, st.p * jw[2]);
+    r[3] = fma(m2, t, st.p * jw[3]);
+    r[4] = st.E * jw[0] + st.rho * st.H * st.ujw + (st.rho * st.H * st.H - st.c2 * st.p * ph.inv_gm1) * jw[4];
+}
+
+// Roe-type entropy-stable interface dissipation D (w_a - w_b) (the matrix alternative to local
+// Lax-Friedrichs).  D = R |Lambda| R^T in the direction n at the averaged state, with R the
+// eigenvectors of the flux Jacobian scaled so that R R^T = dq/dw.  The three eigenvalues u.n share an
+// eigenspace, so D = |u.n| dq/dw + s (|u.n - a|n|| - |u.n|) r1 r1^T + s (|u.n + a|n|| - |u.n|) r5 r5^T,
+// r1,5 = (1, u -+ a nhat, H -+ a u.nhat), s = rho/(2 gamma).  r = dq/dw jw from face_jump_avg.
+__device__ __forceinline__ void matrix_dissipation(const FaceAvg& st, const double jw[5], const double r[5],
+                                                   double n0, double n1, double n2, const Phys& ph, double dm[5]) {
+    const double c = sqrt(st.c2);
     const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
     const double inn = 1.0 / nn;
-    const double un = u0 * n0 + u1 * n1 + u2 * n2;
+    const double un = st.u0 * n0 + st.u1 * n1 + st.u2 * n2;
     const double unh = un * inn;
     const double l2 = fabs(un), l1 = fabs(un - c * nn), l5 = fabs(un + c * nn);
-    // dq/dw jw
-    const double m0 = rho * u0, m1 = rho * u1, m2 = rho * u2;
-    const double ujw = u0 * jw[1] + u1 * jw[2] + u2 * jw[3];
-    const double t = jw[0] + ujw + H * jw[4];
-    double r[5];
-    r[0] = rho * jw[0] + m0 * jw[1] + m1 * jw[2] + m2 * jw[3] + E * jw[4];
-    r[1] = fma(m0, t, p * jw[1]);
-    r[2] = fma(m1, t, p * jw[2]);
-    r[3] = fma(m2, t, p * jw[3]);
-    r[4] = E * jw[0] + rho * H * ujw + (rho * H * H - c2 * p * ph.inv_gm1) * jw[4];
-    // acoustic eigenvector corrections
     const double cn0 = c * n0 * inn, cn1 = c * n1 * inn, cn2 = c * n2 * inn;
     const double njw = cn0 * jw[1] + cn1 * jw[2] + cn2 * jw[3];
-    const double c1 = jw[0] + ujw - njw + (H - c * unh) * jw[4];
-    const double c5 = jw[0] + ujw + njw + (H + c * unh) * jw[4];
-    const double sc = rho / (2.0 * ph.gamma);
+    const double c1 = jw[0] + st.ujw - njw + (st.H - c * unh) * jw[4];
+    const double c5 = jw[0] + st.ujw + njw + (st.H + c * unh) * jw[4];
+    const double sc = st.rho / (2.0 * ph.gamma);
     const double k1 = sc * (l1 - l2) * c1, k5 = sc * (l5 - l2) * c5;
     dm[0] = l2 * r[0] + k1 + k5;
-    dm[1] = l2 * r[1] + k1 * (u0 - cn0) + k5 * (u0 + cn0);
-    dm[2] = l2 * r[2] + k1 * (u1 - cn1) + k5 * (u1 + cn1);
-    dm[3] = l2 * r[3] + k1 * (u2 - cn2) + k5 * (u2 + cn2);
-    dm[4] = l2 * r[4] + k1 * (H - c * unh) + k5 * (H + c * unh);
+    dm[1] = l2 * r[1] + k1 * (st.u0 - cn0) + k5 * (st.u0 + cn0);
+    dm[2] = l2 * r[2] + k1 * (st.u1 - cn1) + k5 * (st.u1 + cn1);
+    dm[3] = l2 * r[3] + k1 * (st.u2 - cn2) + k5 * (st.u2 + cn2);
+    dm[4] = l2 * r[4] + k1 * (st.H - c * unh) + k5 * (st.H + c * unh);
 }
 
 // Volume-flux variants of the kernel (the paper's comparison, Sec. 4): the entropy-stable
@@ -235,7 +242,9 @@ __device__ __forceinline__ void euler_flux_prim(const Prim& s, double RT, double
     f[4] = f1 * fma(ph.gamma * ph.inv_gm1, RT, 2.0 * s.qq);
 }
 
-template <int N, int VF>
+// XF: the face phase also evaluates the matrix dissipation and the interior penalty (compiled only
+// into the instantiations of contexts that use them, so the default kernel carries none of it)
+template <int N, int VF, bool XF>
 __global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::MINB)
 rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const double* __restrict__ geom,
              const int32_t* __restrict__ nbr, double* __restrict__ trace, int64_t K, const Ops ops,
@@ -393,10 +402,25 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             }
             const double E = side ? 1.0 : -1.0;
             double lam = 0.0;
-            double dm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-            if (ph.dissipation == 2) {
-                matrix_dissipation(so, sP[10 * N3 + own], sn, RTn, n0, n1, n2, ph, dm);
-            } else if (ph.dissipation) {
+            double dm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};      // 1/2 D (w_own - w_nbr) + interior penalty
+            if constexpr (XF) {
+                double jw[5], r[5];
+                FaceAvg fa;
+                face_jump_avg(so, sP[10 * N3 + own], sn, RTn, ph, jw, r, fa);
+                if (ph.dissipation == 2) {
+                    matrix_dissipation(fa, jw, r, n0, n1, n2, ph, dm);
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) dm[v] *= 0.5;
+                }
+                if (ph.ip_coef > 0.0) {
+                    // sigma mu |n_J| / h with h = (J_own + J_nbr)/|n_J|
+                    const double nsq = n0 * n0 + n1 * n1 + n2 * n2;
+                    const double cip = ph.ip_coef * ph.mu * nsq / (sG[own] + geom[nb * 10 * N3 + nbn]);
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) dm[v] = fma(cip, r[v], dm[v]);
+                }
+            }
+            if (ph.dissipation == 1) {
                 const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
                 const double lo = 2.0 * fabs(so.hu0 * n0 + so.hu1 * n1 + so.hu2 * n2) + sP[11 * N3 + own] * nn;
                 const double ln = 2.0 * fabs(sn.hu0 * n0 + sn.hu1 * n1 + sn.hu2 * n2) + cn * nn;
@@ -405,7 +429,7 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             const double wi = ops.winv[side ? N - 1 : 0];
             double* R = sR + l * 5 * N3;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) R[v * N3 + own] += (-E * f[v] - lam * (qo[v] - qn[v]) - 0.5 * dm[v]) * wi;
+            for (int v = 0; v < 5; ++v) R[v * N3 + own] += (-E * f[v] - lam * (qo[v] - qn[v]) - dm[v]) * wi;
             double* wf = sWf + (2 * l + side) * 4 * N2 + fi;
             wf[0] = 4.0 * sn.beta * sn.hu0;
             wf[N2] = 4.0 * sn.beta * sn.hu1;
@@ -524,14 +548,14 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
 // BR1 viscous interface term on face nodes, direction by direction (edge nodes see up to 3 faces).
 // ---- host-side launchers
 
-template <int N, int VF>
+template <int N, int VF, bool XF>
 cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s,
                          cudaEvent_t* ev) {
     using C = Cfg<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     if (ev) cudaEventRecord(ev[0], s);
-    rhs_main_f64<N, VF><<<grid, C::THREADS, smem, s>>>(q, dqdt, c->d_geom, c->d_nbr, (double*)c->d_trace, c->K,
+    rhs_main_f64<N, VF, XF><<<grid, C::THREADS, smem, s>>>(q, dqdt, c->d_geom, c->d_nbr, (double*)c->d_trace, c->K,
                                                        c->ops, c->phys);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
@@ -544,27 +568,40 @@ cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaS
     return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t prepare_n(int vf) {
+template <int N, bool XF>
+cudaError_t prepare_xf(int vf) {
     using C = Cfg<N>;
     const int smem = (int)(C::EPB * C::SM * sizeof(double));
     constexpr cudaFuncAttribute kAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     switch (vf) {
-        case kFluxESC: return cudaFuncSetAttribute(rhs_main_f64<N, kFluxESC>, kAttr, smem);
-        case kFluxKG: return cudaFuncSetAttribute(rhs_main_f64<N, kFluxKG>, kAttr, smem);
-        case kFluxDC: return cudaFuncSetAttribute(rhs_main_f64<N, kFluxDC>, kAttr, smem);
+        case kFluxESC: return cudaFuncSetAttribute(rhs_main_f64<N, kFluxESC, XF>, kAttr, smem);
+        case kFluxKG: return cudaFuncSetAttribute(rhs_main_f64<N, kFluxKG, XF>, kAttr, smem);
+        case kFluxDC: return cudaFuncSetAttribute(rhs_main_f64<N, kFluxDC, XF>, kAttr, smem);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool extra_face_terms(const esdc_ctx* c) { return c->phys.dissipation == 2 || c->phys.ip_coef > 0.0; }
+
+template <int N>
+cudaError_t prepare_n(const esdc_ctx* c) {
+    const int vf = c->setup.volume_flux;
+    return extra_face_terms(c) ? prepare_xf<N, true>(vf) : prepare_xf<N, false>(vf);
+}
+
+template <int N, bool XF>
+cudaError_t launch_vf_xf(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev) {
+    switch (c->setup.volume_flux) {
+        case kFluxESC: return launch_rhs_n<N, kFluxESC, XF>(c, q, dqdt, s, ev);
+        case kFluxKG: return launch_rhs_n<N, kFluxKG, XF>(c, q, dqdt, s, ev);
+        case kFluxDC: return launch_rhs_n<N, kFluxDC, XF>(c, q, dqdt, s, ev);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int N>
 cudaError_t launch_vf(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev) {
-    switch (c->setup.volume_flux) {
-        case kFluxESC: return launch_rhs_n<N, kFluxESC>(c, q, dqdt, s, ev);
-        case kFluxKG: return launch_rhs_n<N, kFluxKG>(c, q, dqdt, s, ev);
-        case kFluxDC: return launch_rhs_n<N, kFluxDC>(c, q, dqdt, s, ev);
-        default: return cudaErrorInvalidValue;
-    }
+    return extra_face_terms(c) ? launch_vf_xf<N, true>(c, q, dqdt, s, ev) : launch_vf_xf<N, false>(c, q, dqdt, s, ev);
 }
 
 }  // namespace
@@ -572,13 +609,13 @@ cudaError_t launch_vf(const esdc_ctx* c, const double* q, double* dqdt, cudaStre
 // Opt the fused kernel into more than 48 KB of dynamic shared memory (on the current device).
 cudaError_t prepare_rhs_f64(const esdc_ctx* c) {
     switch (c->N) {
-        case 2: return prepare_n<2>(c->setup.volume_flux);
-        case 3: return prepare_n<3>(c->setup.volume_flux);
-        case 4: return prepare_n<4>(c->setup.volume_flux);
-        case 5: return prepare_n<5>(c->setup.volume_flux);
-        case 6: return prepare_n<6>(c->setup.volume_flux);
-        case 7: return prepare_n<7>(c->setup.volume_flux);
-        case 8: return prepare_n<8>(c->setup.volume_flux);
+        case 2: return prepare_n<2>(c);
+        case 3: return prepare_n<3>(c);
+        case 4: return prepare_n<4>(c);
+        case 5: return prepare_n<5>(c);
+        case 6: return prepare_n<6>(c);
+        case 7: return prepare_n<7>(c);
+        case 8: return prepare_n<8>(c);
         default: return cudaErrorInvalidValue;
     }
 }

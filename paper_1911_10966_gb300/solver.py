@@ -42,10 +42,11 @@ class Solver:
     dissipation: True (local Lax-Friedrichs), False (entropy conservative) or "matrix" (Roe-type
     entropy-stable matrix dissipation; float64 only).
     volume_flux: "esc" (the paper's ES-C), "kg" (SF-KG) or "dc" (DC); the last two float64 only.
+    ip_coef: interior-penalty coefficient (0: off; float64 only).
     """
 
     def __init__(self, p, kx, ky, kz, coords, *, gamma=1.4, Pr=0.72, Ma=0.1, Re=0.0, dissipation=True,
-                 precision="fp64", volume_flux="esc", device=None):
+                 precision="fp64", volume_flux="esc", ip_coef=0.0, device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU implementation exists)")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
@@ -64,7 +65,8 @@ class Solver:
         self.coords = coords
         diss = 2 if dissipation == "matrix" else (1 if dissipation else 0)
         st = nat.Setup(p, kx, ky, kz, gamma, Pr, Ma, Re, diss,
-                       nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32, nat.FLUX[volume_flux])
+                       nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32, nat.FLUX[volume_flux],
+                       float(ip_coef))
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             nat.check(nat.lib().esdc_create(ctypes.byref(st), coords.ctypes.data, ctypes.byref(self._ctx)),

@@ -79,3 +79,25 @@ def test_matrix_dissipation_scheme_conserves_preserves_freestream_and_produces_l
     scale = float((PJ * (O.entropy_variables(q, gas) * r).sum(dim=1).abs()).sum())
     assert abs(dS_0) <= 1e-12 * scale
     assert dS_l < dS_m < -1e-8 * scale
+
+
+def test_interior_penalty_conserves_produces_entropy_and_is_linear():
+    """The interior-penalty term: global conservation, entropy production (dq/dw is positive
+    definite and the term is symmetric in the two sides), linearity in its coefficient, no effect on
+    a freestream, and no term without viscosity."""
+    gas = O.Gas.from_mach(0.3, 200.0)
+    mesh, x = _mesh(3, (3, 2, 2), 0.1, 4)
+    q = torch.tensor(I.perturb(I.taylor_green(x, Ma=0.3), seed=2, rel=0.05))
+    r0 = O.rhs(q, mesh, gas)
+    d1 = O.rhs(q, mesh, gas, ip_coef=1.0) - r0
+    d3 = O.rhs(q, mesh, gas, ip_coef=3.0) - r0
+    PJ = O.quadrature_weights(mesh)
+    for v in range(5):
+        assert abs(float((PJ * d1[:, v]).sum())) <= 1e-12 * (float((PJ * d1[:, v].abs()).sum()) + 1e-300)
+    assert torch.allclose(d3, 3.0 * d1, rtol=1e-9, atol=1e-12 * float(d1.abs().max()))
+    w = O.entropy_variables(q, gas)
+    assert float((PJ * (w * d1).sum(dim=1)).sum()) < 0.0
+    qf = torch.tensor(I.freestream(x, Ma=0.3))
+    assert float((O.rhs(qf, mesh, gas, ip_coef=2.0) - O.rhs(qf, mesh, gas)).abs().max()) == 0.0
+    inv = O.Gas.from_mach(0.3, 0.0)
+    assert torch.equal(O.rhs(q, mesh, inv, ip_coef=2.0), O.rhs(q, mesh, inv))
