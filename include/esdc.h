@@ -74,6 +74,8 @@ typedef struct esdc_setup {
     int precision;          /* ESDC_PREC_FP64 or ESDC_PREC_FP32                                   */
     int volume_flux;        /* ESDC_FLUX_ESC (the method), ESDC_FLUX_KG or ESDC_FLUX_DC           */
     double ip_coef;         /* interior-penalty coefficient sigma >= 0 (0: off; below)             */
+    int bounded;            /* bit l (l = 0, 1, 2) set: the outer faces normal to xi_l are
+                               boundaries with Dirichlet data (esdc_set_exterior); 0: periodic      */
 } esdc_setup_t;
 
 /* Interior penalty (the IP term of eq. NSL; its constants are in the paper's references).  With
@@ -215,6 +217,40 @@ int esdc_budgets(esdc_ctx* ctx, const double* q_dev, const void* dqdt_dev, doubl
  * ordered).  Errors: ESDC_ERR_ARG, ESDC_ERR_CUDA (launch).
  */
 int esdc_budgets_async(esdc_ctx* ctx, const double* q_dev, const void* dqdt_dev, double* out_dev, void* stream);
+
+/*
+ * esdc_set_exterior -- the exterior state of the boundary faces of a bounded box (setup.bounded != 0):
+ * a [K][5][N^3] float64 device array in the layout of q, read only at the boundary face nodes of
+ * each element, where it is the state on the far side of the face.  With it the interface SAT of a
+ * boundary face is the interior one with that state as the neighbour: the two-point flux and the
+ * dissipation of Sec. 3-4 impose the Dirichlet data weakly, the gradient lift (SAT^theta) uses its
+ * entropy variables, and the viscous interface term SAT^(V) is zero (the exterior viscous flux is
+ * read as the interior one; the paper's boundary SATs are in its references).  The pointer is
+ * kept, not copied: the array must stay valid while the context evaluates residuals.  NULL clears
+ * it.  A residual of a bounded box without an exterior state fails with ESDC_ERR_ARG.
+ * Float64 contexts only (float32 contexts cannot be bounded).
+ */
+int esdc_set_exterior(esdc_ctx* ctx, const double* q_ext_dev);
+
+/*
+ * esdc_set_source -- a source term added to dq/dt by every residual of the context, e.g. the
+ * manufactured-solution source of Sec. 5.1 (esdc_mms_fields).  [K][5][N^3] float64 device array,
+ * kept (not copied) until replaced; NULL clears it.  Float64 contexts only (ESDC_ERR_UNSUPPORTED).
+ */
+int esdc_set_source(esdc_ctx* ctx, const double* source_dev);
+
+/*
+ * esdc_mms_fields -- the manufactured solution of the paper's viscous error-vs-cost study (Sec. 5.1,
+ * eq. mms) and its source term, on the host.  Each of rho, u1, u2, u3, p is
+ * phi0 + sum_k phi_k trig_k(alpha_k pi x_k / L) with trig_k = sin or cos as in eq. mms, from
+ * table[5][7] = (phi0, phi_x1, phi_x2, phi_x3, alpha_x1, alpha_x2, alpha_x3) per row (already in the
+ * library's units: rho_inf = T_inf = 1, R = 1/(gamma Ma^2)).  At n points x_host[n][3] it writes the
+ * conserved state q_host[n][5] and the source s_host[n][5] = div(F^I - F^V) of that field (analytic
+ * derivatives; mu = 1/Re, kappa = mu gamma R/((gamma - 1) Pr)), either output nullable.  Host only,
+ * no GPU.  Errors: ESDC_ERR_ARG.
+ */
+int esdc_mms_fields(double gamma, double Ma, double Re, double Pr, double L, const double* table, int64_t n,
+                    const double* x_host, double* q_host, double* s_host);
 
 /*
  * esdc_dt_cfl -- dt = cfl * min(h/(N^2 max(|u|+c)), h^2/(N^4 nu)), nu = max(4/3, gamma/Pr) mu/rho_min,

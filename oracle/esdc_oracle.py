@@ -163,15 +163,21 @@ def metric_terms(x: torch.Tensor, D: torch.Tensor):
     return J, Ja
 
 
-def box_neighbours(kx: int, ky: int, kz: int) -> torch.Tensor:
-    """Face neighbours of a fully periodic structured box, element e = ex + kx*(ey + ky*ez)."""
+def box_neighbours(kx: int, ky: int, kz: int, bounded=(False, False, False)) -> torch.Tensor:
+    """Face neighbours of a structured box, element e = ex + kx*(ey + ky*ez): periodic in every
+    direction except those flagged in `bounded`, whose outer faces get neighbour -1 (a boundary)."""
     K = kx * ky * kz
     e = torch.arange(K)
     ex, ey, ez = e % kx, (e // kx) % ky, e // (kx * ky)
     idx = lambda a, b, c: (a % kx) + kx * ((b % ky) + ky * (c % kz))
-    return torch.stack([idx(ex - 1, ey, ez), idx(ex + 1, ey, ez),
-                        idx(ex, ey - 1, ez), idx(ex, ey + 1, ez),
-                        idx(ex, ey, ez - 1), idx(ex, ey, ez + 1)], dim=1)
+    nb = torch.stack([idx(ex - 1, ey, ez), idx(ex + 1, ey, ez),
+                      idx(ex, ey - 1, ez), idx(ex, ey + 1, ez),
+                      idx(ex, ey, ez - 1), idx(ex, ey, ez + 1)], dim=1)
+    for l, (c, k) in enumerate(((ex, kx), (ey, ky), (ez, kz))):
+        if bounded[l]:
+            nb[:, 2 * l] = torch.where(c == 0, -1, nb[:, 2 * l])
+            nb[:, 2 * l + 1] = torch.where(c == k - 1, -1, nb[:, 2 * l + 1])
+    return nb
 
 
 def smallest_edge(x: torch.Tensor) -> float:
@@ -188,11 +194,26 @@ def smallest_edge(x: torch.Tensor) -> float:
     return float(torch.stack(lens).min())
 
 
-def make_mesh(p: int, x, kx: int, ky: int, kz: int) -> Mesh:
+def make_mesh(p: int, x, kx: int, ky: int, kz: int, bounded=(False, False, False)) -> Mesh:
     sbp = sbp_operator(p)
     x = torch.as_tensor(x, dtype=F64)
     J, Ja = metric_terms(x, sbp.D)
-    return Mesh(sbp, x, J, Ja, box_neighbours(kx, ky, kz), smallest_edge(x))
+    return Mesh(sbp, x, J, Ja, box_neighbours(kx, ky, kz, bounded), smallest_edge(x))
+
+
+def nbr_face(fn, q: torch.Tensor, mesh: Mesh, E: torch.Tensor, l: int, side: int, q_ext=None) -> torch.Tensor:
+    """fn(state) on the neighbour side of face (l, side) of elements E, as seen from E's face nodes.
+    On a boundary face (neighbour -1) the neighbour side is the exterior state q_ext at E's own face
+    nodes (the Dirichlet data of the boundary SAT)."""
+    nb = mesh.nbr[E, 2 * l + side]
+    vals = face(fn(q[nb.clamp(min=0)]), l, 1 - side)
+    if bool((nb < 0).any()):
+        if q_ext is None:
+            raise ValueError("boundary faces need an exterior state")
+        ext = face(fn(torch.as_tensor(q_ext, dtype=F64)[E]), l, side)
+        shape = (-1,) + (1,) * (vals.dim() - 1)
+        vals = torch.where((nb < 0).view(shape), ext, vals)
+    return vals
 
 
 def make_submesh(p: int, x, nbr: torch.Tensor, elems):
@@ -459,7 +480,7 @@ def dc_volume_term(q: torch.Tensor, Ja: torch.Tensor, sbp: SBP, gas: Gas) -> tor
 
 
 def inviscid_sat(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, dissipation=True,
-                 flux=None) -> torch.Tensor:
+                 flux=None, q_ext=None) -> torch.Tensor:
     """SAT^(I) on elements E at every face node: -(1/P_ii) E_ii [f*(own, nbr) - f(own)].n_J minus
     (1/P_ii) lambda/2 (q_own - q_nbr) when dissipation is True (local Lax-Friedrichs reading), or
     minus (1/P_ii) D (w_own - w_nbr)/2 with the Roe-type matrix D when dissipation == "matrix"."""
@@ -472,7 +493,7 @@ def inviscid_sat(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, dissipa
         for side in (0, 1):
             f = 2 * l + side
             qo = face(qE, l, side)
-            qn = face(q[mesh.nbr[E, f]], l, 1 - side)
+            qn = nbr_face(lambda x: x, q, mesh, E, l, side, q_ext)
             nJ = face(mesh.Ja[E, l], l, side)
             n = [nJ[:, m] for m in range(3)]
             sgn = -1.0 if side == 0 else 1.0
@@ -501,7 +522,7 @@ def inviscid_sat(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, dissipa
     return out
 
 
-def entropy_gradient(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor) -> torch.Tensor:
+def entropy_gradient(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, q_ext=None) -> torch.Tensor:
     """theta_a = D_a w + SAT^theta (eq. NSL), with the BR1 lift (1/P_ii) E_ii (w_nbr - w_own)/2 on
     the faces normal to a.  Returns [|E|, 3 (a), 5, N, N, N]."""
     sbp = mesh.sbp
@@ -512,7 +533,7 @@ def entropy_gradient(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor) -> 
         t = dxi(wE, a, sbp.D)
         for side in (0, 1):
             wo = face(wE, a, side)
-            wn = face(entropy_variables(q[mesh.nbr[E, 2 * a + side]], gas), a, 1 - side)
+            wn = nbr_face(lambda x: entropy_variables(x, gas), q, mesh, E, a, side, q_ext)
             sgn = -1.0 if side == 0 else 1.0
             t = _on_face(t, sgn * 0.5 * (wn - wo) / wend, a, side)
         th.append(t)
@@ -525,10 +546,10 @@ def physical_gradient(theta: torch.Tensor, J: torch.Tensor, Ja: torch.Tensor) ->
                         for m in range(3)], dim=1)
 
 
-def contravariant_viscous_flux(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor):
+def contravariant_viscous_flux(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, q_ext=None):
     """Ftilde_l = sum_m Ja[l][m] F^V_m = sum_a Chat_la theta_a (eq. Chatij): [|E|, 3, 5, N, N, N].
     Also returns the physical gradient g used to build it."""
-    th = entropy_gradient(q, mesh, gas, E)
+    th = entropy_gradient(q, mesh, gas, E, q_ext)
     g = physical_gradient(th, mesh.J[E], mesh.Ja[E])
     FV = viscous_flux(q[E], g, gas)
     Ja = mesh.Ja[E]
@@ -536,29 +557,34 @@ def contravariant_viscous_flux(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.T
     return Ft, g
 
 
-def viscous_term(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor) -> torch.Tensor:
+def viscous_term(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, q_ext=None) -> torch.Tensor:
     """sum_l D_l Ftilde_l + SAT^(V), SAT^(V) = (1/P_ii) E_ii (Ftilde_l,nbr - Ftilde_l,own)/2 on the
     xi_l faces (eq. MacroForm / eq. NSL with the BR1 reading; interior penalty off)."""
     sbp = mesh.sbp
     K = q.shape[0]
     E1 = torch.unique(torch.cat([E, mesh.nbr[E].reshape(-1)]))
+    E1 = E1[E1 >= 0]
     pos = torch.full((K,), -1, dtype=torch.long)
     pos[E1] = torch.arange(E1.numel())
-    Ft, _ = contravariant_viscous_flux(q, mesh, gas, E1)
+    Ft, _ = contravariant_viscous_flux(q, mesh, gas, E1, q_ext)
     own = Ft[pos[E]]
     wend = float(sbp.w[0])
     out = sum(dxi(own[:, l], l, sbp.D) for l in range(3))
     for l in range(3):
         for side in (0, 1):
             fo = face(own[:, l], l, side)
-            fn = face(Ft[pos[mesh.nbr[E, 2 * l + side]], l], l, 1 - side)
+            nb = mesh.nbr[E, 2 * l + side]
+            fn = face(Ft[pos[nb.clamp(min=0)], l], l, 1 - side)
+            # boundary faces (reading): the exterior viscous flux is the interior one, no SAT^(V)
+            fn = torch.where((nb < 0).view((-1,) + (1,) * (fn.dim() - 1)), fo, fn)
             sgn = -1.0 if side == 0 else 1.0
             out = _on_face(out, sgn * 0.5 * (fn - fo) / wend, l, side)
     return out
 
 
 
-def interior_penalty(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, coef: float) -> torch.Tensor:
+def interior_penalty(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, coef: float,
+                     q_ext=None) -> torch.Tensor:
     """Interior-penalty term IP (eq. NSL; its constants are in the paper's references).  Reading: at
     every face node -(1/P_ii) coef mu |n_J| / h dq/dw (w_own - w_nbr), with dq/dw at the averaged state
     of the matrix dissipation and h = (J_own + J_nbr)/|n_J| (the sum of the two elements' normal
@@ -570,12 +596,14 @@ def interior_penalty(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, coe
     for l in range(3):
         for side in (0, 1):
             f = 2 * l + side
-            nbE = mesh.nbr[E, f]
             qo = face(qE, l, side)
-            qn = face(q[nbE], l, 1 - side)
+            qn = nbr_face(lambda x: x, q, mesh, E, l, side, q_ext)
             nJ = face(mesh.Ja[E, l], l, side)
             nn = torch.sqrt(nJ[:, 0] ** 2 + nJ[:, 1] ** 2 + nJ[:, 2] ** 2)
-            h = (face(mesh.J[E].unsqueeze(1), l, side)[:, 0] + face(mesh.J[nbE].unsqueeze(1), l, 1 - side)[:, 0]) / nn
+            # on a boundary face the exterior Jacobian is read as the interior one
+            Jo = face(mesh.J[E].unsqueeze(1), l, side)[:, 0]
+            Jn = nbr_face(lambda x: x, mesh.J.unsqueeze(1), mesh, E, l, side, mesh.J.unsqueeze(1))[:, 0]
+            h = (Jo + Jn) / nn
             ro, uo, po, To = primitives(qo, gas)
             rn, un_, pn, Tn = primitives(qn, gas)
             bo, bn = 1.0 / (2.0 * gas.R * To), 1.0 / (2.0 * gas.R * Tn)
@@ -585,32 +613,67 @@ def interior_penalty(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, coe
             out = _on_face(out, val / wend, l, side)
     return out
 
+
+def manufactured_source(prim_fn, x, gas: Gas) -> torch.Tensor:
+    """Source of the method of manufactured solutions (Sec. 5.1): S = div(F^I - F^V) of the exact
+    field, so that dq/dt = R(q) + S is steady at the exact solution.  prim_fn(x1, x2, x3) returns
+    (rho, [u1, u2, u3], p) as differentiable torch functions of the coordinates; the derivatives are
+    taken by autograd (first derivatives for the entropy-variable gradient of F^V, second for the
+    divergence).  x: [K, 3, N, N, N]; returns [K, 5, N, N, N]."""
+    x = torch.as_tensor(x, dtype=F64)
+    shape = x[:, 0].shape
+    xs = [x[:, d].reshape(-1).clone().requires_grad_(True) for d in range(3)]
+    rho, u, p = prim_fn(*xs)
+    E = p / (gas.gamma - 1.0) + 0.5 * rho * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
+    q = torch.stack([rho, rho * u[0], rho * u[1], rho * u[2], E], dim=1)
+    ones = torch.ones_like(rho)
+    zero = torch.zeros_like(rho)
+    Fi = torch.stack([euler_flux_n(q, [ones if m == d else zero for d in range(3)], gas) for m in range(3)], dim=1)
+    w = entropy_variables(q, gas)
+    g = torch.zeros(q.shape[0], 3, 5, dtype=F64)
+    for v in range(5):
+        gv = torch.autograd.grad(w[:, v].sum(), xs, create_graph=True)
+        for m in range(3):
+            g[:, m, v] = gv[m]
+    F = Fi - viscous_flux(q, g, gas)                      # [M, 3 (m), 5]
+    S = torch.zeros(q.shape[0], 5, dtype=F64)
+    for v in range(5):
+        for m in range(3):
+            S[:, v] += torch.autograd.grad(F[:, m, v].sum(), xs[m], retain_graph=True)[0]
+    return S.detach().reshape(shape[0], *shape[1:], 5).movedim(-1, 1).contiguous()
+
 SCHEMES = ("esc", "kg", "dc")
 
 
 def rhs(q, mesh: Mesh, gas: Gas, dissipation=True, elems=None, flux=None, scheme="esc",
-        ip_coef: float = 0.0) -> torch.Tensor:
+        ip_coef: float = 0.0, q_ext=None, source=None) -> torch.Tensor:
     """dq/dt = J^-1 [-volume + SAT^(I) + viscous + SAT^(V)] on elements `elems` (default all).
     scheme: "esc" (Chandrashekar two-point flux, the paper's ES-C), "kg" (Kennedy-Gruber two-point
     flux, SF-KG) or "dc" (nodal fluxes differentiated by D, with the central interface flux).
-    ip_coef > 0 adds the interior-penalty term (viscous runs only)."""
+    ip_coef > 0 adds the interior-penalty term (viscous runs only).  On a mesh with boundary faces,
+    q_ext (same layout as q) holds the exterior (Dirichlet) state read at the boundary face nodes; a
+    source (same layout) is added to dq/dt."""
     q = torch.as_tensor(q, dtype=F64)
     K = q.shape[0]
     E = torch.arange(K) if elems is None else torch.as_tensor(elems, dtype=torch.long)
     if scheme == "dc":
         r = dc_volume_term(q[E], mesh.Ja[E], mesh.sbp, gas) + inviscid_sat(q, mesh, gas, E, dissipation,
-                                                                           central_flux_n)
+                                                                           central_flux_n, q_ext)
     else:
         if scheme == "kg":
             flux = kg_flux_n
         elif scheme != "esc":
             raise ValueError(scheme)
-        r = volume_term(q[E], mesh.Ja[E], mesh.sbp, gas, flux) + inviscid_sat(q, mesh, gas, E, dissipation, flux)
+        r = volume_term(q[E], mesh.Ja[E], mesh.sbp, gas, flux) + inviscid_sat(q, mesh, gas, E, dissipation, flux,
+                                                                             q_ext)
     if gas.mu > 0.0:
-        r = r + viscous_term(q, mesh, gas, E)
+        r = r + viscous_term(q, mesh, gas, E, q_ext)
         if ip_coef > 0.0:
-            r = r + interior_penalty(q, mesh, gas, E, ip_coef)
-    return r / mesh.J[E].unsqueeze(1)
+            r = r + interior_penalty(q, mesh, gas, E, ip_coef, q_ext)
+    r = r / mesh.J[E].unsqueeze(1)
+    if source is not None:
+        r = r + torch.as_tensor(source, dtype=F64)[E]
+    return r
 
 
 # --------------------------------------------------------------------------------------------

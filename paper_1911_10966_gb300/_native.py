@@ -26,7 +26,7 @@ class Setup(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("kx", ctypes.c_int), ("ky", ctypes.c_int), ("kz", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Ma", ctypes.c_double),
                 ("Re", ctypes.c_double), ("dissipation", ctypes.c_int), ("precision", ctypes.c_int),
-                ("volume_flux", ctypes.c_int), ("ip_coef", ctypes.c_double)]
+                ("volume_flux", ctypes.c_int), ("ip_coef", ctypes.c_double), ("bounded", ctypes.c_int)]
 
 
 class EsdcError(RuntimeError):
@@ -61,6 +61,9 @@ def lib() -> ctypes.CDLL:
         "esdc_budgets": (I, [P, P, P, ctypes.POINTER(D), P]),
         "esdc_rk_adaptive": (I, [P, P, D, D, ctypes.POINTER(D), D, D, I, P, S, P, P, I, P]),
         "esdc_budgets_async": (I, [P, P, P, P, P]),
+        "esdc_set_exterior": (I, [P, P]),
+        "esdc_set_source": (I, [P, P]),
+        "esdc_mms_fields": (I, [D, D, D, D, D, P, ctypes.c_int64, P, P, P]),
         "esdc_dt_cfl": (I, [P, P, D, ctypes.POINTER(D), P]),
         "esdc_profile": (I, [P, I]),
         "esdc_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)]),

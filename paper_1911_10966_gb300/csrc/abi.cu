@@ -70,6 +70,8 @@ cudaEvent_t* next_events(esdc_ctx* c) {
 }
 
 int rhs_impl(esdc_ctx* c, const double* q, void* dqdt, cudaStream_t s) {
+    if (c->setup.bounded != 0 && !c->d_qext)
+        return fail(ESDC_ERR_ARG, "a bounded box needs an exterior state (esdc_set_exterior)");
     cudaError_t e;
     if (c->setup.precision == ESDC_PREC_FP64) {
         e = esdc::launch_rhs_f64(c, q, (double*)dqdt, s, next_events(c));
@@ -294,11 +296,20 @@ int rk_adaptive_f64(esdc_ctx* c, double* q, double t0, double t_end, double* dt_
     return ESDC_OK;
 }
 
+// The element kernel instantiation depends on the optional face terms; opt the one in use into its
+// shared-memory size.
+int prepare_variant(esdc_ctx* c) {
+    if (c->setup.precision != ESDC_PREC_FP64) return ESDC_OK;
+    const cudaError_t e = esdc::prepare_rhs_f64(c);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel set-up");
+    return ESDC_OK;
+}
+
 int ensure_adjoint(esdc_ctx* c) {
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
-        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0)
-        return fail(ESDC_ERR_UNSUPPORTED,
-                    "the adjoint is built for float64 ES-C contexts with scalar dissipation and no interior penalty");
+        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with scalar "
+                                          "dissipation, no interior penalty and no source");
     if (c->d_adj_g) return ESDC_OK;
     const size_t N2 = (size_t)c->N * c->N;
     CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
@@ -312,9 +323,9 @@ int ensure_adjoint(esdc_ctx* c) {
 int adjoint_checks(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, void* ws, size_t ws_bytes) {
     if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
-        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0)
-        return fail(ESDC_ERR_UNSUPPORTED,
-                    "the adjoint is built for float64 ES-C contexts with scalar dissipation and no interior penalty");
+        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with scalar "
+                                          "dissipation, no interior penalty and no source");
     if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
     const size_t need = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");
@@ -401,6 +412,9 @@ static int check_setup(const esdc_setup_t& s) {
     if (s.dissipation == ESDC_DISS_MATRIX && s.precision != ESDC_PREC_FP64)
         return fail(ESDC_ERR_UNSUPPORTED, "the matrix dissipation is built for float64 only");
     if (!(s.ip_coef >= 0.0) || !std::isfinite(s.ip_coef)) return fail(ESDC_ERR_ARG, "ip_coef must be finite and >= 0");
+    if (s.bounded < 0 || s.bounded > 7) return fail(ESDC_ERR_ARG, "bounded must be a bit mask in [0, 7]");
+    if (s.bounded != 0 && s.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "bounded boxes are built for float64 only");
     if (s.ip_coef > 0.0 && s.precision != ESDC_PREC_FP64)
         return fail(ESDC_ERR_UNSUPPORTED, "the interior penalty is built for float64 only");
     if (s.precision != ESDC_PREC_FP64 && s.precision != ESDC_PREC_FP32)
@@ -628,6 +642,33 @@ int esdc_budgets_async(esdc_ctx* c, const double* q, const void* dqdt, double* o
     cudaError_t e = esdc::launch_budgets(c, q, dqdt, c->setup.precision == ESDC_PREC_FP32, out_dev,
                                          (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "budgets launch");
+    return ESDC_OK;
+}
+
+int esdc_set_exterior(esdc_ctx* c, const double* q_ext) {
+    if (!c) return fail(ESDC_ERR_ARG, "null context");
+    if (q_ext && c->setup.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "exterior states are used by float64 contexts only");
+    if (q_ext && !aligned(q_ext, 16)) return fail(ESDC_ERR_ARG, "q_ext must be 16-byte aligned");
+    c->d_qext = q_ext;
+    return prepare_variant(c);
+}
+
+int esdc_set_source(esdc_ctx* c, const double* src) {
+    if (!c) return fail(ESDC_ERR_ARG, "null context");
+    if (src && c->setup.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "source terms are added by float64 contexts only");
+    if (src && !aligned(src, 16)) return fail(ESDC_ERR_ARG, "source must be 16-byte aligned");
+    c->d_src = src;
+    return prepare_variant(c);
+}
+
+int esdc_mms_fields(double gamma, double Ma, double Re, double Pr, double L, const double* table, int64_t n,
+                    const double* x, double* q, double* src) {
+    if (!table || !x || n < 0) return fail(ESDC_ERR_ARG, "null argument or negative count");
+    if (!(gamma > 1.0) || !(Ma > 0.0) || !(Pr > 0.0) || !(L > 0.0) || !std::isfinite(Re))
+        return fail(ESDC_ERR_ARG, "gamma > 1, Ma > 0, Pr > 0, L > 0 and finite Re required");
+    esdc::mms_fields(gamma, Ma, Re, Pr, L, table, n, x, q, src);
     return ESDC_OK;
 }
 

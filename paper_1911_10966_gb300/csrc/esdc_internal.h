@@ -58,7 +58,10 @@ struct HostSetup {
 int lgl(int p, double* xi, double* w);
 int build_operators(int p, HostSetup& hs);
 int build_geometry(const esdc_setup_t& s, const double* xyz, HostSetup& hs, std::string& err);
-void build_box_neighbours(int kx, int ky, int kz, std::vector<int32_t>& nbr);
+void build_box_neighbours(int kx, int ky, int kz, int bounded, std::vector<int32_t>& nbr);
+// manufactured solution (q, nullable) and its source div(F^I - F^V) (src, nullable) at n points (host)
+void mms_fields(double gamma, double Ma, double Re, double Pr, double L, const double* table, int64_t n,
+                const double* x, double* q, double* src);
 void set_last_error(const std::string& msg);   // message returned by esdc_last_error on this thread
 
 }  // namespace esdc
@@ -76,6 +79,8 @@ struct esdc_ctx {
     // device buffers owned by the library
     double* d_geom = nullptr;        // [K][10][N3]
     double* d_jinv = nullptr;        // [K][N3] 1/J
+    const double* d_qext = nullptr;  // caller-owned exterior (Dirichlet) state, [K][5][N3] (bounded boxes)
+    const double* d_src = nullptr;   // caller-owned source term added to dq/dt, [K][5][N3]
     float* d_geomf = nullptr;        // [K][10][N3] float32 copy (mixed precision)
     int32_t* d_nbr = nullptr;        // [K][6]
     void* d_trace = nullptr;         // [K][6][4][N2] viscous normal-flux traces (f64 or f32)

@@ -242,13 +242,14 @@ __device__ __forceinline__ void euler_flux_prim(const Prim& s, double RT, double
     f[4] = f1 * fma(ph.gamma * ph.inv_gm1, RT, 2.0 * s.qq);
 }
 
-// XF: the face phase also evaluates the matrix dissipation and the interior penalty (compiled only
-// into the instantiations of contexts that use them, so the default kernel carries none of it)
+// XF: the kernel also handles the matrix dissipation, the interior penalty, boundary faces with an
+// exterior state and a source term (compiled only into the instantiations of contexts that use
+// them, so the default kernel carries none of it)
 template <int N, int VF, bool XF>
 __global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::MINB)
 rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const double* __restrict__ geom,
              const int32_t* __restrict__ nbr, double* __restrict__ trace, int64_t K, const Ops ops,
-             const Phys ph) {
+             const Phys ph, const double* __restrict__ qext, const double* __restrict__ src) {
     constexpr int N2 = Cfg<N>::N2, N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB;
     extern __shared__ double smem[];
     const int t = threadIdx.x;
@@ -377,10 +378,13 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             const int nbn = base + (side ? 0 : (N - 1) * st);
             const int64_t nb = nbr[el * 6 + 2 * l + side];
             double qo[5], qn[5];
+            // a boundary face (neighbour -1, bounded boxes only) sees the exterior state at its own nodes
+            bool bnd = false;
+            if constexpr (XF) bnd = nb < 0;
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
                 qo[v] = q[eoff + v * N3 + own];
-                qn[v] = q[nb * 5 * N3 + v * N3 + nbn];
+                qn[v] = bnd ? qext[eoff + v * N3 + own] : q[nb * 5 * N3 + v * N3 + nbn];
             }
             Prim so, sn;
             double RTn, cn;
@@ -415,7 +419,8 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
                 if (ph.ip_coef > 0.0) {
                     // sigma mu |n_J| / h with h = (J_own + J_nbr)/|n_J|
                     const double nsq = n0 * n0 + n1 * n1 + n2 * n2;
-                    const double cip = ph.ip_coef * ph.mu * nsq / (sG[own] + geom[nb * 10 * N3 + nbn]);
+                    const double Jn = bnd ? sG[own] : geom[nb * 10 * N3 + nbn];
+                    const double cip = ph.ip_coef * ph.mu * nsq / (sG[own] + Jn);
 #pragma unroll
                     for (int v = 0; v < 5; ++v) dm[v] = fma(cip, r[v], dm[v]);
                 }
@@ -540,12 +545,19 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
         }
     }
     if (active) {
+        if constexpr (XF) {
+            if (src) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v)
+                    dqdt[eoff + v * N3 + node] = fma(sR[v * N3 + node], Jinv, src[eoff + v * N3 + node]);
+                return;
+            }
+        }
 #pragma unroll
         for (int v = 0; v < 5; ++v) dqdt[eoff + v * N3 + node] = sR[v * N3 + node] * Jinv;
     }
 }
 
-// BR1 viscous interface term on face nodes, direction by direction (edge nodes see up to 3 faces).
 // ---- host-side launchers
 
 template <int N, int VF, bool XF>
@@ -556,7 +568,7 @@ cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaS
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     if (ev) cudaEventRecord(ev[0], s);
     rhs_main_f64<N, VF, XF><<<grid, C::THREADS, smem, s>>>(q, dqdt, c->d_geom, c->d_nbr, (double*)c->d_trace, c->K,
-                                                       c->ops, c->phys);
+                                                           c->ops, c->phys, c->d_qext, c->d_src);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (c->phys.viscous) {
@@ -581,7 +593,9 @@ cudaError_t prepare_xf(int vf) {
     }
 }
 
-bool extra_face_terms(const esdc_ctx* c) { return c->phys.dissipation == 2 || c->phys.ip_coef > 0.0; }
+bool extra_face_terms(const esdc_ctx* c) {
+    return c->phys.dissipation == 2 || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src;
+}
 
 template <int N>
 cudaError_t prepare_n(const esdc_ctx* c) {

@@ -99,7 +99,8 @@ int build_operators(int p, HostSetup& hs) {
     return ESDC_OK;
 }
 
-void build_box_neighbours(int kx, int ky, int kz, std::vector<int32_t>& nbr) {
+// bounded: bit l set -> the outer faces of direction l are boundaries (neighbour -1)
+void build_box_neighbours(int kx, int ky, int kz, int bounded, std::vector<int32_t>& nbr) {
     const int64_t K = (int64_t)kx * ky * kz;
     nbr.assign(K * 6, 0);
     auto id = [&](int a, int b, int c) {
@@ -117,6 +118,12 @@ void build_box_neighbours(int kx, int ky, int kz, std::vector<int32_t>& nbr) {
         n[3] = id(ex, ey + 1, ez);
         n[4] = id(ex, ey, ez - 1);
         n[5] = id(ex, ey, ez + 1);
+        const int c[3] = {ex, ey, ez}, k[3] = {kx, ky, kz};
+        for (int l = 0; l < 3; ++l)
+            if (bounded & (1 << l)) {
+                if (c[l] == 0) n[2 * l] = -1;
+                if (c[l] == k[l] - 1) n[2 * l + 1] = -1;
+            }
     }
 }
 
@@ -230,8 +237,90 @@ int build_geometry(const esdc_setup_t& s, const double* xyz, HostSetup& hs, std:
         err = "degenerate element edge";
         return ESDC_ERR_MESH;
     }
-    build_box_neighbours(s.kx, s.ky, s.kz, hs.nbr);
+    build_box_neighbours(s.kx, s.ky, s.kz, s.bounded, hs.nbr);
     return ESDC_OK;
+}
+
+// Manufactured solution of Sec. 5.1 (eq. mms) and its source div(F^I - F^V).  Every field is
+// phi0 + sum_k A_k trig_k(c_k x_k) with c_k = alpha_k pi / L, so all first and second derivatives are
+// analytic and the mixed second derivatives vanish; the divergence of tau_ij then reduces to
+// mu (sum_j d_jj u_i + d_ii u_i / 3).
+void mms_fields(double gamma, double Ma, double Re, double Pr, double L, const double* table, int64_t n,
+                const double* x, double* q, double* src) {
+    static const int kind[5][3] = {{0, 1, 0}, {0, 1, 1}, {1, 0, 0}, {0, 0, 1}, {0, 0, 1}};   // 0 sin, 1 cos
+    const double R = 1.0 / (gamma * Ma * Ma);
+    const double mu = Re > 0.0 ? 1.0 / Re : 0.0;
+    const double kappa = mu * gamma * R / ((gamma - 1.0) * Pr);
+    const double pi = 3.14159265358979323846;
+    for (int64_t i = 0; i < n; ++i) {
+        double val[5], d[5][3], dd[5][3];
+        for (int f = 0; f < 5; ++f) {
+            const double* row = table + 7 * f;
+            val[f] = row[0];
+            for (int k = 0; k < 3; ++k) {
+                const double c = row[4 + k] * pi / L;
+                const double arg = c * x[3 * i + k];
+                const double sn = std::sin(arg), cs = std::cos(arg);
+                const double A = row[1 + k];
+                if (kind[f][k] == 0) {
+                    val[f] += A * sn;
+                    d[f][k] = A * c * cs;
+                    dd[f][k] = -A * c * c * sn;
+                } else {
+                    val[f] += A * cs;
+                    d[f][k] = -A * c * sn;
+                    dd[f][k] = -A * c * c * cs;
+                }
+            }
+        }
+        const double rho = val[0], u[3] = {val[1], val[2], val[3]}, p = val[4];
+        const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const double rE = p / (gamma - 1.0) + 0.5 * rho * usq;
+        if (q) {
+            double* o = q + 5 * i;
+            o[0] = rho;
+            for (int k = 0; k < 3; ++k) o[1 + k] = rho * u[k];
+            o[4] = rE;
+        }
+        if (!src) continue;
+        // du[a][m] = d u_a / d x_m
+        double du[3][3], div = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int m = 0; m < 3; ++m) du[a][m] = d[1 + a][m];
+        for (int m = 0; m < 3; ++m) div += du[m][m];
+        // inviscid divergence
+        double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int m = 0; m < 3; ++m) {
+            s[0] += d[0][m] * u[m] + rho * du[m][m];
+            const double dH = gamma / (gamma - 1.0) * d[4][m] + 0.5 * d[0][m] * usq +
+                              rho * (u[0] * du[0][m] + u[1] * du[1][m] + u[2] * du[2][m]);
+            s[4] += du[m][m] * (rE + p) + u[m] * dH;
+        }
+        for (int a = 0; a < 3; ++a) {
+            double t = d[4][a];
+            for (int m = 0; m < 3; ++m) t += d[0][m] * u[m] * u[a] + rho * du[m][m] * u[a] + rho * u[m] * du[a][m];
+            s[1 + a] = t;
+        }
+        // viscous divergence
+        double tau[3][3], dtau[3];
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) tau[a][b] = mu * (du[a][b] + du[b][a] - (a == b ? 2.0 / 3.0 * div : 0.0));
+            dtau[a] = mu * (dd[1 + a][0] + dd[1 + a][1] + dd[1 + a][2] + dd[1 + a][a] / 3.0);
+        }
+        double ven = 0.0, lapT = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) ven += du[a][b] * tau[a][b];
+            ven += u[a] * dtau[a];
+        }
+        for (int m = 0; m < 3; ++m)
+            lapT += (dd[4][m] / rho - 2.0 * d[4][m] * d[0][m] / (rho * rho) - p * dd[0][m] / (rho * rho) +
+                     2.0 * p * d[0][m] * d[0][m] / (rho * rho * rho)) / R;
+        ven += kappa * lapT;
+        double* o = src + 5 * i;
+        o[0] = s[0];
+        for (int a = 0; a < 3; ++a) o[1 + a] = s[1 + a] - dtau[a];
+        o[4] = s[4] - ven;
+    }
 }
 
 }  // namespace esdc

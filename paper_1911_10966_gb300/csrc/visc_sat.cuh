@@ -78,6 +78,8 @@ visc_sat_kernel(T* __restrict__ out, const T* __restrict__ jac, const int32_t* _
         side[l] = ix[l] == N - 1;
         fi[l] = l == 0 ? ix[1] + N * ix[2] : (l == 1 ? ix[0] + N * ix[2] : ix[0] + N * ix[1]);
         nb[l] = on[l] ? nbr[el * 6 + 2 * l + side[l]] : 0;
+        // a boundary face (neighbour -1) reads the exterior viscous flux as the interior one: no term
+        on[l] = on[l] && nb[l] >= 0;
     }
     T own[3][4];
 #pragma unroll

@@ -154,3 +154,52 @@ def random_direction(shape, seed=1234, scale=None) -> np.ndarray:
     if scale is not None:
         v = v * np.asarray(scale).reshape((1, -1) + (1,) * (len(shape) - 2))
     return v
+
+
+# Manufactured solution of the paper's viscous error-vs-cost study (Sec. 5.1, eq. mms and its table of
+# constants) on [0, L]^3, L = 1.  Rows rho, u1, u2, u3, p; columns phi0, phi_x1, phi_x2, phi_x3,
+# alpha_x1, alpha_x2, alpha_x3.  Readings: the table's "U_3^{x3}" in the u1 row is U_1^{x3}; the
+# printed p_x3 = 2/3 is used as printed.  The dimensional values (velocity 800, pressure 1e5, rho 1)
+# are scaled to this module's units: velocities by 800, pressures by 1e5/R, so that the reference
+# Mach number per component is 800 / sqrt(1.4e5) = 2.138 (the paper's Ma ~ 2.14) and T = 1 at the
+# reference state.
+MMS_TABLE = (
+    (1.0, 3.0 / 20.0, -1.0 / 10.0, 1.0 / 5.0, 1.0, 0.5, 1.0),
+    (800.0, 50.0, -30.0, 50.0, 1.5, 0.6, 1.0),
+    (800.0, -75.0, 40.0, 10.0, 0.5, 1.5, 1.5),
+    (800.0, 15.0, -25.0, 20.0, 1.5, 0.5, 1.25),
+    (1.0e5, 2.0e4, 5.0e4, 2.0 / 3.0, 1.0, 1.5, 1.0),
+)
+# trigonometric function of each term (0: sin, 1: cos), per row and direction (eq. mms)
+MMS_KIND = ((0, 1, 0), (0, 1, 1), (1, 0, 0), (0, 0, 1), (0, 0, 1))
+MMS_MA = 800.0 / math.sqrt(1.4e5)
+MMS_RE = 4.0e6
+
+
+def manufactured_primitives(x1, x2, x3, Ma=MMS_MA, gamma=1.4, L=1.0, sin=np.sin, cos=np.cos):
+    """(rho, [u1, u2, u3], p) of the manufactured solution at points (x1, x2, x3) in this module's
+    units.  sin/cos may be any elementwise functions (array libraries other than numpy)."""
+    R = gas_constant(Ma, gamma)
+    scale = (1.0, 1.0 / 800.0, 1.0 / 800.0, 1.0 / 800.0, R / 1.0e5)
+    out = []
+    for row, kind, sc in zip(MMS_TABLE, MMS_KIND, scale):
+        v = row[0]
+        for k, xk in enumerate((x1, x2, x3)):
+            f = cos if kind[k] else sin
+            v = v + row[1 + k] * f(row[4 + k] * math.pi * xk / L)
+        out.append(sc * v)
+    return out[0], out[1:4], out[4]
+
+
+def manufactured(x, Ma=MMS_MA, gamma=1.4, L=1.0) -> np.ndarray:
+    """Conserved state of the manufactured solution at node coordinates x [K, 3, N, N, N]."""
+    rho, u, p = manufactured_primitives(x[:, 0], x[:, 1], x[:, 2], Ma, gamma, L)
+    return primitive_to_conserved(rho, u, p, gamma)
+
+
+def manufactured_table(Ma=MMS_MA, gamma=1.4):
+    """MMS_TABLE in this module's units (the rows scaled as in manufactured_primitives), the layout
+    esdc_mms_fields takes: 5 rows of (phi0, phi_x1, phi_x2, phi_x3, alpha_x1, alpha_x2, alpha_x3)."""
+    R = gas_constant(Ma, gamma)
+    scale = (1.0, 1.0 / 800.0, 1.0 / 800.0, 1.0 / 800.0, R / 1.0e5)
+    return [[r[0] * sc, r[1] * sc, r[2] * sc, r[3] * sc, r[4], r[5], r[6]] for r, sc in zip(MMS_TABLE, scale)]

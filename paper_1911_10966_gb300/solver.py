@@ -30,6 +30,19 @@ def probe_fma(kind: str = "f64") -> float:
     return out.value
 
 
+def mms_fields(x, table, gamma=1.4, Ma=1.0, Re=0.0, Pr=0.72, L=1.0):
+    """The library's manufactured solution and its source term (esdc_mms_fields) at node coordinates
+    x [K, 3, N, N, N] (numpy): returns (q, source), each [K, 5, N, N, N]."""
+    x = np.ascontiguousarray(np.moveaxis(np.asarray(x, dtype=np.float64), 1, -1))
+    n = x.size // 3
+    tab = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(5, 7))
+    q = np.empty(x.shape[:-1] + (5,))
+    s = np.empty(x.shape[:-1] + (5,))
+    nat.check(nat.lib().esdc_mms_fields(gamma, Ma, Re, Pr, L, tab.ctypes.data, n, x.ctypes.data, q.ctypes.data,
+                                        s.ctypes.data), "esdc_mms_fields")
+    return np.ascontiguousarray(np.moveaxis(q, -1, 1)), np.ascontiguousarray(np.moveaxis(s, -1, 1))
+
+
 def _stream_ptr() -> int:
     return torch.cuda.current_stream().cuda_stream
 
@@ -43,10 +56,12 @@ class Solver:
     entropy-stable matrix dissipation; float64 only).
     volume_flux: "esc" (the paper's ES-C), "kg" (SF-KG) or "dc" (DC); the last two float64 only.
     ip_coef: interior-penalty coefficient (0: off; float64 only).
+    bounded: per direction, True for boundary faces with Dirichlet data (set_exterior) instead of
+    periodic connectivity (float64 only).
     """
 
     def __init__(self, p, kx, ky, kz, coords, *, gamma=1.4, Pr=0.72, Ma=0.1, Re=0.0, dissipation=True,
-                 precision="fp64", volume_flux="esc", ip_coef=0.0, device=None):
+                 precision="fp64", volume_flux="esc", ip_coef=0.0, bounded=(False, False, False), device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU implementation exists)")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
@@ -66,7 +81,7 @@ class Solver:
         diss = 2 if dissipation == "matrix" else (1 if dissipation else 0)
         st = nat.Setup(p, kx, ky, kz, gamma, Pr, Ma, Re, diss,
                        nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32, nat.FLUX[volume_flux],
-                       float(ip_coef))
+                       float(ip_coef), sum(1 << l for l in range(3) if bounded[l]))
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             nat.check(nat.lib().esdc_create(ctypes.byref(st), coords.ctypes.data, ctypes.byref(self._ctx)),
@@ -74,6 +89,8 @@ class Solver:
         self._ws = None
         self._adj_ws = None
         self._ada_ws = None
+        self._ext = None
+        self._src = None
 
     @classmethod
     def box(cls, p, kx, ky, kz, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, warp=0.0, seed=0, **kw):
@@ -168,6 +185,23 @@ class Solver:
         if check:
             nat.check(code, "esdc_budgets")
         return tuple(out)
+
+    def set_exterior(self, q_ext):
+        """Exterior (Dirichlet) state of the boundary faces, a state-shaped float64 CUDA tensor read
+        at the boundary face nodes; the solver keeps a reference.  None clears it."""
+        if q_ext is not None:
+            self._check_state(q_ext)
+        nat.check(nat.lib().esdc_set_exterior(self._ctx, q_ext.data_ptr() if q_ext is not None else None),
+                  "esdc_set_exterior")
+        self._ext = q_ext
+
+    def set_source(self, source):
+        """Source term added to dq/dt (state-shaped float64 CUDA tensor, referenced); None clears it."""
+        if source is not None:
+            self._check_state(source)
+        nat.check(nat.lib().esdc_set_source(self._ctx, source.data_ptr() if source is not None else None),
+                  "esdc_set_source")
+        self._src = source
 
     def budgets_async(self, q, out, dqdt=None):
         """Write (sum PJ S, KE, sum PJ w.dq/dt, dKE/dt, non-physical node count) into the float64

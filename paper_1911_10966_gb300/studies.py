@@ -5,6 +5,7 @@
                                                         #   of the paper's cost study, Sec. 5.2, p = 1, 3, 7)
   python -m paper_1911_10966_gb300.studies hconv       # isentropic vortex L2 error, p = 3, 4, 5, 4^3..32^3
   python -m paper_1911_10966_gb300.studies variants    # ES-C / SF-KG / DC DP5 step time, 256^3 nodes, p = 1, 3, 7
+  python -m paper_1911_10966_gb300.studies mms         # manufactured solution, Dirichlet boundaries: error vs cost
 
 All arithmetic runs in libesdc.so; this module only sets up meshes and states, times calls with CUDA
 events and computes error norms of the returned fields.
@@ -163,6 +164,50 @@ def variants():
     return rows
 
 
+def mms(t_end=1.5):
+    """The paper's viscous error-vs-cost study (Sec. 5.1): the supersonic manufactured solution on
+    [0, 1]^3 with exact Dirichlet data on every boundary, Re = 4e6, marched from the exact field with
+    fixed DP5 steps at CFL 0.5 for t_end = 1.5 flow-through times (the supersonic flow carries
+    every perturbation out of the box), ES-C and DC, p = 1..4.  Reports the P-norm L2 error of rho
+    against the exact field and the wall time."""
+    from .solver import mms_fields
+    rows = []
+    for vf in ("esc", "dc"):
+        for p, ks in ((1, (4, 8, 16, 32)), (2, (4, 8, 16)), (3, (4, 8, 16)), (4, (4, 8, 16))):
+            prev = None
+            for k in ks:
+                s = Solver.box(p, k, k, k, lo=(0.0,) * 3, hi=(1.0,) * 3, Ma=I.MMS_MA, Re=I.MMS_RE,
+                               bounded=(True, True, True), volume_flux=vf)
+                qx, src = mms_fields(s.coords, I.manufactured_table(), gamma=1.4, Ma=I.MMS_MA, Re=I.MMS_RE,
+                                     Pr=0.72, L=1.0)
+                exact = s.to_device(qx)
+                sd = s.to_device(src)
+                s.set_exterior(exact)
+                s.set_source(sd)
+                q = exact.clone()
+                dt0 = s.dt_cfl(q, 0.5)
+                nsteps = max(1, int(math.ceil(t_end / dt0)))
+                dt = t_end / nsteps
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.rk_step(q, dt, nsteps)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+                J, _ = s.geometry()
+                _, wq = lgl(p)
+                P = wq[:, None, None] * wq[None, :, None] * wq[None, None, :]
+                err = ((q[:, 0] - exact[:, 0]).cpu().numpy()) ** 2
+                l2 = float(np.sqrt((P[None] * J * err).sum()))
+                row = {"study": "mms", "volume_flux": vf, "p": p, "k": k, "nodes": s.n_nodes, "steps": nsteps,
+                       "l2_rho": l2, "wall_s": wall,
+                       "order": (math.log(prev / l2) / math.log(2.0)) if prev else None}
+                prev = l2
+                print(json.dumps(row), flush=True)
+                rows.append(row)
+                del q, exact, sd, s
+    return rows
+
+
 def _vortex(x, t, u_inf, Ma=0.5):
     """Exact translating isentropic vortex (axis along x3) at time t, periodic images ignored."""
     c = (u_inf[0] * t, u_inf[1] * t, 0.0)
@@ -202,4 +247,4 @@ def hconv(t_final=0.5):
 
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "psweep"
-    {"precision": precision, "psweep": psweep, "hconv": hconv, "variants": variants}[which]()
+    {"precision": precision, "psweep": psweep, "hconv": hconv, "variants": variants, "mms": mms}[which]()
