@@ -355,6 +355,8 @@ def run_ours(args):
         "cpu_baseline": cpu_baseline_sample() if (ws == 1 and not args.no_cpu_baseline) else None,
         "e2e": {"value": e2e_val, "unit": "node-RHS/s", "h2d_bytes_per_step": n * 40,
                 "d2h_bytes_per_step": n * 40 + 40},
+        # per step: element + viscous face kernel per residual, five stage combinations and the
+        # solution update, budgets + final sum
         "gpu_launches": args.steps * (RHS_PER_STEP * 2 + RHS_PER_STEP + 2),
         "clocks": clocks,
         "rhs_only": {"value": n / (ms_rhs * 1e-3), "unit": "node-RHS/s", "ms": ms_rhs,
@@ -433,7 +435,9 @@ def _fp32_leg(args, s64, q_init, dt, flush, barrier, dist, ws):
             "dtype": "f32 residual, f64 state/update/budgets", "roofline": roof,
             "residual_error_vs_f64": {"per_variable": e_v, "variables": ["rho", "rho u1", "rho u2", "rho u3", "rho E"]},
             "ke_rate_rel_error_5_steps": abs(k32 - k64) / abs(k64),
-            "gpu_launches": steps * (RHS_PER_STEP * 2 + RHS_PER_STEP + 1 + 2),
+            # per step: shadow state, element + viscous face kernel per residual (stage states are
+            # formed inside the element kernel), the float64 update, budgets + final sum
+            "gpu_launches": steps * (1 + RHS_PER_STEP * 2 + 1 + 2),
             "speedup_vs_f64_rhs": None}
 
 
