@@ -325,6 +325,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms_rhs = a.elapsed_time(b) / reps
 
+    multi64 = _multi_step_ms(solver, solver.to_device(q_init), dt, 10, flush)
     adj = _adjoint_leg(solver, solver.to_device(q_init), dt, ms_rhs, flush)
     ada = _adaptive_leg(solver, q_init, dt)
     var = _variants_leg(solver, q_init, ms_rhs)
@@ -362,6 +363,7 @@ def run_ours(args):
         "rhs_only": {"value": n / (ms_rhs * 1e-3), "unit": "node-RHS/s", "ms": ms_rhs,
                      "face_kernel_ms": ms_face / max(nres, 1)},
         "fp32_mixed": fp32,
+        "multi_step": multi64,
         "adjoint": adj,
         "adaptive_dp54": ada,
         "volume_flux_variants": var,
@@ -369,6 +371,28 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _multi_step_ms(solver, q, dt, steps, flush):
+    """DP5 steps without budgets, (a) one call per step (direct launches) and (b) one call for all
+    steps (one step captured as a CUDA graph and replayed): ms per step each."""
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    solver.rk_step(q, dt, 2)                  # capture outside the timed region
+    out = {}
+    for name in ("direct", "graph"):
+        flush.fill_(4.0)
+        a.record(stream)
+        if name == "direct":
+            for _ in range(steps):
+                solver.rk_step(q, dt, 1)
+        else:
+            solver.rk_step(q, dt, steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = a.elapsed_time(b) / steps
+    return {"ms_per_step_direct": out["direct"], "ms_per_step_graph": out["graph"], "steps": steps,
+            "what": "DP5 steps without budgets: one call per step vs one multi-step call (CUDA-graph replay)"}
 
 
 def _check_budgets(hist):
@@ -410,6 +434,7 @@ def _fp32_leg(args, s64, q_init, dt, flush, barrier, dist, ws):
     s32.profile(False)
     _check_budgets(hist)
     ms_step = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, dist, q.device)
+    multi = _multi_step_ms(s32, q, dt, 50, flush)
     # kinetic-energy dissipation rate after the same number of steps in both precisions
     qa = s64.to_device(q_init)
     qb = s32.to_device(q_init)
@@ -435,6 +460,7 @@ def _fp32_leg(args, s64, q_init, dt, flush, barrier, dist, ws):
             "dtype": "f32 residual, f64 state/update/budgets", "roofline": roof,
             "residual_error_vs_f64": {"per_variable": e_v, "variables": ["rho", "rho u1", "rho u2", "rho u3", "rho E"]},
             "ke_rate_rel_error_5_steps": abs(k32 - k64) / abs(k64),
+            "multi_step": multi,
             # per step: shadow state, element + viscous face kernel per residual (stage states are
             # formed inside the element kernel), the float64 update, budgets + final sum
             "gpu_launches": steps * (1 + RHS_PER_STEP * 2 + 1 + 2),

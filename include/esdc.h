@@ -190,7 +190,9 @@ int esdc_rk_adaptive(esdc_ctx* ctx, double* q_dev, double t0, double t_end, doub
  * least esdc_workspace_bytes(ctx, 0) bytes, 256-byte aligned.  The solution q and its update
  * q += dt sum_j b_j k_j are float64 in both precision modes; in ESDC_PREC_FP32 the stage states that
  * feed the float32 residual are float32 perturbations (rho - 1, rho u, rho E - E0) formed from the
- * float64 state.  Asynchronous on stream.
+ * float64 state.  With nsteps >= 2 (and profiling off) one step is captured once as a CUDA graph and
+ * replayed nsteps times; the graph is rebuilt when q, the workspace, dt or the exterior/source arrays
+ * change.  Results are identical to nsteps single-step calls.  Asynchronous on stream.
  */
 int esdc_rk_step(esdc_ctx* ctx, double* q_dev, double dt, int nsteps, void* workspace_dev,
                  size_t workspace_bytes, void* stream);

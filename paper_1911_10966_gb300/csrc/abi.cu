@@ -88,14 +88,23 @@ int rhs_impl(esdc_ctx* c, const double* q, void* dqdt, cudaStream_t s) {
 // Mixed precision: nsteps DP5 steps with float32 residuals on float32 perturbation stage states
 // (formed inside the residual kernel from the step's shadow state and the earlier stage
 // derivatives) and the float64 solution update q += dt sum_j b_j k_j (accumulated in float64).
-int rk_step_f32(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s) {
+// the float32 shadow of q in the workspace (the base state of the first step)
+int rk_shadow_f32(esdc_ctx* c, const double* q, void* ws, cudaStream_t s) {
+    const size_t sub = round256((size_t)c->n_nodes * 5 * sizeof(float));
+    cudaError_t e = esdc::launch_shadow(c, q, (float*)((char*)ws + 6 * sub), s);
+    if (e != cudaSuccess) return cuda_fail(e, "shadow");
+    return ESDC_OK;
+}
+
+// nsteps float32-mixed DP5 steps from the shadow already in the workspace (each step's update
+// writes the next shadow)
+int rk_steps_f32(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s) {
     const int64_t n = c->n_nodes * 5;
     const size_t sub = round256((size_t)n * sizeof(float));
     float* k[6];
     for (int j = 0; j < 6; ++j) k[j] = (float*)((char*)ws + j * sub);
     float* base = (float*)((char*)ws + 6 * sub);
-    cudaError_t e = esdc::launch_shadow(c, q, base, s);
-    if (e != cudaSuccess) return cuda_fail(e, "shadow");
+    cudaError_t e;
     for (int step = 0; step < nsteps; ++step) {
         for (int st = 0; st < 6; ++st) {
             esdc::StageF in{};
@@ -120,6 +129,11 @@ int rk_step_f32(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStr
         if (e != cudaSuccess) return cuda_fail(e, "step update (float64)");
     }
     return ESDC_OK;
+}
+
+int rk_step_f32(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s) {
+    const int r = rk_shadow_f32(c, q, ws, s);
+    return r ? r : rk_steps_f32(c, q, dt, nsteps, ws, s);
 }
 
 // nsteps float64 DP5 steps.  stages (nullable): the six stage states of every step are written to
@@ -163,6 +177,51 @@ int rk_step_f64(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStr
         cudaError_t e = esdc::launch_combine(q, q, cb, n, s);
         if (e != cudaSuccess) return cuda_fail(e, "step combine");
     }
+    return ESDC_OK;
+}
+
+// Multi-step esdc_rk_step: one step is captured once as a CUDA graph on a private stream and replayed
+// nsteps times on the caller's stream, so the ~20 launches of a step cost one graph launch.  The
+// graph bakes in the state, workspace, step size and optional-term pointers; any change recaptures.
+// Returns ESDC_OK, or 1 when the graph could not be built (the caller then launches directly).
+int rk_steps_graph(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s) {
+    const void* key[5] = {q, ws, c->d_qext, c->d_src, (const void*)(intptr_t)c->setup.precision};
+    bool valid = c->graph_exec != nullptr && c->graph_dt == dt;
+    for (int i = 0; i < 5 && valid; ++i) valid = key[i] == c->graph_key[i];
+    if (!valid) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        if (!c->capture_stream) {
+            cudaStream_t cs;
+            if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                return 1;
+            }
+            c->capture_stream = cs;
+        }
+        cudaStream_t cs = (cudaStream_t)c->capture_stream;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return 1;
+        }
+        const int r = c->setup.precision == ESDC_PREC_FP32 ? rk_steps_f32(c, q, dt, 1, ws, cs)
+                                                            : rk_step_f64(c, q, dt, 1, ws, cs, nullptr);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &g);
+        cudaGraphExec_t exec = nullptr;
+        const bool ok = r == ESDC_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {
+            cudaGetLastError();
+            return r ? r : 1;
+        }
+        c->graph_exec = exec;
+        c->graph_dt = dt;
+        for (int i = 0; i < 5; ++i) c->graph_key[i] = key[i];
+    }
+    for (int i = 0; i < nsteps; ++i) CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)c->graph_exec, s));
     return ESDC_OK;
 }
 
@@ -344,6 +403,8 @@ int adjoint_finish(esdc_ctx* c, double* grad_mu, cudaStream_t s) {
 
 void free_ctx(esdc_ctx* c) {
     if (!c) return;
+    if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+    if (c->capture_stream) cudaStreamDestroy((cudaStream_t)c->capture_stream);
     for (void* ev : c->prof_events) cudaEventDestroy((cudaEvent_t)ev);
     cudaFree(c->d_geom);
     cudaFree(c->d_jinv);
@@ -619,8 +680,23 @@ int esdc_rk_step(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, size_t
     esdc_workspace_bytes(c, 0, &need);
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "workspace too small");
     if (!aligned(ws, 256) || !aligned(q, 16)) return fail(ESDC_ERR_ARG, "q must be 16-byte and workspace 256-byte aligned");
-    if (c->setup.precision == ESDC_PREC_FP32) return rk_step_f32(c, q, dt, nsteps, ws, (cudaStream_t)stream);
-    return rk_step_f64(c, q, dt, nsteps, ws, (cudaStream_t)stream, nullptr);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->setup.bounded != 0 && !c->d_qext)
+        return fail(ESDC_ERR_ARG, "a bounded box needs an exterior state (esdc_set_exterior)");
+    if (nsteps >= 2 && !c->profiling) {
+        // graph replay; the float32 shadow of q is formed once, before the first step
+        if (c->setup.precision == ESDC_PREC_FP32) {
+            const int r = rk_shadow_f32(c, q, ws, s);
+            if (r) return r;
+        }
+        const int r = rk_steps_graph(c, q, dt, nsteps, ws, s);
+        if (r <= 0) return r;
+        // graph unavailable: direct launches (the shadow is already in place)
+        if (c->setup.precision == ESDC_PREC_FP32) return rk_steps_f32(c, q, dt, nsteps, ws, s);
+        return rk_step_f64(c, q, dt, nsteps, ws, s, nullptr);
+    }
+    if (c->setup.precision == ESDC_PREC_FP32) return rk_step_f32(c, q, dt, nsteps, ws, s);
+    return rk_step_f64(c, q, dt, nsteps, ws, s, nullptr);
 }
 
 int esdc_budgets(esdc_ctx* c, const double* q, const void* dqdt, double out[4], void* stream) {

@@ -94,6 +94,12 @@ struct esdc_ctx {
     double* d_adj_t = nullptr;       // [K][6][4][N2] lifted-gradient cotangents for the neighbour
     double* d_adj_mu = nullptr;      // per-block partial sums of lambda . R_visc
     double* d_adj_acc = nullptr;     // accumulated d/dmu
+    // one DP5 step captured as a CUDA graph, replayed by multi-step esdc_rk_step calls; valid for
+    // the recorded state, workspace, step size and optional-term pointers
+    void* graph_exec = nullptr;      // cudaGraphExec_t
+    void* capture_stream = nullptr;  // cudaStream_t (private, non-blocking) used only for capture
+    const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double graph_dt = 0.0;
     // CUDA-event profiling of the residual kernels (esdc_profile)
     int profiling = 0;
     std::vector<void*> prof_events;  // cudaEvent_t quadruples: main start/stop, face start/stop
