@@ -18,42 +18,63 @@ __device__ __forceinline__ int var_of(int64_t i, DivU64 div_n3, DivU64 div_5) {
     return (int)(row - 5ull * div_5(row));
 }
 
+// q - q_ref for variable v of the layout (rho0 for the density, E0 for the energy)
+__device__ __forceinline__ double less_ref(double x, int v, double rho0, double E0) {
+    if (v == 0) return x - rho0;
+    if (v == 4) return x - E0;
+    return x;
+}
+
+// Two consecutive entries per thread and iteration (16-byte state loads, 8-byte shadow stores).
 __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ q, float* __restrict__ dq,
                                                      int64_t n_nodes, DivU64 div_n3, DivU64 div_5, double rho0,
                                                      double E0) {
-    const int64_t n = n_nodes * 5;
+    const int64_t n = n_nodes * 5, n2 = n / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int v = var_of(i, div_n3, div_5);
-        double x = q[i];
-        if (v == 0) x -= rho0;
-        else if (v == 4) x -= E0;
-        dq[i] = d2f_int(x);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += stride) {
+        const int64_t i = 2 * t;
+        const double2 x = reinterpret_cast<const double2*>(q)[t];
+        const float a = d2f_int(less_ref(x.x, var_of(i, div_n3, div_5), rho0, E0));
+        const float b = d2f_int(less_ref(x.y, var_of(i + 1, div_n3, div_5), rho0, E0));
+        reinterpret_cast<float2*>(dq)[t] = make_float2(a, b);
     }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+        dq[n - 1] = d2f_int(less_ref(q[n - 1], var_of(n - 1, div_n3, div_5), rho0, E0));
 }
 
+// The update of NK stage terms, two consecutive entries per thread and iteration; all loads of an
+// iteration are issued together and the terms are summed in stage order in float64.
+template <int NK>
 __global__ void __launch_bounds__(256) final_kernel(double* __restrict__ q, float* __restrict__ dq_new,
                                                     const Combine64F cb, int64_t n_nodes, DivU64 div_n3,
                                                     DivU64 div_5, double rho0, double E0) {
-    const int64_t n = n_nodes * 5;
+    const int64_t n = n_nodes * 5, n2 = n / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        // all stage loads issued together (fixed trip count, predicated), summed in stage order
-        float kv[6];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += stride) {
+        const int64_t i = 2 * t;
+        float2 kv[NK];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) kv[j] = j < cb.nk ? __ldg(cb.k[j] + i) : 0.0f;
-        const double q0 = q[i];
+        for (int j = 0; j < NK; ++j) kv[j] = __ldg(reinterpret_cast<const float2*>(cb.k[j]) + t);
+        const double2 q0 = reinterpret_cast<const double2*>(q)[t];
+        double ia = 0.0, ib = 0.0;
+#pragma unroll
+        for (int j = 0; j < NK; ++j) {
+            ia = fma(cb.coef[j], f2d_int(kv[j].x), ia);
+            ib = fma(cb.coef[j], f2d_int(kv[j].y), ib);
+        }
+        const double qa = q0.x + ia, qb = q0.y + ib;
+        reinterpret_cast<double2*>(q)[t] = make_double2(qa, qb);
+        reinterpret_cast<float2*>(dq_new)[t] =
+            make_float2(d2f_int(less_ref(qa, var_of(i, div_n3, div_5), rho0, E0)),
+                        d2f_int(less_ref(qb, var_of(i + 1, div_n3, div_5), rho0, E0)));
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         double inc = 0.0;
 #pragma unroll
-        for (int j = 0; j < 6; ++j)
-            if (j < cb.nk) inc = fma(cb.coef[j], f2d_int(kv[j]), inc);
-        const double qn = q0 + inc;
-        q[i] = qn;
-        const int v = var_of(i, div_n3, div_5);
-        double x = qn;
-        if (v == 0) x -= rho0;
-        else if (v == 4) x -= E0;
-        dq_new[i] = d2f_int(x);
+        for (int j = 0; j < NK; ++j) inc = fma(cb.coef[j], f2d_int(cb.k[j][n - 1]), inc);
+        const double qn = q[n - 1] + inc;
+        q[n - 1] = qn;
+        dq_new[n - 1] = d2f_int(less_ref(qn, var_of(n - 1, div_n3, div_5), rho0, E0));
     }
 }
 
@@ -68,15 +89,24 @@ unsigned grid_for(int64_t n) {
 
 cudaError_t launch_shadow(const esdc_ctx* c, const double* q, float* dq, cudaStream_t s) {
     const double E0 = c->phys.R / (c->phys.gamma - 1.0);
-    shadow_kernel<<<grid_for(c->n_nodes * 5), 256, 0, s>>>(q, dq, c->n_nodes, DivU64::make(c->N3), DivU64::make(5),
-                                                           1.0, E0);
+    shadow_kernel<<<grid_for(c->n_nodes * 5 / 2), 256, 0, s>>>(q, dq, c->n_nodes, DivU64::make(c->N3),
+                                                               DivU64::make(5), 1.0, E0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_final_f32(const esdc_ctx* c, double* q, float* dq_new, const Combine64F& cb, cudaStream_t s) {
     const double E0 = c->phys.R / (c->phys.gamma - 1.0);
-    final_kernel<<<grid_for(c->n_nodes * 5), 256, 0, s>>>(q, dq_new, cb, c->n_nodes, DivU64::make(c->N3),
-                                                          DivU64::make(5), 1.0, E0);
+    const unsigned g = grid_for(c->n_nodes * 5 / 2);
+    const DivU64 d3 = DivU64::make(c->N3), d5 = DivU64::make(5);
+    switch (cb.nk) {
+        case 1: final_kernel<1><<<g, 256, 0, s>>>(q, dq_new, cb, c->n_nodes, d3, d5, 1.0, E0); break;
+        case 2: final_kernel<2><<<g, 256, 0, s>>>(q, dq_new, cb, c->n_nodes, d3, d5, 1.0, E0); break;
+        case 3: final_kernel<3><<<g, 256, 0, s>>>(q, dq_new, cb, c->n_nodes, d3, d5, 1.0, E0); break;
+        case 4: final_kernel<4><<<g, 256, 0, s>>>(q, dq_new, cb, c->n_nodes, d3, d5, 1.0, E0); break;
+        case 5: final_kernel<5><<<g, 256, 0, s>>>(q, dq_new, cb, c->n_nodes, d3, d5, 1.0, E0); break;
+        case 6: final_kernel<6><<<g, 256, 0, s>>>(q, dq_new, cb, c->n_nodes, d3, d5, 1.0, E0); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
