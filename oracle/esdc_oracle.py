@@ -13,6 +13,9 @@ Ja[:, l, m] = J dxi_l/dx_m; faces are numbered 2*l + side (side 0 = xi_l = -1, s
 Readings of points the paper leaves open (each one is repeated where it is used):
   * metric terms: conservative curl form of the degree-p interpolant of the mapping; it meets the
     discrete GCL (eq. discGCLconvection) exactly.  The same metrics serve the viscous terms.
+    Alternatively the paper's optimized metrics (Sec. 3): analytic (cofactor) metrics of the
+    interpolant on the faces and the Euclidean-nearest volume metrics that satisfy the discrete
+    GCL with them; the interface terms then use the surface metrics.
   * entropy variables: w = [(gamma - s)/(gamma - 1) - rho|u|^2/(2p), rho u/p, -rho/p] with
     s = log(p rho^-gamma), i.e. S = -rho s/(gamma-1) (a positive rescaling of S = -rho s).
   * inviscid interface term: EC two-point flux plus local Lax-Friedrichs dissipation in the
@@ -134,6 +137,9 @@ class Mesh:
     Ja: torch.Tensor     # [K,3,3,N,N,N]
     nbr: torch.Tensor    # [K,6] long, face neighbours
     h_min: float
+    # metrics the interface terms use at face nodes (the analytic surface metrics of the optimized
+    # metrics, [K,3,3,N,N,N] of which only face values are read); None: the volume metrics Ja
+    Ja_face: torch.Tensor | None = None
 
 
 def metric_terms(x: torch.Tensor, D: torch.Tensor):
@@ -161,6 +167,54 @@ def metric_terms(x: torch.Tensor, D: torch.Tensor):
         for l in range(3):
             Ja[:, l, m] = -curl[l]
     return J, Ja
+
+
+def cofactor_metrics(x: torch.Tensor, D: torch.Tensor) -> torch.Tensor:
+    """Ja[l][m] = (dx/dxi_a x dx/dxi_b)_m with (l, a, b) cyclic: the rows of the cofactor matrix of
+    dx/dxi, i.e. the analytic metric terms of the degree-p interpolant of the mapping at the nodes (D
+    differentiates the interpolant exactly).  On a face xi_l = +-1 row l involves only derivatives
+    along the face, so both elements sharing the face see the same values (to round-off)."""
+    x = x - x[:, :, :1, :1, :1]
+    dX = [[dxi(x[:, m], a, D) for a in range(3)] for m in range(3)]     # dX[m][a] = dx_m/dxi_a
+    K, N = x.shape[0], x.shape[-1]
+    Ja = torch.empty((K, 3, 3, N, N, N), dtype=F64)
+    for l in range(3):
+        a, b = (l + 1) % 3, (l + 2) % 3
+        for m in range(3):
+            m1, m2 = (m + 1) % 3, (m + 2) % 3
+            Ja[:, l, m] = dX[m1][a] * dX[m2][b] - dX[m2][a] * dX[m1][b]
+    return Ja
+
+
+def sbp_3d(sbp: SBP):
+    """Dense tensor-product operators Q_l = P (x) P (x) Q and E_l = P (x) P (x) E along xi_l (Sec. 2),
+    N^3 x N^3 with the nodes numbered xi1 fastest."""
+    P = torch.diag(sbp.w)
+    k3 = lambda A3, A2, A1: torch.kron(torch.kron(A3, A2), A1)
+    Ql = [k3(P, P, sbp.Q), k3(P, sbp.Q, P), k3(sbp.Q, P, P)]
+    El = [k3(P, P, sbp.E), k3(P, sbp.E, P), k3(sbp.E, P, P)]
+    return Ql, El
+
+
+def optimized_metrics(x: torch.Tensor, sbp: SBP):
+    """The paper's optimized metrics (Sec. 3): surface metrics analytic (the cofactor metrics t of
+    the interpolated mapping, read at face nodes) and, for each physical direction m, the volume
+    metrics a_m = (a_1m, a_2m, a_3m) nearest to t_m in the Euclidean norm among those that satisfy
+    the discrete GCL with those surface metrics, sum_l Q_l^T a_lm = sum_l E_l t_lm (the condition under
+    which the skew-symmetric flux differencing with the surface metrics in the interface terms keeps
+    a uniform flow).  With M = [Q_1^T Q_2^T Q_3^T] (N^3 x 3 N^3, rank N^3 - 1) the minimiser is
+    a_m = t_m + M^+ (b_m - M t_m), M^+ the Moore-Penrose pseudo-inverse.  Returns (a, t)."""
+    t = cofactor_metrics(x, sbp.D)
+    Ql, El = sbp_3d(sbp)
+    M = torch.cat([Q.T for Q in Ql], dim=1)
+    Mp = torch.linalg.pinv(M)
+    K, N3 = t.shape[0], sbp.N ** 3
+    a = torch.empty_like(t)
+    for m in range(3):
+        tv = t[:, :, m].reshape(K, 3 * N3)
+        b = sum(t[:, l, m].reshape(K, N3) @ El[l] for l in range(3))
+        a[:, :, m] = (tv + (b - tv @ M.T) @ Mp.T).reshape(t[:, :, m].shape)
+    return a, t
 
 
 def box_neighbours(kx: int, ky: int, kz: int, bounded=(False, False, False)) -> torch.Tensor:
@@ -194,11 +248,23 @@ def smallest_edge(x: torch.Tensor) -> float:
     return float(torch.stack(lens).min())
 
 
-def make_mesh(p: int, x, kx: int, ky: int, kz: int, bounded=(False, False, False)) -> Mesh:
+def _metrics(x: torch.Tensor, sbp: SBP, metrics: str):
+    J, Ja = metric_terms(x, sbp.D)
+    if metrics == "curl":
+        return J, Ja, None
+    if metrics == "optimized":
+        a, t = optimized_metrics(x, sbp)
+        return J, a, t
+    raise ValueError(metrics)
+
+
+def make_mesh(p: int, x, kx: int, ky: int, kz: int, bounded=(False, False, False), metrics: str = "curl") -> Mesh:
+    """metrics: "curl" (conservative curl form everywhere) or "optimized" (the paper's optimized
+    volume metrics, analytic surface metrics in the interface terms)."""
     sbp = sbp_operator(p)
     x = torch.as_tensor(x, dtype=F64)
-    J, Ja = metric_terms(x, sbp.D)
-    return Mesh(sbp, x, J, Ja, box_neighbours(kx, ky, kz, bounded), smallest_edge(x))
+    J, Ja, Jf = _metrics(x, sbp, metrics)
+    return Mesh(sbp, x, J, Ja, box_neighbours(kx, ky, kz, bounded), smallest_edge(x), Jf)
 
 
 def nbr_face(fn, q: torch.Tensor, mesh: Mesh, E: torch.Tensor, l: int, side: int, q_ext=None) -> torch.Tensor:
@@ -216,7 +282,7 @@ def nbr_face(fn, q: torch.Tensor, mesh: Mesh, E: torch.Tensor, l: int, side: int
     return vals
 
 
-def make_submesh(p: int, x, nbr: torch.Tensor, elems):
+def make_submesh(p: int, x, nbr: torch.Tensor, elems, metrics: str = "curl"):
     """The mesh restricted to `elems` and the two rings of face neighbours around them, which is
     all the residual on `elems` reads (the viscous terms need the neighbours' lifted gradients,
     which need their neighbours' face states); metric terms are element-local, so they are the
@@ -231,8 +297,8 @@ def make_submesh(p: int, x, nbr: torch.Tensor, elems):
     sub_nbr = torch.where(sub_nbr < 0, own, sub_nbr)   # outer ring: links never followed for elems
     sbp = sbp_operator(p)
     xs = torch.as_tensor(x[E2.numpy()], dtype=F64)
-    J, Ja = metric_terms(xs, sbp.D)
-    return Mesh(sbp, xs, J, Ja, sub_nbr, smallest_edge(xs)), E2, pos[E]
+    J, Ja, Jf = _metrics(xs, sbp, metrics)
+    return Mesh(sbp, xs, J, Ja, sub_nbr, smallest_edge(xs), Jf), E2, pos[E]
 
 
 # --------------------------------------------------------------------------------------------
@@ -481,9 +547,11 @@ def dc_volume_term(q: torch.Tensor, Ja: torch.Tensor, sbp: SBP, gas: Gas) -> tor
 
 def inviscid_sat(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, dissipation=True,
                  flux=None, q_ext=None) -> torch.Tensor:
-    """SAT^(I) on elements E at every face node: -(1/P_ii) E_ii [f*(own, nbr) - f(own)].n_J minus
+    """SAT^(I) on elements E at every face node: -(1/P_ii) E_ii [f*(own, nbr).n_S - f(own).n_J] minus
     (1/P_ii) lambda/2 (q_own - q_nbr) when dissipation is True (local Lax-Friedrichs reading), or
-    minus (1/P_ii) D (w_own - w_nbr)/2 with the Roe-type matrix D when dissipation == "matrix"."""
+    minus (1/P_ii) D (w_own - w_nbr)/2 with the Roe-type matrix D when dissipation == "matrix".  n_J is
+    the volume metric at the face node, n_S the surface metric (mesh.Ja_face; n_J when it is None);
+    lambda and D are taken with n_S."""
     flux = flux or ec_flux_n
     sbp = mesh.sbp
     qE = q[E]
@@ -495,9 +563,12 @@ def inviscid_sat(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, dissipa
             qo = face(qE, l, side)
             qn = nbr_face(lambda x: x, q, mesh, E, l, side, q_ext)
             nJ = face(mesh.Ja[E, l], l, side)
-            n = [nJ[:, m] for m in range(3)]
+            nv = [nJ[:, m] for m in range(3)]
+            n = nv if mesh.Ja_face is None else [face(mesh.Ja_face[E, l], l, side)[:, m] for m in range(3)]
             sgn = -1.0 if side == 0 else 1.0
-            val = -sgn * (flux(qo, qn, n, gas) - euler_flux_n(qo, n, gas))
+            # the own flux takes the volume metric (it is the E part of the volume term moved to the
+            # face); the two-point flux and the dissipation take the surface metric
+            val = -sgn * (flux(qo, qn, n, gas) - euler_flux_n(qo, nv, gas))
             if dissipation == "matrix":
                 # reading: D at the averaged state (rho_ln, ubar, p = rho_bar/(2 beta_bar)) applied to
                 # the jump of the entropy variables
@@ -598,7 +669,7 @@ def interior_penalty(q: torch.Tensor, mesh: Mesh, gas: Gas, E: torch.Tensor, coe
             f = 2 * l + side
             qo = face(qE, l, side)
             qn = nbr_face(lambda x: x, q, mesh, E, l, side, q_ext)
-            nJ = face(mesh.Ja[E, l], l, side)
+            nJ = face((mesh.Ja if mesh.Ja_face is None else mesh.Ja_face)[E, l], l, side)
             nn = torch.sqrt(nJ[:, 0] ** 2 + nJ[:, 1] ** 2 + nJ[:, 2] ** 2)
             # on a boundary face the exterior Jacobian is read as the interior one
             Jo = face(mesh.J[E].unsqueeze(1), l, side)[:, 0]
