@@ -76,7 +76,22 @@ typedef struct esdc_setup {
     double ip_coef;         /* interior-penalty coefficient sigma >= 0 (0: off; below)             */
     int bounded;            /* bit l (l = 0, 1, 2) set: the outer faces normal to xi_l are
                                boundaries with Dirichlet data (esdc_set_exterior); 0: periodic      */
+    int metrics;            /* ESDC_METRICS_CURL (0) or ESDC_METRICS_OPTIMIZED (1), below          */
 } esdc_setup_t;
+
+/* Metric terms (Sec. 3).  ESDC_METRICS_CURL: the conservative curl form of the degree-p interpolant
+ * of the mapping at every node; it satisfies the discrete GCL sum_l D_l Ja_lm = 0 exactly and the
+ * interface terms use its face values.  ESDC_METRICS_OPTIMIZED: the paper's optimized metrics.  The
+ * surface metrics are analytic: row l of the cofactor matrix of dx/dxi of the interpolated mapping
+ * (dx/dxi_a x dx/dxi_b with (l, a, b) cyclic) at the face nodes of direction l, which depends only on
+ * the face's nodes and so is the same from both sides.  The volume metrics are, for each m, the
+ * Euclidean-nearest values to the cofactor metrics at all nodes that satisfy the discrete GCL with
+ * those surface metrics, sum_l Q_l^T Ja_lm = sum_l E_l Ja^surf_lm (Q_l, E_l the tensor-product SBP
+ * matrices; the condition under which the skew flux differencing keeps a uniform flow).  The
+ * interface SAT (two-point flux, dissipation, interior penalty) then reads the surface metrics; the
+ * volume and viscous terms read the volume metrics.  Float64 only, no adjoint. */
+#define ESDC_METRICS_CURL 0
+#define ESDC_METRICS_OPTIMIZED 1
 
 /* Interior penalty (the IP term of eq. NSL; its constants are in the paper's references).  With
  * ip_coef = sigma > 0 and mu > 0, every face node adds -(1/P_ii) sigma mu |n_J| / h dq/dw (w_own -
@@ -99,12 +114,22 @@ int esdc_operators(int p, double* D_host, double* S_host);
 
 /*
  * esdc_host_geometry -- the metric terms esdc_create would build, computed on the host without a
- * GPU: J_host[K][N^3], Ja_host[K][9][N^3] (entry l*3 + m = J dxi_l/dx_m, conservative curl form,
- * Sec. 3) and the smallest element edge h_min.  Any output may be NULL.
+ * GPU: J_host[K][N^3], Ja_host[K][9][N^3] (entry l*3 + m = J dxi_l/dx_m: the volume metrics of
+ * setup->metrics, Sec. 3) and the smallest element edge h_min.  Any output may be NULL.
  * Errors: ESDC_ERR_ARG, ESDC_ERR_MESH (J <= 0 or non-finite).
  */
 int esdc_host_geometry(const esdc_setup_t* setup, const double* node_xyz_host, double* J_host,
                        double* Ja_host, double* h_min);
+
+/*
+ * esdc_host_surface_metrics -- the metrics the interface terms read at the face nodes, computed on
+ * the host without a GPU (Sec. 3): nsurf_host[K][6][3][N^2], face f = 2 l + side (side 0: xi_l = -1),
+ * component m = 0..2 of Ja_l. at face node t1 + N t2, where (t1, t2) are the node's indices in the
+ * two other directions in increasing direction order.  ESDC_METRICS_OPTIMIZED: the analytic
+ * (cofactor) surface metrics; ESDC_METRICS_CURL: the face values of the curl-form volume metrics.
+ * Errors: ESDC_ERR_ARG (NULL pointers), ESDC_ERR_MESH.
+ */
+int esdc_host_surface_metrics(const esdc_setup_t* setup, const double* node_xyz_host, double* nsurf_host);
 
 /*
  * esdc_create -- build operators and geometry and allocate library buffers on the current device.

@@ -22,11 +22,15 @@ PREC_FP64 = 0
 PREC_FP32 = 1
 
 
+METRICS = {"curl": 0, "optimized": 1}
+
+
 class Setup(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("kx", ctypes.c_int), ("ky", ctypes.c_int), ("kz", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Ma", ctypes.c_double),
                 ("Re", ctypes.c_double), ("dissipation", ctypes.c_int), ("precision", ctypes.c_int),
-                ("volume_flux", ctypes.c_int), ("ip_coef", ctypes.c_double), ("bounded", ctypes.c_int)]
+                ("volume_flux", ctypes.c_int), ("ip_coef", ctypes.c_double), ("bounded", ctypes.c_int),
+                ("metrics", ctypes.c_int)]
 
 
 class EsdcError(RuntimeError):
@@ -50,6 +54,7 @@ def lib() -> ctypes.CDLL:
         "esdc_lgl": (I, [I, P, P]),
         "esdc_operators": (I, [I, P, P]),
         "esdc_host_geometry": (I, [ctypes.POINTER(Setup), P, P, P, ctypes.POINTER(D)]),
+        "esdc_host_surface_metrics": (I, [ctypes.POINTER(Setup), P, P]),
         "esdc_create": (I, [ctypes.POINTER(Setup), P, ctypes.POINTER(P)]),
         "esdc_destroy": (I, [P]),
         "esdc_layout": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]),

@@ -366,9 +366,10 @@ int prepare_variant(esdc_ctx* c) {
 
 int ensure_adjoint(esdc_ctx* c) {
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
-        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src)
+        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src ||
+        c->d_nsurf)
         return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with scalar "
-                                          "dissipation, no interior penalty and no source");
+                                          "dissipation, curl-form metrics, no interior penalty and no source");
     if (c->d_adj_g) return ESDC_OK;
     const size_t N2 = (size_t)c->N * c->N;
     CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
@@ -382,9 +383,10 @@ int ensure_adjoint(esdc_ctx* c) {
 int adjoint_checks(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, void* ws, size_t ws_bytes) {
     if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
-        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src)
+        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src ||
+        c->d_nsurf)
         return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with scalar "
-                                          "dissipation, no interior penalty and no source");
+                                          "dissipation, curl-form metrics, no interior penalty and no source");
     if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
     const size_t need = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");
@@ -408,6 +410,7 @@ void free_ctx(esdc_ctx* c) {
     for (void* ev : c->prof_events) cudaEventDestroy((cudaEvent_t)ev);
     cudaFree(c->d_geom);
     cudaFree(c->d_jinv);
+    cudaFree(c->d_nsurf);
     cudaFree(c->d_geomf);
     cudaFree(c->d_nbr);
     cudaFree(c->d_trace);
@@ -484,6 +487,10 @@ static int check_setup(const esdc_setup_t& s) {
         return fail(ESDC_ERR_ARG, "volume_flux must be ESDC_FLUX_ESC, ESDC_FLUX_KG or ESDC_FLUX_DC");
     if (s.volume_flux != ESDC_FLUX_ESC && s.precision != ESDC_PREC_FP64)
         return fail(ESDC_ERR_UNSUPPORTED, "the KG and DC volume fluxes are built for float64 only");
+    if (s.metrics != ESDC_METRICS_CURL && s.metrics != ESDC_METRICS_OPTIMIZED)
+        return fail(ESDC_ERR_ARG, "metrics must be ESDC_METRICS_CURL or ESDC_METRICS_OPTIMIZED");
+    if (s.metrics == ESDC_METRICS_OPTIMIZED && s.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "the optimized metrics are built for float64 only");
     return ESDC_OK;
 }
 
@@ -504,6 +511,38 @@ int esdc_host_geometry(const esdc_setup_t* setup, const double* xyz, double* J, 
         if (Ja) std::memcpy(Ja + e * 9 * N3, &hs.geom[(e * 10 + 1) * N3], 9 * N3 * sizeof(double));
     }
     if (h_min) *h_min = hs.h_min;
+    return ESDC_OK;
+}
+
+int esdc_host_surface_metrics(const esdc_setup_t* setup, const double* xyz, double* nsurf) {
+    if (!setup || !xyz || !nsurf) return fail(ESDC_ERR_ARG, "null argument");
+    int st = check_setup(*setup);
+    if (st) return st;
+    esdc::HostSetup hs;
+    st = esdc::build_operators(setup->p, hs);
+    if (st) return fail(st, "operator construction failed");
+    std::string err;
+    st = esdc::build_geometry(*setup, xyz, hs, err);
+    if (st) return fail(st, err);
+    const int64_t K = (int64_t)setup->kx * setup->ky * setup->kz;
+    const int N = hs.N, N2 = N * N, N3 = N2 * N;
+    if (!hs.nsurf.empty()) {
+        std::memcpy(nsurf, hs.nsurf.data(), hs.nsurf.size() * sizeof(double));
+        return ESDC_OK;
+    }
+    for (int64_t e = 0; e < K; ++e)
+        for (int l = 0; l < 3; ++l)
+            for (int side = 0; side < 2; ++side) {
+                const int fix = side ? N - 1 : 0;
+                for (int t2 = 0; t2 < N; ++t2)
+                    for (int t1 = 0; t1 < N; ++t1) {
+                        const int node = l == 0 ? fix + N * t1 + N2 * t2
+                                                : (l == 1 ? t1 + N * fix + N2 * t2 : t1 + N * t2 + N2 * fix);
+                        for (int m = 0; m < 3; ++m)
+                            nsurf[((e * 6 + 2 * l + side) * 3 + m) * N2 + t1 + N * t2] =
+                                hs.geom[(e * 10 + 1 + 3 * l + m) * N3 + node];
+                    }
+            }
     return ESDC_OK;
 }
 
@@ -590,6 +629,11 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     }
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_nbr, hs.nbr.data(), hs.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !hs.nsurf.empty()) {
+        e = cudaMalloc(&c->d_nsurf, hs.nsurf.size() * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->d_nsurf, hs.nsurf.data(), hs.nsurf.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = esdc::prepare_rhs_f64(c);
     if (e == cudaSuccess && s.precision == ESDC_PREC_FP32) {
         std::vector<float> gf(hs.geom.size());

@@ -51,6 +51,7 @@ struct HostSetup {
     std::vector<double> D;               // N*N row-major
     std::vector<double> S;               // N*N row-major, exactly skew
     std::vector<double> geom;            // [K][10][N^3]: J, Ja_lm (l-major)
+    std::vector<double> nsurf;           // [K][6][3][N^2] surface metrics (optimized metrics only)
     std::vector<int32_t> nbr;            // [K][6]
     double h_min = 0.0;
 };
@@ -79,6 +80,7 @@ struct esdc_ctx {
     // device buffers owned by the library
     double* d_geom = nullptr;        // [K][10][N3]
     double* d_jinv = nullptr;        // [K][N3] 1/J
+    double* d_nsurf = nullptr;       // [K][6][3][N2] surface metrics of the optimized metrics (else null)
     const double* d_qext = nullptr;  // caller-owned exterior (Dirichlet) state, [K][5][N3] (bounded boxes)
     const double* d_src = nullptr;   // caller-owned source term added to dq/dt, [K][5][N3]
     float* d_geomf = nullptr;        // [K][10][N3] float32 copy (mixed precision)

@@ -249,7 +249,8 @@ template <int N, int VF, bool XF>
 __global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::MINB)
 rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const double* __restrict__ geom,
              const int32_t* __restrict__ nbr, double* __restrict__ trace, int64_t K, const Ops ops,
-             const Phys ph, const double* __restrict__ qext, const double* __restrict__ src) {
+             const Phys ph, const double* __restrict__ qext, const double* __restrict__ src,
+             const double* __restrict__ nsurf) {
     constexpr int N2 = Cfg<N>::N2, N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB;
     extern __shared__ double smem[];
     const int t = threadIdx.x;
@@ -390,8 +391,17 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
             double RTn, cn;
             load_prim(sP, N3, own, so);
             to_prim(qn, ph, sn, RTn, cn);
-            const double n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own],
-                         n2 = sG[(3 + 3 * l) * N3 + own];
+            double n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own], n2 = sG[(3 + 3 * l) * N3 + own];
+            if constexpr (XF) {
+                // optimized metrics: the interface terms take the analytic surface metrics (the own
+                // flux, cancelled against the volume term's boundary part, keeps the volume metrics)
+                if (nsurf) {
+                    const double* ns = nsurf + (el * 6 + 2 * l + side) * 3 * N2 + fi;
+                    n0 = ns[0];
+                    n1 = ns[N2];
+                    n2 = ns[2 * N2];
+                }
+            }
             double f[5];
             if constexpr (VF == kFluxESC) {
                 ec_flux(so, sn, n0, n1, n2, ph, f);
@@ -568,7 +578,7 @@ cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaS
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     if (ev) cudaEventRecord(ev[0], s);
     rhs_main_f64<N, VF, XF><<<grid, C::THREADS, smem, s>>>(q, dqdt, c->d_geom, c->d_nbr, (double*)c->d_trace, c->K,
-                                                           c->ops, c->phys, c->d_qext, c->d_src);
+                                                           c->ops, c->phys, c->d_qext, c->d_src, c->d_nsurf);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (c->phys.viscous) {
@@ -594,7 +604,7 @@ cudaError_t prepare_xf(int vf) {
 }
 
 bool extra_face_terms(const esdc_ctx* c) {
-    return c->phys.dissipation == 2 || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src;
+    return c->phys.dissipation == 2 || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src || c->d_nsurf;
 }
 
 template <int N>

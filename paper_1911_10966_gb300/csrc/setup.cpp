@@ -129,8 +129,9 @@ void build_box_neighbours(int kx, int ky, int kz, int bounded, std::vector<int32
 
 namespace {
 
-// Apply D along direction a (0: xi1 fastest) to a nodal field of one element.
-void apply_d(const std::vector<double>& D, int N, int a, const double* u, double* out) {
+// Apply the N x N matrix M (row-major) along direction a (0: xi1 fastest) to a nodal field of one
+// element: out_i = sum_j M_ij u_j on every line of direction a.
+void apply_mat(const double* M, int N, int a, const double* u, double* out) {
     const int stride = (a == 0) ? 1 : (a == 1 ? N : N * N);
     for (int i3 = 0; i3 < N; ++i3)
         for (int i2 = 0; i2 < N; ++i2)
@@ -139,9 +140,13 @@ void apply_d(const std::vector<double>& D, int N, int a, const double* u, double
                 const int ia = (a == 0) ? i1 : (a == 1 ? i2 : i3);
                 const int base = node - ia * stride;
                 double s = 0.0;
-                for (int j = 0; j < N; ++j) s += D[ia * N + j] * u[base + j * stride];
+                for (int j = 0; j < N; ++j) s += M[ia * N + j] * u[base + j * stride];
                 out[node] = s;
             }
+}
+
+void apply_d(const std::vector<double>& D, int N, int a, const double* u, double* out) {
+    apply_mat(D.data(), N, a, u, out);
 }
 
 // Geometry of one element: J and Ja_lm = J dxi_l/dx_m in conservative curl form,
@@ -184,6 +189,164 @@ bool element_geometry(const std::vector<double>& D, int N, const double* xyz, do
     return ok;
 }
 
+// Eigen-decomposition of a symmetric n x n matrix (row-major) by cyclic Jacobi rotations (Golub and
+// Van Loan, Matrix Computations, Sec. 8.5): A = U diag(lam) U^T with U orthogonal, eigenvectors in
+// its columns.
+void sym_eigen(int n, std::vector<double> A, std::vector<double>& U, std::vector<double>& lam) {
+    U.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) U[i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) (i == j ? diag : off) += A[i * n + j] * A[i * n + j];
+        if (off <= 1e-34 * (diag + off)) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                // rotation angle phi with cot(2 phi) = theta zeroes A_pq
+                const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                const double t = std::fabs(theta) > 1e150
+                                     ? 0.5 / theta
+                                     : std::copysign(1.0, theta) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {     // A <- A J
+                    const double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - sn * akq;
+                    A[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {     // A <- J^T A
+                    const double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - sn * aqk;
+                    A[q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {     // U <- U J
+                    const double ukp = U[k * n + p], ukq = U[k * n + q];
+                    U[k * n + p] = c * ukp - sn * ukq;
+                    U[k * n + q] = sn * ukp + c * ukq;
+                }
+            }
+    }
+    lam.resize(n);
+    for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
+}
+
+// Fast diagonalisation (Lynch, Rice and Thomas, Numer. Math. 6, 1964) of the Gram matrix
+// G = sum_l Q_l^T Q_l of the tensor-product SBP matrices Q_l = P (x) P (x) Q along xi_l: with
+// A = Q^T Q and the generalised eigenvectors A V = P^2 V diag(lam), V^T P^2 V = I, the matrix
+// W = V (x) V (x) V gives W^T G W = diag(lam_k1 + lam_k2 + lam_k3).  G is singular (G 1 = 0; the
+// mode k1 = k2 = k3 = k0 of the zero eigenvalue lam_k0, whose eigenvector is constant); for r
+// orthogonal to 1 the solution y = W diag(1/(lam_k1 + lam_k2 + lam_k3), 0 at the null mode) W^T r
+// satisfies G y = r.
+struct FastDiag {
+    int N = 0, k0 = 0;
+    std::vector<double> V, Vt, lam;   // V[i][k], its transpose, eigenvalues
+};
+
+FastDiag make_fast_diag(const HostSetup& hs) {
+    const int N = hs.N;
+    std::vector<double> Q(N * N), B(N * N);
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) Q[i * N + j] = hs.w[i] * hs.D[i * N + j];
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            double a = 0.0;
+            for (int k = 0; k < N; ++k) a += Q[k * N + i] * Q[k * N + j];
+            B[i * N + j] = a / (hs.w[i] * hs.w[j]);          // P^-1 A P^-1, symmetric
+        }
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < i; ++j) B[i * N + j] = B[j * N + i] = 0.5 * (B[i * N + j] + B[j * N + i]);
+    FastDiag fd;
+    fd.N = N;
+    std::vector<double> U;
+    sym_eigen(N, B, U, fd.lam);
+    fd.V.resize(N * N);
+    fd.Vt.resize(N * N);
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < N; ++k) {
+            fd.V[i * N + k] = U[i * N + k] / hs.w[i];
+            fd.Vt[k * N + i] = fd.V[i * N + k];
+        }
+    fd.k0 = (int)(std::min_element(fd.lam.begin(), fd.lam.end()) - fd.lam.begin());
+    return fd;
+}
+
+// Optimized metrics of one element (Sec. 3).  t_lm = (dx/dxi_a x dx/dxi_b)_m, (l, a, b) cyclic, are
+// the analytic (cofactor) metrics of the interpolated mapping; their face values are the surface
+// metrics, written to ns[6][3][N^2].  For each m the volume metrics are the Euclidean-nearest a_m to
+// t_m with M a_m = b_m, M = [Q_1^T Q_2^T Q_3^T], b_m = sum_l E_l t_lm.  The minimiser is
+// a_m = t_m + M^T y with G y = b_m - M t_m, G = M M^T; since Q_l + Q_l^T = E_l the right-hand side is
+// sum_l Q_l t_lm = P3 sum_l D_l t_lm (P3 the tensor weights), and (M^T y)_l = Q_l y = P3 D_l y.
+// g: [10][N^3] as element_geometry (J, then a_lm l-major).
+bool element_geometry_optimized(const HostSetup& hs, const FastDiag& fd, const double* xyz, double* g, double* ns) {
+    const int N = hs.N, N2 = N * N, N3 = N2 * N;
+    const std::vector<double>& D = hs.D;
+    std::vector<double> X(3 * N3), dX(9 * N3), t(9 * N3), r(N3), z(N3), y(N3), tmp(N3), W3(N3);
+    for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < N3; ++n) X[m * N3 + n] = xyz[m * N3 + n] - xyz[m * N3];
+    for (int m = 0; m < 3; ++m)
+        for (int a = 0; a < 3; ++a) apply_d(D, N, a, &X[m * N3], &dX[(m * 3 + a) * N3]);
+    for (int n = 0; n < N3; ++n) W3[n] = hs.w[n % N] * hs.w[(n / N) % N] * hs.w[n / N2];
+    bool ok = true;
+    auto F = [&](int m, int a, int n) { return dX[(m * 3 + a) * N3 + n]; };
+    for (int n = 0; n < N3; ++n) {
+        const double J = F(0, 0, n) * (F(1, 1, n) * F(2, 2, n) - F(1, 2, n) * F(2, 1, n))
+                       - F(0, 1, n) * (F(1, 0, n) * F(2, 2, n) - F(1, 2, n) * F(2, 0, n))
+                       + F(0, 2, n) * (F(1, 0, n) * F(2, 1, n) - F(1, 1, n) * F(2, 0, n));
+        g[n] = J;
+        if (!(J > 0.0) || !std::isfinite(J)) ok = false;
+    }
+    for (int l = 0; l < 3; ++l) {
+        const int a = (l + 1) % 3, b = (l + 2) % 3;
+        for (int m = 0; m < 3; ++m) {
+            const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
+            for (int n = 0; n < N3; ++n)
+                t[(l * 3 + m) * N3 + n] = F(m1, a, n) * F(m2, b, n) - F(m2, a, n) * F(m1, b, n);
+        }
+    }
+    // surface metrics: row l of t on the two faces of direction l
+    for (int l = 0; l < 3; ++l)
+        for (int side = 0; side < 2; ++side) {
+            const int fix = side ? N - 1 : 0;
+            for (int t2 = 0; t2 < N; ++t2)
+                for (int t1 = 0; t1 < N; ++t1) {
+                    const int node = l == 0 ? fix + N * t1 + N2 * t2 : (l == 1 ? t1 + N * fix + N2 * t2 : t1 + N * t2 + N2 * fix);
+                    for (int m = 0; m < 3; ++m) ns[((2 * l + side) * 3 + m) * N2 + t1 + N * t2] = t[(l * 3 + m) * N3 + node];
+                }
+        }
+    for (int m = 0; m < 3; ++m) {
+        std::fill(r.begin(), r.end(), 0.0);
+        for (int l = 0; l < 3; ++l) {
+            apply_d(D, N, l, &t[(l * 3 + m) * N3], tmp.data());
+            for (int n = 0; n < N3; ++n) r[n] += tmp[n];
+        }
+        for (int n = 0; n < N3; ++n) r[n] *= W3[n];
+        // y = W diag(1/Lambda) W^T r
+        apply_mat(fd.Vt.data(), N, 0, r.data(), z.data());
+        apply_mat(fd.Vt.data(), N, 1, z.data(), tmp.data());
+        apply_mat(fd.Vt.data(), N, 2, tmp.data(), z.data());
+        for (int k3 = 0; k3 < N; ++k3)
+            for (int k2 = 0; k2 < N; ++k2)
+                for (int k1 = 0; k1 < N; ++k1) {
+                    const int k = (k3 * N + k2) * N + k1;
+                    if (k1 == fd.k0 && k2 == fd.k0 && k3 == fd.k0) z[k] = 0.0;
+                    else z[k] /= fd.lam[k1] + fd.lam[k2] + fd.lam[k3];
+                }
+        apply_mat(fd.V.data(), N, 0, z.data(), tmp.data());
+        apply_mat(fd.V.data(), N, 1, tmp.data(), z.data());
+        apply_mat(fd.V.data(), N, 2, z.data(), y.data());
+        for (int l = 0; l < 3; ++l) {
+            apply_d(D, N, l, y.data(), tmp.data());
+            double* dst = g + (1 + l * 3 + m) * N3;
+            for (int n = 0; n < N3; ++n) {
+                dst[n] = t[(l * 3 + m) * N3 + n] + W3[n] * tmp[n];
+                if (!std::isfinite(dst[n])) ok = false;
+            }
+        }
+    }
+    return ok;
+}
+
 double element_min_edge(int N, const double* xyz) {
     const int N3 = N * N * N;
     auto corner = [&](int i3, int i2, int i1, int m) { return xyz[m * N3 + (i3 * N + i2) * N + i1]; };
@@ -209,9 +372,17 @@ double element_min_edge(int N, const double* xyz) {
 }  // namespace
 
 int build_geometry(const esdc_setup_t& s, const double* xyz, HostSetup& hs, std::string& err) {
-    const int N = hs.N, N3 = N * N * N;
+    const int N = hs.N, N3 = N * N * N, N2 = N * N;
     const int64_t K = (int64_t)s.kx * s.ky * s.kz;
     hs.geom.assign((size_t)K * 10 * N3, 0.0);
+    const bool opt = s.metrics == ESDC_METRICS_OPTIMIZED;
+    FastDiag fd;
+    if (opt) {
+        hs.nsurf.assign((size_t)K * 6 * 3 * N2, 0.0);
+        fd = make_fast_diag(hs);
+    } else {
+        hs.nsurf.clear();
+    }
     unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     if (K < 64) nt = 1;
     std::vector<int> bad(nt, 0);
@@ -221,7 +392,10 @@ int build_geometry(const esdc_setup_t& s, const double* xyz, HostSetup& hs, std:
         th.emplace_back([&, t]() {
             for (int64_t e = t; e < K; e += nt) {
                 const double* x = xyz + (size_t)e * 3 * N3;
-                if (!element_geometry(hs.D, N, x, &hs.geom[(size_t)e * 10 * N3])) bad[t] = 1;
+                const bool good = opt ? element_geometry_optimized(hs, fd, x, &hs.geom[(size_t)e * 10 * N3],
+                                                                   &hs.nsurf[(size_t)e * 6 * 3 * N2])
+                                      : element_geometry(hs.D, N, x, &hs.geom[(size_t)e * 10 * N3]);
+                if (!good) bad[t] = 1;
                 hmin[t] = std::min(hmin[t], element_min_edge(N, x));
             }
         });

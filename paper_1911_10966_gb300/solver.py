@@ -58,10 +58,13 @@ class Solver:
     ip_coef: interior-penalty coefficient (0: off; float64 only).
     bounded: per direction, True for boundary faces with Dirichlet data (set_exterior) instead of
     periodic connectivity (float64 only).
+    metrics: "curl" (conservative curl form) or "optimized" (the paper's optimized volume metrics
+    with analytic surface metrics in the interface terms; float64 only).
     """
 
     def __init__(self, p, kx, ky, kz, coords, *, gamma=1.4, Pr=0.72, Ma=0.1, Re=0.0, dissipation=True,
-                 precision="fp64", volume_flux="esc", ip_coef=0.0, bounded=(False, False, False), device=None):
+                 precision="fp64", volume_flux="esc", ip_coef=0.0, bounded=(False, False, False), metrics="curl",
+                 device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU implementation exists)")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
@@ -73,6 +76,9 @@ class Solver:
         if volume_flux not in nat.FLUX:
             raise ValueError("volume_flux must be 'esc', 'kg' or 'dc'")
         self.volume_flux = volume_flux
+        if metrics not in nat.METRICS:
+            raise ValueError("metrics must be 'curl' or 'optimized'")
+        self.metrics = metrics
         self.dtype_r = torch.float64 if precision == "fp64" else torch.float32
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         if coords.shape != (self.K, 3, self.N, self.N, self.N):
@@ -81,7 +87,7 @@ class Solver:
         diss = 2 if dissipation == "matrix" else (1 if dissipation else 0)
         st = nat.Setup(p, kx, ky, kz, gamma, Pr, Ma, Re, diss,
                        nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32, nat.FLUX[volume_flux],
-                       float(ip_coef), sum(1 << l for l in range(3) if bounded[l]))
+                       float(ip_coef), sum(1 << l for l in range(3) if bounded[l]), nat.METRICS[metrics])
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             nat.check(nat.lib().esdc_create(ctypes.byref(st), coords.ctypes.data, ctypes.byref(self._ctx)),

@@ -15,7 +15,8 @@ TWO_PI_BOX = ([-math.pi] * 3, [math.pi] * 3)
 
 
 def make_pair(p, k, *, warp=0.0, seed=0, Ma=0.1, Re=1600.0, dissipation=True, box=TWO_PI_BOX,
-              state="tgv", noise=0.0, noise_seed=1, precision="fp64", oracle_elems=None, volume_flux="esc"):
+              state="tgv", noise=0.0, noise_seed=1, precision="fp64", oracle_elems=None, volume_flux="esc",
+              metrics="curl"):
     """GPU solver + state and the oracle's mesh + state for the same workload.  With oracle_elems
     the oracle side is the two-ring submesh around those elements (returned mesh/state are the
     submesh's; the residual rows of oracle_elems are returned as mesh.rows)."""
@@ -25,16 +26,16 @@ def make_pair(p, k, *, warp=0.0, seed=0, Ma=0.1, Re=1600.0, dissipation=True, bo
     xi_gpu, _ = lgl(p)
     x_gpu = I.box_coords(xi_gpu, kx, ky, kz, lo, hi, warp=warp, seed=seed)
     solver = Solver(p, kx, ky, kz, x_gpu, Ma=Ma, Re=Re, dissipation=dissipation, precision=precision,
-                    volume_flux=volume_flux)
+                    volume_flux=volume_flux, metrics=metrics)
     s = O.sbp_operator(p)
     x_ora = I.box_coords(s.xi.numpy(), kx, ky, kz, lo, hi, warp=warp, seed=seed)
     gas = O.Gas.from_mach(Ma, Re)
     if oracle_elems is not None:
-        mesh, E2, rows = O.make_submesh(p, x_ora, O.box_neighbours(kx, ky, kz), oracle_elems)
+        mesh, E2, rows = O.make_submesh(p, x_ora, O.box_neighbours(kx, ky, kz), oracle_elems, metrics=metrics)
         mesh.rows = rows
         x_ora = x_ora[E2.numpy()]
     else:
-        mesh = O.make_mesh(p, x_ora, kx, ky, kz)
+        mesh = O.make_mesh(p, x_ora, kx, ky, kz, metrics=metrics)
 
     def st(x):
         if state == "tgv":

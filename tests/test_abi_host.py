@@ -67,6 +67,37 @@ def test_host_geometry_matches_oracle(L, p, warp):
     assert abs(h.value - m.h_min) < 1e-14 * m.h_min
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 7])
+def test_host_optimized_metrics_match_oracle(L, p):
+    """The library's optimized metrics (Sec. 3; solved by fast diagonalisation of the Gram matrix of
+    the GCL constraint) against the oracle's (dense pseudo-inverse), volume and surface metrics."""
+    k = (3, 2, 2)
+    s = O.sbp_operator(p)
+    x = np.ascontiguousarray(I.box_coords(s.xi.numpy(), *k, [-math.pi] * 3, [math.pi] * 3, warp=0.1, seed=0))
+    K, N = x.shape[0], p + 1
+    N2, N3 = N * N, N ** 3
+    st = _setup(p, *k)
+    st.metrics = 1
+    J, Ja, ns = np.zeros((K, N3)), np.zeros((K, 9, N3)), np.zeros((K, 6, 3, N2))
+    nat.check(L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, J.ctypes.data, Ja.ctypes.data, None), "geometry")
+    nat.check(L.esdc_host_surface_metrics(ctypes.byref(st), x.ctypes.data, ns.ctypes.data), "surface")
+    m = O.make_mesh(p, x, *k, metrics="optimized")
+    Jao = m.Ja.numpy().reshape(K, 9, N3)
+    nso = np.stack([O.face(m.Ja_face[:, l], l, side).numpy().reshape(K, 3, N2) for l in range(3) for side in (0, 1)],
+                   axis=1)
+    scale = np.abs(Jao).max()
+    assert np.abs(Ja - Jao).max() < 1e-14 * p * p * scale
+    assert np.abs(ns - nso).max() < 1e-14 * p * p * scale
+    assert np.abs(J - m.J.numpy().reshape(K, N3)).max() < 1e-14 * p * p * np.abs(J).max()
+    # the curl-form context reports the face values of its volume metrics as its surface metrics
+    st.metrics = 0
+    nat.check(L.esdc_host_surface_metrics(ctypes.byref(st), x.ctypes.data, ns.ctypes.data), "surface")
+    mc = O.make_mesh(p, x, *k)
+    ncurl = np.stack([O.face(mc.Ja[:, l], l, side).numpy().reshape(K, 3, N2) for l in range(3) for side in (0, 1)],
+                     axis=1)
+    assert np.abs(ns - ncurl).max() < 1e-14 * p * p * scale
+
+
 def test_argument_errors(L):
     xi = np.zeros(9)
     assert L.esdc_lgl(0, xi.ctypes.data, xi.ctypes.data) == nat.ESDC_ERR_ARG
@@ -113,6 +144,13 @@ def test_empty_and_out_of_range_sizes(L):
     st = _setup(1, 1, 1, 1)
     st.precision = 2
     assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_ARG
+    st = _setup(1, 1, 1, 1)
+    st.metrics = 2
+    assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_ARG
+    st.metrics = 1
+    st.precision = nat.PREC_FP32
+    assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_UNSUPPORTED
+    assert L.esdc_host_surface_metrics(ctypes.byref(st), x.ctypes.data, None) == nat.ESDC_ERR_ARG
 
 
 def test_single_element_and_p1_geometry(L):
