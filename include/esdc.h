@@ -64,7 +64,8 @@ typedef struct esdc_ctx esdc_ctx; /* opaque, library owned */
 
 /* Problem description.  Only fully periodic structured boxes are connected by this build. */
 typedef struct esdc_setup {
-    int p;                  /* polynomial degree, 1 <= p <= 7 (N = p + 1 LGL nodes per direction) */
+    int p;                  /* polynomial degree, 1 <= p <= 7 or p = 15 (N = p + 1 LGL nodes per
+                               direction; p = 15 below)                                             */
     int kx, ky, kz;         /* elements per direction, each >= 1                                  */
     double gamma;           /* ratio of specific heats (> 1)                                      */
     double Pr;              /* Prandtl number (> 0)                                               */
@@ -93,6 +94,13 @@ typedef struct esdc_setup {
 #define ESDC_METRICS_CURL 0
 #define ESDC_METRICS_OPTIMIZED 1
 
+/* Degree p = 15 (the top degree of the paper's cost comparison, Sec. 5.2): the float64 residual is
+ * built in several passes instead of one CTA per element.  Built for periodic boxes with the curl-form
+ * metrics, the three volume fluxes and ESDC_DISS_NONE or ESDC_DISS_LLF, viscous or inviscid; float32,
+ * matrix dissipation, interior penalty, boundaries, sources, optimized metrics, the adjoint and
+ * esdc_budgets_noalloc are refused (ESDC_ERR_UNSUPPORTED, or ESDC_ERR_ARG for the last).  Degrees
+ * 8 to 14 are refused with ESDC_ERR_UNSUPPORTED. */
+
 /* Interior penalty (the IP term of eq. NSL; its constants are in the paper's references).  With
  * ip_coef = sigma > 0 and mu > 0, every face node adds -(1/P_ii) sigma mu |n_J| / h dq/dw (w_own -
  * w_nbr), with dq/dw at the averaged state of ESDC_DISS_MATRIX and h = (J_own + J_nbr)/|n_J|; the
@@ -101,7 +109,7 @@ typedef struct esdc_setup {
 /*
  * esdc_lgl -- the N = p+1 LGL nodes xi[N] (ascending on [-1, 1]) and quadrature weights w[N]
  * (Sec. 2, Definition 1: the norm matrix P = diag(w) of the SBP operator).  Host only, no GPU.
- * xi, w: host arrays of N doubles, caller owned.  Errors: ESDC_ERR_ARG for p out of range or NULL.
+ * xi, w: host arrays of N doubles, caller owned.  Errors: ESDC_ERR_ARG for p outside [1, 15] or NULL.
  */
 int esdc_lgl(int p, double* xi_host, double* w_host);
 

@@ -367,9 +367,9 @@ int prepare_variant(esdc_ctx* c) {
 int ensure_adjoint(esdc_ctx* c) {
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
         c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src ||
-        c->d_nsurf)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with scalar "
-                                          "dissipation, curl-form metrics, no interior penalty and no source");
+        c->d_nsurf || c->N > esdc::kMaxN)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with p <= 7, "
+                                          "scalar dissipation, curl-form metrics, no interior penalty and no source");
     if (c->d_adj_g) return ESDC_OK;
     const size_t N2 = (size_t)c->N * c->N;
     CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
@@ -384,9 +384,9 @@ int adjoint_checks(esdc_ctx* c, const double* ckpt, double dt, int nsteps, doubl
     if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
         c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src ||
-        c->d_nsurf)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with scalar "
-                                          "dissipation, curl-form metrics, no interior penalty and no source");
+        c->d_nsurf || c->N > esdc::kMaxN)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with p <= 7, "
+                                          "scalar dissipation, curl-form metrics, no interior penalty and no source");
     if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
     const size_t need = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");
@@ -411,6 +411,9 @@ void free_ctx(esdc_ctx* c) {
     cudaFree(c->d_geom);
     cudaFree(c->d_jinv);
     cudaFree(c->d_nsurf);
+    cudaFree(c->d_lr);
+    cudaFree(c->d_lwf);
+    cudaFree(c->d_lft);
     cudaFree(c->d_geomf);
     cudaFree(c->d_nbr);
     cudaFree(c->d_trace);
@@ -450,13 +453,13 @@ const char* esdc_strerror(int status) {
 }
 
 int esdc_lgl(int p, double* xi_host, double* w_host) {
-    if (p < 1 || p > esdc::kMaxN - 1) return fail(ESDC_ERR_ARG, "p must be in [1, 7]");
+    if (p < 1 || p > esdc::kLargeN - 1) return fail(ESDC_ERR_ARG, "p must be in [1, 15]");
     if (!xi_host || !w_host) return fail(ESDC_ERR_ARG, "null output pointer");
     return esdc::lgl(p, xi_host, w_host);
 }
 
 int esdc_operators(int p, double* D, double* S) {
-    if (p < 1 || p > esdc::kMaxN - 1) return fail(ESDC_ERR_ARG, "p must be in [1, 7]");
+    if (p < 1 || p > esdc::kLargeN - 1) return fail(ESDC_ERR_ARG, "p must be in [1, 15]");
     esdc::HostSetup hs;
     int st = esdc::build_operators(p, hs);
     if (st) return fail(st, "operator construction failed");
@@ -466,7 +469,9 @@ int esdc_operators(int p, double* D, double* S) {
 }
 
 static int check_setup(const esdc_setup_t& s) {
-    if (s.p < 1 || s.p > esdc::kMaxN - 1) return fail(ESDC_ERR_ARG, "p must be in [1, 7]");
+    if (s.p < 1 || s.p > esdc::kLargeN - 1) return fail(ESDC_ERR_ARG, "p must be in [1, 7] or 15");
+    if (s.p > esdc::kMaxN - 1 && s.p != esdc::kLargeN - 1)
+        return fail(ESDC_ERR_UNSUPPORTED, "degrees 8 to 14 are not built (p in [1, 7] or 15)");
     if (s.kx < 1 || s.ky < 1 || s.kz < 1) return fail(ESDC_ERR_ARG, "element counts must be >= 1");
     if ((int64_t)s.kx * s.ky * s.kz > (int64_t)INT32_MAX / 6) return fail(ESDC_ERR_ARG, "too many elements");
     if (!(s.gamma > 1.0) || !(s.Pr > 0.0) || !(s.Ma > 0.0) || !std::isfinite(s.Re))
@@ -491,6 +496,11 @@ static int check_setup(const esdc_setup_t& s) {
         return fail(ESDC_ERR_ARG, "metrics must be ESDC_METRICS_CURL or ESDC_METRICS_OPTIMIZED");
     if (s.metrics == ESDC_METRICS_OPTIMIZED && s.precision != ESDC_PREC_FP64)
         return fail(ESDC_ERR_UNSUPPORTED, "the optimized metrics are built for float64 only");
+    if (s.p == esdc::kLargeN - 1 &&
+        (s.precision != ESDC_PREC_FP64 || s.dissipation == ESDC_DISS_MATRIX || s.ip_coef > 0.0 || s.bounded != 0 ||
+         s.metrics != ESDC_METRICS_CURL))
+        return fail(ESDC_ERR_UNSUPPORTED, "p = 15 is built for float64 periodic boxes with curl-form metrics and "
+                                          "no or local Lax-Friedrichs dissipation, without interior penalty");
     return ESDC_OK;
 }
 
@@ -570,10 +580,16 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     c->h_min = hs.h_min;
     std::memset(&c->ops, 0, sizeof(c->ops));
     std::memset(&c->opsf, 0, sizeof(c->opsf));
-    c->ops.N = c->opsf.N = hs.N;
+    std::memset(&c->opsl, 0, sizeof(c->opsl));
+    c->ops.N = c->opsf.N = c->opsl.N = hs.N;
     for (int i = 0; i < hs.N; ++i) {
-        c->ops.w[i] = hs.w[i];
-        c->ops.winv[i] = 1.0 / hs.w[i];
+        c->ops.w[i] = c->opsl.w[i] = hs.w[i];
+        c->ops.winv[i] = c->opsl.winv[i] = 1.0 / hs.w[i];
+        for (int j = 0; j < hs.N; ++j) {
+            c->opsl.D[i][j] = hs.D[i * hs.N + j];
+            c->opsl.S2[i][j] = 2.0 * hs.S[i * hs.N + j];
+        }
+        if (hs.N > esdc::kMaxN) continue;           // the per-element kernels' operators (p <= 7)
         c->opsf.w[i] = (float)hs.w[i];
         c->opsf.winv[i] = (float)(1.0 / hs.w[i]);
         for (int j = 0; j < hs.N; ++j) {
@@ -629,6 +645,11 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     }
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_nbr, hs.nbr.data(), hs.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && hs.N == esdc::kLargeN) {
+        e = cudaMalloc(&c->d_lr, (size_t)3 * c->n_nodes * 5 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_lwf, (size_t)c->K * 6 * 4 * N2 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_lft, (size_t)c->K * 3 * 4 * c->N3 * sizeof(double));
+    }
     if (e == cudaSuccess && !hs.nsurf.empty()) {
         e = cudaMalloc(&c->d_nsurf, hs.nsurf.size() * sizeof(double));
         if (e == cudaSuccess)
@@ -776,8 +797,8 @@ int esdc_set_exterior(esdc_ctx* c, const double* q_ext) {
 
 int esdc_set_source(esdc_ctx* c, const double* src) {
     if (!c) return fail(ESDC_ERR_ARG, "null context");
-    if (src && c->setup.precision != ESDC_PREC_FP64)
-        return fail(ESDC_ERR_UNSUPPORTED, "source terms are added by float64 contexts only");
+    if (src && (c->setup.precision != ESDC_PREC_FP64 || c->N > esdc::kMaxN))
+        return fail(ESDC_ERR_UNSUPPORTED, "source terms are added by float64 contexts with p <= 7 only");
     if (src && !aligned(src, 16)) return fail(ESDC_ERR_ARG, "source must be 16-byte aligned");
     c->d_src = src;
     return prepare_variant(c);

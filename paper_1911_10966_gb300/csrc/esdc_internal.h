@@ -10,15 +10,25 @@
 
 namespace esdc {
 
-constexpr int kMaxN = 8;   // p <= 7
+constexpr int kMaxN = 8;     // p <= 7: one element per CTA (rhs_f64.cu, rhs_f32.cu, the adjoint)
+constexpr int kLargeN = 16;  // p = 15: the multi-pass float64 residual (rhs_large_f64.cu)
 
 // Per-degree operators passed by value to kernels (lands in the constant bank).
 struct Ops {
     int N;
     double D[kMaxN][kMaxN];    // collocation derivative D = P^-1 Q (Sec. 2, Definition 1)
     double S2[kMaxN][kMaxN];   // 2 S with S = Q - E/2 skew-symmetric
-    double w[kMaxN];           // LGL weights (diagonal of P)
-    double winv[kMaxN];        // 1/w
+    double w[kLargeN];         // LGL weights (diagonal of P), every supported degree
+    double winv[kLargeN];      // 1/w
+};
+
+// The same operators for N = kLargeN (the p = 15 residual passes).
+struct OpsL {
+    int N;
+    double D[kLargeN][kLargeN];
+    double S2[kLargeN][kLargeN];
+    double w[kLargeN];
+    double winv[kLargeN];
 };
 
 struct Phys {
@@ -73,6 +83,7 @@ struct esdc_ctx {
     int N = 0, N3 = 0;
     int64_t K = 0, n_nodes = 0;
     esdc::Ops ops;
+    esdc::OpsL opsl;                 // filled for N = kLargeN only
     esdc::OpsF opsf;
     esdc::Phys phys;
     esdc::PhysF physf;
@@ -81,6 +92,10 @@ struct esdc_ctx {
     double* d_geom = nullptr;        // [K][10][N3]
     double* d_jinv = nullptr;        // [K][N3] 1/J
     double* d_nsurf = nullptr;       // [K][6][3][N2] surface metrics of the optimized metrics (else null)
+    // p = 15 residual passes (N = kLargeN only)
+    double* d_lr = nullptr;          // [3][K][5][N3] per-direction residual parts
+    double* d_lwf = nullptr;         // [K][6][4][N2] neighbour entropy variables at the faces
+    double* d_lft = nullptr;         // [K][3][4][N3] contravariant viscous fluxes
     const double* d_qext = nullptr;  // caller-owned exterior (Dirichlet) state, [K][5][N3] (bounded boxes)
     const double* d_src = nullptr;   // caller-owned source term added to dq/dt, [K][5][N3]
     float* d_geomf = nullptr;        // [K][10][N3] float32 copy (mixed precision)

@@ -20,6 +20,9 @@ struct DivU64 {
 cudaError_t prepare_rhs_f64(const esdc_ctx* c);
 // ev: NULL, or four events recorded around the element kernel and the face kernel
 cudaError_t launch_rhs_f64(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev);
+// the p = 15 float64 residual (N = kLargeN), called by the two above
+cudaError_t prepare_rhs_large(const esdc_ctx* c);
+cudaError_t launch_rhs_large(const esdc_ctx* c, const double* q, double* dqdt, cudaStream_t s, cudaEvent_t* ev);
 
 // out = q0 + sum_j coef[j] * k[j]   (n doubles; k pointers may alias nothing but each other)
 struct Combine {

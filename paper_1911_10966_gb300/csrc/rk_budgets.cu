@@ -138,8 +138,10 @@ __global__ void __launch_bounds__(kRedThreads) budgets_kernel(const double* __re
     __shared__ double sw[kMaxN * kMaxN * kMaxN];     // tensor-product LGL weights w_i1 w_i2 w_i3
     __shared__ double stab[3 * kLnTab];
     const int N3 = N * N * N;
-    for (int node = threadIdx.x; node < N3; node += blockDim.x)
-        sw[node] = ops.w[node % N] * ops.w[(node / N) % N] * ops.w[node / (N * N)];
+    const bool table = N3 <= kMaxN * kMaxN * kMaxN;   // p = 15: weights formed per node below
+    if (table)
+        for (int node = threadIdx.x; node < N3; node += blockDim.x)
+            sw[node] = ops.w[node % N] * ops.w[(node / N) % N] * ops.w[node / (N * N)];
     for (int i = threadIdx.x; i < 3 * kLnTab; i += blockDim.x) stab[i] = lntab[i];
     __syncthreads();
     const int64_t n = K * N3;
@@ -148,7 +150,8 @@ __global__ void __launch_bounds__(kRedThreads) budgets_kernel(const double* __re
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
         const int64_t e = (int64_t)div_n3((unsigned long long)g);
         const int node = (int)(g - e * N3);
-        const double PJ = sw[node] * geom[e * 10 * N3 + node];
+        const double wn = table ? sw[node] : ops.w[node % N] * ops.w[(node / N) % N] * ops.w[node / (N * N)];
+        const double PJ = wn * geom[e * 10 * N3 + node];
         double qv[5];
         for (int v = 0; v < 5; ++v) qv[v] = q[(e * 5 + v) * N3 + node];
         const double rho = qv[0];

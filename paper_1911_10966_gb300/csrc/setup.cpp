@@ -28,7 +28,7 @@ static void legendre3(int n, long double x, long double& P, long double& dP, lon
 // LGL nodes: +-1 and the zeros of P_p', found by Newton on P_p' with P_p'' from Legendre's
 // equation, in long double.  Weights 2/(p(p+1) P_p(x)^2) (Sec. 2, diagonal-norm SBP on LGL nodes).
 int lgl(int p, double* xi, double* w) {
-    if (p < 1 || p > kMaxN - 1 || !xi || !w) return ESDC_ERR_ARG;
+    if (p < 1 || p > kLargeN - 1 || !xi || !w) return ESDC_ERR_ARG;
     const long double pi = 3.141592653589793238462643383279502884L;
     std::vector<long double> x(p + 1);
     x[0] = -1.0L;
