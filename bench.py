@@ -80,10 +80,15 @@ LAUNCHER_MARK = b"// ---- host-side launchers"
 
 
 def _sha(path):
-    """Hash of a kernel source file up to its host-side launcher section (the device code)."""
+    """Hash of a kernel source file up to its host-side launcher section (the device code), followed
+    by the float64 device functions it includes (flux_f64.cuh) when they sit beside it."""
     data = open(path, "rb").read()
     cut = data.find(LAUNCHER_MARK)
-    return hashlib.sha256(data[:cut] if cut >= 0 else data).hexdigest()[:16]
+    data = data[:cut] if cut >= 0 else data
+    inc = os.path.join(os.path.dirname(path), "flux_f64.cuh")
+    if b'#include "flux_f64.cuh"' in data and os.path.exists(inc):
+        data += open(inc, "rb").read()
+    return hashlib.sha256(data).hexdigest()[:16]
 
 
 def _ncu_traffic(kernel_src):

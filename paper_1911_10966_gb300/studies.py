@@ -246,6 +246,23 @@ def hconv(t_final=0.5):
     return rows
 
 
+def rhs(p=4, k=16, volume_flux="esc", Re=1600.0, precision="fp64", warp=0.1, reps=5):
+    """Residual time of one configuration (Taylor-Green on the warped periodic box), `reps` timed
+    calls after one warm-up: the command the kernel profiles are taken on."""
+    s = Solver.box(p, k, k, k, warp=warp, Re=Re, precision=precision, volume_flux=volume_flux)
+    q = s.to_device(I.taylor_green(s.coords))
+    ms = _time_rhs(s, q, reps=reps)
+    row = {"study": "rhs", "p": p, "k": k, "nodes": s.n_nodes, "Re": Re, "precision": precision,
+           "volume_flux": volume_flux, "rhs_ms": ms, "node_rhs_per_s": s.n_nodes / (ms * 1e-3)}
+    print(json.dumps(row), flush=True)
+    return [row]
+
+
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "psweep"
-    {"precision": precision, "psweep": psweep, "hconv": hconv, "variants": variants, "mms": mms}[which]()
+    if which == "rhs":
+        kw = dict(a.split("=", 1) for a in sys.argv[2:])
+        conv = {"p": int, "k": int, "Re": float, "warp": float, "reps": int}
+        rhs(**{key: conv.get(key, str)(val) for key, val in kw.items()})
+    else:
+        {"precision": precision, "psweep": psweep, "hconv": hconv, "variants": variants, "mms": mms}[which]()
