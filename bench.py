@@ -238,7 +238,8 @@ def run_reference(args):
 
 
 def cpu_baseline_sample():
-    """Oracle timed on the host cores: one DP5 step (6 residuals) of the full workload."""
+    """Oracle timed on the host cores: one DP5 step (6 residuals) of the full workload, plus the
+    oracle on the other workload shapes (oracle_config_timings)."""
     O, mesh, gas, q = _oracle_problem()
     p, k = WORKLOAD["p"], WORKLOAD["k"]
     dt = O.cfl_dt(q, mesh, gas, WORKLOAD["cfl"])
@@ -247,7 +248,59 @@ def cpu_baseline_sample():
     el = time.perf_counter() - t0
     cores = torch.get_num_threads()
     return {"value": k ** 3 * (p + 1) ** 3 * RHS_PER_STEP / el, "unit": "node-RHS/s", "cores": cores, "kind": "oracle",
-            "sample": f"one DP5 step (6 residuals) of the full 16^3 p=4 workload, {el:.1f} s on {cores} threads"}
+            "sample": f"one DP5 step (6 residuals) of the full 16^3 p=4 workload, {el:.1f} s on {cores} threads",
+            "configs": oracle_config_timings()}
+
+
+ORACLE_SAMPLE_ELEMENTS = 256
+# elements per direction giving ~16M nodes per degree (the p-sweep meshes)
+PSWEEP_K = {2: 84, 3: 63, 4: 50, 5: 42, 6: 36, 7: 32}
+
+
+def oracle_config_timings():
+    """The oracle (as it stands, float64 torch on the host cores) on the other workload shapes, in
+    node-RHS/s: the 4^3 affine p=3 Taylor-Green box (one residual and ten DP5 steps, whole mesh), the
+    8^3 warped p=4 isentropic vortex (one residual, whole mesh), and one residual of each ~16M-node
+    p-sweep mesh (p = 2..7) restricted to a seeded sample of 256 elements (the whole mesh would take
+    minutes per degree; the count is of the sampled nodes, although the oracle also evaluates the
+    entropy-variable gradients of their face neighbours)."""
+    from oracle import esdc_oracle as O
+    from paper_1911_10966_gb300 import inputs as I
+    out = {}
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    s = O.sbp_operator(3)
+    x = I.box_coords(s.xi.numpy(), 4, 4, 4, [-math.pi] * 3, [math.pi] * 3)
+    mesh = O.make_mesh(3, x, 4, 4, 4)
+    gas = O.Gas.from_mach(0.1, 1600.0)
+    q = torch.tensor(I.taylor_green(x, Ma=0.1))
+    n = q.shape[0] * 64
+    t1 = timed(lambda: O.rhs(q, mesh, gas))
+    dt = O.cfl_dt(q, mesh, gas, 0.5)
+    t10 = timed(lambda: O.rk_step(q, lambda st: O.rhs(st, mesh, gas), dt, 10))
+    out["tgv_4cubed_p3"] = {"rhs_node_rhs_per_s": n / t1, "dp5_10_steps_s": t10,
+                            "dp5_node_rhs_per_s": n * 60 / t10}
+    s = O.sbp_operator(4)
+    x = I.box_coords(s.xi.numpy(), 8, 8, 8, [-5.0] * 3, [5.0] * 3, warp=0.1, seed=1)
+    mesh = O.make_mesh(4, x, 8, 8, 8)
+    gas = O.Gas.from_mach(0.5, 1000.0)
+    q = torch.tensor(I.isentropic_vortex(x, Ma=0.5, u_inf=(1 / math.sqrt(2), -1 / math.sqrt(2), 0.0)))
+    out["vortex_8cubed_p4_warped"] = {"rhs_node_rhs_per_s": q.shape[0] * 125 / timed(lambda: O.rhs(q, mesh, gas))}
+    gas = O.Gas.from_mach(0.1, 1600.0)
+    for p, k in PSWEEP_K.items():
+        s = O.sbp_operator(p)
+        x = I.box_coords(s.xi.numpy(), k, k, k, [-math.pi] * 3, [math.pi] * 3)
+        E = torch.tensor(np.sort(np.random.default_rng(p).choice(k ** 3, ORACLE_SAMPLE_ELEMENTS, replace=False)))
+        sub, E2, rows = O.make_submesh(p, x, O.box_neighbours(k, k, k), E)
+        q = torch.tensor(I.taylor_green(x[E2.numpy()], Ma=0.1))
+        el = timed(lambda: O.rhs(q, sub, gas, elems=rows))
+        out[f"tgv_psweep_p{p}_{k}cubed"] = {"rhs_node_rhs_per_s": ORACLE_SAMPLE_ELEMENTS * (p + 1) ** 3 / el,
+                                            "sample_elements": ORACLE_SAMPLE_ELEMENTS}
+    return out
 
 
 def run_ours(args):

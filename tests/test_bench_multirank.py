@@ -43,3 +43,15 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.replica_throughput(10, 1, 1.0) == pytest.approx(60000.0)
+
+
+def test_oracle_config_timings_cover_every_workload_shape():
+    """The CPU-baseline leg times the oracle on every workload shape: the small Taylor-Green box (one
+    residual and ten steps), the warped vortex box and each p-sweep mesh's sample."""
+    import bench
+    t = bench.oracle_config_timings()
+    assert set(t) == {"tgv_4cubed_p3", "vortex_8cubed_p4_warped"} | {f"tgv_psweep_p{p}_{k}cubed"
+                                                                      for p, k in bench.PSWEEP_K.items()}
+    for row in t.values():
+        assert row["rhs_node_rhs_per_s"] > 0.0
+    assert t["tgv_4cubed_p3"]["dp5_10_steps_s"] > 0.0
