@@ -20,7 +20,7 @@ P = 15
 
 @pytest.mark.parametrize("k,Re,vf,diss", [((2, 2, 2), 1600.0, "esc", True), ((2, 1, 2), 0.0, "esc", False),
                                           ((2, 2, 1), 800.0, "kg", True), ((1, 2, 2), 0.0, "dc", True),
-                                          ((2, 2, 2), 400.0, "dc", False)])
+                                          ((2, 2, 2), 400.0, "dc", False), ((1, 1, 1), 1600.0, "esc", True)])
 def test_p15_residual_parity(k, Re, vf, diss):
     solver, qg, mesh, gas, qo = make_pair(P, k, warp=0.1, seed=4, Re=Re, dissipation=diss, noise=2e-2,
                                           volume_flux=vf)
