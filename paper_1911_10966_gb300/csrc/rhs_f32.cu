@@ -289,14 +289,6 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
         }
     }
     __syncthreads();
-    // sum the three directions into direction 0's slots
-    if (active) {
-        for (int node = tl; node < N3; node += TE)
-#pragma unroll
-            for (int v = 0; v < 6; ++v) sA[v * N3 + node] += sA[(6 + v) * N3 + node] + sA[(12 + v) * N3 + node];
-    }
-    __syncthreads();
-
     // ---- viscous chain
     if (ph.viscous) {
         constexpr int NPT = (N3 + TE - 1) / TE;    // nodes per thread
@@ -366,30 +358,10 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                     FV[m][3] = FV[m][0] * u[0] + FV[m][1] * u[1] + FV[m][2] * u[2] + hc * g[m][3];
                 }
 #pragma unroll
-                for (int l = 0; l < 3; ++l)
+                for (int l = 0; l < 3; ++l) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         Ft[r][l][k] = Ja[l][0] * FV[0][k] + Ja[l][1] * FV[1][k] + Ja[l][2] * FV[2][k];
-            }
-        }
-        // the volume/interface sums in sA[0..5] are complete; move them into sP (free now) so
-        // that sA can hold the viscous fluxes
-        __syncthreads();
-        if (active) {
-            for (int node = tl; node < N3; node += TE)
-#pragma unroll
-                for (int v = 0; v < 6; ++v) sP[v * N3 + node] = sA[v * N3 + node];
-        }
-        __syncthreads();
-        if (active) {
-#pragma unroll
-            for (int r = 0; r < NPT; ++r) {
-                const int node = tl + r * TE;
-                if (node >= N3) break;
-                const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    sF4[l * N3 + node] = make_float4(Ft[r][l][0], Ft[r][l][1], Ft[r][l][2], Ft[r][l][3]);
                     const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
                     if (il == 0 || il == N - 1) {
                         const int side = il == N - 1;
@@ -399,6 +371,22 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                         for (int k = 0; k < 4; ++k) tr[k * N2] = Ft[r][l][k];
                     }
                 }
+                // the node's three directions of volume/interface sums, into the third direction's
+                // slots (the viscous fluxes will overwrite the first two)
+#pragma unroll
+                for (int v = 0; v < 6; ++v)
+                    sA[(12 + v) * N3 + node] = sA[v * N3 + node] + (sA[(6 + v) * N3 + node] + sA[(12 + v) * N3 + node]);
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < NPT; ++r) {
+                const int node = tl + r * TE;
+                if (node >= N3) break;
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+                    sF4[l * N3 + node] = make_float4(Ft[r][l][0], Ft[r][l][1], Ft[r][l][2], Ft[r][l][3]);
             }
         }
         __syncthreads();
@@ -422,21 +410,24 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                     }
                 }
                 const float Jinv = sG4[node].w;
-                const float lin = sP[5 * N3 + node];
-                out[eoff + node] = (sP[node] + ref.rho0 * lin) * Jinv;
+                const float* sum = sA + 12 * N3 + node;
+                const float lin = sum[5 * N3];
+                out[eoff + node] = (sum[0] + ref.rho0 * lin) * Jinv;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) out[eoff + (1 + k) * N3 + node] = (sP[(1 + k) * N3 + node] + vs[k]) * Jinv;
-                out[eoff + 4 * N3 + node] = (sP[4 * N3 + node] + ref.H0 * lin + vs[3]) * Jinv;
+                for (int k = 0; k < 3; ++k) out[eoff + (1 + k) * N3 + node] = (sum[(1 + k) * N3] + vs[k]) * Jinv;
+                out[eoff + 4 * N3 + node] = (sum[4 * N3] + ref.H0 * lin + vs[3]) * Jinv;
             }
         }
     } else if (active) {
         for (int node = tl; node < N3; node += TE) {
-            const float Jinv = sG4[node].w;
-            const float lin = sA[5 * N3 + node];
-            out[eoff + node] = (sA[node] + ref.rho0 * lin) * Jinv;
+            float a[6];
 #pragma unroll
-            for (int k = 1; k < 4; ++k) out[eoff + k * N3 + node] = sA[k * N3 + node] * Jinv;
-            out[eoff + 4 * N3 + node] = (sA[4 * N3 + node] + ref.H0 * lin) * Jinv;
+            for (int v = 0; v < 6; ++v) a[v] = sA[v * N3 + node] + (sA[(6 + v) * N3 + node] + sA[(12 + v) * N3 + node]);
+            const float Jinv = sG4[node].w;
+            out[eoff + node] = (a[0] + ref.rho0 * a[5]) * Jinv;
+#pragma unroll
+            for (int k = 1; k < 4; ++k) out[eoff + k * N3 + node] = a[k] * Jinv;
+            out[eoff + 4 * N3 + node] = (a[4] + ref.H0 * a[5]) * Jinv;
         }
     }
 }
