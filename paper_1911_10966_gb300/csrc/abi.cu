@@ -587,7 +587,7 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
         c->ops.winv[i] = c->opsl.winv[i] = 1.0 / hs.w[i];
         for (int j = 0; j < hs.N; ++j) {
             c->opsl.D[i][j] = hs.D[i * hs.N + j];
-            c->opsl.S2[i][j] = 2.0 * hs.S[i * hs.N + j];
+            c->opsl.S[i][j] = hs.S[i * hs.N + j];
         }
         if (hs.N > esdc::kMaxN) continue;           // the per-element kernels' operators (p <= 7)
         c->opsf.w[i] = (float)hs.w[i];
@@ -595,8 +595,9 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
         for (int j = 0; j < hs.N; ++j) {
             c->ops.D[i][j] = hs.D[i * hs.N + j];
             c->ops.S2[i][j] = 2.0 * hs.S[i * hs.N + j];
+            c->ops.S[i][j] = hs.S[i * hs.N + j];
             c->opsf.D[i][j] = (float)hs.D[i * hs.N + j];
-            c->opsf.S2[i][j] = (float)(2.0 * hs.S[i * hs.N + j]);
+            c->opsf.S[i][j] = (float)hs.S[i * hs.N + j];
         }
     }
     const double R = 1.0 / (s.gamma * s.Ma * s.Ma);

@@ -18,6 +18,7 @@ struct Ops {
     int N;
     double D[kMaxN][kMaxN];    // collocation derivative D = P^-1 Q (Sec. 2, Definition 1)
     double S2[kMaxN][kMaxN];   // 2 S with S = Q - E/2 skew-symmetric
+    double S[kMaxN][kMaxN];    // S itself (the pair coefficient of the forward kernels)
     double w[kLargeN];         // LGL weights (diagonal of P), every supported degree
     double winv[kLargeN];      // 1/w
 };
@@ -26,7 +27,7 @@ struct Ops {
 struct OpsL {
     int N;
     double D[kLargeN][kLargeN];
-    double S2[kLargeN][kLargeN];
+    double S[kLargeN][kLargeN];
     double w[kLargeN];
     double winv[kLargeN];
 };
@@ -43,7 +44,7 @@ struct Phys {
 struct OpsF {
     int N;
     float D[kMaxN][kMaxN];
-    float S2[kMaxN][kMaxN];
+    float S[kMaxN][kMaxN];
     float w[kMaxN];
     float winv[kMaxN];
 };

@@ -62,7 +62,7 @@ __device__ __forceinline__ bool small_jump(double u) { return __double2hiint(u) 
 // (Ismail-Roe style): L = (a+b)/2 G(u), G = 1 - u/3 - 4u^2/45 - 44u^3/945, and
 // 1/L = 2/(a+b) (1 + u/3 + u^2/5 + u^3/7) for u < 1e-4 (truncation below 1e-17), else the
 // logarithmic form.  The flux is linear in n: the volume loop passes n_i + n_j (twice the averaged
-// metric) and halves the pair coefficient instead.
+// metric) and takes S, half of the pair coefficient 2S, instead.
 __device__ __forceinline__ void ec_flux(const Prim& a, const Prim& b, double n0, double n1, double n2,
                                         const Phys& ph, double f[5]) {
     // density log mean from half densities: L = (hr_a + hr_b) G(u)

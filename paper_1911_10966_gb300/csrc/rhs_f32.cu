@@ -224,9 +224,9 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                 load_prim_f(sP4, N3, jj, sj);
                 const float4 nj = nl[jj];
                 float df[5], un;
-                // the flux is linear in n: pass n_i + n_j and halve the pair coefficient
+                // the flux is linear in n: pass n_i + n_j and take S (half of 2S) as the pair coefficient
                 ec_flux_pert(si, sj, ni.x + nj.x, ni.y + nj.y, ni.z + nj.z, ref, df, un);
-                const float c = 0.5f * ops.S2[i][j];
+                const float c = ops.S[i][j];
 #pragma unroll
                 for (int v = 0; v < 5; ++v) {
                     acc[i][v] -= c * df[v];

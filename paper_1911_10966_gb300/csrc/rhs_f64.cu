@@ -144,7 +144,7 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
 #pragma unroll
                         for (int v = 0; v < 5; ++v) f[v] = Fl[i][v] + Fl[j][v];
                     }
-                    const double c = 0.5 * ops.S2[i][j];
+                    const double c = ops.S[i][j];
 #pragma unroll
                     for (int v = 0; v < 5; ++v) {
                         acc[i][v] = fma(-c, f[v], acc[i][v]);

@@ -140,7 +140,7 @@ lg_volume(const double* __restrict__ q, const double* __restrict__ geom, const i
             if constexpr (VF == kFluxESC) ec_flux(si, sj, a0, a1, a2, ph, f);
             else kg_flux(si, sj, sPr[6 * LN2 + ii], sPr[6 * LN2 + jj], a0, a1, a2, ph, f);
         }
-        const double c = 0.5 * ops.S2[i][j];
+        const double c = ops.S[i][j];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             sAc[v * LN2 + ii] = fma(-c, f[v], sAc[v * LN2 + ii]);
