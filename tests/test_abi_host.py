@@ -172,3 +172,37 @@ def test_single_element_and_p1_geometry(L):
     st = _setup(1, 1, 1, 1)
     nat.check(L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, J.ctypes.data, None, None), "geometry")
     assert np.allclose(J, 1.0)
+
+
+@pytest.mark.parametrize("p", [7, 15])
+def test_high_degree_operators_within_ulps_of_40_digit_reference(L, p):
+    """The library's and the oracle's collocation derivatives, each built in its own way (closed form
+    in long double; barycentric weights in float64), are both within a few ulps of |D| of D computed
+    in 40-digit arithmetic on the exact LGL nodes: their metric terms differ only by round-off."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    N = p + 1
+    xi = np.zeros(N)
+    w = np.zeros(N)
+    D = np.zeros(N * N)
+    nat.check(L.esdc_lgl(p, xi.ctypes.data, w.ctypes.data), "lgl")
+    nat.check(L.esdc_operators(p, D.ctypes.data, None), "ops")
+    dP = lambda t: mp.diff(lambda u: mp.legendre(p, u), t)
+    x = [mp.mpf(-1)] + [mp.findroot(dP, mp.mpf(float(xi[i]))) for i in range(1, p)] + [mp.mpf(1)]
+    lam = [mp.mpf(1)] * N
+    for j in range(N):
+        for k in range(N):
+            if k != j:
+                lam[j] /= x[j] - x[k]
+    ref = np.zeros((N, N))
+    for i in range(N):
+        acc = mp.mpf(0)
+        for j in range(N):
+            if i != j:
+                v = (lam[j] / lam[i]) / (x[i] - x[j])
+                ref[i, j] = float(v)
+                acc += v
+        ref[i, i] = float(-acc)
+    scale = np.abs(ref).max() * 2.2e-16
+    assert np.abs(D.reshape(N, N) - ref).max() <= 8 * scale
+    assert np.abs(O.sbp_operator(p).D.numpy() - ref).max() <= 8 * scale
