@@ -141,19 +141,21 @@ __device__ __forceinline__ void load_prim_f(const float4* sP4, int N3, int idx, 
 }
 
 // The residual's input state value at flat index i: base[i] + sum_j c_j k_j[i] (a Runge-Kutta stage
-// formed on the fly; nk = 0 for a plain state).
+// formed on the fly; nk = 0 for a plain state).  NK >= nk terms are compiled (the kernel is built
+// for NK = 0, 2 and 5), so only up to NK - nk loads and multiply-adds are predicated off.
+template <int NK>
 __device__ __forceinline__ float stage_value(const StageF& in, int64_t i) {
     // all loads independent and issued together (predicated on nk), read-only path
-    float kv[6];
+    float kv[NK > 0 ? NK : 1];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) kv[j] = j < in.nk ? __ldg(in.k[j] + i) : 0.0f;
+    for (int j = 0; j < NK; ++j) kv[j] = j < in.nk ? __ldg(in.k[j] + i) : 0.0f;
     float a = __ldg(in.base + i);
 #pragma unroll
-    for (int j = 0; j < 6; ++j) a = fmaf(in.c[j], kv[j], a);
+    for (int j = 0; j < NK; ++j) a = fmaf(in.c[j], kv[j], a);
     return a;
 }
 
-template <int N>
+template <int N, int NK>
 __global__ void __launch_bounds__(CfgF<N>::THREADS, CfgF<N>::MINB)
 rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom,
              const int32_t* __restrict__ nbr, float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph,
@@ -181,7 +183,7 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             float d[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-                d[v] = stage_value(in, eoff + v * N3 + node);
+                d[v] = stage_value<NK>(in, eoff + v * N3 + node);
                 sQ[v * N3 + node] = d[v];
             }
             PrimF s;
@@ -260,7 +262,7 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             const int64_t nb = nbr[el * 6 + 2 * l + side];
             float qn[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) qn[v] = stage_value(in, nb * 5 * N3 + v * N3 + nbn);
+            for (int v = 0; v < 5; ++v) qn[v] = stage_value<NK>(in, nb * 5 * N3 + v * N3 + nbn);
             PrimF so, sn;
             load_prim_f(sP4, N3, own, so);
             to_prim_f(qn, ref, sn);
@@ -448,9 +450,17 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaSt
     ref.gm1 = ph.gamma - 1.0f;
     ref.gamma = ph.gamma;
     ref.inv_p0 = 1.0f / ph.p0;
+    if (in.nk < 0 || in.nk > 5) return cudaErrorInvalidValue;
     if (ev) cudaEventRecord(ev[0], s);
-    rhs_main_f32<N><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf,
-                                                   ph, ref);
+    if (in.nk == 0)
+        rhs_main_f32<N, 0><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K,
+                                                          c->opsf, ph, ref);
+    else if (in.nk <= 2)
+        rhs_main_f32<N, 2><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K,
+                                                          c->opsf, ph, ref);
+    else
+        rhs_main_f32<N, 5><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K,
+                                                          c->opsf, ph, ref);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (ph.viscous) {
@@ -466,7 +476,11 @@ template <int N>
 cudaError_t prepare_f32_n() {
     using C = CfgF<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(float);
-    return cudaFuncSetAttribute(rhs_main_f32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr cudaFuncAttribute kAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(rhs_main_f32<N, 0>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5>, kAttr, (int)smem);
+    return e;
 }
 
 }  // namespace
