@@ -163,6 +163,25 @@ int esdc_layout(const esdc_ctx* ctx, int64_t* K, int* N, int64_t* n_nodes);
 int esdc_geometry(const esdc_ctx* ctx, double* J_host, double* Ja_host);
 
 /*
+ * esdc_init_state -- write an initial state at the node coordinates given to esdc_create into
+ * q_dev[K][5][N^3] (float64 device memory, caller owned), in the library's nondimensionalisation
+ * (rho_inf = T_inf = 1, R = 1/(gamma Ma^2), gamma and Ma of the setup).  Asynchronous on stream.
+ *   ESDC_IC_TGV: the Taylor-Green vortex of Sec. 5.2 with T = 1:
+ *     rho = 1 + gamma Ma^2/16 (cos 2x1 + cos 2x2)(cos 2x3 + 2), u = (sin x1 cos x2 cos x3,
+ *     -cos x1 sin x2 cos x3, 0), p = rho R.  params_host: NULL.
+ *   ESDC_IC_VORTEX: the isentropic vortex of Sec. 5.1.1 (eq. iv_sol) about an axis, plus a uniform
+ *     drift: with r the distance to the axis, T = 1 - (gamma-1) Ma^2 beta^2/(8 pi^2) exp(1 - r^2),
+ *     rho = T^(1/(gamma-1)), u = u_inf + beta/(2 pi) exp((1 - r^2)/2) (a x r_vec), p = rho R T.
+ *     params_host[10] = beta, centre[3], axis[3] (any length > 0), u_inf[3]; NULL: 5, 0, (1, 1, 1), 0.
+ *   ESDC_IC_FREESTREAM: uniform state; params_host[5] = rho, u[3], p; NULL: 1, (0.3, 0.2, 0.1), R.
+ * Errors: ESDC_ERR_ARG (unknown ic, NULL q_dev, zero axis, non-positive rho or p).
+ */
+#define ESDC_IC_TGV 0
+#define ESDC_IC_VORTEX 1
+#define ESDC_IC_FREESTREAM 2
+int esdc_init_state(esdc_ctx* ctx, int ic, const double* params_host, double* q_dev, void* stream);
+
+/*
  * esdc_rhs -- dq/dt = J^-1 [ -I^(E) + SAT^(I) + sum_la D_l Chat_la theta_a + SAT^(V) ] (eq. NSL),
  * with I^(E) the Hadamard flux differencing of eq. discEL using the Chandrashekar two-point flux.
  * q_dev: [K][5][N^3] float64 device state (read only).

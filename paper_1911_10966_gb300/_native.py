@@ -25,6 +25,9 @@ PREC_FP32 = 1
 METRICS = {"curl": 0, "optimized": 1}
 
 
+IC = {"tgv": 0, "vortex": 1, "freestream": 2}
+
+
 class Setup(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("kx", ctypes.c_int), ("ky", ctypes.c_int), ("kz", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Ma", ctypes.c_double),
@@ -55,6 +58,7 @@ def lib() -> ctypes.CDLL:
         "esdc_operators": (I, [I, P, P]),
         "esdc_host_geometry": (I, [ctypes.POINTER(Setup), P, P, P, ctypes.POINTER(D)]),
         "esdc_host_surface_metrics": (I, [ctypes.POINTER(Setup), P, P]),
+        "esdc_init_state": (I, [P, I, P, P, P]),
         "esdc_create": (I, [ctypes.POINTER(Setup), P, ctypes.POINTER(P)]),
         "esdc_destroy": (I, [P]),
         "esdc_layout": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]),

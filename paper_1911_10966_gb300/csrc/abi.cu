@@ -410,6 +410,7 @@ void free_ctx(esdc_ctx* c) {
     for (void* ev : c->prof_events) cudaEventDestroy((cudaEvent_t)ev);
     cudaFree(c->d_geom);
     cudaFree(c->d_jinv);
+    cudaFree(c->d_xyz);
     cudaFree(c->d_nsurf);
     cudaFree(c->d_lr);
     cudaFree(c->d_lwf);
@@ -646,6 +647,11 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     }
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_nbr, hs.nbr.data(), hs.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const size_t xyz_bytes = (size_t)c->K * 3 * c->N3 * sizeof(double);
+        e = cudaMalloc(&c->d_xyz, xyz_bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_xyz, xyz, xyz_bytes, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && hs.N == esdc::kLargeN) {
         e = cudaMalloc(&c->d_lr, (size_t)3 * c->n_nodes * 5 * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&c->d_lwf, (size_t)c->K * 6 * 4 * N2 * sizeof(double));
@@ -689,6 +695,28 @@ int esdc_layout(const esdc_ctx* c, int64_t* K, int* N, int64_t* n_nodes) {
     if (K) *K = c->K;
     if (N) *N = c->N;
     if (n_nodes) *n_nodes = c->n_nodes;
+    return ESDC_OK;
+}
+
+int esdc_init_state(esdc_ctx* c, int ic, const double* params, double* q, void* stream) {
+    if (!c || !q) return fail(ESDC_ERR_ARG, "null argument");
+    esdc::InitParams prm{};
+    const double R = c->phys.R;
+    if (ic == ESDC_IC_TGV) {
+    } else if (ic == ESDC_IC_VORTEX) {
+        const double def[10] = {5.0, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < 10; ++i) prm.v[i] = params ? params[i] : def[i];
+        const double na = std::sqrt(prm.v[4] * prm.v[4] + prm.v[5] * prm.v[5] + prm.v[6] * prm.v[6]);
+        if (!(na > 0.0) || !std::isfinite(na)) return fail(ESDC_ERR_ARG, "the vortex axis must be a nonzero vector");
+        for (int i = 4; i < 7; ++i) prm.v[i] /= na;
+    } else if (ic == ESDC_IC_FREESTREAM) {
+        const double def[5] = {1.0, 0.3, 0.2, 0.1, R};
+        for (int i = 0; i < 5; ++i) prm.v[i] = params ? params[i] : def[i];
+        if (!(prm.v[0] > 0.0) || !(prm.v[4] > 0.0)) return fail(ESDC_ERR_ARG, "rho and p must be positive");
+    } else {
+        return fail(ESDC_ERR_ARG, "ic must be ESDC_IC_TGV, ESDC_IC_VORTEX or ESDC_IC_FREESTREAM");
+    }
+    CUDA_TRY(esdc::launch_init_state(c, ic, prm, q, (cudaStream_t)stream));
     return ESDC_OK;
 }
 

@@ -92,6 +92,7 @@ struct esdc_ctx {
     // device buffers owned by the library
     double* d_geom = nullptr;        // [K][10][N3]
     double* d_jinv = nullptr;        // [K][N3] 1/J
+    double* d_xyz = nullptr;         // [K][3][N3] node coordinates (initial states)
     double* d_nsurf = nullptr;       // [K][6][3][N2] surface metrics of the optimized metrics (else null)
     // p = 15 residual passes (N = kLargeN only)
     double* d_lr = nullptr;          // [3][K][5][N3] per-direction residual parts

@@ -56,6 +56,13 @@ cudaError_t launch_cfl(const esdc_ctx* c, const double* q, cudaStream_t s);
 
 cudaError_t probe_fma(int kind, double* flops_per_s, cudaStream_t s);
 
+// initial states at the node coordinates (ESDC_IC_*); v as documented for esdc_init_state, the
+// vortex axis normalised
+struct InitParams {
+    double v[10];
+};
+cudaError_t launch_init_state(const esdc_ctx* c, int ic, const InitParams& prm, double* q, cudaStream_t s);
+
 // adjoint (float64)
 size_t adjoint_mu_blocks(const esdc_ctx* c);
 cudaError_t prepare_adjoint(const esdc_ctx* c);

@@ -132,6 +132,23 @@ class Solver:
     def to_device(self, q_np):
         return torch.as_tensor(np.ascontiguousarray(q_np), dtype=torch.float64, device=self.device)
 
+    def init_state(self, ic="tgv", params=None):
+        """A new float64 state tensor holding an initial state computed on the device at the node
+        coordinates: "tgv" (Taylor-Green vortex), "vortex" (params: beta, centre[3], axis[3],
+        u_inf[3]) or "freestream" (params: rho, u[3], p); see esdc_init_state."""
+        if ic not in nat.IC:
+            raise ValueError("ic must be 'tgv', 'vortex' or 'freestream'")
+        q = torch.empty((self.K, 5, self.N, self.N, self.N), dtype=torch.float64, device=self.device)
+        pa = None
+        if params is not None:
+            pa = np.ascontiguousarray(params, dtype=np.float64)
+            if pa.size != {"vortex": 10, "freestream": 5}.get(ic, 0):
+                raise ValueError("wrong number of parameters for " + ic)
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_init_state(self._ctx, nat.IC[ic], pa.ctypes.data if pa is not None else None,
+                                                q.data_ptr(), _stream_ptr()), "esdc_init_state")
+        return q
+
     def geometry(self):
         N3 = self.N ** 3
         J = np.zeros((self.K, N3))
