@@ -78,7 +78,20 @@ typedef struct esdc_setup {
     int bounded;            /* bit l (l = 0, 1, 2) set: the outer faces normal to xi_l are
                                boundaries with Dirichlet data (esdc_set_exterior); 0: periodic      */
     int metrics;            /* ESDC_METRICS_CURL (0) or ESDC_METRICS_OPTIMIZED (1), below          */
+    /* box mesh generator, used when esdc_create / esdc_host_* get node_xyz = NULL (below) */
+    double lo[3], hi[3];    /* box corners, hi > lo                                               */
+    double warp_amp;        /* sinusoidal warp amplitude as a fraction of the element size (>= 0) */
+    uint64_t warp_seed;     /* seed of the nine warp phases                                        */
 } esdc_setup_t;
+
+/* Box mesh generator (node_xyz = NULL): element e = ex + kx (ey + ky ez) spans
+ * [lo + (ex, ey, ez) h, lo + (ex + 1, ey + 1, ez + 1) h], h = (hi - lo)/(kx, ky, kz), with the tensor
+ * LGL nodes mapped affinely, then displaced in component i by
+ *   warp_amp h_i prod_k sin(2 pi (X_k - lo_k)/L_k + phi_ik),   L = hi - lo,
+ * which is L-periodic in every direction, so shared and periodic faces keep identical nodes.  The
+ * phases phi_ik (i-major) are successive outputs of splitmix64 (Steele, Lea and Flood, OOPSLA 2014)
+ * started from warp_seed, each mapped to [0, 2 pi) as (z >> 11) 2^-53 2 pi.  With warp_amp = 0 the
+ * mesh is affine and the seed is unused. */
 
 /* Metric terms (Sec. 3).  ESDC_METRICS_CURL: the conservative curl form of the degree-p interpolant
  * of the mapping at every node; it satisfies the discrete GCL sum_l D_l Ja_lm = 0 exactly and the
@@ -140,10 +153,19 @@ int esdc_host_geometry(const esdc_setup_t* setup, const double* node_xyz_host, d
 int esdc_host_surface_metrics(const esdc_setup_t* setup, const double* node_xyz_host, double* nsurf_host);
 
 /*
+ * esdc_host_coordinates -- the node coordinates of the box mesh generator (node_xyz = NULL) for
+ * setup, xyz_host[K][3][N][N][N], computed on the host without a GPU.  esdc_host_geometry and
+ * esdc_host_surface_metrics also accept node_xyz_host = NULL for the same mesh.
+ * Errors: ESDC_ERR_ARG (NULL output, hi <= lo, negative or non-finite warp_amp).
+ */
+int esdc_host_coordinates(const esdc_setup_t* setup, double* xyz_host);
+
+/*
  * esdc_create -- build operators and geometry and allocate library buffers on the current device.
  * node_xyz_host: [K][3][N][N][N] float64 node coordinates (component-major per element), the
  *   degree-p mapping X of every element (Sec. 2, eq. 3d_mapping) sampled at the tensor LGL nodes;
  *   faces shared by neighbours (including periodic images) must hold the same nodes (Assumption 1).
+ *   NULL: the box mesh generator above (setup->lo, hi, warp_amp, warp_seed).
  * Metric terms J dxi_l/dx_m are built on the host in float64 in conservative curl form, which
  * meets the discrete GCL (Sec. 3, eq. discGCLconvection), and J = det(dx/dxi).
  * Synchronous.  Errors: ESDC_ERR_ARG, ESDC_ERR_MESH (J <= 0 or non-finite), ESDC_ERR_CUDA.

@@ -33,7 +33,8 @@ class Setup(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Ma", ctypes.c_double),
                 ("Re", ctypes.c_double), ("dissipation", ctypes.c_int), ("precision", ctypes.c_int),
                 ("volume_flux", ctypes.c_int), ("ip_coef", ctypes.c_double), ("bounded", ctypes.c_int),
-                ("metrics", ctypes.c_int)]
+                ("metrics", ctypes.c_int), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("warp_amp", ctypes.c_double), ("warp_seed", ctypes.c_uint64)]
 
 
 class EsdcError(RuntimeError):
@@ -59,6 +60,7 @@ def lib() -> ctypes.CDLL:
         "esdc_host_geometry": (I, [ctypes.POINTER(Setup), P, P, P, ctypes.POINTER(D)]),
         "esdc_host_surface_metrics": (I, [ctypes.POINTER(Setup), P, P]),
         "esdc_init_state": (I, [P, I, P, P, P]),
+        "esdc_host_coordinates": (I, [ctypes.POINTER(Setup), P]),
         "esdc_create": (I, [ctypes.POINTER(Setup), P, ctypes.POINTER(P)]),
         "esdc_destroy": (I, [P]),
         "esdc_layout": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]),

@@ -505,13 +505,42 @@ static int check_setup(const esdc_setup_t& s) {
     return ESDC_OK;
 }
 
-int esdc_host_geometry(const esdc_setup_t* setup, const double* xyz, double* J, double* Ja, double* h_min) {
-    if (!setup || !xyz) return fail(ESDC_ERR_ARG, "null argument");
+// The node coordinates for setup: the caller's, or the box mesh generator's when xyz is NULL (held
+// in gen).  Operators must be built (hs.xi) first.
+static int resolve_coords(const esdc_setup_t& s, const esdc::HostSetup& hs, const double*& xyz,
+                          std::vector<double>& gen) {
+    if (xyz) return ESDC_OK;
+    if (esdc::generate_box_coords(s, hs.xi, gen) != ESDC_OK)
+        return fail(ESDC_ERR_ARG, "box generator: hi > lo and a finite warp_amp >= 0 required");
+    xyz = gen.data();
+    return ESDC_OK;
+}
+
+int esdc_host_coordinates(const esdc_setup_t* setup, double* out) {
+    if (!setup || !out) return fail(ESDC_ERR_ARG, "null argument");
     int st = check_setup(*setup);
     if (st) return st;
     esdc::HostSetup hs;
     st = esdc::build_operators(setup->p, hs);
     if (st) return fail(st, "operator construction failed");
+    const double* xyz = nullptr;
+    std::vector<double> gen;
+    st = resolve_coords(*setup, hs, xyz, gen);
+    if (st) return st;
+    std::memcpy(out, gen.data(), gen.size() * sizeof(double));
+    return ESDC_OK;
+}
+
+int esdc_host_geometry(const esdc_setup_t* setup, const double* xyz, double* J, double* Ja, double* h_min) {
+    if (!setup) return fail(ESDC_ERR_ARG, "null argument");
+    int st = check_setup(*setup);
+    if (st) return st;
+    esdc::HostSetup hs;
+    st = esdc::build_operators(setup->p, hs);
+    if (st) return fail(st, "operator construction failed");
+    std::vector<double> gen;
+    st = resolve_coords(*setup, hs, xyz, gen);
+    if (st) return st;
     std::string err;
     st = esdc::build_geometry(*setup, xyz, hs, err);
     if (st) return fail(st, err);
@@ -526,12 +555,15 @@ int esdc_host_geometry(const esdc_setup_t* setup, const double* xyz, double* J, 
 }
 
 int esdc_host_surface_metrics(const esdc_setup_t* setup, const double* xyz, double* nsurf) {
-    if (!setup || !xyz || !nsurf) return fail(ESDC_ERR_ARG, "null argument");
+    if (!setup || !nsurf) return fail(ESDC_ERR_ARG, "null argument");
     int st = check_setup(*setup);
     if (st) return st;
     esdc::HostSetup hs;
     st = esdc::build_operators(setup->p, hs);
     if (st) return fail(st, "operator construction failed");
+    std::vector<double> gen;
+    st = resolve_coords(*setup, hs, xyz, gen);
+    if (st) return st;
     std::string err;
     st = esdc::build_geometry(*setup, xyz, hs, err);
     if (st) return fail(st, err);
@@ -558,7 +590,7 @@ int esdc_host_surface_metrics(const esdc_setup_t* setup, const double* xyz, doub
 }
 
 int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
-    if (!setup || !xyz || !out) return fail(ESDC_ERR_ARG, "null argument");
+    if (!setup || !out) return fail(ESDC_ERR_ARG, "null argument");
     *out = nullptr;
     const esdc_setup_t& s = *setup;
     int st0 = check_setup(s);
@@ -567,6 +599,9 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     esdc::HostSetup hs;
     int st = esdc::build_operators(s.p, hs);
     if (st) return fail(st, "operator construction failed");
+    std::vector<double> gen;
+    st = resolve_coords(s, hs, xyz, gen);
+    if (st) return st;
     std::string err;
     st = esdc::build_geometry(s, xyz, hs, err);
     if (st) return fail(st, err);

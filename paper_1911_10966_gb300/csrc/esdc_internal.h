@@ -71,6 +71,8 @@ int lgl(int p, double* xi, double* w);
 int build_operators(int p, HostSetup& hs);
 int build_geometry(const esdc_setup_t& s, const double* xyz, HostSetup& hs, std::string& err);
 void build_box_neighbours(int kx, int ky, int kz, int bounded, std::vector<int32_t>& nbr);
+// node coordinates of the box mesh generator (setup lo, hi, warp_amp, warp_seed) on the LGL nodes xi
+int generate_box_coords(const esdc_setup_t& s, const std::vector<double>& xi, std::vector<double>& xyz);
 // manufactured solution (q, nullable) and its source div(F^I - F^V) (src, nullable) at n points (host)
 void mms_fields(double gamma, double Ma, double Re, double Pr, double L, const double* table, int64_t n,
                 const double* x, double* q, double* src);

@@ -99,6 +99,52 @@ int build_operators(int p, HostSetup& hs) {
     return ESDC_OK;
 }
 
+// splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
+// the state advances by the golden-ratio increment and is scrambled by two xor-shift-multiplies.
+static uint64_t splitmix64(uint64_t& state) {
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int generate_box_coords(const esdc_setup_t& s, const std::vector<double>& xi, std::vector<double>& xyz) {
+    const int N = (int)xi.size(), N3 = N * N * N;
+    const int k[3] = {s.kx, s.ky, s.kz};
+    double L[3], h[3];
+    for (int d = 0; d < 3; ++d) {
+        L[d] = s.hi[d] - s.lo[d];
+        if (!(L[d] > 0.0) || !std::isfinite(L[d])) return ESDC_ERR_ARG;
+        h[d] = L[d] / k[d];
+    }
+    if (!(s.warp_amp >= 0.0) || !std::isfinite(s.warp_amp)) return ESDC_ERR_ARG;
+    const double two_pi = 6.283185307179586476925286766559;
+    double phi[3][3];
+    uint64_t st = s.warp_seed;
+    for (int i = 0; i < 3; ++i)
+        for (int kk = 0; kk < 3; ++kk) phi[i][kk] = (double)(splitmix64(st) >> 11) * 0x1.0p-53 * two_pi;
+    const int64_t K = (int64_t)s.kx * s.ky * s.kz;
+    xyz.assign((size_t)K * 3 * N3, 0.0);
+    for (int64_t e = 0; e < K; ++e) {
+        const int64_t ei[3] = {e % s.kx, (e / s.kx) % s.ky, e / ((int64_t)s.kx * s.ky)};
+        for (int n = 0; n < N3; ++n) {
+            const int ix[3] = {n % N, (n / N) % N, n / (N * N)};
+            double X[3];
+            for (int d = 0; d < 3; ++d) X[d] = s.lo[d] + ((double)ei[d] + (xi[ix[d]] + 1.0) * 0.5) * h[d];
+            for (int i = 0; i < 3; ++i) {
+                double y = X[i];
+                if (s.warp_amp != 0.0) {
+                    double prod = 1.0;
+                    for (int kk = 0; kk < 3; ++kk) prod *= std::sin(two_pi * (X[kk] - s.lo[kk]) / L[kk] + phi[i][kk]);
+                    y = X[i] + s.warp_amp * h[i] * prod;
+                }
+                xyz[((size_t)e * 3 + i) * N3 + n] = y;
+            }
+        }
+    }
+    return ESDC_OK;
+}
+
 // bounded: bit l set -> the outer faces of direction l are boundaries (neighbour -1)
 void build_box_neighbours(int kx, int ky, int kz, int bounded, std::vector<int32_t>& nbr) {
     const int64_t K = (int64_t)kx * ky * kz;

@@ -30,13 +30,31 @@ def warp_phases(seed: int) -> np.ndarray:
     return rng.uniform(0.0, 2.0 * math.pi, size=(3, 3))
 
 
-def box_coords(xi, kx, ky, kz, lo, hi, warp=0.0, seed=0) -> np.ndarray:
+def splitmix64_phases(seed: int) -> np.ndarray:
+    """3x3 phases in [0, 2 pi) (i-major) from successive splitmix64 outputs (Steele, Lea and Flood,
+    OOPSLA 2014) started at seed, each mapped as (z >> 11) 2^-53 2 pi: the phases of the library's
+    own box mesh generator (esdc_create with no node coordinates)."""
+    mask = (1 << 64) - 1
+    state = seed & mask
+    out = np.empty((3, 3))
+    for n in range(9):
+        state = (state + 0x9E3779B97F4A7C15) & mask
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        z ^= z >> 31
+        out[n // 3, n % 3] = float(z >> 11) * 2.0 ** -53 * (2.0 * math.pi)
+    return out
+
+
+def box_coords(xi, kx, ky, kz, lo, hi, warp=0.0, seed=0, phases=None) -> np.ndarray:
     """Node coordinates of a kx*ky*kz hexahedral box mesh, optionally warped.
 
     xi    : the N one-dimensional reference nodes on [-1, 1] (supplied by the caller)
     warp  : amplitude as a fraction of the element size h_i; the displacement of component i is
             warp*h_i*prod_k sin(2 pi (X_k - lo_k)/L_k + phi_ik), L-periodic in every direction, so
             periodic faces and shared faces stay watertight (Sec. 2, Assumption 1).
+    phases: the 3x3 phi (default: warp_phases(seed))
     """
     xi = np.asarray(xi, dtype=np.float64)
     N = xi.size
@@ -56,7 +74,7 @@ def box_coords(xi, kx, ky, kz, lo, hi, warp=0.0, seed=0) -> np.ndarray:
         base = lo[d] + (eidx[d][:, None] + t[None, :]) * h[d]          # [K, N]
         X[:, d] = base.reshape((K,) + shapes[d])
     if warp != 0.0:
-        phi = warp_phases(seed)
+        phi = warp_phases(seed) if phases is None else np.asarray(phases, dtype=np.float64)
         Y = X.copy()
         for i in range(3):
             prod = np.ones((K, N, N, N))

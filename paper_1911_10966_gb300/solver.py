@@ -64,7 +64,9 @@ class Solver:
 
     def __init__(self, p, kx, ky, kz, coords, *, gamma=1.4, Pr=0.72, Ma=0.1, Re=0.0, dissipation=True,
                  precision="fp64", volume_flux="esc", ip_coef=0.0, bounded=(False, False, False), metrics="curl",
-                 device=None):
+                 device=None, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, warp=0.0, seed=0):
+        """coords None: the library's box mesh generator on [lo, hi] with warp amplitude `warp` and
+        splitmix64 phases from `seed` (esdc_host_coordinates); self.coords then holds its nodes."""
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU implementation exists)")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
@@ -80,14 +82,18 @@ class Solver:
             raise ValueError("metrics must be 'curl' or 'optimized'")
         self.metrics = metrics
         self.dtype_r = torch.float64 if precision == "fp64" else torch.float32
+        diss = 2 if dissipation == "matrix" else (1 if dissipation else 0)
+        st = nat.Setup(p, kx, ky, kz, gamma, Pr, Ma, Re, diss,
+                       nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32, nat.FLUX[volume_flux],
+                       float(ip_coef), sum(1 << l for l in range(3) if bounded[l]), nat.METRICS[metrics],
+                       (ctypes.c_double * 3)(*lo), (ctypes.c_double * 3)(*hi), float(warp), int(seed))
+        if coords is None:
+            coords = np.empty((self.K, 3, self.N, self.N, self.N))
+            nat.check(nat.lib().esdc_host_coordinates(ctypes.byref(st), coords.ctypes.data), "esdc_host_coordinates")
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         if coords.shape != (self.K, 3, self.N, self.N, self.N):
             raise ValueError(f"coords must have shape {(self.K, 3, self.N, self.N, self.N)}, got {coords.shape}")
         self.coords = coords
-        diss = 2 if dissipation == "matrix" else (1 if dissipation else 0)
-        st = nat.Setup(p, kx, ky, kz, gamma, Pr, Ma, Re, diss,
-                       nat.PREC_FP64 if precision == "fp64" else nat.PREC_FP32, nat.FLUX[volume_flux],
-                       float(ip_coef), sum(1 << l for l in range(3) if bounded[l]), nat.METRICS[metrics])
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             nat.check(nat.lib().esdc_create(ctypes.byref(st), coords.ctypes.data, ctypes.byref(self._ctx)),

@@ -206,3 +206,40 @@ def test_high_degree_operators_within_ulps_of_40_digit_reference(L, p):
     scale = np.abs(ref).max() * 2.2e-16
     assert np.abs(D.reshape(N, N) - ref).max() <= 8 * scale
     assert np.abs(O.sbp_operator(p).D.numpy() - ref).max() <= 8 * scale
+
+
+@pytest.mark.parametrize("p,k,warp,seed", [(2, (3, 2, 4), 0.0, 0), (3, (2, 3, 2), 0.1, 7), (4, (2, 2, 2), 0.15, 2 ** 63 + 5)])
+def test_box_generator_matches_inputs(L, p, k, warp, seed):
+    """esdc_host_coordinates (the generator behind node_xyz = NULL) equals the input module's box mesh
+    with the same splitmix64 phases; geometry from NULL coordinates equals geometry from those nodes."""
+    xi = O.sbp_operator(p).xi.numpy()
+    lo, hi = [-1.0, 0.0, 2.0], [1.0, 3.0, 2.5]
+    st = _setup(p, *k)
+    st.lo[:] = lo
+    st.hi[:] = hi
+    st.warp_amp = warp
+    st.warp_seed = seed
+    K, N3 = k[0] * k[1] * k[2], (p + 1) ** 3
+    x = np.zeros((K, 3, p + 1, p + 1, p + 1))
+    nat.check(L.esdc_host_coordinates(ctypes.byref(st), x.ctypes.data), "coordinates")
+    want = I.box_coords(xi, *k, lo, hi, warp=warp, phases=I.splitmix64_phases(seed))
+    assert np.abs(x - want).max() <= 4e-16 * np.abs(want).max()
+    J1, J2 = np.zeros((K, N3)), np.zeros((K, N3))
+    nat.check(L.esdc_host_geometry(ctypes.byref(st), None, J1.ctypes.data, None, None), "geometry")
+    nat.check(L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, J2.ctypes.data, None, None), "geometry")
+    assert np.array_equal(J1, J2)
+    bad = _setup(p, *k)
+    bad.lo[:] = lo
+    bad.hi[:] = [1.0, 3.0, 2.0]          # hi == lo in x3
+    assert L.esdc_host_coordinates(ctypes.byref(bad), x.ctypes.data) == nat.ESDC_ERR_ARG
+    bad.hi[:] = hi
+    bad.warp_amp = -0.1
+    assert L.esdc_host_geometry(ctypes.byref(bad), None, None, None, None) == nat.ESDC_ERR_ARG
+
+
+def test_splitmix64_published_values():
+    """First outputs of splitmix64 from seed 0 as published with the reference implementation
+    (0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4), checked through the phase mapping."""
+    ph = I.splitmix64_phases(0)
+    for z, got in ((0xE220A8397B1DCDAF, ph[0, 0]), (0x6E789E6AA1B965F4, ph[0, 1])):
+        assert got == float(z >> 11) * 2.0 ** -53 * (2.0 * math.pi)
