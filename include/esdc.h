@@ -5,7 +5,8 @@
  * conforming hexahedral meshes with Legendre-Gauss-Lobatto (LGL) collocation (arXiv 1911.10966,
  * Sec. 4, eq. NSL): Chandrashekar flux differencing (eq. discEL), entropy-variable BR1 viscous
  * terms (eq. MacroForm), entropy-stable interface SATs and curvilinear metric terms (Sec. 3), and
- * advances it with the Dormand-Prince 5(4) explicit Runge-Kutta scheme at a fixed step (Sec. 5).
+ * advances it with the Dormand-Prince 5(4) explicit Runge-Kutta scheme (Sec. 5), at a fixed step or
+ * with an adaptive step (esdc_rk_adaptive).
  *
  * Conventions for every entry point:
  *   - Return value: ESDC_OK (0) or a negative ESDC_ERR_* code; esdc_last_error() gives a message
@@ -62,7 +63,8 @@ extern "C" {
 
 typedef struct esdc_ctx esdc_ctx; /* opaque, library owned */
 
-/* Problem description.  Only fully periodic structured boxes are connected by this build. */
+/* Problem description: a kx*ky*kz structured box of hexahedra, periodic in every direction except
+ * those flagged in `bounded` (Dirichlet data on their outer faces). */
 typedef struct esdc_setup {
     int p;                  /* polynomial degree, 1 <= p <= 7 or p = 15 (N = p + 1 LGL nodes per
                                direction; p = 15 below)                                             */
