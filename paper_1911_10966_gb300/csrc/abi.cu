@@ -411,6 +411,7 @@ void free_ctx(esdc_ctx* c) {
     cudaFree(c->d_geom);
     cudaFree(c->d_jinv);
     cudaFree(c->d_xyz);
+    cudaFree(c->d_fnorm);
     cudaFree(c->d_nsurf);
     cudaFree(c->d_lr);
     cudaFree(c->d_lwf);
@@ -691,6 +692,31 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
         e = cudaMalloc(&c->d_lr, (size_t)3 * c->n_nodes * 5 * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&c->d_lwf, (size_t)c->K * 6 * 4 * N2 * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&c->d_lft, (size_t)c->K * 3 * 4 * c->N3 * sizeof(double));
+    }
+    if (e == cudaSuccess) {
+        // |n_J| of the metric the interface terms use (surface metrics of the optimized metrics,
+        // else the face values of the volume metrics), per face node in the kernels' face order
+        const int N = hs.N, NN = N * N, N3 = NN * N;
+        std::vector<double> fn((size_t)c->K * 6 * NN);
+        for (int64_t el = 0; el < c->K; ++el)
+            for (int l = 0; l < 3; ++l)
+                for (int side = 0; side < 2; ++side) {
+                    const int fix = side ? N - 1 : 0;
+                    for (int t2 = 0; t2 < N; ++t2)
+                        for (int t1 = 0; t1 < N; ++t1) {
+                            const int fi = t1 + N * t2;
+                            const int node = l == 0 ? fix + N * t1 + NN * t2
+                                                    : (l == 1 ? t1 + N * fix + NN * t2 : t1 + N * t2 + NN * fix);
+                            double n[3];
+                            for (int m = 0; m < 3; ++m)
+                                n[m] = hs.nsurf.empty()
+                                           ? hs.geom[((size_t)el * 10 + 1 + 3 * l + m) * N3 + node]
+                                           : hs.nsurf[(((size_t)el * 6 + 2 * l + side) * 3 + m) * NN + fi];
+                            fn[((size_t)el * 6 + 2 * l + side) * NN + fi] = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                        }
+                }
+        e = cudaMalloc(&c->d_fnorm, fn.size() * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_fnorm, fn.data(), fn.size() * sizeof(double), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess && !hs.nsurf.empty()) {
         e = cudaMalloc(&c->d_nsurf, hs.nsurf.size() * sizeof(double));

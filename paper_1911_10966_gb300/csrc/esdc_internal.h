@@ -95,6 +95,7 @@ struct esdc_ctx {
     double* d_geom = nullptr;        // [K][10][N3]
     double* d_jinv = nullptr;        // [K][N3] 1/J
     double* d_xyz = nullptr;         // [K][3][N3] node coordinates (initial states)
+    double* d_fnorm = nullptr;       // [K][6][N2] |n_J| of the interface metric at the face nodes
     double* d_nsurf = nullptr;       // [K][6][3][N2] surface metrics of the optimized metrics (else null)
     // p = 15 residual passes (N = kLargeN only)
     double* d_lr = nullptr;          // [3][K][5][N3] per-direction residual parts

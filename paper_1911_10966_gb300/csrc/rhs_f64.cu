@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::MINB)
 rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const double* __restrict__ geom,
              const int32_t* __restrict__ nbr, double* __restrict__ trace, int64_t K, const Ops ops,
              const Phys ph, const double* __restrict__ qext, const double* __restrict__ src,
-             const double* __restrict__ nsurf) {
+             const double* __restrict__ nsurf, const double* __restrict__ fnorm) {
     constexpr int N2 = Cfg<N>::N2, N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB;
     extern __shared__ double smem[];
     const int t = threadIdx.x;
@@ -232,7 +232,7 @@ rhs_main_f64(const double* __restrict__ q, double* __restrict__ dqdt, const doub
                 }
             }
             if (ph.dissipation == 1) {
-                const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+                const double nn = fnorm[(el * 6 + 2 * l + side) * N2 + fi];     // |n_J|, from the setup
                 const double lo = 2.0 * fabs(so.hu0 * n0 + so.hu1 * n1 + so.hu2 * n2) + sP[11 * N3 + own] * nn;
                 const double ln = 2.0 * fabs(sn.hu0 * n0 + sn.hu1 * n1 + sn.hu2 * n2) + cn * nn;
                 lam = 0.5 * fmax(lo, ln);
@@ -374,7 +374,8 @@ cudaError_t launch_rhs_n(const esdc_ctx* c, const double* q, double* dqdt, cudaS
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     if (ev) cudaEventRecord(ev[0], s);
     rhs_main_f64<N, VF, XF><<<grid, C::THREADS, smem, s>>>(q, dqdt, c->d_geom, c->d_nbr, (double*)c->d_trace, c->K,
-                                                           c->ops, c->phys, c->d_qext, c->d_src, c->d_nsurf);
+                                                           c->ops, c->phys, c->d_qext, c->d_src, c->d_nsurf,
+                                                           c->d_fnorm);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (c->phys.viscous) {

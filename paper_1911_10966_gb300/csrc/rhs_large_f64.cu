@@ -72,7 +72,8 @@ constexpr int vol_smem_doubles() {
 template <int VF>
 __global__ void __launch_bounds__(LTHREADS)
 lg_volume(const double* __restrict__ q, const double* __restrict__ geom, const int32_t* __restrict__ nbr,
-          double* __restrict__ rl, double* __restrict__ wf_out, int64_t K, const OpsL ops, const Phys ph) {
+          const double* __restrict__ fnorm, double* __restrict__ rl, double* __restrict__ wf_out, int64_t K,
+          const OpsL ops, const Phys ph) {
     extern __shared__ double sm[];
     double* sPr = sm;
     double* sNm = sPr + 8 * LN2;
@@ -184,7 +185,7 @@ lg_volume(const double* __restrict__ q, const double* __restrict__ geom, const i
         const double E = side ? 1.0 : -1.0;
         double lam = 0.0;
         if (ph.dissipation == 1) {
-            const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+            const double nn = fnorm[(el * 6 + 2 * l + side) * LN2 + line + LN * t2];     // |n_J|
             const double lo = 2.0 * fabs(so.hu0 * n0 + so.hu1 * n1 + so.hu2 * n2) + sPr[7 * LN2 + si] * nn;
             const double ln = 2.0 * fabs(sn.hu0 * n0 + sn.hu1 * n1 + sn.hu2 * n2) + cn * nn;
             lam = 0.5 * fmax(lo, ln);
@@ -370,8 +371,8 @@ lg_finish(const double* __restrict__ rl, const double* __restrict__ jinv, double
 template <int VF>
 cudaError_t launch_volume(const esdc_ctx* c, const double* q, cudaStream_t s) {
     const size_t smem = (size_t)vol_smem_doubles<VF>() * sizeof(double);
-    lg_volume<VF><<<(unsigned)(c->K * 3 * LN), LTHREADS, smem, s>>>(q, c->d_geom, c->d_nbr, c->d_lr, c->d_lwf, c->K,
-                                                                    c->opsl, c->phys);
+    lg_volume<VF><<<(unsigned)(c->K * 3 * LN), LTHREADS, smem, s>>>(q, c->d_geom, c->d_nbr, c->d_fnorm, c->d_lr,
+                                                                    c->d_lwf, c->K, c->opsl, c->phys);
     return cudaGetLastError();
 }
 
