@@ -25,57 +25,75 @@ __device__ __forceinline__ double less_ref(double x, int v, double rho0, double 
     return x;
 }
 
-// Two consecutive entries per thread and iteration (16-byte state loads, 8-byte shadow stores).
+// Four consecutive entries per thread and iteration (two 16-byte state loads, one 16-byte shadow
+// store); the remaining n mod 4 entries are done by one thread.  Several independent entries per
+// thread keep the float64 pipe busy despite its latency.
 __global__ void __launch_bounds__(256) shadow_kernel(const double* __restrict__ q, float* __restrict__ dq,
                                                      int64_t n_nodes, DivU64 div_n3, DivU64 div_5, double rho0,
                                                      double E0) {
-    const int64_t n = n_nodes * 5, n2 = n / 2;
+    const int64_t n = n_nodes * 5, n4 = n / 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += stride) {
-        const int64_t i = 2 * t;
-        const double2 x = reinterpret_cast<const double2*>(q)[t];
-        const float a = d2f_int(less_ref(x.x, var_of(i, div_n3, div_5), rho0, E0));
-        const float b = d2f_int(less_ref(x.y, var_of(i + 1, div_n3, div_5), rho0, E0));
-        reinterpret_cast<float2*>(dq)[t] = make_float2(a, b);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
+        const int64_t i = 4 * t;
+        const double2 x0 = reinterpret_cast<const double2*>(q)[2 * t], x1 = reinterpret_cast<const double2*>(q)[2 * t + 1];
+        const double x[4] = {x0.x, x0.y, x1.x, x1.y};
+        float r[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) r[e] = d2f_int(less_ref(x[e], var_of(i + e, div_n3, div_5), rho0, E0));
+        reinterpret_cast<float4*>(dq)[t] = make_float4(r[0], r[1], r[2], r[3]);
     }
-    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
-        dq[n - 1] = d2f_int(less_ref(q[n - 1], var_of(n - 1, div_n3, div_5), rho0, E0));
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = 4 * n4; i < n; ++i) dq[i] = d2f_int(less_ref(q[i], var_of(i, div_n3, div_5), rho0, E0));
 }
 
-// The update of NK stage terms, two consecutive entries per thread and iteration; all loads of an
-// iteration are issued together and the terms are summed in stage order in float64.
+// The update of NK stage terms, four consecutive entries per thread and iteration; all loads of an
+// iteration are issued together and each entry's terms are summed in stage order in float64.
+template <int NK>
+__device__ __forceinline__ double stage_sum(const Combine64F& cb, const float* kv) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < NK; ++j) acc = fma(cb.coef[j], f2d_int(kv[j]), acc);
+    return acc;
+}
+
 template <int NK>
 __global__ void __launch_bounds__(256) final_kernel(double* __restrict__ q, float* __restrict__ dq_new,
                                                     const Combine64F cb, int64_t n_nodes, DivU64 div_n3,
                                                     DivU64 div_5, double rho0, double E0) {
-    const int64_t n = n_nodes * 5, n2 = n / 2;
+    const int64_t n = n_nodes * 5, n4 = n / 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += stride) {
-        const int64_t i = 2 * t;
-        float2 kv[NK];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
+        const int64_t i = 4 * t;
+        float4 k4[NK];
 #pragma unroll
-        for (int j = 0; j < NK; ++j) kv[j] = __ldg(reinterpret_cast<const float2*>(cb.k[j]) + t);
-        const double2 q0 = reinterpret_cast<const double2*>(q)[t];
-        double ia = 0.0, ib = 0.0;
+        for (int j = 0; j < NK; ++j) k4[j] = __ldg(reinterpret_cast<const float4*>(cb.k[j]) + t);
+        const double2 q0 = reinterpret_cast<const double2*>(q)[2 * t], q1 = reinterpret_cast<const double2*>(q)[2 * t + 1];
+        float kx[NK], ky[NK], kz[NK], kw[NK];
 #pragma unroll
         for (int j = 0; j < NK; ++j) {
-            ia = fma(cb.coef[j], f2d_int(kv[j].x), ia);
-            ib = fma(cb.coef[j], f2d_int(kv[j].y), ib);
+            kx[j] = k4[j].x;
+            ky[j] = k4[j].y;
+            kz[j] = k4[j].z;
+            kw[j] = k4[j].w;
         }
-        const double qa = q0.x + ia, qb = q0.y + ib;
-        reinterpret_cast<double2*>(q)[t] = make_double2(qa, qb);
-        reinterpret_cast<float2*>(dq_new)[t] =
-            make_float2(d2f_int(less_ref(qa, var_of(i, div_n3, div_5), rho0, E0)),
-                        d2f_int(less_ref(qb, var_of(i + 1, div_n3, div_5), rho0, E0)));
-    }
-    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        double inc = 0.0;
+        const double qn[4] = {q0.x + stage_sum<NK>(cb, kx), q0.y + stage_sum<NK>(cb, ky), q1.x + stage_sum<NK>(cb, kz),
+                              q1.y + stage_sum<NK>(cb, kw)};
+        reinterpret_cast<double2*>(q)[2 * t] = make_double2(qn[0], qn[1]);
+        reinterpret_cast<double2*>(q)[2 * t + 1] = make_double2(qn[2], qn[3]);
+        float r[4];
 #pragma unroll
-        for (int j = 0; j < NK; ++j) inc = fma(cb.coef[j], f2d_int(cb.k[j][n - 1]), inc);
-        const double qn = q[n - 1] + inc;
-        q[n - 1] = qn;
-        dq_new[n - 1] = d2f_int(less_ref(qn, var_of(n - 1, div_n3, div_5), rho0, E0));
+        for (int e = 0; e < 4; ++e) r[e] = d2f_int(less_ref(qn[e], var_of(i + e, div_n3, div_5), rho0, E0));
+        reinterpret_cast<float4*>(dq_new)[t] = make_float4(r[0], r[1], r[2], r[3]);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = 4 * n4; i < n; ++i) {
+            float kv[NK];
+#pragma unroll
+            for (int j = 0; j < NK; ++j) kv[j] = cb.k[j][i];
+            const double qi = q[i] + stage_sum<NK>(cb, kv);
+            q[i] = qi;
+            dq_new[i] = d2f_int(less_ref(qi, var_of(i, div_n3, div_5), rho0, E0));
+        }
 }
 
 unsigned grid_for(int64_t n) {
@@ -89,14 +107,14 @@ unsigned grid_for(int64_t n) {
 
 cudaError_t launch_shadow(const esdc_ctx* c, const double* q, float* dq, cudaStream_t s) {
     const double E0 = c->phys.R / (c->phys.gamma - 1.0);
-    shadow_kernel<<<grid_for(c->n_nodes * 5 / 2), 256, 0, s>>>(q, dq, c->n_nodes, DivU64::make(c->N3),
+    shadow_kernel<<<grid_for(c->n_nodes * 5 / 4), 256, 0, s>>>(q, dq, c->n_nodes, DivU64::make(c->N3),
                                                                DivU64::make(5), 1.0, E0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_final_f32(const esdc_ctx* c, double* q, float* dq_new, const Combine64F& cb, cudaStream_t s) {
     const double E0 = c->phys.R / (c->phys.gamma - 1.0);
-    const unsigned g = grid_for(c->n_nodes * 5 / 2);
+    const unsigned g = grid_for(c->n_nodes * 5 / 4);
     const DivU64 d3 = DivU64::make(c->N3), d5 = DivU64::make(5);
     switch (cb.nk) {
         case 1: final_kernel<1><<<g, 256, 0, s>>>(q, dq_new, cb, c->n_nodes, d3, d5, 1.0, E0); break;
