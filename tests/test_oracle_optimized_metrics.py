@@ -6,7 +6,8 @@ surface metrics seen from the two sides of every face, the orthogonality of the 
 independently built family of feasible directions (discrete curls of fields that vanish on the
 element boundary), and the consequences for the scheme: uniform flow kept on a warped mesh for every
 volume flux and interface option, conservation, zero entropy production of the entropy-conservative
-scheme, and the truncation order on the manufactured solution."""
+scheme, the truncation order on the manufactured solution, and design-order convergence of both
+metric constructions to the metrics of the exact (non-polynomial) warped mapping."""
 import math
 
 import numpy as np
@@ -152,3 +153,53 @@ def test_manufactured_solution_truncation_order(p):
         errs.append(float(torch.sqrt((PJ * r ** 2).sum() / (PJ * S ** 2).sum())))
     rate = math.log2(errs[1] / errs[2])
     assert rate >= p - 0.3, (errs, rate)
+
+
+def _exact_metrics(xi, k, lo, hi, warp, seed):
+    """Cofactor metrics of the exact warped mapping (not its interpolant) at the LGL nodes, by
+    autograd of the mapping xi -> x of each element, written out from the warp formula of the input
+    module."""
+    N = xi.numel()
+    lo_t, hi_t = torch.tensor(lo, dtype=F64), torch.tensor(hi, dtype=F64)
+    L = hi_t - lo_t
+    h = L / k
+    phi = torch.tensor(I.warp_phases(seed), dtype=F64)
+    g = torch.meshgrid(xi, xi, xi, indexing="ij")                                    # (xi3, xi2, xi1)
+    ref = torch.stack([g[2], g[1], g[0]], dim=0).reshape(3, -1)                      # [3 (xi_a), N^3]
+    out = torch.empty(k ** 3, 3, 3, N, N, N, dtype=F64)
+    for el in range(k ** 3):
+        eidx = torch.tensor([el % k, (el // k) % k, el // (k * k)], dtype=F64)
+        r = ref.clone().requires_grad_(True)
+        X = lo_t[:, None] + (eidx[:, None] + (r + 1.0) * 0.5) * h[:, None]
+        ph = 2.0 * math.pi * (X - lo_t[:, None]) / L[:, None]
+        x = torch.stack([X[i] + warp * h[i] * torch.prod(torch.sin(ph + phi[i][:, None]), dim=0) for i in range(3)])
+        dx = torch.empty(3, 3, N ** 3, dtype=F64)                                   # dx_m / dxi_a
+        for m in range(3):
+            dx[m] = torch.autograd.grad(x[m].sum(), r, retain_graph=True)[0]
+        for l in range(3):
+            a, b = (l + 1) % 3, (l + 2) % 3
+            for m in range(3):
+                m1, m2 = (m + 1) % 3, (m + 2) % 3
+                out[el, l, m] = (dx[m1, a] * dx[m2, b] - dx[m2, a] * dx[m1, b]).reshape(N, N, N)
+    return out
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_metrics_converge_to_the_exact_mapping_metrics(p):
+    """Both metric constructions approximate the metrics of the exact (non-polynomial) warped mapping
+    at design order: the max error falls at rate >= p - 0.5 from 4^3 to 8^3 elements, and the
+    optimized volume metrics are not farther from them than the curl form by more than a few
+    percent (they are the nearest feasible ones to the interpolant's analytic metrics)."""
+    s = O.sbp_operator(p)
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    errs = {"curl": [], "optimized": []}
+    for k in (4, 8):
+        x = I.box_coords(s.xi.numpy(), k, k, k, lo, hi, warp=0.1, seed=0)
+        ex = _exact_metrics(s.xi, k, lo, hi, 0.1, 0)
+        scale = float(ex.abs().max())
+        for met in errs:
+            m = O.make_mesh(p, x, k, k, k, metrics=met)
+            errs[met].append(float((m.Ja - ex).abs().max()) / scale)
+    for met, (e4, e8) in errs.items():
+        assert math.log2(e4 / e8) >= p - 0.5, (met, e4, e8)
+    assert errs["optimized"][1] <= 1.05 * errs["curl"][1], errs
