@@ -75,3 +75,9 @@ def test_generated_mesh_residual_parity():
     q = s.init_state("tgv")
     qo = torch.tensor(I.taylor_green(xo, Ma=0.1))
     assert_parity(s.rhs(q), O.rhs(qo, mesh, gas), qo, mesh, gas)
+
+
+def test_init_state_p15():
+    from paper_1911_10966_gb300.solver import Solver
+    s = Solver.box(15, 2, 1, 1, warp=0.1, seed=4, Ma=0.1, Re=1600.0)
+    assert _rel(s.init_state("tgv"), I.taylor_green(s.coords, Ma=0.1)) <= 1e-14

@@ -80,3 +80,16 @@ def test_optimized_metrics_unsupported():
     assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
     with pytest.raises(ValueError):
         Solver(2, 2, 2, 2, solver.coords, metrics="exact")
+
+
+def test_optimized_metrics_dp5_steps():
+    """Five fixed DP5 steps, viscous, warped mesh, optimized metrics: the increment against the
+    oracle's."""
+    from tests.gpu_common import normwise_errors
+    solver, qg, mesh, gas, qo = make_pair(3, (3, 2, 2), warp=0.1, seed=6, Re=800.0, metrics="optimized")
+    dt = solver.dt_cfl(qg, 0.5)
+    q0 = qg.clone()
+    solver.rk_step(qg, dt, 5)
+    qn = O.rk_step(qo, lambda s: O.rhs(s, mesh, gas), dt, 5)
+    e = normwise_errors(qg - q0, qn - qo)
+    assert max(e) <= 1e-10, e
