@@ -367,9 +367,9 @@ int prepare_variant(esdc_ctx* c) {
 int ensure_adjoint(esdc_ctx* c) {
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
         c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src ||
-        c->d_nsurf || c->N > esdc::kMaxN)
+        c->N > esdc::kMaxN)
         return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with p <= 7, "
-                                          "scalar dissipation, curl-form metrics, no interior penalty and no source");
+                                          "scalar dissipation, no interior penalty and no source");
     if (c->d_adj_g) return ESDC_OK;
     const size_t N2 = (size_t)c->N * c->N;
     CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
@@ -384,9 +384,9 @@ int adjoint_checks(esdc_ctx* c, const double* ckpt, double dt, int nsteps, doubl
     if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
     if (c->setup.precision != ESDC_PREC_FP64 || c->setup.volume_flux != ESDC_FLUX_ESC ||
         c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 || c->d_src ||
-        c->d_nsurf || c->N > esdc::kMaxN)
+        c->N > esdc::kMaxN)
         return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 ES-C contexts with p <= 7, "
-                                          "scalar dissipation, curl-form metrics, no interior penalty and no source");
+                                          "scalar dissipation, no interior penalty and no source");
     if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
     const size_t need = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");

@@ -159,7 +159,8 @@ template <int N>
 __global__ void __launch_bounds__(CfgA<N>::THREADS, CfgA<N>::MINB)
 adj_main(const double* __restrict__ q, const double* __restrict__ lam, const double* __restrict__ geom,
          const int32_t* __restrict__ nbr, double* __restrict__ grad, double* __restrict__ gbuf,
-         double* __restrict__ tbuf, double* __restrict__ mupart, int64_t K, const Ops ops, const Phys ph) {
+         double* __restrict__ tbuf, double* __restrict__ mupart, int64_t K, const Ops ops, const Phys ph,
+         const double* __restrict__ nsurf) {
     constexpr int N2 = CfgA<N>::N2, N3 = CfgA<N>::N3, EPB = CfgA<N>::EPB;
     extern __shared__ double smem[];
     __shared__ double red[CfgA<N>::THREADS];
@@ -280,8 +281,13 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
             Prim so, sn;
             load_prim(sP, N3, own, so);
             to_prim(qn, ph, sn);
-            const double n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own],
-                         n2 = sG[(3 + 3 * l) * N3 + own];
+            double n0 = sG[(1 + 3 * l) * N3 + own], n1 = sG[(2 + 3 * l) * N3 + own], n2 = sG[(3 + 3 * l) * N3 + own];
+            if (nsurf) {   // optimized metrics: the interface terms take the surface metrics
+                const double* ns = nsurf + (el * 6 + 2 * l + side) * 3 * N2 + fi;
+                n0 = ns[0];
+                n1 = ns[N2];
+                n2 = ns[2 * N2];
+            }
             const double E = side ? 1.0 : -1.0;
             const double wi = ops.winv[side ? N - 1 : 0];
             double nu[5], muf[5];
@@ -609,7 +615,7 @@ cudaError_t launch_adj_n(const esdc_ctx* c, const double* q, const double* lam, 
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     adj_main<N><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
-                                               c->d_adj_mu, c->K, c->ops, c->phys);
+                                               c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
     const unsigned g2 = (unsigned)((c->K + C::EPB_F - 1) / C::EPB_F);
     adj_face<N><<<g2, C::EPB_F * 2 * C::N2, 0, s>>>(q, c->d_nbr, c->d_adj_g, c->d_adj_t, grad, c->K, c->ops, c->phys);
     if (mu_acc) {

@@ -75,11 +75,22 @@ def test_optimized_metrics_unsupported():
     with pytest.raises(nat.EsdcError) as ei:
         Solver(2, 2, 2, 2, solver.coords, Re=100.0, precision="fp32", metrics="optimized")
     assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
-    with pytest.raises(nat.EsdcError) as ei:
-        solver.rhs_vjp(qg, torch.ones_like(qg))
-    assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
     with pytest.raises(ValueError):
         Solver(2, 2, 2, 2, solver.coords, metrics="exact")
+
+
+@pytest.mark.parametrize("p,diss,Re", [(3, True, 800.0), (2, False, 0.0), (4, True, 200.0)])
+def test_optimized_metrics_vjp_matches_oracle_autograd(p, diss, Re):
+    """The hand-written adjoint with the surface metrics in its interface terms against the oracle's
+    autograd VJP of the optimized-metric residual."""
+    from tests.gpu_common import normwise_errors
+    solver, qg, mesh, gas, qo = make_pair(p, (3, 2, 2), warp=0.1, seed=3, Re=Re, dissipation=diss, noise=2e-2,
+                                          metrics="optimized")
+    lam = torch.randn(qo.shape, generator=torch.Generator().manual_seed(12), dtype=torch.float64)
+    qq = qo.clone().requires_grad_(True)
+    (go,) = torch.autograd.grad(O.rhs(qq, mesh, gas, dissipation=diss), qq, lam)
+    e = normwise_errors(solver.rhs_vjp(qg, lam.cuda()), go)
+    assert max(e) <= 1e-10, e
 
 
 def test_optimized_metrics_dp5_steps():
