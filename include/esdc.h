@@ -345,8 +345,10 @@ int esdc_dt_cfl(esdc_ctx* ctx, const double* q_dev, double cfl, double* dt_host,
  * the cotangent of max(a, b) in half at a tie.  If grad_mu_host is not NULL it also returns
  * lambda . dR/dmu (R is linear in mu through mu and kappa = mu cp/Pr) and synchronises stream.
  * q_dev, lambda_dev, grad_dev: [K][5][N^3] float64 device arrays (grad_dev must not alias the
- * others).  ESDC_PREC_FP64 contexts only (ESDC_ERR_UNSUPPORTED otherwise).  The first call
- * allocates the adjoint face buffers (K*6*9*N^2 float64), kept until esdc_destroy.
+ * others).  ESDC_PREC_FP64 contexts with p <= 7, the ES-C flux, no or local Lax-Friedrichs
+ * dissipation, no interior penalty and periodic boxes (ESDC_ERR_UNSUPPORTED otherwise); either
+ * metric option; a source term (esdc_set_source) is constant in q and leaves the product unchanged.
+ * The first call allocates the adjoint face buffers (K*6*9*N^2 float64), kept until esdc_destroy.
  */
 int esdc_rhs_vjp(esdc_ctx* ctx, const double* q_dev, const double* lambda_dev, double* grad_dev,
                  double* grad_mu_host, void* stream);

@@ -179,3 +179,27 @@ def test_trajectory_gradient_matches_oracle_autograd():
     print("trajectory gradient vs oracle", ["%.1e" % x for x in e], float(mu.grad), float(gmo))
     assert max(e) <= 1e-9, e
     assert abs(float(mu.grad) - float(gmo)) <= 1e-9 * abs(float(gmo))
+
+
+def test_vjp_and_trajectory_gradient_ignore_a_constant_source():
+    """A source term is constant in q: the VJP is unchanged bit for bit, and the trajectory gradient
+    through DP5 steps with the source (whose stages do depend on it) matches the oracle's autograd."""
+    solver, qg, mesh, gas, qo = make_pair(3, (2, 2, 2), warp=0.1, seed=4, Re=400.0, noise=1e-2)
+    lam = torch.randn(qo.shape, generator=torch.Generator().manual_seed(13), dtype=torch.float64).cuda()
+    g0 = solver.rhs_vjp(qg, lam)
+    src = torch.tensor(I.random_direction(tuple(qo.shape), seed=21, scale=1.0), device=qg.device)
+    solver.set_source(src)
+    g1 = solver.rhs_vjp(qg, lam)
+    assert torch.equal(g0, g1)
+    dt = 0.5 * solver.dt_cfl(qg, 0.5)
+    from paper_1911_10966_gb300.autograd import Trajectory, KineticEnergy
+    q0 = qg.clone().requires_grad_(True)
+    mu = torch.tensor(solver.mu, dtype=torch.float64, requires_grad=True)
+    KineticEnergy.apply(Trajectory.apply(q0, mu, solver, dt, 2), solver).backward()
+    so = src.cpu()
+    qq = qo.clone().requires_grad_(True)
+    qn = O.rk_step(qq, lambda s: O.rhs(s, mesh, gas, source=so), dt, 2)
+    ke = O.kinetic_energy(qn, mesh)
+    (go,) = torch.autograd.grad(ke, qq)
+    e = normwise_errors(q0.grad, go)
+    assert max(e) <= 1e-9, e
