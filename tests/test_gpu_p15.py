@@ -80,3 +80,18 @@ def test_p15_unsupported_combinations():
     with pytest.raises(nat.EsdcError) as ei:
         solver.set_source(torch.zeros_like(qg))
     assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
+
+
+def test_p15_adaptive_matches_oracle():
+    """Adaptive DP5(4) at p = 15 (one element periodic onto itself): the same accepted and rejected
+    steps as the oracle's integrator and the same final state (tolerances of the p <= 7 test)."""
+    solver, qg, mesh, gas, qo = make_pair(P, (1, 1, 1), warp=0.1, seed=2, Re=200.0, noise=1e-2)
+    dt_cfl = solver.dt_cfl(qg, 0.5)
+    st = solver.rk_adaptive(qg, 0.0, 6.0 * dt_cfl, 3.0 * dt_cfl, rtol=1e-6, atol=1e-6, max_steps=200, history=500)
+    qo_end, so = O.rk_adaptive(qo, lambda s: O.rhs(s, mesh, gas), 0.0, 6.0 * dt_cfl, 3.0 * dt_cfl, 1e-6, 1e-6,
+                               max_steps=200)
+    assert st["accepted"] == len(so["accepted"]) and st["rejected"] == so["rejected"]
+    for a, b in zip(st["dt_history"], so["accepted"]):
+        assert abs(a - b) <= 1e-8 * b
+    e = normwise_errors(qg, qo_end)
+    assert max(e) <= 1e-9, e
