@@ -105,7 +105,8 @@ typedef struct esdc_setup {
  * those surface metrics, sum_l Q_l^T Ja_lm = sum_l E_l Ja^surf_lm (Q_l, E_l the tensor-product SBP
  * matrices; the condition under which the skew flux differencing keeps a uniform flow).  The
  * interface SAT (two-point flux, dissipation, interior penalty) then reads the surface metrics; the
- * volume and viscous terms read the volume metrics.  Float64 only; the adjoint supports them. */
+ * volume and viscous terms read the volume metrics.  Float64 and float32-mixed; the adjoint
+ * supports them. */
 #define ESDC_METRICS_CURL 0
 #define ESDC_METRICS_OPTIMIZED 1
 

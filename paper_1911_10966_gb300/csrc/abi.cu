@@ -417,6 +417,7 @@ void free_ctx(esdc_ctx* c) {
     cudaFree(c->d_lwf);
     cudaFree(c->d_lft);
     cudaFree(c->d_geomf);
+    cudaFree(c->d_nsurff);
     cudaFree(c->d_nbr);
     cudaFree(c->d_trace);
     cudaFree(c->d_shadow);
@@ -496,8 +497,6 @@ static int check_setup(const esdc_setup_t& s) {
         return fail(ESDC_ERR_UNSUPPORTED, "the KG and DC volume fluxes are built for float64 only");
     if (s.metrics != ESDC_METRICS_CURL && s.metrics != ESDC_METRICS_OPTIMIZED)
         return fail(ESDC_ERR_ARG, "metrics must be ESDC_METRICS_CURL or ESDC_METRICS_OPTIMIZED");
-    if (s.metrics == ESDC_METRICS_OPTIMIZED && s.precision != ESDC_PREC_FP64)
-        return fail(ESDC_ERR_UNSUPPORTED, "the optimized metrics are built for float64 only");
     if (s.p == esdc::kLargeN - 1 &&
         (s.precision != ESDC_PREC_FP64 || s.dissipation == ESDC_DISS_MATRIX || s.ip_coef > 0.0 || s.bounded != 0 ||
          s.metrics != ESDC_METRICS_CURL))
@@ -730,6 +729,12 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
         e = cudaMalloc(&c->d_geomf, gf.size() * sizeof(float));
         if (e == cudaSuccess) e = cudaMemcpy(c->d_geomf, gf.data(), gf.size() * sizeof(float), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMalloc(&c->d_shadow, (size_t)c->n_nodes * 5 * sizeof(float));
+        if (e == cudaSuccess && !hs.nsurf.empty()) {
+            std::vector<float> nf(hs.nsurf.size());
+            for (size_t i = 0; i < nf.size(); ++i) nf[i] = (float)hs.nsurf[i];
+            e = cudaMalloc(&c->d_nsurff, nf.size() * sizeof(float));
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_nsurff, nf.data(), nf.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
         if (e == cudaSuccess) e = esdc::prepare_rhs_f32(c);
     }
     if (e != cudaSuccess) {

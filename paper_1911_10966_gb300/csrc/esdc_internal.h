@@ -104,6 +104,7 @@ struct esdc_ctx {
     const double* d_qext = nullptr;  // caller-owned exterior (Dirichlet) state, [K][5][N3] (bounded boxes)
     const double* d_src = nullptr;   // caller-owned source term added to dq/dt, [K][5][N3]
     float* d_geomf = nullptr;        // [K][10][N3] float32 copy (mixed precision)
+    float* d_nsurff = nullptr;       // [K][6][3][N2] float32 copy of the surface metrics (mixed precision)
     int32_t* d_nbr = nullptr;        // [K][6]
     void* d_trace = nullptr;         // [K][6][4][N2] viscous normal-flux traces (f64 or f32)
     float* d_shadow = nullptr;       // [K][5][N3] float32 perturbation state (mixed precision)

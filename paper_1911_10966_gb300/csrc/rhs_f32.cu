@@ -159,7 +159,7 @@ template <int N, int NK>
 __global__ void __launch_bounds__(CfgF<N>::THREADS, CfgF<N>::MINB)
 rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom,
              const int32_t* __restrict__ nbr, float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph,
-             const Ref ref) {
+             const Ref ref, const float* __restrict__ nsurf) {
     using C = CfgF<N>;
     constexpr int N2 = C::N2, N3 = C::N3, TE = C::TE;
     extern __shared__ float smf[];
@@ -267,7 +267,13 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             load_prim_f(sP4, N3, own, so);
             to_prim_f(qn, ref, sn);
             const float4 nv = sG4[l * N3 + own];
-            const float n0 = nv.x, n1 = nv.y, n2 = nv.z;
+            float n0 = nv.x, n1 = nv.y, n2 = nv.z;
+            if (nsurf) {   // optimized metrics: the interface terms take the surface metrics
+                const float* ns = nsurf + (el * 6 + 2 * l + side) * 3 * N2 + fi;
+                n0 = ns[0];
+                n1 = ns[N2];
+                n2 = ns[2 * N2];
+            }
             float df[5], un;
             ec_flux_pert(so, sn, n0, n1, n2, ref, df, un);
             const float E = side ? 1.0f : -1.0f;
@@ -454,13 +460,13 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaSt
     if (ev) cudaEventRecord(ev[0], s);
     if (in.nk == 0)
         rhs_main_f32<N, 0><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K,
-                                                          c->opsf, ph, ref);
+                                                          c->opsf, ph, ref, c->d_nsurff);
     else if (in.nk <= 2)
         rhs_main_f32<N, 2><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K,
-                                                          c->opsf, ph, ref);
+                                                          c->opsf, ph, ref, c->d_nsurff);
     else
         rhs_main_f32<N, 5><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K,
-                                                          c->opsf, ph, ref);
+                                                          c->opsf, ph, ref, c->d_nsurff);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (ph.viscous) {

@@ -160,7 +160,8 @@ def test_empty_and_out_of_range_sizes(L):
     assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_ARG
     st.metrics = 1
     st.precision = nat.PREC_FP32
-    assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_UNSUPPORTED
+    # float32 with the optimized metrics passes the setup checks (the all-zero nodes then fail as a mesh)
+    assert L.esdc_host_geometry(ctypes.byref(st), x.ctypes.data, None, None, None) == nat.ESDC_ERR_MESH
     assert L.esdc_host_surface_metrics(ctypes.byref(st), x.ctypes.data, None) == nat.ESDC_ERR_ARG
 
 

@@ -124,3 +124,21 @@ def test_fp32_residual_48cubed_p7_full_size_sampled():
     r = solver.rhs(qg)
     e, c = _report(r[E.cuda()], O.rhs(qo, mesh, gas, elems=mesh.rows), qo, mesh, gas, elems=mesh.rows)
     assert max(c) <= C_MAX
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_fp32_residual_optimized_metrics(p):
+    """The mixed-precision residual with the optimized metrics (surface metrics in its interface
+    terms) against the oracle's optimized-metric residual, same bounds as the curl-form cases; a
+    uniform flow stays steady to float32 rounding."""
+    solver, qg, mesh, gas, qo = make_pair(p, (3, 2, 2), warp=0.1, seed=2, Re=100.0, noise=0.05, precision="fp32",
+                                          metrics="optimized")
+    e, c = _report(solver.rhs(qg), O.rhs(qo, mesh, gas), qo, mesh, gas)
+    assert max(c) <= C_MAX
+    assert max(e) <= 1e-5
+    solver, qg, mesh, gas, qo = make_pair(p, (3, 2, 2), warp=0.1, seed=2, Re=100.0, state="freestream",
+                                          precision="fp32", metrics="optimized")
+    r = solver.rhs(qg)
+    T = term_scale(qo, mesh, gas)
+    for v in range(5):
+        assert float(r[:, v].abs().max()) <= C_MAX * EPS32 * T[v], (v, float(r[:, v].abs().max()), T[v])
