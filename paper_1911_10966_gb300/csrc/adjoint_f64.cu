@@ -135,6 +135,52 @@ __device__ __forceinline__ void ec_flux_vjp(const Prim& a, const Prim& b, double
     bb.u2 += 0.5 * ubb2;
 }
 
+// Reverse of the contracted Kennedy-Gruber flux (the SF-KG variant): with arithmetic means
+// rho_bar, u_bar, p_bar = (p_a + p_b)/2 (p = rho RT, RT = 1/(2 beta)) and e_bar = (RT_a + RT_b)/
+// (2 (gamma-1)) + (|u_a|^2 + |u_b|^2)/4, f1 = rho_bar u_bar.n, f_m = f1 u_bar_m + p_bar n_m,
+// f5 = f1 e_bar + p_bar u_bar.n.  Adds the primitive cotangents of both states to ab, bb.
+__device__ __forceinline__ void kg_flux_vjp(const Prim& a, const Prim& b, double n0, double n1, double n2,
+                                            const double mu[5], const Phys& ph, PBar& ab, PBar& bb) {
+    const double RTa = 0.5 / a.beta, RTb = 0.5 / b.beta;
+    const double rb = 0.5 * (a.rho + b.rho);
+    const double ub0 = 0.5 * (a.u0 + b.u0), ub1 = 0.5 * (a.u1 + b.u1), ub2 = 0.5 * (a.u2 + b.u2);
+    const double pb = 0.5 * (a.rho * RTa + b.rho * RTb);
+    const double eb = 0.5 * ph.inv_gm1 * (RTa + RTb) + 0.25 * (a.usq + b.usq);
+    const double un = ub0 * n0 + ub1 * n1 + ub2 * n2;
+    const double f1 = rb * un;
+    // reverse
+    const double f1b = mu[0] + mu[1] * ub0 + mu[2] * ub1 + mu[3] * ub2 + mu[4] * eb;
+    const double pbb = mu[1] * n0 + mu[2] * n1 + mu[3] * n2 + mu[4] * un;
+    const double ebb = mu[4] * f1;
+    const double unb = mu[4] * pb + f1b * rb;
+    const double rbb = f1b * un;
+    const double ubb0 = mu[1] * f1 + unb * n0, ubb1 = mu[2] * f1 + unb * n1, ubb2 = mu[3] * f1 + unb * n2;
+    const double RTab = 0.5 * pbb * a.rho + 0.5 * ph.inv_gm1 * ebb;
+    const double RTbb = 0.5 * pbb * b.rho + 0.5 * ph.inv_gm1 * ebb;
+    ab.rho += 0.5 * rbb + 0.5 * pbb * RTa;
+    bb.rho += 0.5 * rbb + 0.5 * pbb * RTb;
+    ab.u0 += 0.5 * ubb0;
+    ab.u1 += 0.5 * ubb1;
+    ab.u2 += 0.5 * ubb2;
+    bb.u0 += 0.5 * ubb0;
+    bb.u1 += 0.5 * ubb1;
+    bb.u2 += 0.5 * ubb2;
+    ab.usq += 0.25 * ebb;
+    bb.usq += 0.25 * ebb;
+    ab.beta += RTab * (-2.0 * RTa * RTa);      // dRT/dbeta = -1/(2 beta^2) = -2 RT^2
+    bb.beta += RTbb * (-2.0 * RTb * RTb);
+}
+
+// volume-flux variants of the adjoint kernel (the values of ESDC_FLUX_ESC and ESDC_FLUX_KG)
+enum : int { kAdjESC = 0, kAdjKG = 1 };
+
+template <int VF>
+__device__ __forceinline__ void flux_vjp(const Prim& a, const Prim& b, double n0, double n1, double n2,
+                                         const double mu[5], const Phys& ph, PBar& ab, PBar& bb) {
+    if constexpr (VF == kAdjKG) kg_flux_vjp(a, b, n0, n1, n2, mu, ph, ab, bb);
+    else ec_flux_vjp(a, b, n0, n1, n2, mu, ph, ab, bb);
+}
+
 template <int N>
 __device__ __forceinline__ int line_base(int l, int t1, int t2) {
     return l == 0 ? (t1 * N + t2 * N * N) : (l == 1 ? (t1 + t2 * N * N) : (t1 + t2 * N));
@@ -155,7 +201,7 @@ __device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Pri
 
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
-template <int N>
+template <int N, int VF>
 __global__ void __launch_bounds__(CfgA<N>::THREADS, CfgA<N>::MINB)
 adj_main(const double* __restrict__ q, const double* __restrict__ lam, const double* __restrict__ geom,
          const int32_t* __restrict__ nbr, double* __restrict__ grad, double* __restrict__ gbuf,
@@ -239,8 +285,8 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                     double mu[5];
 #pragma unroll
                     for (int v = 0; v < 5; ++v) mu[v] = c * (sL[v * N3 + jj] * ops.winv[j] - li[v]);
-                    ec_flux_vjp(si, sj, 0.5 * (a0 + n0p[jj]), 0.5 * (a1 + n1p[jj]), 0.5 * (a2 + n2p[jj]), mu, ph,
-                                acc[i], acc[j]);
+                    flux_vjp<VF>(si, sj, 0.5 * (a0 + n0p[jj]), 0.5 * (a1 + n1p[jj]), 0.5 * (a2 + n2p[jj]), mu, ph,
+                                 acc[i], acc[j]);
                 }
             }
 #pragma unroll
@@ -297,7 +343,7 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                 muf[v] = -E * nu[v];
             }
             PBar bo{0, 0, 0, 0, 0, 0}, bn{0, 0, 0, 0, 0, 0};
-            ec_flux_vjp(so, sn, n0, n1, n2, muf, ph, bo, bn);
+            flux_vjp<VF>(so, sn, n0, n1, n2, muf, ph, bo, bn);
             double qbo[5] = {0, 0, 0, 0, 0}, qbn[5] = {0, 0, 0, 0, 0};
             if (ph.dissipation) {
                 const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
@@ -614,8 +660,12 @@ cudaError_t launch_adj_n(const esdc_ctx* c, const double* q, const double* lam, 
     using C = CfgA<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
-    adj_main<N><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
-                                               c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
+    if (c->setup.volume_flux == ESDC_FLUX_KG)
+        adj_main<N, kAdjKG><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
+                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
+    else
+        adj_main<N, kAdjESC><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
+                                                            c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
     const unsigned g2 = (unsigned)((c->K + C::EPB_F - 1) / C::EPB_F);
     adj_face<N><<<g2, C::EPB_F * 2 * C::N2, 0, s>>>(q, c->d_nbr, c->d_adj_g, c->d_adj_t, grad, c->K, c->ops, c->phys);
     if (mu_acc) {
@@ -629,7 +679,11 @@ template <int N>
 cudaError_t prepare_adj_n() {
     using C = CfgA<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
-    return cudaFuncSetAttribute(adj_main<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaFuncSetAttribute(adj_main<N, kAdjESC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    return e != cudaSuccess ? e
+                            : cudaFuncSetAttribute(adj_main<N, kAdjKG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
 }
 
 }  // namespace

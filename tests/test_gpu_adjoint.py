@@ -203,3 +203,28 @@ def test_vjp_and_trajectory_gradient_ignore_a_constant_source():
     (go,) = torch.autograd.grad(ke, qq)
     e = normwise_errors(q0.grad, go)
     assert max(e) <= 1e-9, e
+
+
+@pytest.mark.parametrize("p,diss,Re", [(2, True, 200.0), (3, False, 0.0), (4, True, 800.0)])
+def test_kg_vjp_matches_oracle_autograd(p, diss, Re):
+    """The adjoint of the SF-KG variant (Kennedy-Gruber two-point flux) against the oracle's autograd
+    VJP, and a two-step trajectory gradient against the oracle's."""
+    solver, qg, mesh, gas, qo = make_pair(p, (3, 2, 2), warp=0.1, seed=3, Re=Re, dissipation=diss, noise=2e-2,
+                                          volume_flux="kg")
+    lam = torch.randn(qo.shape, generator=torch.Generator().manual_seed(14), dtype=torch.float64)
+    qq = qo.clone().requires_grad_(True)
+    (go,) = torch.autograd.grad(O.rhs(qq, mesh, gas, dissipation=diss, scheme="kg"), qq, lam)
+    e = normwise_errors(solver.rhs_vjp(qg, lam.cuda()), go)
+    assert max(e) <= 1e-10, e
+    if p != 3:
+        return
+    from paper_1911_10966_gb300.autograd import Trajectory, KineticEnergy
+    dt = 0.5 * solver.dt_cfl(qg, 0.5)
+    q0 = qg.clone().requires_grad_(True)
+    mu = torch.tensor(solver.mu, dtype=torch.float64, requires_grad=True)
+    KineticEnergy.apply(Trajectory.apply(q0, mu, solver, dt, 2), solver).backward()
+    qq = qo.clone().requires_grad_(True)
+    ke = O.kinetic_energy(O.rk_step(qq, lambda s: O.rhs(s, mesh, gas, dissipation=diss, scheme="kg"), dt, 2), mesh)
+    (gt,) = torch.autograd.grad(ke, qq)
+    e = normwise_errors(q0.grad, gt)
+    assert max(e) <= 1e-9, e

@@ -39,11 +39,11 @@ def test_variant_freestream_and_dp5_steps(scheme):
 def test_variant_unsupported_combinations():
     from paper_1911_10966_gb300 import _native as nat
     from paper_1911_10966_gb300.solver import Solver
-    solver, qg, mesh, gas, qo = make_pair(2, (2, 2, 2), Re=100.0, volume_flux="kg")
+    solver, qg, mesh, gas, qo = make_pair(2, (2, 2, 2), Re=100.0, volume_flux="dc")
     with pytest.raises(nat.EsdcError) as ei:
         Solver(2, 2, 2, 2, solver.coords, Re=100.0, precision="fp32", volume_flux="dc")
     assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
-    with pytest.raises(nat.EsdcError) as ei:
+    with pytest.raises(nat.EsdcError) as ei:       # the adjoint covers ES-C and SF-KG, not DC
         solver.rhs_vjp(qg, torch.ones_like(qg))
     assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
     with pytest.raises(ValueError):
