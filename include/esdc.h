@@ -46,7 +46,7 @@ extern "C" {
  * the Kennedy-Gruber two-point flux (the paper's SF-KG).  ESDC_FLUX_DC: standard collocation, D
  * applied to the nodal contravariant Euler fluxes (the paper's DC), with the central interface flux.
  * All three use the same interface dissipation, viscous terms and metrics; KG and DC are float64
- * only, and DC has no adjoint (ESDC_ERR_UNSUPPORTED). */
+ * only; all three have an adjoint. */
 /* Interface dissipation of SAT^(I) (the paper defers the SAT to its references).  ESDC_DISS_NONE:
  * entropy conservative.  ESDC_DISS_LLF: local Lax-Friedrichs, lambda/2 (q_own - q_nbr) with
  * lambda = max over both sides of |u.n_J| + c |n_J|.  ESDC_DISS_MATRIX: Roe-type entropy-stable
@@ -346,7 +346,7 @@ int esdc_dt_cfl(esdc_ctx* ctx, const double* q_dev, double cfl, double* dt_host,
  * the cotangent of max(a, b) in half at a tie.  If grad_mu_host is not NULL it also returns
  * lambda . dR/dmu (R is linear in mu through mu and kappa = mu cp/Pr) and synchronises stream.
  * q_dev, lambda_dev, grad_dev: [K][5][N^3] float64 device arrays (grad_dev must not alias the
- * others).  ESDC_PREC_FP64 contexts with p <= 7, the ES-C or SF-KG flux, no or local Lax-Friedrichs
+ * others).  ESDC_PREC_FP64 contexts with p <= 7, any volume flux, no or local Lax-Friedrichs
  * dissipation, no interior penalty and periodic boxes (ESDC_ERR_UNSUPPORTED otherwise); either
  * metric option; a source term (esdc_set_source) is constant in q and leaves the product unchanged.
  * The first call allocates the adjoint face buffers (K*6*9*N^2 float64), kept until esdc_destroy.

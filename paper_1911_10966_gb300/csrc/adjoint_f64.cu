@@ -171,14 +171,46 @@ __device__ __forceinline__ void kg_flux_vjp(const Prim& a, const Prim& b, double
     bb.beta += RTbb * (-2.0 * RTb * RTb);
 }
 
-// volume-flux variants of the adjoint kernel (the values of ESDC_FLUX_ESC and ESDC_FLUX_KG)
-enum : int { kAdjESC = 0, kAdjKG = 1 };
+// Reverse of the Euler flux of one state contracted with n (the DC variant differentiates nodal
+// fluxes): f1 = rho u.n, f_m = rho u_m u.n + p n_m, f5 = rho u.n H, with p = rho RT, RT = 1/(2 beta)
+// and H = gamma/(gamma-1) RT + |u|^2/2.  Adds the primitive cotangents of the state to sb.
+__device__ __forceinline__ void euler_flux_vjp(const Prim& s, double n0, double n1, double n2, const double mu[5],
+                                               const Phys& ph, PBar& sb) {
+    const double RT = 0.5 / s.beta;
+    const double un = s.u0 * n0 + s.u1 * n1 + s.u2 * n2;
+    const double H = ph.gamma * ph.inv_gm1 * RT + 0.5 * s.usq;
+    const double A = s.rho * un;                                   // mass flux
+    const double Ab = mu[0] + mu[1] * s.u0 + mu[2] * s.u1 + mu[3] * s.u2 + mu[4] * H;
+    const double pb = mu[1] * n0 + mu[2] * n1 + mu[3] * n2;
+    const double Hb = mu[4] * A;
+    const double unb = Ab * s.rho;
+    const double RTb = Hb * ph.gamma * ph.inv_gm1 + pb * s.rho;
+    sb.rho += Ab * un + pb * RT;
+    sb.u0 += mu[1] * A + unb * n0;
+    sb.u1 += mu[2] * A + unb * n1;
+    sb.u2 += mu[3] * A + unb * n2;
+    sb.usq += 0.5 * Hb;
+    sb.beta += RTb * (-2.0 * RT * RT);         // dRT/dbeta = -2 RT^2
+}
+
+// volume-flux variants of the adjoint kernel (the values of ESDC_FLUX_ESC, _KG and _DC)
+enum : int { kAdjESC = 0, kAdjKG = 1, kAdjDC = 2 };
 
 template <int VF>
 __device__ __forceinline__ void flux_vjp(const Prim& a, const Prim& b, double n0, double n1, double n2,
                                          const double mu[5], const Phys& ph, PBar& ab, PBar& bb) {
-    if constexpr (VF == kAdjKG) kg_flux_vjp(a, b, n0, n1, n2, mu, ph, ab, bb);
-    else ec_flux_vjp(a, b, n0, n1, n2, mu, ph, ab, bb);
+    if constexpr (VF == kAdjKG) {
+        kg_flux_vjp(a, b, n0, n1, n2, mu, ph, ab, bb);
+    } else if constexpr (VF == kAdjDC) {
+        // central interface flux (f(a) + f(b))/2
+        double h[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) h[v] = 0.5 * mu[v];
+        euler_flux_vjp(a, n0, n1, n2, h, ph, ab);
+        euler_flux_vjp(b, n0, n1, n2, h, ph, bb);
+    } else {
+        ec_flux_vjp(a, b, n0, n1, n2, mu, ph, ab, bb);
+    }
 }
 
 template <int N>
@@ -285,8 +317,18 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                     double mu[5];
 #pragma unroll
                     for (int v = 0; v < 5; ++v) mu[v] = c * (sL[v * N3 + jj] * ops.winv[j] - li[v]);
-                    flux_vjp<VF>(si, sj, 0.5 * (a0 + n0p[jj]), 0.5 * (a1 + n1p[jj]), 0.5 * (a2 + n2p[jj]), mu, ph,
-                                 acc[i], acc[j]);
+                    if constexpr (VF == kAdjDC) {
+                        // the pair term is 2 S_ij times the central flux (F(q_i).Ja_l(i) + F(q_j).Ja_l(j))/2
+                        // of the nodal contravariant fluxes (D applied to nodal fluxes)
+                        double h[5];
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) h[v] = 0.5 * mu[v];
+                        euler_flux_vjp(si, a0, a1, a2, h, ph, acc[i]);
+                        euler_flux_vjp(sj, n0p[jj], n1p[jj], n2p[jj], h, ph, acc[j]);
+                    } else {
+                        flux_vjp<VF>(si, sj, 0.5 * (a0 + n0p[jj]), 0.5 * (a1 + n1p[jj]), 0.5 * (a2 + n2p[jj]), mu,
+                                     ph, acc[i], acc[j]);
+                    }
                 }
             }
 #pragma unroll
@@ -663,6 +705,9 @@ cudaError_t launch_adj_n(const esdc_ctx* c, const double* q, const double* lam, 
     if (c->setup.volume_flux == ESDC_FLUX_KG)
         adj_main<N, kAdjKG><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
                                                            c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
+    else if (c->setup.volume_flux == ESDC_FLUX_DC)
+        adj_main<N, kAdjDC><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
+                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
     else
         adj_main<N, kAdjESC><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
                                                             c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
@@ -681,9 +726,13 @@ cudaError_t prepare_adj_n() {
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(double);
     const cudaError_t e = cudaFuncSetAttribute(adj_main<N, kAdjESC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
-    return e != cudaSuccess ? e
-                            : cudaFuncSetAttribute(adj_main<N, kAdjKG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
+    const cudaError_t e2 = e != cudaSuccess ? e
+                                            : cudaFuncSetAttribute(adj_main<N, kAdjKG>,
+                                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                                   (int)smem);
+    return e2 != cudaSuccess ? e2
+                             : cudaFuncSetAttribute(adj_main<N, kAdjDC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem);
 }
 
 }  // namespace

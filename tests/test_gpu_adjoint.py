@@ -205,15 +205,17 @@ def test_vjp_and_trajectory_gradient_ignore_a_constant_source():
     assert max(e) <= 1e-9, e
 
 
-@pytest.mark.parametrize("p,diss,Re", [(2, True, 200.0), (3, False, 0.0), (4, True, 800.0)])
-def test_kg_vjp_matches_oracle_autograd(p, diss, Re):
-    """The adjoint of the SF-KG variant (Kennedy-Gruber two-point flux) against the oracle's autograd
-    VJP, and a two-step trajectory gradient against the oracle's."""
+@pytest.mark.parametrize("vf,p,diss,Re", [("kg", 2, True, 200.0), ("kg", 3, False, 0.0), ("kg", 4, True, 800.0),
+                                          ("dc", 2, True, 200.0), ("dc", 3, True, 400.0), ("dc", 4, False, 0.0)])
+def test_variant_vjp_matches_oracle_autograd(vf, p, diss, Re):
+    """The adjoint of the SF-KG (Kennedy-Gruber two-point flux) and DC (nodal Euler fluxes, central
+    interface flux) variants against the oracle's autograd VJP, and a two-step trajectory gradient
+    against the oracle's."""
     solver, qg, mesh, gas, qo = make_pair(p, (3, 2, 2), warp=0.1, seed=3, Re=Re, dissipation=diss, noise=2e-2,
-                                          volume_flux="kg")
+                                          volume_flux=vf)
     lam = torch.randn(qo.shape, generator=torch.Generator().manual_seed(14), dtype=torch.float64)
     qq = qo.clone().requires_grad_(True)
-    (go,) = torch.autograd.grad(O.rhs(qq, mesh, gas, dissipation=diss, scheme="kg"), qq, lam)
+    (go,) = torch.autograd.grad(O.rhs(qq, mesh, gas, dissipation=diss, scheme=vf), qq, lam)
     e = normwise_errors(solver.rhs_vjp(qg, lam.cuda()), go)
     assert max(e) <= 1e-10, e
     if p != 3:
@@ -224,7 +226,7 @@ def test_kg_vjp_matches_oracle_autograd(p, diss, Re):
     mu = torch.tensor(solver.mu, dtype=torch.float64, requires_grad=True)
     KineticEnergy.apply(Trajectory.apply(q0, mu, solver, dt, 2), solver).backward()
     qq = qo.clone().requires_grad_(True)
-    ke = O.kinetic_energy(O.rk_step(qq, lambda s: O.rhs(s, mesh, gas, dissipation=diss, scheme="kg"), dt, 2), mesh)
+    ke = O.kinetic_energy(O.rk_step(qq, lambda s: O.rhs(s, mesh, gas, dissipation=diss, scheme=vf), dt, 2), mesh)
     (gt,) = torch.autograd.grad(ke, qq)
     e = normwise_errors(q0.grad, gt)
     assert max(e) <= 1e-9, e

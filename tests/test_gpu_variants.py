@@ -43,8 +43,5 @@ def test_variant_unsupported_combinations():
     with pytest.raises(nat.EsdcError) as ei:
         Solver(2, 2, 2, 2, solver.coords, Re=100.0, precision="fp32", volume_flux="dc")
     assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
-    with pytest.raises(nat.EsdcError) as ei:       # the adjoint covers ES-C and SF-KG, not DC
-        solver.rhs_vjp(qg, torch.ones_like(qg))
-    assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
     with pytest.raises(ValueError):
         Solver(2, 2, 2, 2, solver.coords, volume_flux="roe")
