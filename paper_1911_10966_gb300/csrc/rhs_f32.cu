@@ -43,12 +43,20 @@ struct CfgF {
     static constexpr int MINB = N <= 4 ? 4 : (N == 5 ? 6 : 2);
 };
 
+// Per-node primitives in the form the pair loop consumes: half the density perturbation and half the
+// velocity (so that averages are single additions), the velocity itself, and the perturbation of
+// beta = rho/(2p) relative to beta0, dbn = beta/beta0 - 1 (so that the reference values are 1).
 struct PrimF {
-    float rho, dr, u0, u1, u2, usq, beta, db;
+    float hdr, hu0, hu1, hu2, dbn, u0, u1, u2;
 };
 
 struct Ref {
-    float rho0, p0, beta0, RT0, H0, inv_gm1, gm1, gamma, inv_p0;
+    float rho0, p0, RT0, H0, gm1, gamma;
+    float hrho0;     // rho0 / 2
+    float two_RT0;   // 2 RT0
+    float c5;        // RT0 / (gamma - 1)
+    float inv_rho0;
+    float two_beta0; // rho0 / p0
 };
 
 // approximate reciprocal and square root (about 1 ulp): the float32 residual's rounding is
@@ -64,57 +72,70 @@ __device__ __forceinline__ float fsqrt(float x) {
     return r;
 }
 
-// primitives from the float32 perturbation state
+// primitives from the float32 perturbation state; with p = p0 + dp,
+// beta/beta0 - 1 = (drho p0 - rho0 dp) / (rho0 p)
 __device__ __forceinline__ void to_prim_f(const float dq[5], const Ref& r, PrimF& s) {
-    s.dr = dq[0];
-    s.rho = r.rho0 + dq[0];
-    const float ri = frcp(s.rho);
+    const float rho = r.rho0 + dq[0];
+    const float ri = frcp(rho);
     s.u0 = dq[1] * ri;
     s.u1 = dq[2] * ri;
     s.u2 = dq[3] * ri;
-    s.usq = s.u0 * s.u0 + s.u1 * s.u1 + s.u2 * s.u2;
-    const float dp = r.gm1 * (dq[4] - 0.5f * s.rho * s.usq);
-    const float h = 0.5f * frcp(r.p0 + dp);          // 1/(2p)
-    s.beta = s.rho * h;
-    s.db = (s.dr * r.p0 - r.rho0 * dp) * h * r.inv_p0;   // beta - beta0 = (drho p0 - rho0 dp)/(2 p p0)
+    const float usq = s.u0 * s.u0 + s.u1 * s.u1 + s.u2 * s.u2;
+    const float dp = r.gm1 * (dq[4] - 0.5f * rho * usq);
+    s.dbn = (dq[0] * r.p0 - r.rho0 * dp) * frcp(r.p0 + dp) * r.inv_rho0;
+    s.hdr = 0.5f * dq[0];
+    s.hu0 = 0.5f * s.u0;
+    s.hu1 = 0.5f * s.u1;
+    s.hu2 = 0.5f * s.u2;
 }
 
-// perturbation part of the two-point flux (df[0..4]) and ubar.n (the linear reference part)
+// 2 beta of a node (the entropy variables are 2 beta u and -2 beta) and RT = 1/(2 beta)
+__device__ __forceinline__ float two_beta(const PrimF& s, const Ref& r) { return r.two_beta0 * (1.0f + s.dbn); }
+__device__ __forceinline__ float node_RT(float dbn, const Ref& r) { return r.RT0 * frcp(1.0f + dbn); }
+
+// perturbation part of the two-point flux (df[0..4]) and ubar.n (the linear reference part).  a
+// supplies u (the full velocity), b half of it, both the halved density perturbation and dbn.
+//   density: rho_bar = rho0 + dbar with dbar the mean perturbation, f = (drho_a - drho_b)/(rho_a + rho_b),
+//     drho_ln = dbar + rho_bar (G(f^2) - 1), G = 1 - u/3 - 4u^2/45 - 44u^3/945 for f^2 < 1e-2
+//   beta (in units of beta0): 1/(2 beta_ln) - RT0 = RT0 dIn, dIn = (2 (F - 1) - dbs)/(2 + dbs) with
+//     dbs = dbn_a + dbn_b and F = 1 + u/3 + u^2/5 + u^3/7 in u = ((dbn_a - dbn_b)/(2 + dbs))^2
+//   p_t - p0 = rho_bar/(2 beta_bar) - p0 = 2 RT0 (dbar - rho0 dbs / 2) / (2 + dbs)
+//   df5 = RT0/(gamma-1) ubar.n (rho0 dIn + drho_ln (1 + dIn)) + f1 (u_a.u_b)/2 + (p_t - p0) ubar.n
 __device__ __forceinline__ void ec_flux_pert(const PrimF& a, const PrimF& b, float n0, float n1, float n2,
                                              const Ref& r, float df[5], float& un) {
-    // density log mean: drho_ln = drho_bar + rho_bar (G(u) - 1), series branch for u < 1e-2
-    const float s = a.rho + b.rho;
-    const float f = (a.dr - b.dr) * frcp(s);
+    const float dbar = a.hdr + b.hdr;
+    const float rb = r.rho0 + dbar;
+    const float f = (a.hdr - b.hdr) * frcp(rb);
     const float uu = f * f;
     float drl;
     if (uu < 1.0e-2f) {
-        drl = 0.5f * (a.dr + b.dr) + 0.5f * s * (uu * (-1.0f / 3.0f + uu * (-4.0f / 45.0f + uu * (-44.0f / 945.0f))));
+        drl = fmaf(rb, uu * (-1.0f / 3.0f + uu * (-4.0f / 45.0f + uu * (-44.0f / 945.0f))), dbar);
     } else {
-        drl = (a.rho - b.rho) * frcp(logf(a.rho * frcp(b.rho))) - r.rho0;
+        const float ra = r.rho0 + 2.0f * a.hdr, rbb = r.rho0 + 2.0f * b.hdr;
+        drl = (ra - rbb) * frcp(logf(ra * frcp(rbb))) - r.rho0;
     }
-    // beta: 1/(2 beta_ln) - RT0 and p_t - p0 from the perturbations
-    const float sb = a.beta + b.beta;
-    const float rsb = frcp(sb);
-    const float dbs = a.db + b.db;
-    const float fb = (a.db - b.db) * rsb;
+    const float dbs = a.dbn + b.dbn;
+    const float rsb = frcp(2.0f + dbs);
+    const float db = a.dbn - b.dbn;
+    const float fb = db * rsb;
     const float ub = fb * fb;
-    float dI;
+    float dIn;
     if (ub < 1.0e-2f) {
-        const float Fm1 = ub * (1.0f / 3.0f + ub * (1.0f / 5.0f + ub * (1.0f / 7.0f)));
-        dI = (2.0f * r.beta0 * Fm1 - dbs) * rsb * r.RT0;
+        dIn = (ub * (2.0f / 3.0f + ub * (2.0f / 5.0f + ub * (2.0f / 7.0f))) - dbs) * rsb;
     } else {
-        dI = 0.5f * logf(a.beta * frcp(b.beta)) * frcp(a.beta - b.beta) - r.RT0;
+        dIn = logf((1.0f + a.dbn) * frcp(1.0f + b.dbn)) * frcp(db) - 1.0f;
     }
-    const float dpt = (r.beta0 * (a.dr + b.dr) - r.rho0 * dbs) * rsb * r.RT0;
-    const float ub0 = 0.5f * (a.u0 + b.u0), ub1 = 0.5f * (a.u1 + b.u1), ub2 = 0.5f * (a.u2 + b.u2);
+    const float dpt = (r.two_RT0 * rsb) * fmaf(-r.hrho0, dbs, dbar);
+    const float ub0 = a.hu0 + b.hu0, ub1 = a.hu1 + b.hu1, ub2 = a.hu2 + b.hu2;
     un = ub0 * n0 + ub1 * n1 + ub2 * n2;
-    const float f1 = (r.rho0 + drl) * un;
+    const float rr = r.rho0 + drl;
+    const float f1 = rr * un;
     df[0] = drl * un;
     df[1] = f1 * ub0 + dpt * n0;
     df[2] = f1 * ub1 + dpt * n1;
     df[3] = f1 * ub2 + dpt * n2;
-    const float uab = a.u0 * b.u0 + a.u1 * b.u1 + a.u2 * b.u2;
-    df[4] = un * r.inv_gm1 * (r.rho0 * dI + drl * (r.RT0 + dI)) + 0.5f * f1 * uab + dpt * un;
+    const float hab = a.u0 * b.hu0 + a.u1 * b.hu1 + a.u2 * b.hu2;
+    df[4] = fmaf(r.c5 * un, fmaf(dIn, rr, drl), fmaf(f1, hab, dpt * un));
 }
 
 template <int N>
@@ -127,17 +148,26 @@ __device__ __forceinline__ int dir_stride_f(int l) {
     return l == 0 ? 1 : (l == 1 ? N : N * N);
 }
 
-// node primitives stored as two float4 per node: (rho, drho, u0, u1), (u2, |u|^2, beta, dbeta)
+// node primitives stored as two float4 per node: (drho/2, u/2), (dbn, u)
 __device__ __forceinline__ void load_prim_f(const float4* sP4, int N3, int idx, PrimF& s) {
     const float4 a = sP4[idx], b = sP4[N3 + idx];
-    s.rho = a.x;
-    s.dr = a.y;
-    s.u0 = a.z;
-    s.u1 = a.w;
-    s.u2 = b.x;
-    s.usq = b.y;
-    s.beta = b.z;
-    s.db = b.w;
+    s.hdr = a.x;
+    s.hu0 = a.y;
+    s.hu1 = a.z;
+    s.hu2 = a.w;
+    s.dbn = b.x;
+    s.u0 = b.y;
+    s.u1 = b.z;
+    s.u2 = b.w;
+}
+// the part the second member of a pair uses (no full velocity)
+__device__ __forceinline__ void load_prim_half(const float4* sP4, int N3, int idx, PrimF& s) {
+    const float4 a = sP4[idx];
+    s.hdr = a.x;
+    s.hu0 = a.y;
+    s.hu1 = a.z;
+    s.hu2 = a.w;
+    s.dbn = reinterpret_cast<const float*>(sP4 + N3 + idx)[0];
 }
 
 // The residual's input state value at flat index i: base[i] + sum_j c_j k_j[i] (a Runge-Kutta stage
@@ -188,10 +218,11 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             }
             PrimF s;
             to_prim_f(d, ref, s);
-            sP4[node] = make_float4(s.rho, s.dr, s.u0, s.u1);
-            sP4[N3 + node] = make_float4(s.u2, s.usq, s.beta, s.db);
-            // w5 - w5_ref: the constant has no gradient
-            sW4[node] = make_float4(2.0f * s.beta * s.u0, 2.0f * s.beta * s.u1, 2.0f * s.beta * s.u2, -2.0f * s.db);
+            sP4[node] = make_float4(s.hdr, s.hu0, s.hu1, s.hu2);
+            sP4[N3 + node] = make_float4(s.dbn, s.u0, s.u1, s.u2);
+            // w5 - w5_ref = -2 (beta - beta0): the constant has no gradient
+            const float tb = two_beta(s, ref);
+            sW4[node] = make_float4(tb * s.u0, tb * s.u1, tb * s.u2, -ref.two_beta0 * s.dbn);
             float gv[10];
 #pragma unroll
             for (int c = 0; c < 10; ++c) gv[c] = geom[(el * 10 + c) * N3 + node];
@@ -223,7 +254,7 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             for (int j = i + 1; j < N; ++j) {
                 const int jj = base + j * st;
                 PrimF sj;
-                load_prim_f(sP4, N3, jj, sj);
+                load_prim_half(sP4, N3, jj, sj);
                 const float4 nj = nl[jj];
                 float df[5], un;
                 // the flux is linear in n: pass n_i + n_j and take S (half of 2S) as the pair coefficient
@@ -280,8 +311,8 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             float lam = 0.0f;
             if (ph.dissipation) {
                 const float nn = fsqrt(n0 * n0 + n1 * n1 + n2 * n2);
-                const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + fsqrt(0.5f * ref.gamma * frcp(so.beta)) * nn;
-                const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + fsqrt(0.5f * ref.gamma * frcp(sn.beta)) * nn;
+                const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + fsqrt(ref.gamma * node_RT(so.dbn, ref)) * nn;
+                const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + fsqrt(ref.gamma * node_RT(sn.dbn, ref)) * nn;
                 lam = 0.5f * fmaxf(lo, ln);
             }
             const float wi = ops.winv[side ? N - 1 : 0];
@@ -290,10 +321,11 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             for (int v = 0; v < 5; ++v) A[v * N3 + own] += (-E * df[v] - lam * (sQ[v * N3 + own] - qn[v])) * wi;
             A[5 * N3 + own] += -E * un * wi;
             float* wf = sWf + (2 * l + side) * 4 * N2 + fi;
-            wf[0] = 2.0f * sn.beta * sn.u0;
-            wf[N2] = 2.0f * sn.beta * sn.u1;
-            wf[2 * N2] = 2.0f * sn.beta * sn.u2;
-            wf[3 * N2] = -2.0f * sn.db;
+            const float tb = two_beta(sn, ref);
+            wf[0] = tb * sn.u0;
+            wf[N2] = tb * sn.u1;
+            wf[2 * N2] = tb * sn.u2;
+            wf[3 * N2] = -ref.two_beta0 * sn.dbn;
         }
     }
     __syncthreads();
@@ -347,9 +379,9 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         g[m][k] = Jinv * (Ja[0][m] * th[0][k] + Ja[1][m] * th[1][k] + Ja[2][m] * th[2][k]);
-                const float4 P0 = sP4[node], P1 = sP4[N3 + node];
-                const float RT = 0.5f * frcp(P1.z);
-                const float u[3] = {P0.z, P0.w, P1.x};
+                const float4 P1 = sP4[N3 + node];
+                const float RT = node_RT(P1.x, ref);
+                const float u[3] = {P1.y, P1.z, P1.w};
                 float du[3][3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
@@ -449,13 +481,15 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaSt
     Ref ref;
     ref.rho0 = ph.rho0;
     ref.p0 = ph.p0;
-    ref.beta0 = ph.rho0 / (2.0f * ph.p0);
     ref.RT0 = ph.p0 / ph.rho0;
     ref.H0 = ph.gamma * ph.p0 / (ph.gamma - 1.0f);
-    ref.inv_gm1 = ph.inv_gm1;
     ref.gm1 = ph.gamma - 1.0f;
     ref.gamma = ph.gamma;
-    ref.inv_p0 = 1.0f / ph.p0;
+    ref.hrho0 = 0.5f * ph.rho0;
+    ref.two_RT0 = 2.0f * ref.RT0;
+    ref.c5 = ref.RT0 * ph.inv_gm1;
+    ref.inv_rho0 = 1.0f / ph.rho0;
+    ref.two_beta0 = ph.rho0 / ph.p0;
     if (in.nk < 0 || in.nk > 5) return cudaErrorInvalidValue;
     if (ev) cudaEventRecord(ev[0], s);
     if (in.nk == 0)
