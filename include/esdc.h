@@ -306,7 +306,7 @@ int esdc_budgets_async(esdc_ctx* ctx, const double* q_dev, const void* dqdt_dev,
  * entropy variables, and the viscous interface term SAT^(V) is zero (the exterior viscous flux is
  * read as the interior one; the paper's boundary SATs are in its references).  The pointer is
  * kept, not copied: the array must stay valid while the context evaluates residuals.  NULL clears
- * it.  A residual of a bounded box without an exterior state fails with ESDC_ERR_ARG.
+ * it.  A residual or adjoint of a bounded box without an exterior state fails with ESDC_ERR_ARG.
  * Float64 contexts only (float32 contexts cannot be bounded).
  */
 int esdc_set_exterior(esdc_ctx* ctx, const double* q_ext_dev);
@@ -347,8 +347,10 @@ int esdc_dt_cfl(esdc_ctx* ctx, const double* q_dev, double cfl, double* dt_host,
  * lambda . dR/dmu (R is linear in mu through mu and kappa = mu cp/Pr) and synchronises stream.
  * q_dev, lambda_dev, grad_dev: [K][5][N^3] float64 device arrays (grad_dev must not alias the
  * others).  ESDC_PREC_FP64 contexts with p <= 7, any volume flux, no or local Lax-Friedrichs
- * dissipation, no interior penalty and periodic boxes (ESDC_ERR_UNSUPPORTED otherwise); either
- * metric option; a source term (esdc_set_source) is constant in q and leaves the product unchanged.
+ * dissipation and no interior penalty (ESDC_ERR_UNSUPPORTED otherwise); either metric option;
+ * periodic or bounded boxes.  On a bounded box the exterior state (esdc_set_exterior, ESDC_ERR_ARG
+ * if absent) is constant in q: a boundary face passes its cotangent to the own nodes only.  A source
+ * term (esdc_set_source) is constant in q too and leaves the product unchanged.
  * The first call allocates the adjoint face buffers (K*6*9*N^2 float64), kept until esdc_destroy.
  */
 int esdc_rhs_vjp(esdc_ctx* ctx, const double* q_dev, const double* lambda_dev, double* grad_dev,

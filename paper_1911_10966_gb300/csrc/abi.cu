@@ -366,10 +366,11 @@ int prepare_variant(esdc_ctx* c) {
 
 int ensure_adjoint(esdc_ctx* c) {
     if (c->setup.precision != ESDC_PREC_FP64 ||
-        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 ||
-        c->N > esdc::kMaxN)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 contexts with p <= 7, scalar "
+        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->N > esdc::kMaxN)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 contexts with p <= 7, scalar "
                                           "dissipation and no interior penalty");
+    if (c->setup.bounded != 0 && !c->d_qext)
+        return fail(ESDC_ERR_ARG, "a bounded box needs an exterior state (esdc_set_exterior)");
     if (c->d_adj_g) return ESDC_OK;
     const size_t N2 = (size_t)c->N * c->N;
     CUDA_TRY(cudaMalloc(&c->d_adj_g, (size_t)c->K * 6 * 5 * N2 * sizeof(double)));
@@ -382,11 +383,6 @@ int ensure_adjoint(esdc_ctx* c) {
 
 int adjoint_checks(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, void* ws, size_t ws_bytes) {
     if (!c || !ckpt || !lam || !ws) return fail(ESDC_ERR_ARG, "null argument");
-    if (c->setup.precision != ESDC_PREC_FP64 ||
-        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->setup.bounded != 0 ||
-        c->N > esdc::kMaxN)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for periodic float64 contexts with p <= 7, scalar "
-                                          "dissipation and no interior penalty");
     if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
     const size_t need = 12 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "adjoint workspace too small");

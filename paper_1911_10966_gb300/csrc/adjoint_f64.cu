@@ -13,6 +13,9 @@
 // node by node with the transposed derivative D_l^T along lines, the lifted-gradient cotangent on
 // faces written to tbuf for the neighbour.  Kernel adj_main does everything inside an element,
 // kernel adj_face adds what the neighbours wrote for this element's face nodes.
+// On a bounded box a boundary face (neighbour -1) takes the exterior state q_ext, which does not
+// depend on q, as its neighbour: the interface cotangent stays with the own node, the lift keeps its
+// own part, and the viscous interface term, zero on such faces, has no transpose.
 // Non-smooth points follow the convention of reverse-mode differentiation: d|x| = sign(x) with
 // sign(0) = 0, and max(a, b) splits its cotangent in half at a tie.
 #include <cuda_runtime.h>
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(CfgA<N>::THREADS, CfgA<N>::MINB)
 adj_main(const double* __restrict__ q, const double* __restrict__ lam, const double* __restrict__ geom,
          const int32_t* __restrict__ nbr, double* __restrict__ grad, double* __restrict__ gbuf,
          double* __restrict__ tbuf, double* __restrict__ mupart, int64_t K, const Ops ops, const Phys ph,
-         const double* __restrict__ nsurf) {
+         const double* __restrict__ nsurf, const double* __restrict__ qext) {
     constexpr int N2 = CfgA<N>::N2, N3 = CfgA<N>::N3, EPB = CfgA<N>::EPB;
     extern __shared__ double smem[];
     __shared__ double red[CfgA<N>::THREADS];
@@ -360,11 +363,12 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
             const int own = base + (side ? (N - 1) * st : 0);
             const int nbn = base + (side ? 0 : (N - 1) * st);
             const int64_t nb = nbr[el * 6 + 2 * l + side];
+            const bool bnd = nb < 0;        // bounded boxes only: the exterior state at the own nodes
             double qo[5], qn[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
                 qo[v] = q[eoff + v * N3 + own];
-                qn[v] = q[nb * 5 * N3 + v * N3 + nbn];
+                qn[v] = bnd ? qext[eoff + v * N3 + own] : q[nb * 5 * N3 + v * N3 + nbn];
             }
             Prim so, sn;
             load_prim(sP, N3, own, so);
@@ -504,11 +508,11 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                     for (int i = 0; i < N; ++i) s += ops.D[i][il] * sL[(1 + k) * N3 + lb + i * st];
                     Phi[l][k] = s;
                 }
-                if (il == 0 || il == N - 1) {
+                const int64_t nb = (il == 0 || il == N - 1) ? nbr[el * 6 + 2 * l + (il == N - 1)] : -1;
+                if (nb >= 0) {     // interior face (a boundary face has no viscous interface term)
                     const int side = il == N - 1;
                     const int st2 = dir_stride<N>(l);
                     const int nbn = node + (side ? -(N - 1) * st2 : (N - 1) * st2);   // matching node in nb
-                    const int64_t nb = nbr[el * 6 + 2 * l + side];
                     const double Jn = 1.0 / geom[nb * 10 * N3 + nbn];
                     const double E = side ? 0.5 : -0.5;
 #pragma unroll
@@ -647,10 +651,11 @@ adj_face(const double* __restrict__ q, const int32_t* __restrict__ nbr, const do
     const bool active = el < K;
 #pragma unroll 1
     for (int l = 0; l < 3; ++l) {
-        if (active) {
+        // a boundary face (neighbour -1) receives nothing; every thread still reaches the barrier
+        const int64_t nb = active ? nbr[el * 6 + 2 * l + side] : -1;
+        if (nb >= 0) {
             const int st = dir_stride<N>(l);
             const int own = line_base<N>(l, fi % N, fi / N) + (side ? (N - 1) * st : 0);
-            const int64_t nb = nbr[el * 6 + 2 * l + side];
             const int nside = 1 - side;
             const double* gb = gbuf + ((nb * 6 + 2 * l + nside) * 5) * N2 + fi;
             double add[5];
@@ -704,13 +709,13 @@ cudaError_t launch_adj_n(const esdc_ctx* c, const double* q, const double* lam, 
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     if (c->setup.volume_flux == ESDC_FLUX_KG)
         adj_main<N, kAdjKG><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
-                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
+                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext);
     else if (c->setup.volume_flux == ESDC_FLUX_DC)
         adj_main<N, kAdjDC><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
-                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
+                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext);
     else
         adj_main<N, kAdjESC><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
-                                                            c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf);
+                                                            c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext);
     const unsigned g2 = (unsigned)((c->K + C::EPB_F - 1) / C::EPB_F);
     adj_face<N><<<g2, C::EPB_F * 2 * C::N2, 0, s>>>(q, c->d_nbr, c->d_adj_g, c->d_adj_t, grad, c->K, c->ops, c->phys);
     if (mu_acc) {

@@ -1,7 +1,8 @@
 """Bounded boxes with Dirichlet exterior data and a source term (the manufactured-solution setting of
 Sec. 5.1) on the GPU: residual parity with the oracle on warped bounded boxes, with all interface
 options; the source array is added as given; and the GPU's own manufactured source (esdc_mms_fields)
-makes the exact solution's residual vanish at the operator's truncation order."""
+makes the exact solution's residual vanish at the operator's truncation order; the adjoint on
+bounded boxes against the oracle's autograd."""
 import math
 
 import numpy as np
@@ -10,7 +11,7 @@ import torch
 
 from oracle import esdc_oracle as O
 from paper_1911_10966_gb300 import inputs as I
-from tests.gpu_common import assert_parity
+from tests.gpu_common import assert_parity, normwise_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -81,7 +82,67 @@ def test_bounded_box_requirements():
     with pytest.raises(nat.EsdcError) as ei:
         Solver(2, 2, 2, 2, xg, Ma=I.MMS_MA, Re=100.0, bounded=(True, False, False), precision="fp32")
     assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
-    solver.set_exterior(q)
+    # the adjoint of a bounded box needs the exterior state as well
     with pytest.raises(nat.EsdcError) as ei:
         solver.rhs_vjp(q, torch.ones_like(q))
-    assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
+    assert ei.value.code == nat.ESDC_ERR_ARG
+    solver.set_exterior(q)
+    assert torch.isfinite(solver.rhs_vjp(q, torch.ones_like(q))).all()
+
+
+@pytest.mark.parametrize("p,k,Re,kw", [(2, 3, 1.0e3, {}), (3, 2, 0.0, {"dissipation": False}),
+                                       (3, 2, 4.0e2, {"volume_flux": "kg"}), (2, 2, 1.0e3, {"volume_flux": "dc"}),
+                                       (3, 2, 1.0e3, {"metrics": "optimized"})])
+def test_bounded_box_vjp_matches_oracle_autograd(p, k, Re, kw):
+    """The adjoint on a warped bounded box (exterior data constant in q, source constant in q)
+    against the oracle's autograd VJP of the same residual, and lambda . dR/dmu against the oracle's
+    derivative in mu."""
+    solver, xg, mesh, xo, gas = _pair(p, k, 0.1, Re, **kw)
+    if kw.get("metrics") == "optimized":
+        mesh = O.make_mesh(p, xo, k, k, k, bounded=(True, True, True), metrics="optimized")
+    qg = solver.to_device(I.perturb(I.manufactured(xg), seed=4, rel=1e-2))
+    qo = torch.tensor(I.perturb(I.manufactured(xo), seed=4, rel=1e-2))
+    solver.set_exterior(solver.to_device(I.manufactured(xg)))
+    src = I.random_direction(tuple(qo.shape), seed=5, scale=1.0)
+    solver.set_source(solver.to_device(src))
+    lam = torch.randn(qo.shape, generator=torch.Generator().manual_seed(12), dtype=torch.float64)
+    qq = qo.clone().requires_grad_(True)
+    viscous = Re > 0.0
+    mo = torch.tensor(gas.mu, dtype=torch.float64, requires_grad=True)
+    g2 = O.Gas(gas.gamma, gas.R, mo, gas.Pr) if viscous else gas
+    r = O.rhs(qq, mesh, g2, dissipation=kw.get("dissipation", True), scheme=kw.get("volume_flux", "esc"),
+              q_ext=torch.tensor(I.manufactured(xo)), source=torch.tensor(src))
+    grads = torch.autograd.grad(r, (qq, mo) if viscous else (qq,), lam)
+    gg, gmu = solver.rhs_vjp(qg, lam.cuda(), want_mu=True)
+    e = normwise_errors(gg, grads[0])
+    print("bounded vjp vs oracle autograd", ["%.1e" % x for x in e])
+    assert max(e) <= 1e-10, e
+    if viscous:
+        assert abs(gmu - float(grads[1])) <= 1e-10 * abs(float(grads[1])), (gmu, float(grads[1]))
+
+
+def test_bounded_box_trajectory_gradient_matches_oracle_autograd():
+    """Two DP5 steps on a warped bounded p = 3 box with Dirichlet exterior data and a source: the GPU
+    adjoint gradient of the final kinetic energy w.r.t. q_0 and mu equals the oracle's autograd
+    gradient."""
+    from paper_1911_10966_gb300.autograd import KineticEnergy, Trajectory
+    solver, xg, mesh, xo, gas = _pair(3, 2, 0.1, 1.0e3)
+    qg = solver.to_device(I.perturb(I.manufactured(xg), seed=6, rel=1e-2))
+    qo = torch.tensor(I.perturb(I.manufactured(xo), seed=6, rel=1e-2))
+    solver.set_exterior(solver.to_device(I.manufactured(xg)))
+    src = I.random_direction(tuple(qo.shape), seed=7, scale=1.0)
+    solver.set_source(solver.to_device(src))
+    dt = 0.5 * solver.dt_cfl(qg, 0.5)
+    q0 = qg.clone().requires_grad_(True)
+    mu = torch.tensor(solver.mu, dtype=torch.float64, requires_grad=True)
+    KineticEnergy.apply(Trajectory.apply(q0, mu, solver, dt, 2), solver).backward()
+    qq = qo.clone().requires_grad_(True)
+    mo = torch.tensor(gas.mu, dtype=torch.float64, requires_grad=True)
+    g2 = O.Gas(gas.gamma, gas.R, mo, gas.Pr)
+    qe, so = torch.tensor(I.manufactured(xo)), torch.tensor(src)
+    ke = O.kinetic_energy(O.rk_step(qq, lambda s: O.rhs(s, mesh, g2, q_ext=qe, source=so), dt, 2), mesh)
+    gqo, gmo = torch.autograd.grad(ke, (qq, mo))
+    e = normwise_errors(q0.grad, gqo)
+    print("bounded trajectory gradient vs oracle", ["%.1e" % x for x in e], float(mu.grad), float(gmo))
+    assert max(e) <= 1e-9, e
+    assert abs(float(mu.grad) - float(gmo)) <= 1e-9 * abs(float(gmo))
