@@ -52,7 +52,7 @@ extern "C" {
  * lambda = max over both sides of |u.n_J| + c |n_J|.  ESDC_DISS_MATRIX: Roe-type entropy-stable
  * matrix dissipation D (w_own - w_nbr)/2, D = R |Lambda| R^T at the averaged state (log-mean
  * density, mean velocity, p = rho_bar/(2 beta_bar)) with eigenvectors scaled so that R R^T = dq/dw;
- * float64 only, no adjoint (ESDC_ERR_UNSUPPORTED). */
+ * float64 only (ESDC_ERR_UNSUPPORTED for float32); the adjoint supports it. */
 #define ESDC_DISS_NONE 0
 #define ESDC_DISS_LLF 1
 #define ESDC_DISS_MATRIX 2
@@ -120,7 +120,8 @@ typedef struct esdc_setup {
 /* Interior penalty (the IP term of eq. NSL; its constants are in the paper's references).  With
  * ip_coef = sigma > 0 and mu > 0, every face node adds -(1/P_ii) sigma mu |n_J| / h dq/dw (w_own -
  * w_nbr), with dq/dw at the averaged state of ESDC_DISS_MATRIX and h = (J_own + J_nbr)/|n_J|; the
- * term is symmetric in the two sides, conserves, and produces entropy.  Float64 only, no adjoint. */
+ * term is symmetric in the two sides, conserves, and produces entropy.  Float64 only; the adjoint
+ * supports it (the term is linear in mu, so it enters lambda . dR/dmu). */
 
 /*
  * esdc_lgl -- the N = p+1 LGL nodes xi[N] (ascending on [-1, 1]) and quadrature weights w[N]
@@ -344,11 +345,11 @@ int esdc_dt_cfl(esdc_ctx* ctx, const double* q_dev, double cfl, double* dt_host,
  * through the Chandrashekar flux and its log means, the interface dissipation, the BR1 viscous
  * chain and the metric terms.  At non-smooth points it uses d|x| = sign(x), sign(0) = 0, and splits
  * the cotangent of max(a, b) in half at a tie.  If grad_mu_host is not NULL it also returns
- * lambda . dR/dmu (R is linear in mu through mu and kappa = mu cp/Pr) and synchronises stream.
- * q_dev, lambda_dev, grad_dev: [K][5][N^3] float64 device arrays (grad_dev must not alias the
- * others).  ESDC_PREC_FP64 contexts with p <= 7, any volume flux, no or local Lax-Friedrichs
- * dissipation and no interior penalty (ESDC_ERR_UNSUPPORTED otherwise); either metric option;
- * periodic or bounded boxes.  On a bounded box the exterior state (esdc_set_exterior, ESDC_ERR_ARG
+ * lambda . dR/dmu (R is linear in mu through mu, kappa = mu cp/Pr and the interior penalty) and
+ * synchronises stream.  q_dev, lambda_dev, grad_dev: [K][5][N^3] float64 device arrays (grad_dev
+ * must not alias the others).  ESDC_PREC_FP64 contexts with p <= 7 (ESDC_ERR_UNSUPPORTED
+ * otherwise): any volume flux, any interface dissipation, the interior penalty, either metric
+ * option, periodic or bounded boxes.  On a bounded box the exterior state (esdc_set_exterior, ESDC_ERR_ARG
  * if absent) is constant in q: a boundary face passes its cotangent to the own nodes only.  A source
  * term (esdc_set_source) is constant in q too and leaves the product unchanged.
  * The first call allocates the adjoint face buffers (K*6*9*N^2 float64), kept until esdc_destroy.

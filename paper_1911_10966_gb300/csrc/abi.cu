@@ -365,10 +365,8 @@ int prepare_variant(esdc_ctx* c) {
 }
 
 int ensure_adjoint(esdc_ctx* c) {
-    if (c->setup.precision != ESDC_PREC_FP64 ||
-        c->setup.dissipation == ESDC_DISS_MATRIX || c->phys.ip_coef > 0.0 || c->N > esdc::kMaxN)
-        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 contexts with p <= 7, scalar "
-                                          "dissipation and no interior penalty");
+    if (c->setup.precision != ESDC_PREC_FP64 || c->N > esdc::kMaxN)
+        return fail(ESDC_ERR_UNSUPPORTED, "the adjoint is built for float64 contexts with p <= 7");
     if (c->setup.bounded != 0 && !c->d_qext)
         return fail(ESDC_ERR_ARG, "a bounded box needs an exterior state (esdc_set_exterior)");
     if (c->d_adj_g) return ESDC_OK;

@@ -236,6 +236,180 @@ __device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Pri
 
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
+// Reverse of the interface terms built on the face-averaged state: the matrix dissipation
+// (1/2) D (w_own - w_nbr) (D = R |Lambda| R^T in the direction n, split into |u.n| dq/dw and the two
+// acoustic rank-one parts) and the interior penalty cip dq/dw (w_own - w_nbr).  The forward quantities
+// are recomputed: the entropy-variable jump jw (with s = log p - gamma log rho), the averaged state
+// (rho_ln, ubar, p = avg(rho)/(2 avg(beta)), c^2 = gamma p/rho_ln, H, rho E) and r = dq/dw jw.  dmb
+// is the cotangent of the sum of the two terms; the primitive cotangents of both states are added
+// to ab, bb.  Returns dmb . (interior-penalty term), the term's share of lambda . R (linear in mu).
+// Kept out of line: only contexts with these options call it.
+__device__ __noinline__ double face_avg_vjp(const Prim& a, const Prim& b, double n0, double n1, double n2,
+                                            const Phys& ph, bool matrix, double cip, const double dmb[5], PBar& ab,
+                                            PBar& bb) {
+    const double g = ph.gamma, igm1 = ph.inv_gm1;
+    const double ua[3] = {a.u0, a.u1, a.u2}, uv[3] = {b.u0, b.u1, b.u2};
+    const double nv[3] = {n0, n1, n2};
+    // ---- forward
+    const double ds = log((a.rho / a.beta) / (b.rho / b.beta)) - g * log(a.rho / b.rho);
+    double jw[5];
+    jw[0] = -ds * igm1 - (a.beta * a.usq - b.beta * b.usq);
+    for (int k = 0; k < 3; ++k) jw[1 + k] = 2.0 * (a.beta * ua[k] - b.beta * uv[k]);
+    jw[4] = -2.0 * (a.beta - b.beta);
+    double L, La, Lb;
+    ln_mean_d(a.rho, b.rho, L, La, Lb);
+    const double sb = a.beta + b.beta;
+    const double p = 0.5 * (a.rho + b.rho) / sb;
+    double u[3], m[3];
+    for (int k = 0; k < 3; ++k) u[k] = 0.5 * (ua[k] + uv[k]);
+    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double c2 = g * p / L;
+    const double H = c2 * igm1 + 0.5 * usq;
+    const double E = p * igm1 + 0.5 * L * usq;
+    for (int k = 0; k < 3; ++k) m[k] = L * u[k];
+    const double ujw = u[0] * jw[1] + u[1] * jw[2] + u[2] * jw[3];
+    const double t = jw[0] + ujw + H * jw[4];
+    double r[5];
+    r[0] = L * jw[0] + m[0] * jw[1] + m[1] * jw[2] + m[2] * jw[3] + E * jw[4];
+    for (int k = 0; k < 3; ++k) r[1 + k] = m[k] * t + p * jw[1 + k];
+    r[4] = E * jw[0] + L * H * ujw + (L * H * H - c2 * p * igm1) * jw[4];
+    // ---- reverse
+    double rb[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, jb[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, ubar[3] = {0.0, 0.0, 0.0};
+    double Lbar = 0.0, Hb = 0.0, c2b = 0.0, pb = 0.0, ujwb = 0.0;
+    double ip_dot = 0.0;
+    if (cip != 0.0) {
+        for (int v = 0; v < 5; ++v) {
+            rb[v] += cip * dmb[v];
+            ip_dot += dmb[v] * cip * r[v];
+        }
+    }
+    if (matrix) {
+        double D[5];
+        for (int v = 0; v < 5; ++v) D[v] = 0.5 * dmb[v];
+        const double c = sqrt(c2);
+        const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+        const double inn = 1.0 / nn;
+        const double un = u[0] * n0 + u[1] * n1 + u[2] * n2;
+        const double unh = un * inn;
+        const double e1 = un - c * nn, e5 = un + c * nn;
+        const double l2 = fabs(un), l1 = fabs(e1), l5 = fabs(e5);
+        double cn[3];
+        for (int k = 0; k < 3; ++k) cn[k] = c * nv[k] * inn;
+        const double njw = cn[0] * jw[1] + cn[1] * jw[2] + cn[2] * jw[3];
+        const double cu = c * unh;
+        const double c1 = jw[0] + ujw - njw + (H - cu) * jw[4];
+        const double c5 = jw[0] + ujw + njw + (H + cu) * jw[4];
+        const double sc = L / (2.0 * g);
+        const double k1 = sc * (l1 - l2) * c1, k5 = sc * (l5 - l2) * c5;
+        // dm = l2 r + k1 (1, u - cn, H - cu) + k5 (1, u + cn, H + cu)
+        double l2b = 0.0;
+        for (int v = 0; v < 5; ++v) {
+            l2b += D[v] * r[v];
+            rb[v] += l2 * D[v];
+        }
+        double k1b = D[0] + D[4] * (H - cu), k5b = D[0] + D[4] * (H + cu);
+        double cnb[3];
+        for (int k = 0; k < 3; ++k) {
+            k1b += D[1 + k] * (u[k] - cn[k]);
+            k5b += D[1 + k] * (u[k] + cn[k]);
+            ubar[k] += (k1 + k5) * D[1 + k];
+            cnb[k] = (k5 - k1) * D[1 + k];
+        }
+        Hb += (k1 + k5) * D[4];
+        double cub = (k5 - k1) * D[4];
+        const double scb = k1b * (l1 - l2) * c1 + k5b * (l5 - l2) * c5;
+        const double l1b = k1b * sc * c1, l5b = k5b * sc * c5;
+        l2b -= k1b * sc * c1 + k5b * sc * c5;
+        const double c1b = k1b * sc * (l1 - l2), c5b = k5b * sc * (l5 - l2);
+        jb[0] += c1b + c5b;
+        ujwb += c1b + c5b;
+        const double njwb = c5b - c1b;
+        Hb += (c1b + c5b) * jw[4];
+        cub += (c5b - c1b) * jw[4];
+        jb[4] += c1b * (H - cu) + c5b * (H + cu);
+        for (int k = 0; k < 3; ++k) {
+            cnb[k] += njwb * jw[1 + k];
+            jb[1 + k] += njwb * cn[k];
+        }
+        Lbar += scb / (2.0 * g);
+        double cb = cub * unh;
+        for (int k = 0; k < 3; ++k) cb += cnb[k] * nv[k] * inn;
+        const double unb = l2b * sgn(un) + l1b * sgn(e1) + l5b * sgn(e5) + cub * c * inn;
+        cb += (l5b * sgn(e5) - l1b * sgn(e1)) * nn;
+        for (int k = 0; k < 3; ++k) ubar[k] += unb * nv[k];
+        c2b += cb / (2.0 * c);
+    }
+    // r = dq/dw jw at the averaged state
+    const double Eb = rb[4] * jw[0] + rb[0] * jw[4];
+    jb[0] += rb[4] * E + rb[0] * L;
+    Lbar += rb[4] * (H * ujw + H * H * jw[4]) + rb[0] * jw[0];
+    Hb += rb[4] * (L * ujw + 2.0 * L * H * jw[4]);
+    ujwb += rb[4] * L * H;
+    c2b -= rb[4] * p * jw[4] * igm1;
+    pb -= rb[4] * c2 * jw[4] * igm1;
+    jb[4] += rb[4] * (L * H * H - c2 * p * igm1) + rb[0] * E;
+    double tb = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double mb = rb[1 + k] * t + rb[0] * jw[1 + k];
+        tb += rb[1 + k] * m[k];
+        pb += rb[1 + k] * jw[1 + k];
+        jb[1 + k] += rb[1 + k] * p + rb[0] * m[k];
+        Lbar += mb * u[k];
+        ubar[k] += mb * L;
+    }
+    jb[0] += tb;
+    ujwb += tb;
+    Hb += tb * jw[4];
+    jb[4] += tb * H;
+    for (int k = 0; k < 3; ++k) {
+        ubar[k] += ujwb * jw[1 + k];
+        jb[1 + k] += ujwb * u[k];
+    }
+    pb += Eb * igm1;
+    Lbar += 0.5 * Eb * usq;
+    double usqb = 0.5 * Eb * L;
+    c2b += Hb * igm1;
+    usqb += 0.5 * Hb;
+    pb += c2b * g / L;
+    Lbar -= c2b * c2 / L;
+    for (int k = 0; k < 3; ++k) ubar[k] += 2.0 * usqb * u[k];
+    // back to the two states
+    ab.u0 += 0.5 * ubar[0];
+    ab.u1 += 0.5 * ubar[1];
+    ab.u2 += 0.5 * ubar[2];
+    bb.u0 += 0.5 * ubar[0];
+    bb.u1 += 0.5 * ubar[1];
+    bb.u2 += 0.5 * ubar[2];
+    ab.rho += pb * 0.5 / sb + Lbar * La;
+    bb.rho += pb * 0.5 / sb + Lbar * Lb;
+    ab.beta -= pb * p / sb + 2.0 * jb[4];
+    bb.beta += -pb * p / sb + 2.0 * jb[4];
+    double aub[3] = {0.0, 0.0, 0.0}, bub[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 3; ++k) {
+        ab.beta += 2.0 * jb[1 + k] * ua[k];
+        aub[k] = 2.0 * jb[1 + k] * a.beta;
+        bb.beta -= 2.0 * jb[1 + k] * uv[k];
+        bub[k] = -2.0 * jb[1 + k] * b.beta;
+    }
+    ab.u0 += aub[0];
+    ab.u1 += aub[1];
+    ab.u2 += aub[2];
+    bb.u0 += bub[0];
+    bb.u1 += bub[1];
+    bb.u2 += bub[2];
+    // jw0 = -ds/(gamma-1) - (beta_a |u_a|^2 - beta_b |u_b|^2), ds = (1-gamma) log(rho_a/rho_b) - log(beta_a/beta_b)
+    const double dsb = -jb[0] * igm1;
+    ab.beta -= jb[0] * a.usq;
+    ab.usq -= jb[0] * a.beta;
+    bb.beta += jb[0] * b.usq;
+    bb.usq += jb[0] * b.beta;
+    ab.rho += dsb * (1.0 - g) / a.rho;
+    bb.rho -= dsb * (1.0 - g) / b.rho;
+    ab.beta -= dsb / a.beta;
+    bb.beta += dsb / b.beta;
+    return ip_dot;
+}
+
 template <int N, int VF>
 __global__ void __launch_bounds__(CfgA<N>::THREADS, CfgA<N>::MINB)
 adj_main(const double* __restrict__ q, const double* __restrict__ lam, const double* __restrict__ geom,
@@ -391,7 +565,19 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
             PBar bo{0, 0, 0, 0, 0, 0}, bn{0, 0, 0, 0, 0, 0};
             flux_vjp<VF>(so, sn, n0, n1, n2, muf, ph, bo, bn);
             double qbo[5] = {0, 0, 0, 0, 0}, qbn[5] = {0, 0, 0, 0, 0};
-            if (ph.dissipation) {
+            if (ph.dissipation == 2 || ph.ip_coef > 0.0) {
+                // matrix dissipation and interior penalty (out of line); their term enters as -dm wi
+                double dmb[5];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) dmb[v] = -nu[v];
+                double cip = 0.0;
+                if (ph.ip_coef > 0.0) {
+                    const double Jn = bnd ? sG[own] : geom[nb * 10 * N3 + nbn];
+                    cip = ph.ip_coef * ph.mu * (n0 * n0 + n1 * n1 + n2 * n2) / (sG[own] + Jn);
+                }
+                mu_acc += face_avg_vjp(so, sn, n0, n1, n2, ph, ph.dissipation == 2, cip, dmb, bo, bn);
+            }
+            if (ph.dissipation == 1) {
                 const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
                 const double uo = so.u0 * n0 + so.u1 * n1 + so.u2 * n2;
                 const double un_ = sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2;

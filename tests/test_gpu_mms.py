@@ -92,7 +92,8 @@ def test_bounded_box_requirements():
 
 @pytest.mark.parametrize("p,k,Re,kw", [(2, 3, 1.0e3, {}), (3, 2, 0.0, {"dissipation": False}),
                                        (3, 2, 4.0e2, {"volume_flux": "kg"}), (2, 2, 1.0e3, {"volume_flux": "dc"}),
-                                       (3, 2, 1.0e3, {"metrics": "optimized"})])
+                                       (3, 2, 1.0e3, {"metrics": "optimized"}),
+                                       (3, 2, 4.0e2, {"dissipation": "matrix", "ip_coef": 2.0})])
 def test_bounded_box_vjp_matches_oracle_autograd(p, k, Re, kw):
     """The adjoint on a warped bounded box (exterior data constant in q, source constant in q)
     against the oracle's autograd VJP of the same residual, and lambda . dR/dmu against the oracle's
@@ -111,7 +112,7 @@ def test_bounded_box_vjp_matches_oracle_autograd(p, k, Re, kw):
     mo = torch.tensor(gas.mu, dtype=torch.float64, requires_grad=True)
     g2 = O.Gas(gas.gamma, gas.R, mo, gas.Pr) if viscous else gas
     r = O.rhs(qq, mesh, g2, dissipation=kw.get("dissipation", True), scheme=kw.get("volume_flux", "esc"),
-              q_ext=torch.tensor(I.manufactured(xo)), source=torch.tensor(src))
+              ip_coef=kw.get("ip_coef", 0.0), q_ext=torch.tensor(I.manufactured(xo)), source=torch.tensor(src))
     grads = torch.autograd.grad(r, (qq, mo) if viscous else (qq,), lam)
     gg, gmu = solver.rhs_vjp(qg, lam.cuda(), want_mu=True)
     e = normwise_errors(gg, grads[0])
