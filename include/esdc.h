@@ -308,14 +308,16 @@ int esdc_budgets_async(esdc_ctx* ctx, const double* q_dev, const void* dqdt_dev,
  * read as the interior one; the paper's boundary SATs are in its references).  The pointer is
  * kept, not copied: the array must stay valid while the context evaluates residuals.  NULL clears
  * it.  A residual or adjoint of a bounded box without an exterior state fails with ESDC_ERR_ARG.
- * Float64 contexts only (float32 contexts cannot be bounded).
+ * Float64 and float32-mixed contexts; the float32 residual rounds the exterior state, less the
+ * reference state, to float32 as it does the state.
  */
 int esdc_set_exterior(esdc_ctx* ctx, const double* q_ext_dev);
 
 /*
  * esdc_set_source -- a source term added to dq/dt by every residual of the context, e.g. the
  * manufactured-solution source of Sec. 5.1 (esdc_mms_fields).  [K][5][N^3] float64 device array,
- * kept (not copied) until replaced; NULL clears it.  Float64 contexts only (ESDC_ERR_UNSUPPORTED).
+ * kept (not copied) until replaced; NULL clears it.  Float64 and float32-mixed contexts with p <= 7
+ * (ESDC_ERR_UNSUPPORTED at p = 15); the float32 residual adds it rounded to float32.
  */
 int esdc_set_source(esdc_ctx* ctx, const double* source_dev);
 

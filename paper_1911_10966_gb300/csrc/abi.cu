@@ -479,8 +479,6 @@ static int check_setup(const esdc_setup_t& s) {
         return fail(ESDC_ERR_UNSUPPORTED, "the matrix dissipation is built for float64 only");
     if (!(s.ip_coef >= 0.0) || !std::isfinite(s.ip_coef)) return fail(ESDC_ERR_ARG, "ip_coef must be finite and >= 0");
     if (s.bounded < 0 || s.bounded > 7) return fail(ESDC_ERR_ARG, "bounded must be a bit mask in [0, 7]");
-    if (s.bounded != 0 && s.precision != ESDC_PREC_FP64)
-        return fail(ESDC_ERR_UNSUPPORTED, "bounded boxes are built for float64 only");
     if (s.ip_coef > 0.0 && s.precision != ESDC_PREC_FP64)
         return fail(ESDC_ERR_UNSUPPORTED, "the interior penalty is built for float64 only");
     if (s.precision != ESDC_PREC_FP64 && s.precision != ESDC_PREC_FP32)
@@ -877,8 +875,6 @@ int esdc_budgets_async(esdc_ctx* c, const double* q, const void* dqdt, double* o
 
 int esdc_set_exterior(esdc_ctx* c, const double* q_ext) {
     if (!c) return fail(ESDC_ERR_ARG, "null context");
-    if (q_ext && c->setup.precision != ESDC_PREC_FP64)
-        return fail(ESDC_ERR_UNSUPPORTED, "exterior states are used by float64 contexts only");
     if (q_ext && !aligned(q_ext, 16)) return fail(ESDC_ERR_ARG, "q_ext must be 16-byte aligned");
     c->d_qext = q_ext;
     return prepare_variant(c);
@@ -886,8 +882,7 @@ int esdc_set_exterior(esdc_ctx* c, const double* q_ext) {
 
 int esdc_set_source(esdc_ctx* c, const double* src) {
     if (!c) return fail(ESDC_ERR_ARG, "null context");
-    if (src && (c->setup.precision != ESDC_PREC_FP64 || c->N > esdc::kMaxN))
-        return fail(ESDC_ERR_UNSUPPORTED, "source terms are added by float64 contexts with p <= 7 only");
+    if (src && c->N > esdc::kMaxN) return fail(ESDC_ERR_UNSUPPORTED, "source terms are added for p <= 7 only");
     if (src && !aligned(src, 16)) return fail(ESDC_ERR_ARG, "source must be 16-byte aligned");
     c->d_src = src;
     return prepare_variant(c);

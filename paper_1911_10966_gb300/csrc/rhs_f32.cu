@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "esdc_internal.h"
+#include "fpconv.cuh"
 #include "kernels.h"
 #include "visc_sat.cuh"
 
@@ -57,6 +58,7 @@ struct Ref {
     float c5;        // RT0 / (gamma - 1)
     float inv_rho0;
     float two_beta0; // rho0 / p0
+    double rho0d, E0d;   // the reference density and energy in float64 (exterior states)
 };
 
 // approximate reciprocal and square root (about 1 ulp): the float32 residual's rounding is
@@ -185,11 +187,14 @@ __device__ __forceinline__ float stage_value(const StageF& in, int64_t i) {
     return a;
 }
 
-template <int N, int NK>
+// XF: boundary faces (bounded boxes) and a source term, compiled only into the instantiations that
+// need them (a run-time test for them cost 2% on periodic boxes)
+template <int N, int NK, bool XF>
 __global__ void __launch_bounds__(CfgF<N>::THREADS, CfgF<N>::MINB)
 rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom,
              const int32_t* __restrict__ nbr, float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph,
-             const Ref ref, const float* __restrict__ nsurf) {
+             const Ref ref, const float* __restrict__ nsurf, const double* __restrict__ qext,
+             const double* __restrict__ src) {
     using C = CfgF<N>;
     constexpr int N2 = C::N2, N3 = C::N3, TE = C::TE;
     extern __shared__ float smf[];
@@ -292,8 +297,18 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             const int nbn = base + (side ? 0 : (N - 1) * st);
             const int64_t nb = nbr[el * 6 + 2 * l + side];
             float qn[5];
+            if (!XF || nb >= 0) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) qn[v] = stage_value<NK>(in, nb * 5 * N3 + v * N3 + nbn);
+                for (int v = 0; v < 5; ++v) qn[v] = stage_value<NK>(in, nb * 5 * N3 + v * N3 + nbn);
+            } else {
+                // boundary face of a bounded box: the float64 exterior state at the own nodes, less
+                // the reference state, rounded once
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    const double x = qext[eoff + v * N3 + own];
+                    qn[v] = d2f_int(v == 0 ? x - ref.rho0d : (v == 4 ? x - ref.E0d : x));
+                }
+            }
             PrimF so, sn;
             load_prim_f(sP4, N3, own, so);
             to_prim_f(qn, ref, sn);
@@ -452,10 +467,16 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                 const float Jinv = sG4[node].w;
                 const float* sum = sA + 12 * N3 + node;
                 const float lin = sum[5 * N3];
-                out[eoff + node] = (sum[0] + ref.rho0 * lin) * Jinv;
+                float sv[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                if (XF && src) {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) out[eoff + (1 + k) * N3 + node] = (sum[(1 + k) * N3] + vs[k]) * Jinv;
-                out[eoff + 4 * N3 + node] = (sum[4 * N3] + ref.H0 * lin + vs[3]) * Jinv;
+                    for (int v = 0; v < 5; ++v) sv[v] = d2f_int(src[eoff + v * N3 + node]);
+                }
+                out[eoff + node] = (sum[0] + ref.rho0 * lin) * Jinv + sv[0];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    out[eoff + (1 + k) * N3 + node] = (sum[(1 + k) * N3] + vs[k]) * Jinv + sv[1 + k];
+                out[eoff + 4 * N3 + node] = (sum[4 * N3] + ref.H0 * lin + vs[3]) * Jinv + sv[4];
             }
         }
     } else if (active) {
@@ -464,10 +485,15 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
 #pragma unroll
             for (int v = 0; v < 6; ++v) a[v] = sA[v * N3 + node] + (sA[(6 + v) * N3 + node] + sA[(12 + v) * N3 + node]);
             const float Jinv = sG4[node].w;
-            out[eoff + node] = (a[0] + ref.rho0 * a[5]) * Jinv;
+            float sv[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (XF && src) {
 #pragma unroll
-            for (int k = 1; k < 4; ++k) out[eoff + k * N3 + node] = a[k] * Jinv;
-            out[eoff + 4 * N3 + node] = (a[4] + ref.H0 * a[5]) * Jinv;
+                for (int v = 0; v < 5; ++v) sv[v] = d2f_int(src[eoff + v * N3 + node]);
+            }
+            out[eoff + node] = (a[0] + ref.rho0 * a[5]) * Jinv + sv[0];
+#pragma unroll
+            for (int k = 1; k < 4; ++k) out[eoff + k * N3 + node] = a[k] * Jinv + sv[k];
+            out[eoff + 4 * N3 + node] = (a[4] + ref.H0 * a[5]) * Jinv + sv[4];
         }
     }
 }
@@ -490,17 +516,21 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaSt
     ref.c5 = ref.RT0 * ph.inv_gm1;
     ref.inv_rho0 = 1.0f / ph.rho0;
     ref.two_beta0 = ph.rho0 / ph.p0;
+    ref.rho0d = 1.0;                                      // the float64 reference of the shadow state
+    ref.E0d = c->phys.R / (c->phys.gamma - 1.0);
     if (in.nk < 0 || in.nk > 5) return cudaErrorInvalidValue;
     if (ev) cudaEventRecord(ev[0], s);
+    const bool xf = c->setup.bounded != 0 || c->d_src != nullptr;
+    auto go = [&](auto kern) {
+        kern<<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf, ph, ref,
+                                            c->d_nsurff, c->d_qext, c->d_src);
+    };
     if (in.nk == 0)
-        rhs_main_f32<N, 0><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K,
-                                                          c->opsf, ph, ref, c->d_nsurff);
+        xf ? go(rhs_main_f32<N, 0, true>) : go(rhs_main_f32<N, 0, false>);
     else if (in.nk <= 2)
-        rhs_main_f32<N, 2><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K,
-                                                          c->opsf, ph, ref, c->d_nsurff);
+        xf ? go(rhs_main_f32<N, 2, true>) : go(rhs_main_f32<N, 2, false>);
     else
-        rhs_main_f32<N, 5><<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K,
-                                                          c->opsf, ph, ref, c->d_nsurff);
+        xf ? go(rhs_main_f32<N, 5, true>) : go(rhs_main_f32<N, 5, false>);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (ph.viscous) {
@@ -517,9 +547,12 @@ cudaError_t prepare_f32_n() {
     using C = CfgF<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(float);
     constexpr cudaFuncAttribute kAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(rhs_main_f32<N, 0>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5>, kAttr, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(rhs_main_f32<N, 0, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 0, true>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, true>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, true>, kAttr, (int)smem);
     return e;
 }
 
