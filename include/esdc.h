@@ -230,7 +230,8 @@ int esdc_rhs_host(esdc_ctx* ctx, const double* q_host, void* dqdt_host, void* st
  * esdc_workspace_bytes -- device workspace needed by esdc_rk_step (what = 0): for ESDC_PREC_FP64
  * six stage derivatives and one stage state, each K*5*N^3 float64; for ESDC_PREC_FP32 six float32
  * stage derivatives and one float32 perturbation state (each sub-buffer 256-byte aligned).
- * what = 1: esdc_rk_adaptive's workspace, nine K*5*N^3 float64 buffers.
+ * what = 1: esdc_rk_adaptive's workspace: for ESDC_PREC_FP64 nine K*5*N^3 float64 buffers; for
+ * ESDC_PREC_FP32 nine K*5*N^3 float32 buffers and one float64 buffer.
  */
 int esdc_workspace_bytes(const esdc_ctx* ctx, int what, size_t* bytes);
 
@@ -254,8 +255,11 @@ int esdc_workspace_bytes(const esdc_ctx* ctx, int what, size_t* bytes);
  * esdc_workspace_bytes(ctx, 1) bytes, 256-byte aligned.  stats_host[4] (nullable): accepted steps,
  * rejected steps, residual evaluations, time reached.  dt_history_host (nullable): the first
  * history_capacity accepted step sizes.  The accept/reject decision runs on the host: the call
- * synchronises stream once per attempted step.  ESDC_PREC_FP64 contexts only
- * (ESDC_ERR_UNSUPPORTED otherwise).
+ * synchronises stream once per attempted step.  Float64 and float32-mixed contexts: in the latter
+ * the seven stage derivatives are float32 residuals of float32 perturbation stage states, and the
+ * candidate solution, the error estimate and the controller are float64 (tolerances well above
+ * float32 rounding of the residual, ~1e-6 relative, are meaningful).  A bounded box without an
+ * exterior state fails with ESDC_ERR_ARG.
  */
 int esdc_rk_adaptive(esdc_ctx* ctx, double* q_dev, double t0, double t_end, double* dt_inout, double rtol,
                      double atol, int max_steps, void* workspace_dev, size_t workspace_bytes, double* stats_host,

@@ -355,6 +355,105 @@ int rk_adaptive_f64(esdc_ctx* c, double* q, double t0, double t_end, double* dt_
     return ESDC_OK;
 }
 
+// Adaptive DP5(4) on a float32-mixed context: the same controller as rk_adaptive_f64; the stage
+// derivatives are float32 residuals of float32 perturbation stage states formed on load from the
+// step's shadow state, the candidate solution q + h sum_j b_j k_j and the error estimate are float64.
+// Workspace: 7 float32 stage derivatives, the shadows of q and of the candidate, the float64
+// candidate.
+int rk_adaptive_f32(esdc_ctx* c, double* q, double t0, double t_end, double* dt_io, double rtol, double atol,
+                    int max_steps, void* ws, double* stats, double* hist, int hist_cap, cudaStream_t s) {
+    const int64_t n = c->n_nodes * 5;
+    const size_t sub = round256((size_t)n * sizeof(float));
+    float* k[7];
+    for (int j = 0; j < 7; ++j) k[j] = (float*)((char*)ws + j * sub);
+    float* base = (float*)((char*)ws + 7 * sub);
+    float* base_n = (float*)((char*)ws + 8 * sub);
+    double* qn = (double*)((char*)ws + 9 * sub);
+    double t = t0, dt = *dt_io;
+    int acc = 0, rej = 0;
+    int64_t nrhs = 0;
+    double err_prev = -1.0, h_prev = -1.0;
+    cudaError_t e;
+    if (t < t_end) {
+        e = esdc::launch_shadow(c, q, base, s);
+        if (e != cudaSuccess) return cuda_fail(e, "shadow");
+        esdc::StageF in{};
+        in.base = base;
+        e = esdc::launch_rhs_f32(c, in, k[0], s, next_events(c));
+        if (e != cudaSuccess) return cuda_fail(e, "residual (float32)");
+        ++nrhs;
+    }
+    while (t < t_end && acc + rej < max_steps) {
+        const bool last = t + dt >= t_end;
+        const double h = last ? t_end - t : dt;
+        for (int st = 1; st < 6; ++st) {
+            esdc::StageF in{};
+            in.base = base;
+            for (int j = 0; j < st; ++j) {
+                if (kA[st][j] == 0.0) continue;
+                in.k[in.nk] = k[j];
+                in.c[in.nk] = (float)(h * kA[st][j]);
+                ++in.nk;
+            }
+            e = esdc::launch_rhs_f32(c, in, k[st], s, next_events(c));
+            if (e != cudaSuccess) return cuda_fail(e, "residual (float32)");
+        }
+        // candidate: qn = q + h sum_j b_j k_j in float64, and its shadow
+        CUDA_TRY(cudaMemcpyAsync(qn, q, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        esdc::Combine64F cb{};
+        for (int j = 0; j < 6; ++j)
+            if (kB[j] != 0.0) {
+                cb.k[cb.nk] = k[j];
+                cb.coef[cb.nk] = h * kB[j];
+                ++cb.nk;
+            }
+        e = esdc::launch_final_f32(c, qn, base_n, cb, s);
+        if (e != cudaSuccess) return cuda_fail(e, "candidate solution");
+        esdc::StageF in{};
+        in.base = base_n;
+        e = esdc::launch_rhs_f32(c, in, k[6], s, next_events(c));
+        if (e != cudaSuccess) return cuda_fail(e, "residual (float32)");
+        nrhs += 6;
+        esdc::LinCombF lc{};
+        for (int j = 0; j < 7; ++j) {
+            const double d = (j < 6 ? kB[j] : 0.0) - kBhat[j];
+            if (d != 0.0) {
+                lc.x[lc.n] = k[j];
+                lc.c[lc.n++] = h * d;
+            }
+        }
+        e = esdc::launch_dp54_error_f32(c, q, qn, lc, rtol, atol, s);
+        if (e != cudaSuccess) return cuda_fail(e, "error estimate");
+        double sum = 0.0;
+        CUDA_TRY(cudaMemcpyAsync(&sum, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        const double err = std::sqrt(sum / (double)n);
+        if (err <= 1.0) {
+            const double rho = h211b_ratio(err, err_prev < 0.0 ? err : err_prev, h_prev < 0.0 ? 1.0 : h / h_prev);
+            CUDA_TRY(cudaMemcpyAsync(q, qn, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            std::swap(k[0], k[6]);          // first same as last
+            std::swap(base, base_n);        // the candidate's shadow is the next step's base
+            t = last ? t_end : t + h;
+            if (hist && acc < hist_cap) hist[acc] = h;
+            ++acc;
+            err_prev = err;
+            h_prev = h;
+            dt = h * step_limiter(rho);
+        } else {
+            ++rej;
+            dt = h * step_limiter(std::isfinite(err) ? std::pow(kCtrlTheta / err, 1.0 / kCtrlK) : 0.0);
+        }
+    }
+    *dt_io = dt;
+    if (stats) {
+        stats[0] = acc;
+        stats[1] = rej;
+        stats[2] = (double)nrhs;
+        stats[3] = t;
+    }
+    return ESDC_OK;
+}
+
 // The element kernel instantiation depends on the optional face terms; opt the one in use into its
 // shared-memory size.
 int prepare_variant(esdc_ctx* c) {
@@ -819,7 +918,9 @@ int esdc_rhs_host(esdc_ctx* c, const double* q_host, void* dqdt_host, void* stre
 int esdc_workspace_bytes(const esdc_ctx* c, int what, size_t* bytes) {
     if (!c || !bytes) return fail(ESDC_ERR_ARG, "null argument");
     if (what != 0 && what != 1) return fail(ESDC_ERR_ARG, "unknown workspace kind");
-    if (what == 1) *bytes = 9 * round256((size_t)c->n_nodes * 5 * sizeof(double));
+    if (what == 1 && c->setup.precision == ESDC_PREC_FP32)
+        *bytes = 9 * round256((size_t)c->n_nodes * 5 * sizeof(float)) + round256((size_t)c->n_nodes * 5 * sizeof(double));
+    else if (what == 1) *bytes = 9 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     else if (c->setup.precision == ESDC_PREC_FP64) *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     else *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(float));
     return ESDC_OK;
@@ -944,8 +1045,6 @@ int esdc_rk_adaptive(esdc_ctx* c, double* q, double t0, double t_end, double* dt
                      int max_steps, void* ws, size_t ws_bytes, double* stats, double* dt_history, int history_capacity,
                      void* stream) {
     if (!c || !q || !ws || !dt_inout) return fail(ESDC_ERR_ARG, "null argument");
-    if (c->setup.precision != ESDC_PREC_FP64)
-        return fail(ESDC_ERR_UNSUPPORTED, "adaptive stepping needs a float64 context");
     if (!std::isfinite(t0) || !std::isfinite(t_end) || t_end < t0 || !(*dt_inout > 0.0) ||
         !std::isfinite(*dt_inout) || !(rtol > 0.0) || !(atol > 0.0) || max_steps < 0 || history_capacity < 0)
         return fail(ESDC_ERR_ARG, "need t0 <= t_end, dt > 0, rtol > 0, atol > 0, max_steps >= 0");
@@ -954,6 +1053,11 @@ int esdc_rk_adaptive(esdc_ctx* c, double* q, double t0, double t_end, double* dt
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "workspace too small");
     if (!aligned(ws, 256) || !aligned(q, 16))
         return fail(ESDC_ERR_ARG, "q must be 16-byte and workspace 256-byte aligned");
+    if (c->setup.bounded != 0 && !c->d_qext)
+        return fail(ESDC_ERR_ARG, "a bounded box needs an exterior state (esdc_set_exterior)");
+    if (c->setup.precision == ESDC_PREC_FP32)
+        return rk_adaptive_f32(c, q, t0, t_end, dt_inout, rtol, atol, max_steps, ws, stats, dt_history,
+                               history_capacity, (cudaStream_t)stream);
     return rk_adaptive_f64(c, q, t0, t_end, dt_inout, rtol, atol, max_steps, ws, stats, dt_history, history_capacity,
                            (cudaStream_t)stream);
 }

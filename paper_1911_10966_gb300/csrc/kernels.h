@@ -43,6 +43,14 @@ cudaError_t launch_lincomb(double* out, const LinComb& lc, int64_t n, cudaStream
 // (5 to 7 terms)
 cudaError_t launch_dp54_error(const esdc_ctx* c, const double* q0, const double* q1, const LinComb& lc, double rtol,
                               double atol, cudaStream_t s);
+// the same with float32 stage derivatives (the float32-mixed form)
+struct LinCombF {
+    const float* x[7];
+    double c[7];
+    int n;
+};
+cudaError_t launch_dp54_error_f32(const esdc_ctx* c, const double* q0, const double* q1, const LinCombF& lc,
+                                  double rtol, double atol, cudaStream_t s);
 
 // Reductions: budgets (4 sums + non-physical count) and CFL inputs (max |u|+c, min rho).
 // Table of the budgets' logarithm: entry k (0 <= k < kLnTab) holds T_k = 1/c_k rounded to double,

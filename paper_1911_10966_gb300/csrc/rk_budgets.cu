@@ -194,9 +194,9 @@ __global__ void __launch_bounds__(kRedThreads) budgets_kernel(const double* __re
 // e = sum_j d_j k_j (d_j = dt (b_j - bhat_j), NT nonzero terms), sc = atol + rtol max(|q0|, |q1|),
 // and the block sums of (e/sc)^2 (the weighted RMS norm of Hairer, Norsett & Wanner, eq. II.4.11,
 // before the mean and square root).
-template <int NT>
+template <int NT, typename LC>
 __global__ void __launch_bounds__(kRedThreads) dp54_err_kernel(const double* __restrict__ q0,
-                                                               const double* __restrict__ q1, const LinComb lc,
+                                                               const double* __restrict__ q1, const LC lc,
                                                                double rtol, double atol, int64_t n,
                                                                double* __restrict__ part) {
     __shared__ double sh[kRedThreads];
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kRedThreads) dp54_err_kernel(const double* __r
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double kv[NT];
 #pragma unroll
-        for (int j = 0; j < NT; ++j) kv[j] = lc.x[j][i];
+        for (int j = 0; j < NT; ++j) kv[j] = (double)lc.x[j][i];
         const double a = q0[i], b = q1[i];
         double e = lc.c[0] * kv[0];
 #pragma unroll
@@ -391,17 +391,28 @@ cudaError_t launch_lincomb(double* out, const LinComb& lc, int64_t n, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_dp54_error(const esdc_ctx* c, const double* q0, const double* q1, const LinComb& lc, double rtol,
-                              double atol, cudaStream_t s) {
+template <typename LC>
+cudaError_t dp54_error_any(const esdc_ctx* c, const double* q0, const double* q1, const LC& lc, double rtol,
+                           double atol, cudaStream_t s) {
     const int64_t n = c->n_nodes * 5;
     switch (lc.n) {
-        case 5: dp54_err_kernel<5><<<c->red_blocks, kRedThreads, 0, s>>>(q0, q1, lc, rtol, atol, n, c->d_red); break;
-        case 6: dp54_err_kernel<6><<<c->red_blocks, kRedThreads, 0, s>>>(q0, q1, lc, rtol, atol, n, c->d_red); break;
-        case 7: dp54_err_kernel<7><<<c->red_blocks, kRedThreads, 0, s>>>(q0, q1, lc, rtol, atol, n, c->d_red); break;
+        case 5: dp54_err_kernel<5, LC><<<c->red_blocks, kRedThreads, 0, s>>>(q0, q1, lc, rtol, atol, n, c->d_red); break;
+        case 6: dp54_err_kernel<6, LC><<<c->red_blocks, kRedThreads, 0, s>>>(q0, q1, lc, rtol, atol, n, c->d_red); break;
+        case 7: dp54_err_kernel<7, LC><<<c->red_blocks, kRedThreads, 0, s>>>(q0, q1, lc, rtol, atol, n, c->d_red); break;
         default: return cudaErrorInvalidValue;
     }
     finish_sum<<<1, kRedThreads, 0, s>>>(c->d_red, c->red_blocks, 1, c->d_red_out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_dp54_error(const esdc_ctx* c, const double* q0, const double* q1, const LinComb& lc, double rtol,
+                              double atol, cudaStream_t s) {
+    return dp54_error_any(c, q0, q1, lc, rtol, atol, s);
+}
+
+cudaError_t launch_dp54_error_f32(const esdc_ctx* c, const double* q0, const double* q1, const LinCombF& lc,
+                                  double rtol, double atol, cudaStream_t s) {
+    return dp54_error_any(c, q0, q1, lc, rtol, atol, s);
 }
 
 cudaError_t launch_budgets(const esdc_ctx* c, const double* q, const void* dqdt, int dq_f32, double* out,

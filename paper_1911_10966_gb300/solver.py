@@ -267,7 +267,7 @@ class Solver:
         return g
 
     def rk_adaptive(self, q, t0, t_end, dt0, rtol=1e-6, atol=1e-6, max_steps=100000, history=0):
-        """Advance q in place from t0 to t_end with adaptive DP5(4) (float64 contexts).  Returns a
+        """Advance q in place from t0 to t_end with adaptive DP5(4) (float64 or float32-mixed).  Returns a
         dict: accepted, rejected, rhs (residual evaluations), t (time reached), dt_next and, if
         history > 0, dt_history (the first `history` accepted step sizes)."""
         self._check_state(q)
