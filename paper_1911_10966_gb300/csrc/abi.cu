@@ -584,8 +584,8 @@ static int check_setup(const esdc_setup_t& s) {
         return fail(ESDC_ERR_ARG, "precision must be ESDC_PREC_FP64 or ESDC_PREC_FP32");
     if (s.volume_flux != ESDC_FLUX_ESC && s.volume_flux != ESDC_FLUX_KG && s.volume_flux != ESDC_FLUX_DC)
         return fail(ESDC_ERR_ARG, "volume_flux must be ESDC_FLUX_ESC, ESDC_FLUX_KG or ESDC_FLUX_DC");
-    if (s.volume_flux != ESDC_FLUX_ESC && s.precision != ESDC_PREC_FP64)
-        return fail(ESDC_ERR_UNSUPPORTED, "the KG and DC volume fluxes are built for float64 only");
+    if (s.volume_flux == ESDC_FLUX_DC && s.precision != ESDC_PREC_FP64)
+        return fail(ESDC_ERR_UNSUPPORTED, "the DC volume flux is built for float64 only");
     if (s.metrics != ESDC_METRICS_CURL && s.metrics != ESDC_METRICS_OPTIMIZED)
         return fail(ESDC_ERR_ARG, "metrics must be ESDC_METRICS_CURL or ESDC_METRICS_OPTIMIZED");
     if (s.p == esdc::kLargeN - 1 &&

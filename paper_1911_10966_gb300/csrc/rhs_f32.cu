@@ -27,7 +27,7 @@
 namespace esdc {
 namespace {
 
-template <int N>
+template <int N, bool KG = false>
 struct CfgF {
     static constexpr int N2 = N * N, N3 = N * N * N;
     static constexpr int LINES = 3 * N2;                       // all three directions at once
@@ -38,7 +38,10 @@ struct CfgF {
     static constexpr int THREADS = EPB * TE;
     // shared floats per element: prim 2 x float4 | w float4 | geometry 3 x float4 | accumulators 3 x 6
     // (aliased by the 3 x float4 viscous fluxes) | own dq 5 | face w 24 N^2 (rounded to whole float4)
-    static constexpr int SM = ((8 + 4 + 12 + 18 + 5) * N3 + 24 * N2 + 3) / 4 * 4;
+    // (+ 2 N3 for the Kennedy-Gruber pair quantities, half the pressure perturbation and eh, as
+    // float2 from an even offset)
+    static constexpr int KG_OFF = (8 + 4 + 12 + 18 + 5) * N3 + 24 * N2;
+    static constexpr int SM = (KG_OFF + (KG ? (KG_OFF & 1) + 2 * N3 : 0) + 3) / 4 * 4;
     // resident CTAs the registers are sized for (N = 5: one element of 125 threads per CTA, six CTAs
     // per SM measured 10% faster than three CTAs of two elements)
     static constexpr int MINB = N <= 4 ? 4 : (N == 5 ? 6 : 2);
@@ -49,6 +52,7 @@ struct CfgF {
 // beta = rho/(2p) relative to beta0, dbn = beta/beta0 - 1 (so that the reference values are 1).
 struct PrimF {
     float hdr, hu0, hu1, hu2, dbn, u0, u1, u2;
+    float hdp, eh;   // SF-KG: half the pressure perturbation, (RT - RT0)/(2(gamma-1)) + |u|^2/4
 };
 
 struct Ref {
@@ -59,6 +63,8 @@ struct Ref {
     float inv_rho0;
     float two_beta0; // rho0 / p0
     double rho0d, E0d;   // the reference density and energy in float64 (exterior states)
+    float e0;            // RT0 / (gamma - 1)
+    float inv_2gm1;      // 1 / (2 (gamma - 1))
 };
 
 // approximate reciprocal and square root (about 1 ulp): the float32 residual's rounding is
@@ -85,6 +91,8 @@ __device__ __forceinline__ void to_prim_f(const float dq[5], const Ref& r, PrimF
     const float usq = s.u0 * s.u0 + s.u1 * s.u1 + s.u2 * s.u2;
     const float dp = r.gm1 * (dq[4] - 0.5f * rho * usq);
     s.dbn = (dq[0] * r.p0 - r.rho0 * dp) * frcp(r.p0 + dp) * r.inv_rho0;
+    s.hdp = 0.5f * dp;
+    s.eh = (r.rho0 * dp - r.p0 * dq[0]) * ri * r.inv_rho0 * r.inv_2gm1 + 0.25f * usq;   // RT - RT0 = (rho0 dp - p0 drho)/(rho rho0)
     s.hdr = 0.5f * dq[0];
     s.hu0 = 0.5f * s.u0;
     s.hu1 = 0.5f * s.u1;
@@ -140,6 +148,26 @@ __device__ __forceinline__ void ec_flux_pert(const PrimF& a, const PrimF& b, flo
     df[4] = fmaf(r.c5 * un, fmaf(dIn, rr, drl), fmaf(f1, hab, dpt * un));
 }
 
+// Kennedy-Gruber two-point flux (the SF-KG variant, Sec. 4) split as above: with arithmetic means
+// rho_bar = rho0 + dbar, u_bar, p_bar = p0 + dp_bar and e_bar = e0 + de (e = RT/(gamma-1) + |u|^2/2,
+// de = eh_a + eh_b), f = f_ref + df with df1 = dbar ubar.n, df_m = f1 ubar_m + dp_bar n_m and
+// df5 = ubar.n (rho0 de + dbar (e0 + de) + dp_bar); the reference part f_ref is that of the ES-C
+// split (rho0 e0 + p0 = gamma p0/(gamma-1)).
+__device__ __forceinline__ void kg_flux_pert(const PrimF& a, const PrimF& b, float n0, float n1, float n2,
+                                             const Ref& r, float df[5], float& un) {
+    const float dbar = a.hdr + b.hdr;
+    const float ub0 = a.hu0 + b.hu0, ub1 = a.hu1 + b.hu1, ub2 = a.hu2 + b.hu2;
+    un = ub0 * n0 + ub1 * n1 + ub2 * n2;
+    const float dpb = a.hdp + b.hdp;
+    const float de = a.eh + b.eh;
+    const float f1 = (r.rho0 + dbar) * un;
+    df[0] = dbar * un;
+    df[1] = f1 * ub0 + dpb * n0;
+    df[2] = f1 * ub1 + dpb * n1;
+    df[3] = f1 * ub2 + dpb * n2;
+    df[4] = un * (r.rho0 * de + dbar * (r.e0 + de) + dpb);
+}
+
 template <int N>
 __device__ __forceinline__ int line_base_f(int l, int t1, int t2) {
     return l == 0 ? (t1 * N + t2 * N * N) : (l == 1 ? (t1 + t2 * N * N) : (t1 + t2 * N));
@@ -189,13 +217,13 @@ __device__ __forceinline__ float stage_value(const StageF& in, int64_t i) {
 
 // XF: boundary faces (bounded boxes) and a source term, compiled only into the instantiations that
 // need them (a run-time test for them cost 2% on periodic boxes)
-template <int N, int NK, bool XF>
+template <int N, int NK, bool XF, bool KG>
 __global__ void __launch_bounds__(CfgF<N>::THREADS, CfgF<N>::MINB)
 rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom,
              const int32_t* __restrict__ nbr, float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph,
              const Ref ref, const float* __restrict__ nsurf, const double* __restrict__ qext,
              const double* __restrict__ src) {
-    using C = CfgF<N>;
+    using C = CfgF<N, KG>;
     constexpr int N2 = C::N2, N3 = C::N3, TE = C::TE;
     extern __shared__ float smf[];
     const int t = threadIdx.x;
@@ -211,6 +239,7 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
     float4* sF4 = reinterpret_cast<float4*>(sA);
     float* sQ = sA + 18 * N3;                        // [5][N3] own dq
     float* sWf = sQ + 5 * N3;                        // [6][4][N2] neighbour entropy variables
+    float2* sK2 = reinterpret_cast<float2*>(sP + C::KG_OFF + (C::KG_OFF & 1));   // [N3] (hdp, eh), SF-KG only
     const int64_t eoff = el * 5 * N3;
 
     if (active) {
@@ -225,6 +254,7 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             to_prim_f(d, ref, s);
             sP4[node] = make_float4(s.hdr, s.hu0, s.hu1, s.hu2);
             sP4[N3 + node] = make_float4(s.dbn, s.u0, s.u1, s.u2);
+            if constexpr (KG) sK2[node] = make_float2(s.hdp, s.eh);
             // w5 - w5_ref = -2 (beta - beta0): the constant has no gradient
             const float tb = two_beta(s, ref);
             sW4[node] = make_float4(tb * s.u0, tb * s.u1, tb * s.u2, -ref.two_beta0 * s.dbn);
@@ -254,6 +284,11 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             const int ii = base + i * st;
             PrimF si;
             load_prim_f(sP4, N3, ii, si);
+            if constexpr (KG) {
+                const float2 k2 = sK2[ii];
+                si.hdp = k2.x;
+                si.eh = k2.y;
+            }
             const float4 ni = nl[ii];
 #pragma unroll
             for (int j = i + 1; j < N; ++j) {
@@ -263,7 +298,14 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                 const float4 nj = nl[jj];
                 float df[5], un;
                 // the flux is linear in n: pass n_i + n_j and take S (half of 2S) as the pair coefficient
-                ec_flux_pert(si, sj, ni.x + nj.x, ni.y + nj.y, ni.z + nj.z, ref, df, un);
+                if constexpr (KG) {
+                    const float2 k2 = sK2[jj];
+                    sj.hdp = k2.x;
+                    sj.eh = k2.y;
+                    kg_flux_pert(si, sj, ni.x + nj.x, ni.y + nj.y, ni.z + nj.z, ref, df, un);
+                } else {
+                    ec_flux_pert(si, sj, ni.x + nj.x, ni.y + nj.y, ni.z + nj.z, ref, df, un);
+                }
                 const float c = ops.S[i][j];
 #pragma unroll
                 for (int v = 0; v < 5; ++v) {
@@ -311,6 +353,11 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             }
             PrimF so, sn;
             load_prim_f(sP4, N3, own, so);
+            if constexpr (KG) {
+                const float2 k2 = sK2[own];
+                so.hdp = k2.x;
+                so.eh = k2.y;
+            }
             to_prim_f(qn, ref, sn);
             const float4 nv = sG4[l * N3 + own];
             float n0 = nv.x, n1 = nv.y, n2 = nv.z;
@@ -321,7 +368,8 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
                 n2 = ns[2 * N2];
             }
             float df[5], un;
-            ec_flux_pert(so, sn, n0, n1, n2, ref, df, un);
+            if constexpr (KG) kg_flux_pert(so, sn, n0, n1, n2, ref, df, un);
+            else ec_flux_pert(so, sn, n0, n1, n2, ref, df, un);
             const float E = side ? 1.0f : -1.0f;
             float lam = 0.0f;
             if (ph.dissipation) {
@@ -518,19 +566,31 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaSt
     ref.two_beta0 = ph.rho0 / ph.p0;
     ref.rho0d = 1.0;                                      // the float64 reference of the shadow state
     ref.E0d = c->phys.R / (c->phys.gamma - 1.0);
+    ref.e0 = ref.RT0 * ph.inv_gm1;
+    ref.inv_2gm1 = 0.5f * ph.inv_gm1;
     if (in.nk < 0 || in.nk > 5) return cudaErrorInvalidValue;
     if (ev) cudaEventRecord(ev[0], s);
     const bool xf = c->setup.bounded != 0 || c->d_src != nullptr;
-    auto go = [&](auto kern) {
-        kern<<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf, ph, ref,
-                                            c->d_nsurff, c->d_qext, c->d_src);
+    const bool kg = c->setup.volume_flux == ESDC_FLUX_KG;
+    auto go = [&](auto kern, size_t bytes) {
+        kern<<<grid, C::THREADS, bytes, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf, ph,
+                                             ref, c->d_nsurff, c->d_qext, c->d_src);
     };
-    if (in.nk == 0)
-        xf ? go(rhs_main_f32<N, 0, true>) : go(rhs_main_f32<N, 0, false>);
-    else if (in.nk <= 2)
-        xf ? go(rhs_main_f32<N, 2, true>) : go(rhs_main_f32<N, 2, false>);
-    else
-        xf ? go(rhs_main_f32<N, 5, true>) : go(rhs_main_f32<N, 5, false>);
+    const size_t smem_kg = (size_t)C::EPB * CfgF<N, true>::SM * sizeof(float);
+    if (kg) {
+        if (in.nk == 0)
+            xf ? go(rhs_main_f32<N, 0, true, true>, smem_kg) : go(rhs_main_f32<N, 0, false, true>, smem_kg);
+        else if (in.nk <= 2)
+            xf ? go(rhs_main_f32<N, 2, true, true>, smem_kg) : go(rhs_main_f32<N, 2, false, true>, smem_kg);
+        else
+            xf ? go(rhs_main_f32<N, 5, true, true>, smem_kg) : go(rhs_main_f32<N, 5, false, true>, smem_kg);
+    } else if (in.nk == 0) {
+        xf ? go(rhs_main_f32<N, 0, true, false>, smem) : go(rhs_main_f32<N, 0, false, false>, smem);
+    } else if (in.nk <= 2) {
+        xf ? go(rhs_main_f32<N, 2, true, false>, smem) : go(rhs_main_f32<N, 2, false, false>, smem);
+    } else {
+        xf ? go(rhs_main_f32<N, 5, true, false>, smem) : go(rhs_main_f32<N, 5, false, false>, smem);
+    }
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (ph.viscous) {
@@ -547,12 +607,19 @@ cudaError_t prepare_f32_n() {
     using C = CfgF<N>;
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(float);
     constexpr cudaFuncAttribute kAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(rhs_main_f32<N, 0, false>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, false>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, false>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 0, true>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, true>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, true>, kAttr, (int)smem);
+    const int sk = (int)((size_t)C::EPB * CfgF<N, true>::SM * sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(rhs_main_f32<N, 0, false, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, false, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, false, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 0, true, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, true, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, true, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 0, false, true>, kAttr, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, false, true>, kAttr, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, false, true>, kAttr, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 0, true, true>, kAttr, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, true, true>, kAttr, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, true, true>, kAttr, sk);
     return e;
 }
 

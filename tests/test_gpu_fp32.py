@@ -181,3 +181,25 @@ def test_fp32_bounded_box_with_exterior_state_and_source(p, k, Re, diss):
     e = normwise_errors(q32 - q0, (q64 - q0).cpu())
     print("fp32 vs fp64 increments after 10 DP5 steps", ["%.1e" % x for x in e])
     assert max(e) <= 1e-4, e
+
+
+@pytest.mark.parametrize("p", [1, 3, 4, 7])
+def test_fp32_kennedy_gruber_variant(p):
+    """The SF-KG volume flux in the float32-mixed form (split about the same reference state) against
+    the oracle's "kg" scheme under the same conditioning-normalised bound, and five DP5 steps against
+    the float64 SF-KG solver's."""
+    from paper_1911_10966_gb300.solver import Solver
+    solver, qg, mesh, gas, qo = make_pair(p, (3, 2, 2), warp=0.1, seed=2, Re=400.0, noise=0.05, precision="fp32",
+                                          volume_flux="kg")
+    e, c = _report(solver.rhs(qg), O.rhs(qo, mesh, gas, scheme="kg"), qo, mesh, gas)
+    assert max(c) <= C_MAX
+    assert max(e) <= 1e-5
+    s64 = Solver(p, 3, 2, 2, solver.coords, Re=400.0, volume_flux="kg")
+    q64 = qg.clone()
+    dt = 0.5 * s64.dt_cfl(q64, 0.5)
+    q0 = qg.clone()
+    s64.rk_step(q64, dt, 5)
+    solver.rk_step(qg, dt, 5)
+    e = normwise_errors(qg - q0, (q64 - q0).cpu())
+    print("fp32 vs fp64 SF-KG increments after 5 DP5 steps", ["%.1e" % x for x in e])
+    assert max(e) <= 1e-4, e

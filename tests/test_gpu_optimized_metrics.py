@@ -73,7 +73,7 @@ def test_optimized_metrics_unsupported():
     from paper_1911_10966_gb300.solver import Solver
     solver, qg, mesh, gas, qo = make_pair(2, (2, 2, 2), warp=0.1, Re=100.0, metrics="optimized")
     with pytest.raises(nat.EsdcError) as ei:
-        Solver(2, 2, 2, 2, solver.coords, Re=100.0, precision="fp32", metrics="optimized", volume_flux="kg")
+        Solver(2, 2, 2, 2, solver.coords, Re=100.0, precision="fp32", metrics="optimized", volume_flux="dc")
     assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
     with pytest.raises(ValueError):
         Solver(2, 2, 2, 2, solver.coords, metrics="exact")
