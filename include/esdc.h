@@ -45,8 +45,8 @@ extern "C" {
  * (Chandrashekar two-point flux, eq. discEL).  ESDC_FLUX_KG: the same Hadamard flux differencing with
  * the Kennedy-Gruber two-point flux (the paper's SF-KG).  ESDC_FLUX_DC: standard collocation, D
  * applied to the nodal contravariant Euler fluxes (the paper's DC), with the central interface flux.
- * All three use the same interface dissipation, viscous terms and metrics; KG and DC are float64
- * only; all three have an adjoint. */
+ * All three use the same interface dissipation, viscous terms and metrics; ESC and KG also run in
+ * the float32-mixed form, DC is float64 only (ESDC_ERR_UNSUPPORTED); all three have an adjoint. */
 /* Interface dissipation of SAT^(I) (the paper defers the SAT to its references).  ESDC_DISS_NONE:
  * entropy conservative.  ESDC_DISS_LLF: local Lax-Friedrichs, lambda/2 (q_own - q_nbr) with
  * lambda = max over both sides of |u.n_J| + c |n_J|.  ESDC_DISS_MATRIX: Roe-type entropy-stable
