@@ -113,7 +113,7 @@ typedef struct esdc_setup {
 /* Degree p = 15 (the top degree of the paper's cost comparison, Sec. 5.2): the float64 residual is
  * built in several passes instead of one CTA per element.  Built for periodic boxes with the curl-form
  * metrics, the three volume fluxes and ESDC_DISS_NONE or ESDC_DISS_LLF, viscous or inviscid; float32,
- * matrix dissipation, interior penalty, boundaries, sources, optimized metrics, the adjoint and
+ * matrix dissipation, interior penalty, boundaries, optimized metrics, the adjoint and
  * esdc_budgets_noalloc are refused (ESDC_ERR_UNSUPPORTED, or ESDC_ERR_ARG for the last).  Degrees
  * 8 to 14 are refused with ESDC_ERR_UNSUPPORTED. */
 
@@ -320,8 +320,8 @@ int esdc_set_exterior(esdc_ctx* ctx, const double* q_ext_dev);
 /*
  * esdc_set_source -- a source term added to dq/dt by every residual of the context, e.g. the
  * manufactured-solution source of Sec. 5.1 (esdc_mms_fields).  [K][5][N^3] float64 device array,
- * kept (not copied) until replaced; NULL clears it.  Float64 and float32-mixed contexts with p <= 7
- * (ESDC_ERR_UNSUPPORTED at p = 15); the float32 residual adds it rounded to float32.
+ * kept (not copied) until replaced; NULL clears it.  Every context (p = 15 included); the float32
+ * residual adds it rounded to float32.
  */
 int esdc_set_source(esdc_ctx* ctx, const double* source_dev);
 

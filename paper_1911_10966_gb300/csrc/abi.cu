@@ -983,7 +983,6 @@ int esdc_set_exterior(esdc_ctx* c, const double* q_ext) {
 
 int esdc_set_source(esdc_ctx* c, const double* src) {
     if (!c) return fail(ESDC_ERR_ARG, "null context");
-    if (src && c->N > esdc::kMaxN) return fail(ESDC_ERR_UNSUPPORTED, "source terms are added for p <= 7 only");
     if (src && !aligned(src, 16)) return fail(ESDC_ERR_ARG, "source must be 16-byte aligned");
     c->d_src = src;
     return prepare_variant(c);

@@ -13,7 +13,7 @@
 //      contravariant viscous fluxes Ftilde_l, written to global memory with their face traces.
 //   3. lg_visc_div (mu > 0), one CTA per (element, l, plane): r_l += D_l Ftilde_l along the lines
 //      plus the BR1 interface term (E_ii/2)(Ftilde_nbr - Ftilde_own)/w_i at the line ends.
-//   4. lg_finish: dq/dt = (r_0 + (r_1 + r_2)) / J.
+//   4. lg_finish: dq/dt = (r_0 + (r_1 + r_2)) / J, plus the source term if one is set.
 // Volume flux variants ES-C, SF-KG and DC and the none / local Lax-Friedrichs interface dissipation
 // are supported; the other optional terms of rhs_f64.cu are not built at this degree.
 #include <cuda_runtime.h>
@@ -353,7 +353,8 @@ lg_visc_div(const double* __restrict__ ft, const double* __restrict__ trace, con
 
 // dq/dt = (r_0 + (r_1 + r_2)) / J, one thread per node.
 __global__ void __launch_bounds__(256)
-lg_finish(const double* __restrict__ rl, const double* __restrict__ jinv, double* __restrict__ dqdt, int64_t K) {
+lg_finish(const double* __restrict__ rl, const double* __restrict__ jinv, double* __restrict__ dqdt, int64_t K,
+          const double* __restrict__ src) {
     const int64_t n = K * LN3, part = K * 5 * LN3;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
@@ -363,7 +364,8 @@ lg_finish(const double* __restrict__ rl, const double* __restrict__ jinv, double
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             const int64_t i = (el * 5 + v) * LN3 + node;
-            dqdt[i] = (rl[i] + (rl[part + i] + rl[2 * part + i])) * Jinv;
+            const double r = (rl[i] + (rl[part + i] + rl[2 * part + i])) * Jinv;
+            dqdt[i] = src ? r + src[i] : r;
         }
     }
 }
@@ -404,7 +406,7 @@ cudaError_t launch_rhs_large(const esdc_ctx* c, const double* q, double* dqdt, c
     }
     int64_t blocks = (c->n_nodes + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    lg_finish<<<(unsigned)blocks, 256, 0, s>>>(c->d_lr, c->d_jinv, dqdt, c->K);
+    lg_finish<<<(unsigned)blocks, 256, 0, s>>>(c->d_lr, c->d_jinv, dqdt, c->K, c->d_src);
     if (ev) {
         cudaEventRecord(ev[1], s);
         cudaEventRecord(ev[2], s);
