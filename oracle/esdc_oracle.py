@@ -22,9 +22,13 @@ Readings of points the paper leaves open (each one is repeated where it is used)
     conserved variables, lambda = max over both sides of |u.n_J| + c |n_J|.
   * viscous interface terms: BR1 (central) lifting of the entropy-variable jump into the gradient
     and central viscous interface flux; interior penalty optional (default off).
-Parity status: every function below is pinned by tests in tests/test_oracle_*.py except the
-numerical values of the interface-dissipation and viscous-interface readings (only their
-conservation and entropy properties are pinned: "parity unpinned" for those constants).
+Parity status: every function below is pinned by tests in tests/test_oracle_*.py.  The paper fixes
+no constant of its interface terms (it defers them to its references), so the readings above are
+pinned as readings: the local Lax-Friedrichs magnitude by the closed-form face sum of its entropy
+production (lambda/2 (w_L - w_R).(q_L - q_R) over every interface node, computed from face states
+alone), the BR1 viscous interface terms by the exact discrete identity sum P w.visc =
+-sum P J g^T C g, the matrix dissipation against an eigendecomposition of the flux Jacobian and the
+interior penalty by its linearity, conservation and entropy production.
 """
 from __future__ import annotations
 

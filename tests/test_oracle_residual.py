@@ -209,3 +209,53 @@ def test_submesh_residual_matches_full_mesh():
     r_sub = O.rhs(q[E2], sub, gas, elems=rows)
     r_full = O.rhs(q, mesh, gas, elems=E)
     assert (r_sub - r_full).abs().max() <= 1e-14 * r_full.abs().max()
+
+
+@pytest.mark.parametrize("p,k,warp", [(2, (3, 4, 2), 0.1), (3, (2, 3, 3), 0.0)])
+def test_llf_dissipation_entropy_production_face_identity(p, k, warp):
+    """Magnitude of the local Lax-Friedrichs interface dissipation (SAT^(I) reading: lambda/2 (q_own -
+    q_nbr) lifted by 1/P_ii, lambda = max over both sides of |u.n_J| + c |n_J|).  Its contribution to
+    the entropy budget sum P J w.dq/dt is, after pairing the two sides of every interface,
+        dS(LLF) - dS(EC) = - sum_interfaces sum_face_nodes w_a w_b lambda/2 (w_L - w_R).(q_L - q_R),
+    with w_a w_b the face quadrature weights.  The right side is computed here from the face states
+    alone, with this test's own face indexing and sound speed, so a halved or doubled lambda, a dropped
+    |n_J|, a wrong lift weight or a dissipation on the wrong side fails it.  The box is anisotropic and
+    scaled so that |n_J| is far from 1."""
+    kx, ky, kz = k
+    s = O.sbp_operator(p)
+    lo, hi = [-0.4, -0.9, -0.3], [0.6, 0.3, 0.5]
+    x = I.box_coords(s.xi.numpy(), kx, ky, kz, lo, hi, warp=warp, seed=5)
+    mesh = O.make_mesh(p, x, kx, ky, kz)
+    gas = O.Gas.from_mach(0.3, 0.0)
+    q = torch.tensor(I.perturb(I.density_wave(x, amp=0.2, Ma=0.3), seed=4, rel=2e-2))
+    dS_llf = O.budgets(q, O.rhs(q, mesh, gas, dissipation=True), mesh, gas)[2]
+    dS_ec = O.budgets(q, O.rhs(q, mesh, gas, dissipation=False), mesh, gas)[2]
+
+    g = gas.gamma
+    N = p + 1
+    wq = s.w.double()
+    W2 = wq[:, None] * wq[None, :]                          # face weights (axis order kept)
+    w = O.entropy_variables(q, gas)
+    nbr = O.box_neighbours(kx, ky, kz)
+    total = 0.0
+    for l in range(3):
+        ax = 4 - l                                           # array axis of xi_{l+1} in [K, 5, N, N, N]
+        qL = q.select(ax, N - 1)                            # +xi_l face of every element
+        wL = w.select(ax, N - 1)
+        R = nbr[:, 2 * l + 1]                                # its neighbour across that face
+        qR = q[R].select(ax, 0)
+        wR = w[R].select(ax, 0)
+        n = mesh.Ja[:, l].select(ax, N - 1)                  # [K, 3, face nodes] contravariant normal
+        nmag = torch.sqrt((n ** 2).sum(dim=1))
+
+        def lam(qq):
+            rho = qq[:, 0]
+            u = qq[:, 1:4] / rho.unsqueeze(1)
+            pr = (g - 1.0) * (qq[:, 4] - 0.5 * rho * (u ** 2).sum(dim=1))
+            return (u * n).sum(dim=1).abs() + torch.sqrt(g * pr / rho) * nmag
+
+        lmax = torch.maximum(lam(qL), lam(qR))
+        quad = ((wL - wR) * (qL - qR)).sum(dim=1)
+        total += float((W2 * 0.5 * lmax * quad).sum())
+    assert total > 0.0
+    assert dS_llf - dS_ec == pytest.approx(-total, rel=1e-11, abs=0.0)
