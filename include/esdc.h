@@ -442,9 +442,11 @@ int esdc_probe_fma(int kind, double* flops_per_s, void* stream);
  *   of non-finite or non-physical nodes); out_dev[2..3] are 0 when dqdt_dev is NULL.
  * Scratch: a static device array of 65536 x 5 doubles (2.6 MB) in every process that loads the
  * library, held on each GPU until exit; inputs above 268,435,456 nodes are rejected with
- * ESDC_ERR_ARG.  The first call on a device looks the array's device address up (cudaGetSymbolAddress
- * with that device current), so make that first call before any stream capture.  All calls share
- * the array: calls that overlap on the GPU (other streams, other threads) race and give wrong sums.
+ * ESDC_ERR_ARG.  A call on a stream that is not being captured looks the array's device address up
+ * (cudaGetSymbolAddress with the current device), so the address stays valid after a device reset;
+ * a call during stream capture reuses the address of the last uncaptured call on that device, so
+ * make one call on each device before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race and give wrong sums.
  * Asynchronous on stream; deterministic order.  Errors: ESDC_ERR_ARG, ESDC_ERR_CUDA.
  */
 int esdc_budgets_noalloc(int N, int64_t K, double gamma, const double* w_host, const double* q_dev,

@@ -6,6 +6,7 @@
 #include <utility>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -530,6 +531,20 @@ void free_ctx(esdc_ctx* c) {
 
 namespace esdc {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+int sm_count() {
+    static std::mutex mu;
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 148;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
 }  // namespace esdc
 
 extern "C" {
@@ -751,7 +766,8 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     cudaError_t e = cudaGetDevice(&c->device);
     const size_t N2 = (size_t)hs.N * hs.N;
     const size_t geom_bytes = (size_t)c->K * 10 * c->N3 * sizeof(double);
-    c->red_blocks = 608;             // 4 blocks of 256 threads per SM on 152 SMs
+    c->red_blocks = 4 * esdc::sm_count();  // 4 blocks of 256 threads per SM, fixed per context (the order of
+                                     // the reduction, so its result, depends only on the device)
     if (e == cudaSuccess) e = cudaMalloc(&c->d_geom, geom_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_nbr, (size_t)c->K * 6 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_trace, (size_t)c->K * 6 * 4 * N2 * sizeof(double));

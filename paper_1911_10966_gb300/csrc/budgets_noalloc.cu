@@ -95,12 +95,14 @@ __global__ void __launch_bounds__(kThreads) final_kernel(const double* __restric
     }
 }
 
-// Device address of g_scratch, looked up once per device (with that device current).
+// Device address of g_scratch per device (with that device current).  Outside stream capture the
+// address is looked up again on every call, so a device reset (which reloads the module and moves
+// the array) never leaves a stale pointer behind; during capture the last looked-up address is used.
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 double* g_addr[kMaxDevices] = {nullptr};
 
-int scratch_for_current_device(double** out) {
+int scratch_for_current_device(bool refresh, double** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -112,7 +114,7 @@ int scratch_for_current_device(double** out) {
         return ESDC_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (refresh || !g_addr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) {
@@ -140,13 +142,19 @@ extern "C" int esdc_budgets_noalloc(int N, int64_t K, double gamma, const double
                              " nodes");
         return ESDC_ERR_ARG;
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cs);
+    if (ce != cudaSuccess) {
+        esdc::set_last_error(std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+        return ESDC_ERR_CUDA;
+    }
     double* scratch = nullptr;
-    int st = scratch_for_current_device(&scratch);
+    int st = scratch_for_current_device(cs == cudaStreamCaptureStatusNone, &scratch);
     if (st) return st;
     W w{};
     for (int i = 0; i < N; ++i) w.w[i] = w_host[i];
     const int64_t rows = (n + (int64_t)kThreads * kNodesPerThread - 1) / ((int64_t)kThreads * kNodesPerThread);
-    cudaStream_t s = (cudaStream_t)stream;
     partial_kernel<<<(unsigned)rows, kThreads, 0, s>>>(q_dev, dqdt_dev, J_dev, n, N, gamma, w, scratch);
     final_kernel<<<1, kThreads, 0, s>>>(scratch, rows, out_dev);
     cudaError_t e = cudaGetLastError();

@@ -77,6 +77,10 @@ int generate_box_coords(const esdc_setup_t& s, const std::vector<double>& xi, st
 void mms_fields(double gamma, double Ma, double Re, double Pr, double L, const double* table, int64_t n,
                 const double* x, double* q, double* src);
 void set_last_error(const std::string& msg);   // message returned by esdc_last_error on this thread
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, looked up once per
+// device); grid-stride launches are capped at grid_cap() = 16 CTAs per SM.
+int sm_count();
+inline long long grid_cap() { return 16LL * sm_count(); }
 
 }  // namespace esdc
 

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256) init_kernel(int ic, const InitParams prm,
 
 cudaError_t launch_init_state(const esdc_ctx* c, int ic, const InitParams& prm, double* q, cudaStream_t s) {
     int64_t blocks = (c->n_nodes + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > grid_cap()) blocks = grid_cap();
     if (blocks < 1) blocks = 1;
     init_kernel<<<(unsigned)blocks, 256, 0, s>>>(ic, prm, c->d_xyz, q, c->K, c->N3, c->phys.gamma, c->setup.Ma,
                                                  c->phys.R);

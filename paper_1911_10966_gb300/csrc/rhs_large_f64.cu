@@ -405,7 +405,7 @@ cudaError_t launch_rhs_large(const esdc_ctx* c, const double* q, double* dqdt, c
                                                              c->K, c->opsl);
     }
     int64_t blocks = (c->n_nodes + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > grid_cap()) blocks = grid_cap();
     lg_finish<<<(unsigned)blocks, 256, 0, s>>>(c->d_lr, c->d_jinv, dqdt, c->K, c->d_src);
     if (ev) {
         cudaEventRecord(ev[1], s);

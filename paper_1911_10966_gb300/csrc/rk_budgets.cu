@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(256) ke_grad_kernel(const double* __restrict__
 
 cudaError_t launch_scale(double* out, const double* x, double a, int64_t n, cudaStream_t s) {
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > grid_cap()) blocks = grid_cap();
     if (blocks < 1) blocks = 1;
     scale_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, x, a, n);
     return cudaGetLastError();
@@ -327,7 +327,7 @@ cudaError_t launch_scale(double* out, const double* x, double a, int64_t n, cuda
 
 cudaError_t launch_ke_gradient(const esdc_ctx* c, const double* q, double* grad, cudaStream_t s) {
     int64_t blocks = (c->n_nodes + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > grid_cap()) blocks = grid_cap();
     if (blocks < 1) blocks = 1;
     ke_grad_kernel<<<(unsigned)blocks, 256, 0, s>>>(q, c->d_geom, c->K, c->N, c->ops, grad);
     return cudaGetLastError();
@@ -336,7 +336,7 @@ cudaError_t launch_ke_gradient(const esdc_ctx* c, const double* q, double* grad,
 cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int64_t n, cudaStream_t s) {
     int64_t blocks = (n / 2 + 255) / 256;
     if (blocks < 1) blocks = 1;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > grid_cap()) blocks = grid_cap();
     const unsigned g = (unsigned)blocks;
     switch (cb.nk) {
         case 1: combine_kernel<1><<<g, 256, 0, s>>>(out, q0, cb, n); break;
@@ -376,7 +376,7 @@ Ln2 ln2_split() {
 cudaError_t launch_lincomb(double* out, const LinComb& lc, int64_t n, cudaStream_t s) {
     int64_t blocks = (n / 2 + 255) / 256;
     if (blocks < 1) blocks = 1;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > grid_cap()) blocks = grid_cap();
     const unsigned g = (unsigned)blocks;
     switch (lc.n) {
         case 1: lincomb_kernel<1><<<g, 256, 0, s>>>(out, lc, n); break;

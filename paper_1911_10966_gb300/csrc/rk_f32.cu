@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) final_kernel(double* __restrict__ q, floa
 unsigned grid_for(int64_t n) {
     int64_t b = (n + 255) / 256;
     if (b < 1) b = 1;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > grid_cap()) b = grid_cap();
     return (unsigned)b;
 }
 

@@ -65,3 +65,35 @@ def test_budgets_noalloc_rejects_oversized_input():
                                   out.data_ptr(), None)
     assert code == nat.ESDC_ERR_ARG
     assert b"static scratch limit" in L.esdc_last_error()
+
+
+def test_budgets_noalloc_counts_nonphysical_nodes_like_context_budgets():
+    """A negative density and a non-finite residual entry: both reductions skip the non-physical node's
+    entropy and energy terms and count two bad nodes; their sums agree on the remaining nodes."""
+    solver, q, _, _, _ = make_pair(3, (4, 3, 2), warp=0.1, seed=3, Re=1600.0, noise=1e-2)
+    w = np.zeros(solver.N)
+    xi = np.zeros(solver.N)
+    nat.check(nat.lib().esdc_lgl(solver.p, xi.ctypes.data, w.ctypes.data), "esdc_lgl")
+    J, _ = solver.geometry()
+    J_dev = torch.as_tensor(np.ascontiguousarray(J), device=q.device)
+    dq = solver.rhs(q)
+    bad = q.clone()
+    bad[2, 0, 1, 2, 0] = -0.5
+    dq[5, 3, 0, 1, 1] = float("nan")
+    ctx = torch.full((5,), float("nan"), dtype=torch.float64, device=q.device)
+    solver.budgets_async(bad, ctx)
+    out = torch.full((5,), float("nan"), dtype=torch.float64, device=q.device)
+    got = _noalloc(solver, w, J_dev, bad, None, out)
+    ref = ctx.cpu().numpy()
+    assert got[4] == ref[4] == 1.0
+    assert _close(got[0], ref[0], 1e-13) and _close(got[1], ref[1], 1e-13), (got, ref)
+    solver.budgets_async(bad, ctx, dq)
+    got = _noalloc(solver, w, J_dev, bad, dq, out)
+    ref = ctx.cpu().numpy()
+    assert got[4] == ref[4] == 2.0
+    assert _close(got[0], ref[0], 1e-13) and _close(got[1], ref[1], 1e-13), (got, ref)
+    assert np.isnan(got[2]) and np.isnan(ref[2]) and np.isnan(got[3]) and np.isnan(ref[3])
+    # the same input once more after a clean call: nothing of the earlier call leaks into the sums
+    _noalloc(solver, w, J_dev, q, solver.rhs(q), out)
+    got2 = _noalloc(solver, w, J_dev, bad, None, out)
+    assert got2[4] == 1.0 and _close(got2[1], got[1], 1e-13)
