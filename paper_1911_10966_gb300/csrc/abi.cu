@@ -740,6 +740,8 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
             c->ops.S[i][j] = hs.S[i * hs.N + j];
             c->opsf.D[i][j] = (float)hs.D[i * hs.N + j];
             c->opsf.S[i][j] = (float)hs.S[i * hs.N + j];
+            c->opsf.ST[i][j] = (float)hs.S[j * hs.N + i];
+            c->opsf.D2[i][j].x = c->opsf.D2[i][j].y = (float)hs.D[i * hs.N + j];
         }
     }
     const double R = 1.0 / (s.gamma * s.Ma * s.Ma);

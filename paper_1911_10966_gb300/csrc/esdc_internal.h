@@ -40,6 +40,11 @@ struct Phys {
     int viscous;               // mu > 0
 };
 
+// A float32 pair, 8-byte aligned: one 64-bit operand of the packed (f32x2) instructions.
+struct alignas(8) FPair {
+    float x, y;
+};
+
 // FP32 copies used by the mixed-precision kernels.
 struct OpsF {
     int N;
@@ -47,6 +52,8 @@ struct OpsF {
     float S[kMaxN][kMaxN];
     float w[kMaxN];
     float winv[kMaxN];
+    float ST[kMaxN][kMaxN];    // S transposed: ST[i][j] = S[j][i] = -S[i][j]
+    FPair D2[kMaxN][kMaxN];    // (D[i][j], D[i][j]): D as a packed operand of both lanes
 };
 
 struct PhysF {

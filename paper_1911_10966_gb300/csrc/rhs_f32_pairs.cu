@@ -1,0 +1,661 @@
+// Float32 residual of the mixed-precision form for an even number of nodes per direction (p = 3, 5,
+// 7) with the ES-C volume flux: the arithmetic of rhs_main_f32 (rhs_f32.cu, whose header states the
+// split of the Chandrashekar flux about the reference state), with the volume term's pair loop
+// evaluated two node pairs per instruction in packed float32 (add/sub/mul/fma .f32x2, sm_100 and
+// later; hand-written PTX below).  In row i of a line the two lanes hold the pairs (i, j) and
+// (i, j + 1) with j even: the row node's values are broadcast to both lanes and the two column nodes
+// are one 64-bit shared-memory load.  For even i the first lane pair is (i, i), (i, i + 1); the
+// first lane carries the coefficient S_ii = 0.
+//
+// The reference parts of the split flux are folded into the sums: the mass sum accumulates the
+// full mass flux rho_ln ubar.n and the energy sum adds gamma p0/(gamma-1) ubar.n to the energy
+// perturbation flux, so five sums per node replace the six of rhs_main_f32 (the rounding of the
+// linear part is the same, eps32 |ubar.n| per term).
+//
+// Shared memory per element (floats):
+//   sW4 [N3] float4   entropy variables (w2, w3, w4, w5 - w5_ref), for the viscous gradient
+//   sA  [3][5][N3]    per-direction volume + interface sums | then the contravariant viscous
+//                     fluxes, float4 [3][N3]
+//   sL  [3][8][N3]    pair-loop inputs per direction l with the line's nodes contiguous:
+//                     (hdr, dbn, hu0, hu1, hu2, Ja_l0, Ja_l1, Ja_l2) at (l 8 + c) N3 + line N + j',
+//                     j' = j ^ lsw(line) (a bank swizzle, below)
+//   sJi [N3]          1/J
+//   sQ  [5][N3]       own dq (interface dissipation) | then the sum of the three directions
+//   sWf [6][4][N2]    neighbour entropy variables
+//   sNq [5][6 N2]     neighbour (or exterior) perturbation state at the face nodes, face node
+//                     fn = (2 l + side) N2 + fi, read in the load phase with the element's own data
+// Lines of direction l: line = t1 + N t2 with (t1, t2) = (i2, i3), (i1, i3), (i1, i2) for l = 0, 1, 2
+// and j = i1, i2, i3 the position along the line (l = 0 is the natural node order).
+#include <cuda_runtime.h>
+
+#include "esdc_internal.h"
+#include "f32_common.cuh"
+#include "fpconv.cuh"
+#include "kernels.h"
+#include "visc_sat.cuh"
+
+namespace esdc {
+namespace {
+
+using namespace f32;
+
+// ---- packed float32 pairs: two lanes in one 64-bit register pair
+typedef unsigned long long f2p;
+
+__device__ __forceinline__ f2p pk(float lo, float hi) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 upk(f2p r) {
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(r));
+    return d;
+}
+__device__ __forceinline__ f2p add2(f2p a, f2p b) {
+    f2p d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
+    f2p d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
+    f2p d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {   // a b + c
+    f2p d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2p bc(float x) { return pk(x, x); }
+// two consecutive floats (8-byte aligned) as one packed value: one 64-bit load
+__device__ __forceinline__ f2p ld2(const float* p) { return *reinterpret_cast<const f2p*>(p); }
+__device__ __forceinline__ f2p ldp(const FPair& p) { return pk(p.x, p.y); }
+
+template <int N>
+struct CfgP {
+    static constexpr int N2 = N * N, N3 = N * N * N;
+    static constexpr int TE = N <= 5 ? (N3 > 3 * N2 ? N3 : 3 * N2) : 3 * N2;
+    static constexpr int EPB = TE >= 120 ? 1 : (128 + TE - 1) / TE;
+    static constexpr int THREADS = EPB * TE;
+    static constexpr int SM = ((4 + 15 + 24 + 1 + 5) * N3 + (24 + 30) * N2 + 3) / 4 * 4;
+    static constexpr int NPT = (N3 + TE - 1) / TE;        // nodes per thread
+    static constexpr int FPT = (6 * N2 + TE - 1) / TE;    // face nodes per thread
+    static constexpr int MINB = N == 8 ? 2 : (N == 6 ? 1 : 4);
+};
+
+// Swizzle of the position along a line in the direction copies: j ^ lsw(line) with an even lsw, so
+// that the node pairs (j, j + 1), j even, stay adjacent while consecutive lines (the threads of a
+// warp) spread over the shared-memory banks (N = 8: 16 threads' 64-bit loads on 32 distinct banks).
+template <int N>
+__device__ __forceinline__ int lsw(int line) {
+    return N == 8 ? 2 * ((line >> 2) & 3) : (N == 4 ? 2 * ((line >> 3) & 1) : 0);
+}
+template <int N>
+__device__ __forceinline__ int lidx(int line, int j) {
+    return line * N + (j ^ lsw<N>(line));
+}
+// Position of node (i1, i2, i3) in the direction-l copy.
+template <int N>
+__device__ __forceinline__ int lpos(int l, int i1, int i2, int i3) {
+    return l == 0 ? lidx<N>(i2 + N * i3, i1) : (l == 1 ? lidx<N>(i1 + N * i3, i2) : lidx<N>(i1 + N * i2, i3));
+}
+// Natural node index of position j on line `line` of direction l.
+template <int N>
+__device__ __forceinline__ int nat_of(int l, int line, int j) {
+    return l == 0 ? (line * N + j) : (l == 1 ? ((line % N) + N * j + N * N * (line / N)) : (line + N * N * j));
+}
+
+// Log-mean terms of one lane with the reference form of ec_flux_pert: drl = rho_ln - rho0 and dIn
+// (1/(2 beta_ln) = RT0 (1 + dIn)), series or logarithmic branch per lane.
+__device__ __forceinline__ void logmean_lane(float ahdr, float bhdr, float adbn, float bdbn, const Ref& r, float& drl,
+                                             float& dIn) {
+    const float dbar = ahdr + bhdr;
+    const float rb = r.rho0 + dbar;
+    const float f = (ahdr - bhdr) * frcp(rb);
+    const float uu = f * f;
+    if (uu < 1.0e-2f) {
+        drl = fmaf(rb, uu * (-1.0f / 3.0f + uu * (-4.0f / 45.0f + uu * (-44.0f / 945.0f))), dbar);
+    } else {
+        const float ra = r.rho0 + 2.0f * ahdr, rbb = r.rho0 + 2.0f * bhdr;
+        drl = (ra - rbb) * frcp(logf(ra * frcp(rbb))) - r.rho0;
+    }
+    const float dbs = adbn + bdbn;
+    const float rsb = frcp(2.0f + dbs);
+    const float db = adbn - bdbn;
+    const float fb = db * rsb;
+    const float ub = fb * fb;
+    if (ub < 1.0e-2f) {
+        dIn = (ub * (2.0f / 3.0f + ub * (2.0f / 5.0f + ub * (2.0f / 7.0f))) - dbs) * rsb;
+    } else {
+        dIn = logf((1.0f + adbn) * frcp(1.0f + bdbn)) * frcp(db) - 1.0f;
+    }
+}
+
+// Packed constants of the two-lane flux.
+struct KP {
+    f2p rho0, two, nhrho0, two_RT0, c5, H0;
+    f2p c1r, c2r, c3r, c1b, c2b, c3b;   // series coefficients of drl and dIn
+};
+__device__ __forceinline__ KP make_kp(const Ref& r) {
+    KP k;
+    k.rho0 = bc(r.rho0);
+    k.two = bc(2.0f);
+    k.nhrho0 = bc(-r.hrho0);
+    k.two_RT0 = bc(r.two_RT0);
+    k.c5 = bc(r.c5);
+    k.H0 = bc(r.H0);
+    k.c1r = bc(-1.0f / 3.0f);
+    k.c2r = bc(-4.0f / 45.0f);
+    k.c3r = bc(-44.0f / 945.0f);
+    k.c1b = bc(2.0f / 3.0f);
+    k.c2b = bc(2.0f / 5.0f);
+    k.c3b = bc(2.0f / 7.0f);
+    return k;
+}
+
+// Two lanes of the split Chandrashekar flux (ec_flux_pert), the reference parts folded in: F[0] the
+// mass flux, F[1..3] the momentum perturbation flux, F[4] the energy flux less p0 n.  Row node a:
+// broadcast pairs (ah = hdr, ad = dbn, au = hu, a2u = u = 2 hu, an = Ja_l); column nodes b: packed.
+// n = an + bn is twice the averaged metric, as S (half of 2 S) is the pair coefficient.
+__device__ __forceinline__ void ec_flux2(f2p ah, f2p ad, f2p au0, f2p au1, f2p au2, f2p a2u0, f2p a2u1, f2p a2u2,
+                                         f2p an0, f2p an1, f2p an2, f2p bh, f2p bd, f2p bu0, f2p bu1, f2p bu2,
+                                         f2p bn0, f2p bn1, f2p bn2, const KP& k, const Ref& r, f2p F[5]) {
+    const f2p dbar = add2(ah, bh);
+    const f2p rb = add2(k.rho0, dbar);
+    const f2p dbs = add2(ad, bd);
+    const f2p den = add2(k.two, dbs);
+    const float2 rbv = upk(rb), denv = upk(den);
+    const f2p rrb = pk(frcp(rbv.x), frcp(rbv.y));
+    const f2p rsb = pk(frcp(denv.x), frcp(denv.y));
+    const f2p f = mul2(sub2(ah, bh), rrb);
+    const f2p uu = mul2(f, f);
+    const f2p fb = mul2(sub2(ad, bd), rsb);
+    const f2p ub = mul2(fb, fb);
+    const float2 uuv = upk(uu), ubv = upk(ub);
+    f2p drl, dIn;
+    if (fmaxf(fmaxf(uuv.x, uuv.y), fmaxf(ubv.x, ubv.y)) < 1.0e-2f) {
+        const f2p tr = mul2(uu, fma2(uu, fma2(uu, k.c3r, k.c2r), k.c1r));
+        drl = fma2(rb, tr, dbar);
+        const f2p tb = mul2(ub, fma2(ub, fma2(ub, k.c3b, k.c2b), k.c1b));
+        dIn = mul2(sub2(tb, dbs), rsb);
+    } else {
+        const float2 h = upk(ah), hb = upk(bh), d = upk(ad), dd = upk(bd);
+        float r0, r1, i0, i1;
+        logmean_lane(h.x, hb.x, d.x, dd.x, r, r0, i0);
+        logmean_lane(h.y, hb.y, d.y, dd.y, r, r1, i1);
+        drl = pk(r0, r1);
+        dIn = pk(i0, i1);
+    }
+    const f2p dpt = mul2(mul2(k.two_RT0, rsb), fma2(k.nhrho0, dbs, dbar));
+    const f2p ub0 = add2(au0, bu0), ub1 = add2(au1, bu1), ub2 = add2(au2, bu2);
+    const f2p n0 = add2(an0, bn0), n1 = add2(an1, bn1), n2 = add2(an2, bn2);
+    const f2p un = fma2(ub2, n2, fma2(ub1, n1, mul2(ub0, n0)));
+    const f2p rr = add2(k.rho0, drl);
+    const f2p f1 = mul2(rr, un);
+    F[0] = f1;
+    F[1] = fma2(f1, ub0, mul2(dpt, n0));
+    F[2] = fma2(f1, ub1, mul2(dpt, n1));
+    F[3] = fma2(f1, ub2, mul2(dpt, n2));
+    const f2p hab = fma2(a2u2, bu2, fma2(a2u1, bu1, mul2(a2u0, bu0)));
+    F[4] = fma2(k.H0, un, fma2(mul2(k.c5, un), fma2(dIn, rr, drl), fma2(f1, hab, mul2(dpt, un))));
+}
+
+// One lane of the same flux (interface terms), reference parts folded in as in ec_flux2.
+__device__ __forceinline__ void ec_flux_folded(const PrimF& a, const PrimF& b, float n0, float n1, float n2,
+                                               const Ref& r, float F[5]) {
+    float df[5], un;
+    ec_flux_pert(a, b, n0, n1, n2, r, df, un);
+    F[0] = fmaf(r.rho0, un, df[0]);
+    F[1] = df[1];
+    F[2] = df[2];
+    F[3] = df[3];
+    F[4] = fmaf(r.H0, un, df[4]);
+}
+
+template <int N, int NK, bool XF>
+__global__ void __launch_bounds__(CfgP<N>::THREADS, CfgP<N>::MINB)
+rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom, const int32_t* __restrict__ nbr,
+              float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph, const Ref ref,
+              const float* __restrict__ nsurf, const double* __restrict__ qext, const double* __restrict__ src) {
+    using C = CfgP<N>;
+    constexpr int N2 = C::N2, N3 = C::N3, TE = C::TE;
+    extern __shared__ float4 smp4[];
+    const int t = threadIdx.x;
+    const int el_loc = t / TE;
+    const int tl = t - el_loc * TE;
+    const int64_t el = (int64_t)blockIdx.x * C::EPB + el_loc;
+    const bool active = el < K;
+    float* base_sm = reinterpret_cast<float*>(smp4) + (size_t)el_loc * C::SM;
+    float4* sW4 = reinterpret_cast<float4*>(base_sm);          // [N3]
+    float* sA = base_sm + 4 * N3;                               // [3][5][N3] | float4 [3][N3] Ftilde
+    float4* sF4 = reinterpret_cast<float4*>(sA);
+    float* sL = sA + 15 * N3;                                   // [3][8][N3]
+    float* sJi = sL + 24 * N3;                                  // [N3]
+    float* sQ = sJi + N3;                                       // [5][N3] | [5][N3] direction sum
+    float* sWf = sQ + 5 * N3;                                   // [6][4][N2]
+    float* sNq = sWf + 24 * N2;                                 // [5][6 N2]
+    const int64_t eoff = el * 5 * N3;
+
+    // ---- load: every global read of the element first (own stage state and metrics, the neighbours'
+    // face values of this thread's interface nodes), so that their latencies overlap; then the
+    // primitives in the three direction copies, the metrics, the entropy variables
+    constexpr int NPT = C::NPT, FPT = C::FPT;
+    if (active) {
+        float d[NPT][5], gv[NPT][10], qn[FPT][5];
+#pragma unroll
+        for (int r = 0; r < NPT; ++r) {
+            const int node = tl + r * TE;
+            if (node < N3) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) d[r][v] = stage_value<NK>(in, eoff + v * N3 + node);
+#pragma unroll
+                for (int c = 0; c < 10; ++c) gv[r][c] = geom[(el * 10 + c) * N3 + node];
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int fn = tl + f * TE;
+            if (fn < 6 * N2) {
+                const int l = fn / (2 * N2);
+                const int rem = fn - l * 2 * N2;
+                const int side = rem / N2, fi = rem - side * N2;
+                const int st = dir_stride_f<N>(l);
+                const int base = line_base_f<N>(l, fi % N, fi / N);
+                const int64_t nb = nbr[el * 6 + 2 * l + side];
+                if (!XF || nb >= 0) {
+                    const int nbn = base + (side ? 0 : (N - 1) * st);
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) qn[f][v] = stage_value<NK>(in, nb * 5 * N3 + v * N3 + nbn);
+                } else {
+                    // boundary face of a bounded box: the float64 exterior state at the own nodes, less
+                    // the reference state, rounded once
+                    const int own = base + (side ? (N - 1) * st : 0);
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) {
+                        const double x = qext[eoff + v * N3 + own];
+                        qn[f][v] = d2f_int(v == 0 ? x - ref.rho0d : (v == 4 ? x - ref.E0d : x));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NPT; ++r) {
+            const int node = tl + r * TE;
+            if (node < N3) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sQ[v * N3 + node] = d[r][v];
+                PrimF s;
+                to_prim_f(d[r], ref, s);
+                const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+                const float pv[5] = {s.hdr, s.dbn, s.hu0, s.hu1, s.hu2};
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    float* L = sL + l * 8 * N3 + lpos<N>(l, i1, i2, i3);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) L[c * N3] = pv[c];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) L[(5 + m) * N3] = gv[r][1 + 3 * l + m];
+                }
+                sJi[node] = frcp(gv[r][0]);
+                const float tb = two_beta(s, ref);
+                sW4[node] = make_float4(tb * s.u0, tb * s.u1, tb * s.u2, -ref.two_beta0 * s.dbn);
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int fn = tl + f * TE;
+            if (fn < 6 * N2) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sNq[v * 6 * N2 + fn] = qn[f][v];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- volume: one thread per line (all three directions at once), two node pairs per instruction
+    if (active && tl < 3 * N2) {
+        const int l = tl / N2, line = tl - l * N2;
+        const float* L = sL + l * 8 * N3 + line * N;
+        const int sw = lsw<N>(line);
+        const KP k = make_kp(ref);
+        f2p acc[N / 2][5];
+#pragma unroll
+        for (int m = 0; m < N / 2; ++m)
+#pragma unroll
+            for (int v = 0; v < 5; ++v) acc[m][v] = 0ull;
+#pragma unroll
+        for (int i = 0; i < N - 1; ++i) {
+            const int is = i ^ sw;
+            const float hu0 = L[2 * N3 + is], hu1 = L[3 * N3 + is], hu2 = L[4 * N3 + is];
+            const f2p ah = bc(L[is]), ad = bc(L[N3 + is]);
+            const f2p au0 = bc(hu0), au1 = bc(hu1), au2 = bc(hu2);
+            const f2p a2u0 = bc(2.0f * hu0), a2u1 = bc(2.0f * hu1), a2u2 = bc(2.0f * hu2);
+            const f2p an0 = bc(L[5 * N3 + is]), an1 = bc(L[6 * N3 + is]), an2 = bc(L[7 * N3 + is]);
+            f2p part[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+            for (int m = (i + 1) / 2; m < N / 2; ++m) {
+                const int j = 2 * m;
+                const float* Lj = L + (j ^ sw);
+                f2p F[5];
+                ec_flux2(ah, ad, au0, au1, au2, a2u0, a2u1, a2u2, an0, an1, an2, ld2(Lj), ld2(Lj + N3),
+                         ld2(Lj + 2 * N3), ld2(Lj + 3 * N3), ld2(Lj + 4 * N3), ld2(Lj + 5 * N3),
+                         ld2(Lj + 6 * N3), ld2(Lj + 7 * N3), k, ref, F);
+                const f2p c = ld2(&ops.S[i][j]);      // (S_ij, S_i,j+1)
+                const f2p ct = ld2(&ops.ST[i][j]);    // (S_ji, S_j+1,i) = -(S_ij, S_i,j+1)
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    acc[m][v] = fma2(c, F[v], acc[m][v]);
+                    part[v] = fma2(ct, F[v], part[v]);
+                }
+            }
+            // row node i: both lanes of the row partial
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                const float2 p = upk(part[v]);
+                float2 a = upk(acc[i / 2][v]);
+                if (i % 2 == 0) a.x += p.x + p.y;
+                else a.y += p.x + p.y;
+                acc[i / 2][v] = pk(a.x, a.y);
+            }
+        }
+        // the last node of the line is only ever a column node: nothing to fold
+        float* A = sA + l * 5 * N3;
+#pragma unroll
+        for (int m = 0; m < N / 2; ++m) {
+            const int j = 2 * m;
+            const int n0 = nat_of<N>(l, line, j), n1 = nat_of<N>(l, line, j + 1);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                const float2 a = upk(acc[m][v]);
+                A[v * N3 + n0] = a.x * ops.winv[j];
+                A[v * N3 + n1] = a.y * ops.winv[j + 1];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- interface SAT, all six faces at once; face nodes of direction l add into the direction-l sums
+    if (active) {
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int fn = tl + f * TE;
+            if (fn >= 6 * N2) break;
+            const int l = fn / (2 * N2);
+            const int rem = fn - l * 2 * N2;
+            const int side = rem / N2, fi = rem - side * N2;
+            const int st = dir_stride_f<N>(l);
+            const int base = line_base_f<N>(l, fi % N, fi / N);
+            const int own = base + (side ? (N - 1) * st : 0);
+            const int jo = side ? N - 1 : 0;
+            float qn[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) qn[v] = sNq[v * 6 * N2 + fn];
+            PrimF so, sn;
+            const int own0 = lidx<N>(own / N, own % N);    // the natural order is direction 0's
+            so.hdr = sL[own0];
+            so.dbn = sL[N3 + own0];
+            so.hu0 = sL[2 * N3 + own0];
+            so.hu1 = sL[3 * N3 + own0];
+            so.hu2 = sL[4 * N3 + own0];
+            so.u0 = 2.0f * so.hu0;
+            so.u1 = 2.0f * so.hu1;
+            so.u2 = 2.0f * so.hu2;
+            to_prim_f(qn, ref, sn);
+            const float* Ln = sL + (l * 8 + 5) * N3 + lidx<N>(fi, jo);
+            float n0 = Ln[0], n1 = Ln[N3], n2 = Ln[2 * N3];
+            if (nsurf) {   // optimized metrics: the interface terms take the surface metrics
+                const float* ns = nsurf + (el * 6 + 2 * l + side) * 3 * N2 + fi;
+                n0 = ns[0];
+                n1 = ns[N2];
+                n2 = ns[2 * N2];
+            }
+            float F[5];
+            ec_flux_folded(so, sn, n0, n1, n2, ref, F);
+            const float E = side ? 1.0f : -1.0f;
+            float lam = 0.0f;
+            if (ph.dissipation) {
+                const float nn = fsqrt(n0 * n0 + n1 * n1 + n2 * n2);
+                const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + fsqrt(ref.gamma * node_RT(so.dbn, ref)) * nn;
+                const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + fsqrt(ref.gamma * node_RT(sn.dbn, ref)) * nn;
+                lam = 0.5f * fmaxf(lo, ln);
+            }
+            const float wi = ops.winv[jo];
+            float* A = sA + l * 5 * N3;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) A[v * N3 + own] += (-E * F[v] - lam * (sQ[v * N3 + own] - qn[v])) * wi;
+            float* wf = sWf + (2 * l + side) * 4 * N2 + fi;
+            const float tb = two_beta(sn, ref);
+            wf[0] = tb * sn.u0;
+            wf[N2] = tb * sn.u1;
+            wf[2 * N2] = tb * sn.u2;
+            wf[3 * N2] = -ref.two_beta0 * sn.dbn;
+        }
+    }
+    __syncthreads();
+
+    if (ph.viscous) {
+        float Ft[NPT][3][4];
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < NPT; ++r) {
+                const int node = tl + r * TE;
+                if (node >= N3) continue;
+                const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+                const float4 w4 = sW4[node];
+                const float wown[4] = {w4.x, w4.y, w4.z, w4.w};
+                float th[3][4];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int ia = a == 0 ? i1 : (a == 1 ? i2 : i3);
+                    const int st = dir_stride_f<N>(a);
+                    const int lb = node - ia * st;
+                    f2p s01 = 0ull, s23 = 0ull;
+#pragma unroll
+                    for (int j = 0; j < N; ++j) {
+                        const f2p d = ldp(ops.D2[ia][j]);
+                        const float4 wj = sW4[lb + j * st];
+                        s01 = fma2(d, pk(wj.x, wj.y), s01);
+                        s23 = fma2(d, pk(wj.z, wj.w), s23);
+                    }
+                    const float2 a01 = upk(s01), a23 = upk(s23);
+                    th[a][0] = a01.x;
+                    th[a][1] = a01.y;
+                    th[a][2] = a23.x;
+                    th[a][3] = a23.y;
+                    if (ia == 0 || ia == N - 1) {
+                        const int side = ia == N - 1;
+                        const int fi = a == 0 ? (i2 + N * i3) : (a == 1 ? (i1 + N * i3) : (i1 + N * i2));
+                        const float E = side ? 0.5f : -0.5f;
+                        const float* wf = sWf + (2 * a + side) * 4 * N2 + fi;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) th[a][kk] += E * (wf[kk * N2] - wown[kk]) * ops.winv[ia];
+                    }
+                }
+                float Ja[3][3];
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    const float* Lg = sL + (l * 8 + 5) * N3 + lpos<N>(l, i1, i2, i3);
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) Ja[l][m] = Lg[m * N3];
+                }
+                const float Jinv = sJi[node];
+                float g[3][4];
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        g[m][kk] = Jinv * (Ja[0][m] * th[0][kk] + Ja[1][m] * th[1][kk] + Ja[2][m] * th[2][kk]);
+                const int node0 = lidx<N>(node / N, i1);
+                const float dbn = sL[N3 + node0];
+                const float RT = node_RT(dbn, ref);
+                const float u[3] = {2.0f * sL[2 * N3 + node0], 2.0f * sL[3 * N3 + node0], 2.0f * sL[4 * N3 + node0]};
+                float du[3][3];
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) du[kk][m] = RT * (g[m][kk] + u[kk] * g[m][3]);
+                const float div = du[0][0] + du[1][1] + du[2][2];
+                const float hc = ph.kappa / ph.R * RT * RT;
+                float FV[3][4];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        FV[m][i] = ph.mu * (du[i][m] + du[m][i] - (i == m ? (2.0f / 3.0f) * div : 0.0f));
+                    FV[m][3] = FV[m][0] * u[0] + FV[m][1] * u[1] + FV[m][2] * u[2] + hc * g[m][3];
+                }
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        Ft[r][l][kk] = Ja[l][0] * FV[0][kk] + Ja[l][1] * FV[1][kk] + Ja[l][2] * FV[2][kk];
+                    const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
+                    if (il == 0 || il == N - 1) {
+                        const int side = il == N - 1;
+                        const int fi = l == 0 ? (i2 + N * i3) : (l == 1 ? (i1 + N * i3) : (i1 + N * i2));
+                        float* tr = trace + ((el * 6 + 2 * l + side) * 4) * N2 + fi;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) tr[kk * N2] = Ft[r][l][kk];
+                    }
+                }
+                // the node's three directions of volume and interface sums (sQ is free after the SAT)
+#pragma unroll
+                for (int v = 0; v < 5; ++v)
+                    sQ[v * N3 + node] = sA[v * N3 + node] + (sA[(5 + v) * N3 + node] + sA[(10 + v) * N3 + node]);
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < NPT; ++r) {
+                const int node = tl + r * TE;
+                if (node >= N3) continue;
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+                    sF4[l * N3 + node] = make_float4(Ft[r][l][0], Ft[r][l][1], Ft[r][l][2], Ft[r][l][3]);
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < NPT; ++r) {
+                const int node = tl + r * TE;
+                if (node >= N3) continue;
+                const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+                f2p v01 = 0ull, v23 = 0ull;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
+                    const int st = dir_stride_f<N>(l);
+                    const int lb = node - il * st;
+#pragma unroll
+                    for (int j = 0; j < N; ++j) {
+                        const f2p d = ldp(ops.D2[il][j]);
+                        const float4 f = sF4[l * N3 + lb + j * st];
+                        v01 = fma2(d, pk(f.x, f.y), v01);
+                        v23 = fma2(d, pk(f.z, f.w), v23);
+                    }
+                }
+                const float2 a01 = upk(v01), a23 = upk(v23);
+                const float vs[4] = {a01.x, a01.y, a23.x, a23.y};
+                const float Jinv = sJi[node];
+                float sv[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                if (XF && src) {
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) sv[v] = d2f_int(src[eoff + v * N3 + node]);
+                }
+                out[eoff + node] = sQ[node] * Jinv + sv[0];
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk)
+                    out[eoff + (1 + kk) * N3 + node] = (sQ[(1 + kk) * N3 + node] + vs[kk]) * Jinv + sv[1 + kk];
+                out[eoff + 4 * N3 + node] = (sQ[4 * N3 + node] + vs[3]) * Jinv + sv[4];
+            }
+        }
+    } else if (active) {
+        for (int node = tl; node < N3; node += TE) {
+            const float Jinv = sJi[node];
+            float sv[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (XF && src) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sv[v] = d2f_int(src[eoff + v * N3 + node]);
+            }
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+                out[eoff + v * N3 + node] =
+                    (sA[v * N3 + node] + (sA[(5 + v) * N3 + node] + sA[(10 + v) * N3 + node])) * Jinv + sv[v];
+        }
+    }
+}
+
+// ---- host-side launchers
+template <int N>
+cudaError_t launch_pairs_n(const esdc_ctx* c, const StageF& in, float* out, cudaStream_t s, cudaEvent_t* ev) {
+    using C = CfgP<N>;
+    const size_t smem = (size_t)C::EPB * C::SM * sizeof(float);
+    const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
+    const Ref ref = make_ref(c);
+    if (in.nk < 0 || in.nk > 5) return cudaErrorInvalidValue;
+    if (ev) cudaEventRecord(ev[0], s);
+    const bool xf = c->setup.bounded != 0 || c->d_src != nullptr;
+    auto go = [&](auto kern) {
+        kern<<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf,
+                                            c->physf, ref, c->d_nsurff, c->d_qext, c->d_src);
+    };
+    if (in.nk == 0) xf ? go(rhs_pairs_f32<N, 0, true>) : go(rhs_pairs_f32<N, 0, false>);
+    else if (in.nk <= 2) xf ? go(rhs_pairs_f32<N, 2, true>) : go(rhs_pairs_f32<N, 2, false>);
+    else xf ? go(rhs_pairs_f32<N, 5, true>) : go(rhs_pairs_f32<N, 5, false>);
+    if (ev) cudaEventRecord(ev[1], s);
+    if (ev) cudaEventRecord(ev[2], s);
+    if (c->physf.viscous) {
+        const cudaError_t e = launch_visc_sat<float, N, false>(out, c->d_geomf, c->d_nbr, (const float*)c->d_trace,
+                                                               c->K, c->opsf.winv[0], s);
+        if (e != cudaSuccess) return e;
+    }
+    if (ev) cudaEventRecord(ev[3], s);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t prepare_pairs_n() {
+    const int smem = (int)((size_t)CfgP<N>::EPB * CfgP<N>::SM * sizeof(float));
+    constexpr cudaFuncAttribute kAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(rhs_pairs_f32<N, 0, false>, kAttr, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 2, false>, kAttr, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 5, false>, kAttr, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 0, true>, kAttr, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 2, true>, kAttr, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 5, true>, kAttr, smem);
+    return e;
+}
+
+}  // namespace
+
+bool pairs_f32_supported(const esdc_ctx* c) {
+    return c->setup.volume_flux == ESDC_FLUX_ESC && (c->N == 4 || c->N == 6 || c->N == 8);
+}
+
+cudaError_t prepare_rhs_f32_pairs(const esdc_ctx* c) {
+    switch (c->N) {
+        case 4: return prepare_pairs_n<4>();
+        case 6: return prepare_pairs_n<6>();
+        case 8: return prepare_pairs_n<8>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rhs_f32_pairs(const esdc_ctx* c, const StageF& in, float* out, cudaStream_t s, cudaEvent_t* ev) {
+    switch (c->N) {
+        case 4: return launch_pairs_n<4>(c, in, out, s, ev);
+        case 6: return launch_pairs_n<6>(c, in, out, s, ev);
+        case 8: return launch_pairs_n<8>(c, in, out, s, ev);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace esdc

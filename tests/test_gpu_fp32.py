@@ -60,6 +60,21 @@ def test_fp32_residual_16cubed_p4_warped_sampled():
     e, c = _report(r[E.cuda()], O.rhs(qo, mesh, gas, elems=E), qo, mesh, gas, elems=E)
     assert max(c) <= C_MAX
     assert e[1] <= 1e-3 and e[2] <= 1e-3 and e[3] <= 1e-3      # momentum (perturbation split)
+    # mass and energy: measured 4.9e-3 and 7.9e-3 on this state (the float32 conditioning floor, see
+    # test_fp32_tgv_mass_energy_miss_the_1e5_target); a regression beyond 2e-2 fails here
+    assert e[0] <= 2e-2 and e[4] <= 2e-2
+
+
+@pytest.mark.xfail(strict=True, reason="float32 state rounding alone gives mass/energy errors of 3e-4..9e-3 "
+                                       "on the unperturbed Taylor-Green state (tests/test_oracle_physics.py "
+                                       "float32 floor); the 1e-5 per-variable target is not reachable there")
+def test_fp32_tgv_mass_energy_miss_the_1e5_target():
+    """Record of the one per-variable target the float32-mixed residual misses: on the unperturbed
+    Taylor-Green state its mass and energy errors stay above 1e-5 (strict xfail: if this ever passes,
+    the record is out of date)."""
+    solver, qg, mesh, gas, qo = make_pair(4, (8, 8, 8), warp=0.1, seed=0, Re=1600.0, precision="fp32")
+    e, _ = _report(solver.rhs(qg), O.rhs(qo, mesh, gas), qo, mesh, gas)
+    assert e[0] <= 1e-5 and e[4] <= 1e-5
 
 
 def test_fp32_rk_steps_and_ke_rate():
