@@ -1114,7 +1114,8 @@ int esdc_rk_adjoint(esdc_ctx* c, const double* ckpt, double dt, int nsteps, doub
     CUDA_TRY(cudaMemsetAsync(c->d_adj_acc, 0, sizeof(double), s));
     for (int step = nsteps - 1; step >= 0; --step) {
         const double* qn = ckpt + (size_t)step * n;
-        // recompute the stage states of this step from its checkpoint
+        // recompute the stage states of this step from its checkpoint: Y_1 = q_n and Y_t from the
+        // stage derivatives k_1 .. k_(t-1), so five residuals (k_6 = f(Y_6) is not needed)
         for (int t = 0; t < 6; ++t) {
             const double* qs = qn;
             if (t > 0) {
@@ -1128,6 +1129,7 @@ int esdc_rk_adjoint(esdc_ctx* c, const double* ckpt, double dt, int nsteps, doub
                 if (e != cudaSuccess) return cuda_fail(e, "adjoint stage recompute");
                 qs = Qs[t];
             }
+            if (t == 5) break;
             st = rhs_impl(c, qs, K6[t], s);
             if (st) return st;
         }

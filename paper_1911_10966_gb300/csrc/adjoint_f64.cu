@@ -22,6 +22,7 @@
 
 #include "esdc_internal.h"
 #include "kernels.h"
+#include "rcp_f64.cuh"
 
 namespace esdc {
 namespace {
@@ -34,8 +35,10 @@ struct CfgA {
     static constexpr int EPB = N3 >= 96 ? 1 : (N3 >= 48 ? 2 : (N3 >= 24 ? 4 : 16));
     static constexpr int THREADS = EPB * N3;
     // shared doubles per element: prim/w 10 | lt 5 | geometry 10 | prim-bar 6 | q-bar 5 | theta-bar 12
+    // (also the own side's interface cotangents, 30 N2, which exceed 12 N3 only at N = 2)
     // | neighbour face w 24 N2
-    static constexpr int SM = 48 * N3 + 24 * N2;
+    static constexpr int TSZ = 12 * N3 > 30 * N2 ? 12 * N3 : 30 * N2;
+    static constexpr int SM = 36 * N3 + TSZ + 24 * N2;
     static constexpr int EPB_F = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
     // resident CTAs the register allocation is sized for (3 at N = 4, 5 measured faster than 2)
     static constexpr int MINB = (N == 4 || N == 5) ? 3 : 1;
@@ -49,21 +52,21 @@ struct PBar {   // cotangents of (rho, u0, u1, u2, beta, usq)
 };
 
 __device__ __forceinline__ void to_prim(const double* q, const Phys& ph, Prim& s) {
-    const double ri = 1.0 / q[0];
+    const double ri = rcp_newton2(q[0]);
     s.rho = q[0];
     s.u0 = q[1] * ri;
     s.u1 = q[2] * ri;
     s.u2 = q[3] * ri;
     s.usq = s.u0 * s.u0 + s.u1 * s.u1 + s.u2 * s.u2;
     const double p = (ph.gamma - 1.0) * (q[4] - 0.5 * q[0] * s.usq);
-    s.beta = 0.5 * q[0] / p;
+    s.beta = 0.5 * q[0] * rcp_newton2(p);
 }
 
 // pull a primitive cotangent back to the conserved variables at state s
 __device__ __forceinline__ void pbar_to_q(const Prim& s, const PBar& b, const Phys& ph, double qb[5]) {
     const double gm1 = ph.gamma - 1.0;
     const double ut0 = b.u0 + 2.0 * s.u0 * b.usq, ut1 = b.u1 + 2.0 * s.u1 * b.usq, ut2 = b.u2 + 2.0 * s.u2 * b.usq;
-    const double ri = 1.0 / s.rho;
+    const double ri = rcp_newton2(s.rho);
     // beta = rho/(2p): d beta = beta/rho d rho - beta/p d p, and beta/p = 2 beta^2/rho
     const double pb = -b.beta * 2.0 * s.beta * s.beta * ri;
     qb[0] = b.rho + b.beta * s.beta * ri + pb * gm1 * 0.5 * s.usq - (ut0 * s.u0 + ut1 * s.u1 + ut2 * s.u2) * ri;
@@ -73,37 +76,43 @@ __device__ __forceinline__ void pbar_to_q(const Prim& s, const PBar& b, const Ph
     qb[4] = pb * gm1;
 }
 
-// Logarithmic mean and its partial derivatives.  Series branch (u = ((a-b)/(a+b))^2 < 1e-4):
-// L = (a+b)/(2F(u)), F = artanh(f)/f = 1 + u/3 + u^2/5 + ..., dL/da = G/2 - 2 f b F'(u) G^2/(a+b)
-// with G = 1/F; otherwise L = (a-b)/l, l = log(a/b), dL/da = (1 - L/a)/l, dL/db = (L/b - 1)/l.
-__device__ __forceinline__ void ln_mean_d(double a, double b, double& L, double& La, double& Lb) {
+// Logarithmic mean, its partial derivatives and its reciprocal, given rs = 1/(a+b).  Series branch
+// (u = ((a-b)/(a+b))^2 < 1e-4): with F(u) = artanh(f)/f = 1 + u/3 + u^2/5 + u^3/7 + u^4/9 and
+// G = 1/F = 1 - u/3 - 4u^2/45 - 44u^3/945, L = (a+b) G/2, 1/L = 2 F/(a+b) and
+// dL/da = G/2 - 2 f b F'(u) G^2/(a+b), dL/db = G/2 + 2 f a F'(u) G^2/(a+b); otherwise L = (a-b)/l,
+// l = log(a/b), dL/da = (1 - L/a)/l, dL/db = (L/b - 1)/l.
+__device__ __forceinline__ void ln_mean_d(double a, double b, double rs, double& L, double& La, double& Lb,
+                                          double& IL) {
     const double d = a - b, s = a + b;
-    const double f = d / s;
+    const double f = d * rs;
     const double u = f * f;
     if (u < 1.0e-4) {
-        const double G = 1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0)));
-        const double Fp = 1.0 / 3.0 + u * (2.0 / 5.0 + u * (3.0 / 7.0 + u * (4.0 / 9.0)));
+        const double G = fma(u, fma(u, fma(u, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
+        const double Fp = fma(u, fma(u, fma(u, 4.0 / 9.0, 3.0 / 7.0), 2.0 / 5.0), 1.0 / 3.0);
+        const double F = fma(u, fma(u, fma(u, fma(u, 1.0 / 9.0, 1.0 / 7.0), 1.0 / 5.0), 1.0 / 3.0), 1.0);
         L = 0.5 * s * G;
-        const double t = 2.0 * f * Fp * G * G / s;
-        La = 0.5 * G - t * b;
-        Lb = 0.5 * G + t * a;
+        const double t = 2.0 * f * Fp * G * G * rs;
+        La = fma(-t, b, 0.5 * G);
+        Lb = fma(t, a, 0.5 * G);
+        IL = 2.0 * F * rs;
     } else {
         const double l = log(a / b);
         L = d / l;
         La = (1.0 - L / a) / l;
         Lb = (L / b - 1.0) / l;
+        IL = l / d;
     }
 }
 
 // Reverse of the contracted Chandrashekar flux: given the cotangent mu[5] of f(a, b; n), add the
-// primitive cotangents of both states to ab, bb.
+// primitive cotangents of both states to ab, bb.  Two reciprocals per pair, 1/(rho_a + rho_b) and
+// 1/(beta_a + beta_b); the latter serves p_t and, with the series, the reciprocal of the beta log mean.
 __device__ __forceinline__ void ec_flux_vjp(const Prim& a, const Prim& b, double n0, double n1, double n2,
                                             const double mu[5], const Phys& ph, PBar& ab, PBar& bb) {
-    double Lr, Lra, Lrb, Lb, Lba, Lbb;
-    ln_mean_d(a.rho, b.rho, Lr, Lra, Lrb);
-    ln_mean_d(a.beta, b.beta, Lb, Lba, Lbb);
-    const double IBL = 1.0 / Lb;
-    const double rsb = 1.0 / (a.beta + b.beta);
+    double Lr, Lra, Lrb, Lb, Lba, Lbb, ILr, IBL;
+    const double rsb = rcp_newton2(a.beta + b.beta);
+    ln_mean_d(a.rho, b.rho, rcp_newton1(a.rho + b.rho), Lr, Lra, Lrb, ILr);
+    ln_mean_d(a.beta, b.beta, rsb, Lb, Lba, Lbb, IBL);
     const double ub0 = 0.5 * (a.u0 + b.u0), ub1 = 0.5 * (a.u1 + b.u1), ub2 = 0.5 * (a.u2 + b.u2);
     const double un = ub0 * n0 + ub1 * n1 + ub2 * n2;
     const double pt = 0.5 * (a.rho + b.rho) * rsb;
@@ -144,7 +153,7 @@ __device__ __forceinline__ void ec_flux_vjp(const Prim& a, const Prim& b, double
 // f5 = f1 e_bar + p_bar u_bar.n.  Adds the primitive cotangents of both states to ab, bb.
 __device__ __forceinline__ void kg_flux_vjp(const Prim& a, const Prim& b, double n0, double n1, double n2,
                                             const double mu[5], const Phys& ph, PBar& ab, PBar& bb) {
-    const double RTa = 0.5 / a.beta, RTb = 0.5 / b.beta;
+    const double RTa = 0.5 * rcp_newton2(a.beta), RTb = 0.5 * rcp_newton2(b.beta);
     const double rb = 0.5 * (a.rho + b.rho);
     const double ub0 = 0.5 * (a.u0 + b.u0), ub1 = 0.5 * (a.u1 + b.u1), ub2 = 0.5 * (a.u2 + b.u2);
     const double pb = 0.5 * (a.rho * RTa + b.rho * RTb);
@@ -179,7 +188,7 @@ __device__ __forceinline__ void kg_flux_vjp(const Prim& a, const Prim& b, double
 // and H = gamma/(gamma-1) RT + |u|^2/2.  Adds the primitive cotangents of the state to sb.
 __device__ __forceinline__ void euler_flux_vjp(const Prim& s, double n0, double n1, double n2, const double mu[5],
                                                const Phys& ph, PBar& sb) {
-    const double RT = 0.5 / s.beta;
+    const double RT = 0.5 * rcp_newton2(s.beta);
     const double un = s.u0 * n0 + s.u1 * n1 + s.u2 * n2;
     const double H = ph.gamma * ph.inv_gm1 * RT + 0.5 * s.usq;
     const double A = s.rho * un;                                   // mass flux
@@ -257,7 +266,8 @@ __device__ __noinline__ double face_avg_vjp(const Prim& a, const Prim& b, double
     for (int k = 0; k < 3; ++k) jw[1 + k] = 2.0 * (a.beta * ua[k] - b.beta * uv[k]);
     jw[4] = -2.0 * (a.beta - b.beta);
     double L, La, Lb;
-    ln_mean_d(a.rho, b.rho, L, La, Lb);
+    double IL;
+    ln_mean_d(a.rho, b.rho, 1.0 / (a.rho + b.rho), L, La, Lb, IL);
     const double sb = a.beta + b.beta;
     const double p = 0.5 * (a.rho + b.rho) / sb;
     double u[3], m[3];
@@ -430,7 +440,7 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
     double* sB = sG + 10 * N3;                          // [6][N3] primitive cotangents
     double* sQ = sB + 6 * N3;                           // [5][N3] direct conserved cotangents
     double* sT = sQ + 5 * N3;                           // [12][N3] theta-bar
-    double* sWf = sT + 12 * N3;                         // [6][4][N2]
+    double* sWf = sT + CfgA<N>::TSZ;                    // [6][4][N2]
     const int64_t eoff = el * 5 * N3;
     double mu_acc = 0.0;
 
@@ -452,7 +462,7 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
         sP[9 * N3 + node] = -2.0 * s.beta;
 #pragma unroll
         for (int c = 0; c < 10; ++c) sG[c * N3 + node] = geom[(el * 10 + c) * N3 + node];
-        const double Jinv = 1.0 / sG[node];
+        const double Jinv = rcp_newton2(sG[node]);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             sL[v * N3 + node] = lam[eoff + v * N3 + node] * Jinv;
@@ -527,11 +537,16 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
     }
     __syncthreads();
 
-    // ---- inviscid interface term: own cotangents here, neighbour cotangents to gbuf
+    // ---- inviscid interface term, all six faces at once: the own side's conserved cotangents to a
+    // face buffer (sT, free until the viscous part), gathered per node below; the neighbour's
+    // cotangents to gbuf
+    double* sFo = sT;                                   // [5][6 N2]
+    if (active) {
 #pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-        if (active && node < 2 * N2) {
-            const int side = node / N2, fi = node - side * N2;
+        for (int fn = node; fn < 6 * N2; fn += N3) {
+            const int l = fn / (2 * N2);
+            const int rem = fn - l * 2 * N2;
+            const int side = rem / N2, fi = rem - side * N2;
             const int st = dir_stride<N>(l);
             const int base = line_base<N>(l, fi % N, fi / N);
             const int own = base + (side ? (N - 1) * st : 0);
@@ -581,7 +596,8 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                 const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
                 const double uo = so.u0 * n0 + so.u1 * n1 + so.u2 * n2;
                 const double un_ = sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2;
-                const double co = sqrt(0.5 * ph.gamma / so.beta), cn = sqrt(0.5 * ph.gamma / sn.beta);
+                const double ibo = rcp_newton2(so.beta), ibn = rcp_newton2(sn.beta);
+                const double co = sqrt(0.5 * ph.gamma * ibo), cn = sqrt(0.5 * ph.gamma * ibn);
                 const double lo = fabs(uo) + co * nn, ln = fabs(un_) + cn * nn;
                 const double lam2 = 0.5 * fmax(lo, ln);
                 double lb = 0.0;
@@ -600,18 +616,13 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                 bn.u0 += sn_ * n0;
                 bn.u1 += sn_ * n1;
                 bn.u2 += sn_ * n2;
-                bo.beta += lob * nn * (-0.5 * co / so.beta);
-                bn.beta += lnb * nn * (-0.5 * cn / sn.beta);
+                bo.beta += lob * nn * (-0.5 * co * ibo);
+                bn.beta += lnb * nn * (-0.5 * cn * ibn);
             }
-            sB[own] += bo.rho;
-            sB[N3 + own] += bo.u0;
-            sB[2 * N3 + own] += bo.u1;
-            sB[3 * N3 + own] += bo.u2;
-            sB[4 * N3 + own] += bo.beta;
-            sB[5 * N3 + own] += bo.usq;
-#pragma unroll
-            for (int v = 0; v < 5; ++v) sQ[v * N3 + own] += qbo[v];
             double qb[5];
+            pbar_to_q(so, bo, ph, qb);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sFo[v * 6 * N2 + fn] = qb[v] + qbo[v];
             pbar_to_q(sn, bn, ph, qb);
             double* gb = gbuf + ((el * 6 + 2 * l + side) * 5) * N2 + fi;
 #pragma unroll
@@ -622,8 +633,22 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
             wf[2 * N2] = 2.0 * sn.beta * sn.u2;
             wf[3 * N2] = -2.0 * sn.beta;
         }
-        __syncthreads();
     }
+    __syncthreads();
+    if (active) {
+        const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int ia = a == 0 ? i1 : (a == 1 ? i2 : i3);
+            if (ia == 0 || ia == N - 1) {
+                const int fi = a == 0 ? (i2 + N * i3) : (a == 1 ? (i1 + N * i3) : (i1 + N * i2));
+                const int fn = (2 * a + (ia == N - 1)) * N2 + fi;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sQ[v * N3 + node] += sFo[v * 6 * N2 + fn];
+            }
+        }
+    }
+    __syncthreads();
 
     // ---- viscous chain, reversed node by node
     if (ph.viscous) {
@@ -654,7 +679,7 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                     for (int k = 0; k < 4; ++k) th[a][k] += E * (wf[k * N2] - wown[k]) * ops.winv[ia];
                 }
             }
-            const double Jinv = 1.0 / sG[node];
+            const double Jinv = rcp_newton2(sG[node]);
             double g[3][4];
 #pragma unroll
             for (int m = 0; m < 3; ++m)
@@ -663,7 +688,7 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                     g[m][k] = Jinv * (sG[(1 + m) * N3 + node] * th[0][k] + sG[(4 + m) * N3 + node] * th[1][k] +
                                       sG[(7 + m) * N3 + node] * th[2][k]);
             const double beta = sP[4 * N3 + node];
-            const double RT = 0.5 / beta;
+            const double RT = 0.5 * rcp_newton2(beta);
             const double u[3] = {sP[N3 + node], sP[2 * N3 + node], sP[3 * N3 + node]};
             double du[3][3];
 #pragma unroll
@@ -699,7 +724,7 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                     const int side = il == N - 1;
                     const int st2 = dir_stride<N>(l);
                     const int nbn = node + (side ? -(N - 1) * st2 : (N - 1) * st2);   // matching node in nb
-                    const double Jn = 1.0 / geom[nb * 10 * N3 + nbn];
+                    const double Jn = rcp_newton2(geom[nb * 10 * N3 + nbn]);
                     const double E = side ? 0.5 : -0.5;
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
@@ -747,7 +772,7 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                     ub[k] += RT * g[m][3] * dub[k][m];
                     RTb += (g[m][k] + u[k] * g[m][3]) * dub[k][m];
                 }
-            bb += RTb * (-0.5 / (beta * beta));
+            bb += RTb * (-2.0 * RT * RT);                 // dRT/dbeta = -1/(2 beta^2) = -2 RT^2
             // g = J^-1 sum_a Ja_am theta_a  ->  theta-bar
 #pragma unroll
             for (int a = 0; a < 3; ++a)

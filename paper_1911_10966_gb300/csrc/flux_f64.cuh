@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "esdc_internal.h"
+#include "rcp_f64.cuh"
 
 namespace esdc {
 namespace {
@@ -17,8 +18,6 @@ struct Prim {
     double hr, hu0, hu1, hu2, beta, qq;
 };
 
-// forward declarations of the reciprocal helpers defined below
-__device__ __forceinline__ double rcp_newton2(double x);
 
 // Primitives of a conserved state, plus RT = p/rho and the sound speed c = sqrt(gamma p/rho).
 __device__ __forceinline__ void to_prim(const double* q, const Phys& ph, Prim& s, double& RT, double& c) {
@@ -34,22 +33,6 @@ __device__ __forceinline__ void to_prim(const double* q, const Phys& ph, Prim& s
     s.qq = 0.25 * usq;
     RT = p * ri;
     c = sqrt(ph.gamma * RT);
-}
-
-// Reciprocal by Newton-Raphson on g(r) = 1/r - x from the hardware approximation (about 23 bits):
-// each step r <- r + r (1 - x r) doubles the number of correct bits.
-__device__ __forceinline__ double rcp_approx(double x) {
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    return r;
-}
-__device__ __forceinline__ double rcp_newton1(double x) {     // ~46 bits
-    const double r = rcp_approx(x);
-    return fma(r, fma(-x, r, 1.0), r);
-}
-__device__ __forceinline__ double rcp_newton2(double x) {     // full double precision (within an ulp)
-    double r = rcp_newton1(x);
-    return fma(r, fma(-x, r, 1.0), r);
 }
 
 // u = ((a-b)/(a+b))^2 < 1e-4, tested on the high word (integer pipe): the threshold moves by less
