@@ -1080,15 +1080,19 @@ def _stable_cfl(s, q0, steps=100, lo=0.25, hi=4.0, tol=0.02):
     return lo
 
 
-def study_ipsweep(Re_oddeven=100.0, steps_oddeven=200):
-    """The interior-penalty coefficient sweep (the IP term of eq. NSL): sigma in IP_SIGMAS.
+def study_ipsweep(Re_jump=100.0, steps_jump=200):
+    """The interior-penalty coefficient sweep (the IP term of eq. NSL), sigma in IP_SIGMAS.  The term
+    acts only on jumps of the entropy variables across element faces.
     (1) Manufactured solution (Re 4e6, exact Dirichlet data), p = 3, 4 on 8^3 elements: P-norm L2
         error of rho after 1.5 flow-through times.
-    (2) The 16^3 warped p = 4 Taylor-Green workload (Re 1600): entropy production sum P J w.dq/dt of
-        the initial state, and the largest stable CFL number over 100 DP5 steps.
-    (3) Odd-even damping: a uniform flow (Ma 0.1) on the 8^3 warped p = 4 box with a node-wise
-        alternating density perturbation of 1e-3 (pressure uniform) at Re_oddeven: the P-norm L2 norm of
-        the perturbation after steps_oddeven DP5 steps at CFL 0.5, relative to its initial norm."""
+    (2) The 16^3 warped p = 4 Taylor-Green workload (Re 1600): entropy and kinetic-energy rates of the
+        state after 100 DP5 steps at CFL 0.5 (the initial state is continuous, so the term is zero
+        there), and the largest stable CFL number over 100 DP5 steps.
+    (3) Element-wise jumps: a uniform flow (Ma 0.1, u = (0.3, 0.2, 0.1)) on the 8^3 warped p = 4 box
+        with a density perturbation of +-1e-3 alternating from element to element (pressure uniform),
+        at Re_jump, with the local Lax-Friedrichs interface dissipation and without it (EC): the
+        entropy rate of that state, the P-norm L2 norm of the perturbation after steps_jump DP5 steps
+        at CFL 0.5 relative to its initial norm, and the largest stable CFL."""
     from paper_1911_10966_gb300 import inputs as I
     from paper_1911_10966_gb300.solver import Solver
     for p in (3, 4):
@@ -1097,39 +1101,41 @@ def study_ipsweep(Re_oddeven=100.0, steps_oddeven=200):
             print(json.dumps({"study": "ipsweep", "case": "mms_8cubed", "p": p, "sigma": sig, "l2_rho": l2,
                               "steps": nsteps, "dt": dt, "wall_s": wall}), flush=True)
     W = TGV_WARPED
-    coords = None
+    x = I.box_coords(_lgl_nodes(W["p"]), W["k"], W["k"], W["k"], *PI_BOX, warp=W["warp"], seed=W["seed"])
     for sig in IP_SIGMAS:
-        s = Solver(W["p"], W["k"], W["k"], W["k"], coords if coords is not None else
-                   I.box_coords(_lgl_nodes(W["p"]), W["k"], W["k"], W["k"], *PI_BOX, warp=W["warp"], seed=W["seed"]),
-                   Ma=W["Ma"], Re=W["Re"], ip_coef=sig)
-        coords = s.coords
-        q = s.init_state("tgv")
+        s = Solver(W["p"], W["k"], W["k"], W["k"], x, Ma=W["Ma"], Re=W["Re"], ip_coef=sig)
+        q0 = s.init_state("tgv")
+        q = q0.clone()
+        s.rk_step(q, s.dt_cfl(q0, 0.5), 100)
         b = s.budgets(q, s.rhs(q))
         print(json.dumps({"study": "ipsweep", "case": "tgv_16cubed_p4_warped", "sigma": sig,
-                          "entropy_rate": b[2], "ke_rate": b[3], "stable_cfl_100_steps": _stable_cfl(s, q)}),
-              flush=True)
+                          "entropy_rate_after_100_steps": b[2], "ke_rate_after_100_steps": b[3],
+                          "stable_cfl_100_steps": _stable_cfl(s, q0)}), flush=True)
         s.close()
     k, p, Ma = 8, 4, 0.1
-    xi = _lgl_nodes(p)
-    x = I.box_coords(xi, k, k, k, *PI_BOX, warp=0.1, seed=0)
+    x = I.box_coords(_lgl_nodes(p), k, k, k, *PI_BOX, warp=0.1, seed=0)
     N = p + 1
-    i = np.arange(N)
-    sign = (-1.0) ** (i[:, None, None] + i[None, :, None] + i[None, None, :])
+    e = np.arange(k ** 3)
+    parity = (-1.0) ** ((e % k) + (e // k) % k + e // (k * k))
     R = 1.0 / (1.4 * Ma * Ma)
-    rho = np.broadcast_to(1.0 + 1e-3 * sign, (x.shape[0], N, N, N)).copy()
+    rho = np.broadcast_to((1.0 + 1e-3 * parity)[:, None, None, None], (k ** 3, N, N, N)).copy()
     u = (0.3, 0.2, 0.1)
     q_np = I.primitive_to_conserved(rho, [np.full_like(rho, c) for c in u], np.full_like(rho, R), 1.4)
     base = I.freestream(x, u=u, Ma=Ma)
-    for sig in IP_SIGMAS:
-        s = Solver(p, k, k, k, x, Ma=Ma, Re=float(Re_oddeven), ip_coef=sig)
-        q = s.to_device(q_np)
+    for diss, sig in [(d, g) for d in (True, False) for g in IP_SIGMAS]:
+        s = Solver(p, k, k, k, x, Ma=Ma, Re=float(Re_jump), ip_coef=sig, dissipation=diss)
+        q0 = s.to_device(q_np)
         qb = s.to_device(base)
-        n0 = _p_norm_l2(s, q, qb)
-        dt = s.dt_cfl(q, 0.5)
-        s.rk_step(q, dt, int(steps_oddeven))
-        print(json.dumps({"study": "ipsweep", "case": "oddeven_8cubed_p4_warped", "Re": float(Re_oddeven),
-                          "sigma": sig, "steps": int(steps_oddeven), "dt": dt,
-                          "perturbation_rel_norm": _p_norm_l2(s, q, qb) / n0}), flush=True)
+        n0 = _p_norm_l2(s, q0, qb)
+        b = s.budgets(q0, s.rhs(q0))
+        q = q0.clone()
+        dt = s.dt_cfl(q0, 0.5)
+        s.rk_step(q, dt, int(steps_jump))
+        print(json.dumps({"study": "ipsweep", "case": "element_jumps_8cubed_p4_warped", "Re": float(Re_jump),
+                          "interface_dissipation": "llf" if diss else "none", "sigma": sig,
+                          "entropy_rate": b[2], "steps": int(steps_jump), "dt": dt,
+                          "perturbation_rel_norm": _p_norm_l2(s, q, qb) / n0,
+                          "stable_cfl_100_steps": _stable_cfl(s, q0)}), flush=True)
         s.close()
 
 
