@@ -120,13 +120,25 @@ LAUNCHER_MARK = b"// ---- host-side launchers"
 
 def _sha(path):
     """Hash of a kernel source file up to its host-side launcher section (the device code), followed
-    by the float64 device functions it includes (flux_f64.cuh) when they sit beside it."""
+    by the local device headers it includes (recursively, each once)."""
+    import re
     data = open(path, "rb").read()
     cut = data.find(LAUNCHER_MARK)
     data = data[:cut] if cut >= 0 else data
-    inc = os.path.join(os.path.dirname(path), "flux_f64.cuh")
-    if b'#include "flux_f64.cuh"' in data and os.path.exists(inc):
-        data += open(inc, "rb").read()
+    seen = set()
+
+    def add(buf):
+        out = b""
+        for name in re.findall(rb'#include "([A-Za-z0-9_]+\.cuh)"', buf):
+            f = os.path.join(os.path.dirname(path), name.decode())
+            if name in seen or not os.path.exists(f):
+                continue
+            seen.add(name)
+            inc = open(f, "rb").read()
+            out += inc + add(inc)
+        return out
+
+    data += add(data)
     return hashlib.sha256(data).hexdigest()[:16]
 
 
@@ -647,9 +659,9 @@ def _fp32_object(p, n, ms_step, kernel_ms, face_ms, peak32, e_v, ws, dist, devic
         roof = {"bound": "hbm", "achieved": by / (kernel_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_source": hbm_src}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof.update({"kernel": f"rhs_main_f32<{p + 1}>", "kernel_ms": kernel_ms, "face_kernel_ms": face_ms,
+    roof.update({"kernel": f"rhs_pairs_f32<{p + 1}>", "kernel_ms": kernel_ms, "face_kernel_ms": face_ms,
                  "flops_per_launch": fl, "bytes_per_launch": by,
-                 "traffic": _ncu_traffic("rhs_main_f32_tgv_p7.md", _src("rhs_f32.cu"), n),
+                 "traffic": _ncu_traffic("rhs_pairs_f32_tgv_p7.md", _src("rhs_f32_pairs.cu"), n),
                  "alu_frac": fl / (kernel_ms * 1e-3) / peak32, "hbm_frac": by / (kernel_ms * 1e-3) / (hbm * 1e9)})
     ms_max = max_over_ranks(ms_step, dist, device)
     return {"value": replica_throughput(n, ws, ms_max), "unit": "node-RHS/s", "ms_per_step": ms_max,

@@ -184,8 +184,12 @@ int rk_step_f64(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStr
 // Multi-step esdc_rk_step: one step is captured once as a CUDA graph on a private stream and replayed
 // nsteps times on the caller's stream, so the ~20 launches of a step cost one graph launch.  The
 // graph bakes in the state, workspace, step size and optional-term pointers; any change recaptures.
-// Returns ESDC_OK, or 1 when the graph could not be built (the caller then launches directly).
+// While esdc_profile is on, no graph is used: a replayed graph would repeat the event records of
+// its capture without the counts that esdc_profile_read reports, so profiled steps launch directly.
+// Returns ESDC_OK, or 1 when the graph could not be built or is not used (the caller then launches
+// directly).
 int rk_steps_graph(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s) {
+    if (c->profiling) return 1;
     const void* key[5] = {q, ws, c->d_qext, c->d_src, (const void*)(intptr_t)c->setup.precision};
     bool valid = c->graph_exec != nullptr && c->graph_dt == dt;
     for (int i = 0; i < 5 && valid; ++i) valid = key[i] == c->graph_key[i];

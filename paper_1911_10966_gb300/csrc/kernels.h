@@ -89,8 +89,8 @@ struct StageF {             // residual input base + sum_j c_j k_j (float32 pert
 };
 cudaError_t prepare_rhs_f32(const esdc_ctx* c);
 cudaError_t launch_rhs_f32(const esdc_ctx* c, const StageF& in, float* out, cudaStream_t s, cudaEvent_t* ev);
-// the ES-C float32 residual for N = 4, 6, 8 with packed (f32x2) pair evaluation (rhs_f32_pairs.cu),
-// taken by the two above where supported
+// the ES-C float32 residual with packed (f32x2) pair evaluation (rhs_f32_pairs.cu; built for N = 4,
+// 6, 8, taken for N = 4, 8), called by the two above where supported
 bool pairs_f32_supported(const esdc_ctx* c);
 cudaError_t prepare_rhs_f32_pairs(const esdc_ctx* c);
 cudaError_t launch_rhs_f32_pairs(const esdc_ctx* c, const StageF& in, float* out, cudaStream_t s, cudaEvent_t* ev);

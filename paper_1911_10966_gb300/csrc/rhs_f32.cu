@@ -46,8 +46,11 @@ struct CfgF {
     static constexpr int KG_OFF = (8 + 4 + 12 + 18 + 5) * N3 + 24 * N2;
     static constexpr int SM = (KG_OFF + (KG ? (KG_OFF & 1) + 2 * N3 : 0) + 3) / 4 * 4;
     // resident CTAs the registers are sized for (N = 5: one element of 125 threads per CTA, six CTAs
-    // per SM measured 10% faster than three CTAs of two elements)
-    static constexpr int MINB = N <= 4 ? 4 : (N == 5 ? 6 : 2);
+    // per SM measured 10% faster than three CTAs of two elements), capped by the CTAs whose shared
+    // memory fits one SM (228 KB, 1 KB reserved per CTA): the SF-KG instances need more of it
+    static constexpr int MINB0 = N <= 4 ? 4 : (N == 5 ? 6 : 2);
+    static constexpr int BY_SMEM = (228 * 1024) / (EPB * SM * 4 + 1024);
+    static constexpr int MINB = BY_SMEM < 1 ? 1 : (BY_SMEM < MINB0 ? BY_SMEM : MINB0);
 };
 
 // Kennedy-Gruber two-point flux (the SF-KG variant, Sec. 4) split as above: with arithmetic means
@@ -95,7 +98,7 @@ __device__ __forceinline__ void load_prim_half(const float4* sP4, int N3, int id
 // XF: boundary faces (bounded boxes) and a source term, compiled only into the instantiations that
 // need them (a run-time test for them cost 2% on periodic boxes)
 template <int N, int NK, bool XF, bool KG>
-__global__ void __launch_bounds__(CfgF<N>::THREADS, CfgF<N>::MINB)
+__global__ void __launch_bounds__(CfgF<N>::THREADS, CfgF<N, KG>::MINB)
 rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom,
              const int32_t* __restrict__ nbr, float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph,
              const Ref ref, const float* __restrict__ nsurf, const double* __restrict__ qext,
