@@ -218,6 +218,29 @@ __device__ __forceinline__ void ec_flux_folded(const PrimF& a, const PrimF& b, f
     F[4] = fmaf(r.H0, un, df[4]);
 }
 
+// Two lanes of to_prim_f: packed primitives of two float32 perturbation states (the pair-loop form:
+// half density perturbation, beta/beta0 - 1, half velocity; u = 2 hu is formed where needed).
+struct PrimP {
+    f2p hdr, dbn, hu0, hu1, hu2;
+};
+__device__ __forceinline__ PrimP to_prim2(const f2p dq[5], const Ref& r) {
+    const f2p rho = add2(bc(r.rho0), dq[0]);
+    const float2 rv = upk(rho);
+    const f2p ri = pk(frcp(rv.x), frcp(rv.y));
+    const f2p u0 = mul2(dq[1], ri), u1 = mul2(dq[2], ri), u2 = mul2(dq[3], ri);
+    const f2p usq = fma2(u2, u2, fma2(u1, u1, mul2(u0, u0)));
+    const f2p dp = mul2(bc(r.gm1), fma2(bc(-0.5f), mul2(rho, usq), dq[4]));
+    const float2 den = upk(add2(bc(r.p0), dp));
+    const f2p ip = pk(frcp(den.x), frcp(den.y));
+    PrimP s;
+    s.dbn = mul2(mul2(fma2(bc(-r.rho0), dp, mul2(dq[0], bc(r.p0))), ip), bc(r.inv_rho0));
+    s.hdr = mul2(bc(0.5f), dq[0]);
+    s.hu0 = mul2(bc(0.5f), u0);
+    s.hu1 = mul2(bc(0.5f), u1);
+    s.hu2 = mul2(bc(0.5f), u2);
+    return s;
+}
+
 template <int N, int NK, bool XF>
 __global__ void __launch_bounds__(CfgP<N>::THREADS, CfgP<N>::MINB)
 rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom, const int32_t* __restrict__ nbr,
@@ -380,65 +403,151 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
     }
     __syncthreads();
 
-    // ---- interface SAT, all six faces at once; face nodes of direction l add into the direction-l sums
-    if (active) {
+    // ---- interface SAT, all six faces at once; face nodes of direction l add into the direction-l sums.
+    // With two face nodes per thread (FPT == 2) they are the two lanes of packed instructions.
+    if constexpr (FPT == 2) {
+        if (active) {
+            int fnv[2], lv[2], sidev[2], fiv[2], ownv[2], jov[2];
+            float qn[2][5], so[2][5], nv[2][3], qo[2][5];
 #pragma unroll
-        for (int f = 0; f < FPT; ++f) {
-            const int fn = tl + f * TE;
-            if (fn >= 6 * N2) break;
-            const int l = fn / (2 * N2);
-            const int rem = fn - l * 2 * N2;
-            const int side = rem / N2, fi = rem - side * N2;
-            const int st = dir_stride_f<N>(l);
-            const int base = line_base_f<N>(l, fi % N, fi / N);
-            const int own = base + (side ? (N - 1) * st : 0);
-            const int jo = side ? N - 1 : 0;
-            float qn[5];
+            for (int h = 0; h < 2; ++h) {
+                // a thread without a second face node repeats its first in lane y and drops its result
+                const int fn = (h == 1 && tl + TE < 6 * N2) ? tl + TE : tl;
+                const int l = fn / (2 * N2);
+                const int rem = fn - l * 2 * N2;
+                const int side = rem / N2, fi = rem - side * N2;
+                const int st = dir_stride_f<N>(l);
+                const int own = line_base_f<N>(l, fi % N, fi / N) + (side ? (N - 1) * st : 0);
+                const int jo = side ? N - 1 : 0;
+                fnv[h] = fn; lv[h] = l; sidev[h] = side; fiv[h] = fi; ownv[h] = own; jov[h] = jo;
+                const int own0 = lidx<N>(own / N, own % N);    // the natural order is direction 0's
 #pragma unroll
-            for (int v = 0; v < 5; ++v) qn[v] = sNq[v * 6 * N2 + fn];
-            PrimF so, sn;
-            const int own0 = lidx<N>(own / N, own % N);    // the natural order is direction 0's
-            so.hdr = sL[own0];
-            so.dbn = sL[N3 + own0];
-            so.hu0 = sL[2 * N3 + own0];
-            so.hu1 = sL[3 * N3 + own0];
-            so.hu2 = sL[4 * N3 + own0];
-            so.u0 = 2.0f * so.hu0;
-            so.u1 = 2.0f * so.hu1;
-            so.u2 = 2.0f * so.hu2;
-            to_prim_f(qn, ref, sn);
-            const float* Ln = sL + (l * 8 + 5) * N3 + lidx<N>(fi, jo);
-            float n0 = Ln[0], n1 = Ln[N3], n2 = Ln[2 * N3];
-            if (nsurf) {   // optimized metrics: the interface terms take the surface metrics
-                const float* ns = nsurf + (el * 6 + 2 * l + side) * 3 * N2 + fi;
-                n0 = ns[0];
-                n1 = ns[N2];
-                n2 = ns[2 * N2];
+                for (int c = 0; c < 5; ++c) {
+                    qn[h][c] = sNq[c * 6 * N2 + fn];
+                    so[h][c] = sL[c * N3 + own0];
+                    qo[h][c] = sQ[c * N3 + own];
+                }
+                const float* Ln = sL + (l * 8 + 5) * N3 + lidx<N>(fi, jo);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) nv[h][m] = Ln[m * N3];
+                if (nsurf) {   // optimized metrics: the interface terms take the surface metrics
+                    const float* ns = nsurf + (el * 6 + 2 * l + side) * 3 * N2 + fi;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) nv[h][m] = ns[m * N2];
+                }
             }
-            float F[5];
-            ec_flux_folded(so, sn, n0, n1, n2, ref, F);
-            const float E = side ? 1.0f : -1.0f;
-            float lam = 0.0f;
+            f2p QN[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) QN[c] = pk(qn[0][c], qn[1][c]);
+            const PrimP sn = to_prim2(QN, ref);
+            const f2p oh = pk(so[0][0], so[1][0]), od = pk(so[0][1], so[1][1]);
+            const f2p ou0 = pk(so[0][2], so[1][2]), ou1 = pk(so[0][3], so[1][3]), ou2 = pk(so[0][4], so[1][4]);
+            const f2p n0 = pk(nv[0][0], nv[1][0]), n1 = pk(nv[0][1], nv[1][1]), n2 = pk(nv[0][2], nv[1][2]);
+            const KP k = make_kp(ref);
+            f2p F[5];
+            // the interface flux takes n itself: a-side n, b-side 0 (ec_flux2 sums the two)
+            ec_flux2(oh, od, ou0, ou1, ou2, add2(ou0, ou0), add2(ou1, ou1), add2(ou2, ou2), n0, n1, n2, sn.hdr,
+                     sn.dbn, sn.hu0, sn.hu1, sn.hu2, 0ull, 0ull, 0ull, k, ref, F);
+            f2p lam = 0ull;
             if (ph.dissipation) {
-                const float nn = fsqrt(n0 * n0 + n1 * n1 + n2 * n2);
-                const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + fsqrt(ref.gamma * node_RT(so.dbn, ref)) * nn;
-                const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + fsqrt(ref.gamma * node_RT(sn.dbn, ref)) * nn;
-                lam = 0.5f * fmaxf(lo, ln);
+                const float2 nn2 = upk(fma2(n2, n2, fma2(n1, n1, mul2(n0, n0))));
+                const f2p nn = pk(fsqrt(nn2.x), fsqrt(nn2.y));
+                // |u.n| + c |n| on both sides, u = 2 hu, c^2 = gamma RT = gamma RT0 / (1 + dbn)
+                const float2 uo = upk(mul2(bc(2.0f), fma2(ou2, n2, fma2(ou1, n1, mul2(ou0, n0)))));
+                const float2 un = upk(mul2(bc(2.0f), fma2(sn.hu2, n2, fma2(sn.hu1, n1, mul2(sn.hu0, n0)))));
+                const float2 dpo = upk(add2(bc(1.0f), od)), dpn = upk(add2(bc(1.0f), sn.dbn));
+                const float gRT0 = ref.gamma * ref.RT0;
+                const f2p co = pk(fsqrt(gRT0 * frcp(dpo.x)), fsqrt(gRT0 * frcp(dpo.y)));
+                const f2p cn = pk(fsqrt(gRT0 * frcp(dpn.x)), fsqrt(gRT0 * frcp(dpn.y)));
+                const float2 lo = upk(fma2(co, nn, pk(fabsf(uo.x), fabsf(uo.y))));
+                const float2 ln = upk(fma2(cn, nn, pk(fabsf(un.x), fabsf(un.y))));
+                lam = pk(0.5f * fmaxf(lo.x, ln.x), 0.5f * fmaxf(lo.y, ln.y));
             }
-            const float wi = ops.winv[jo];
-            float* A = sA + l * 5 * N3;
+            const f2p mE = pk(sidev[0] ? -1.0f : 1.0f, sidev[1] ? -1.0f : 1.0f);
+            const f2p wi = pk(ops.winv[jov[0]], ops.winv[jov[1]]);
+            float val[5][2];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) A[v * N3 + own] += (-E * F[v] - lam * (sQ[v * N3 + own] - qn[v])) * wi;
-            float* wf = sWf + (2 * l + side) * 4 * N2 + fi;
-            const float tb = two_beta(sn, ref);
-            wf[0] = tb * sn.u0;
-            wf[N2] = tb * sn.u1;
-            wf[2 * N2] = tb * sn.u2;
-            wf[3 * N2] = -ref.two_beta0 * sn.dbn;
+            for (int v = 0; v < 5; ++v) {
+                const f2p jump = sub2(pk(qo[0][v], qo[1][v]), QN[v]);
+                const float2 t = upk(mul2(fma2(mE, F[v], mul2(sub2(0ull, lam), jump)), wi));
+                val[v][0] = t.x;
+                val[v][1] = t.y;
+            }
+            const f2p tb = mul2(bc(ref.two_beta0), add2(bc(1.0f), sn.dbn));
+            const float2 w0 = upk(mul2(bc(2.0f), mul2(tb, sn.hu0))), w1 = upk(mul2(bc(2.0f), mul2(tb, sn.hu1)));
+            const float2 w2 = upk(mul2(bc(2.0f), mul2(tb, sn.hu2))), w3 = upk(mul2(bc(-ref.two_beta0), sn.dbn));
+            const float wv[4][2] = {{w0.x, w0.y}, {w1.x, w1.y}, {w2.x, w2.y}, {w3.x, w3.y}};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && !(tl + TE < 6 * N2)) break;
+                float* A = sA + lv[h] * 5 * N3;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) A[v * N3 + ownv[h]] += val[v][h];
+                float* wf = sWf + (2 * lv[h] + sidev[h]) * 4 * N2 + fiv[h];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) wf[c * N2] = wv[c][h];
+            }
+            (void)fnv;
         }
+    } else {
+        if (active) {
+    #pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const int fn = tl + f * TE;
+                if (fn >= 6 * N2) break;
+                const int l = fn / (2 * N2);
+                const int rem = fn - l * 2 * N2;
+                const int side = rem / N2, fi = rem - side * N2;
+                const int st = dir_stride_f<N>(l);
+                const int base = line_base_f<N>(l, fi % N, fi / N);
+                const int own = base + (side ? (N - 1) * st : 0);
+                const int jo = side ? N - 1 : 0;
+                float qn[5];
+    #pragma unroll
+                for (int v = 0; v < 5; ++v) qn[v] = sNq[v * 6 * N2 + fn];
+                PrimF so, sn;
+                const int own0 = lidx<N>(own / N, own % N);    // the natural order is direction 0's
+                so.hdr = sL[own0];
+                so.dbn = sL[N3 + own0];
+                so.hu0 = sL[2 * N3 + own0];
+                so.hu1 = sL[3 * N3 + own0];
+                so.hu2 = sL[4 * N3 + own0];
+                so.u0 = 2.0f * so.hu0;
+                so.u1 = 2.0f * so.hu1;
+                so.u2 = 2.0f * so.hu2;
+                to_prim_f(qn, ref, sn);
+                const float* Ln = sL + (l * 8 + 5) * N3 + lidx<N>(fi, jo);
+                float n0 = Ln[0], n1 = Ln[N3], n2 = Ln[2 * N3];
+                if (nsurf) {   // optimized metrics: the interface terms take the surface metrics
+                    const float* ns = nsurf + (el * 6 + 2 * l + side) * 3 * N2 + fi;
+                    n0 = ns[0];
+                    n1 = ns[N2];
+                    n2 = ns[2 * N2];
+                }
+                float F[5];
+                ec_flux_folded(so, sn, n0, n1, n2, ref, F);
+                const float E = side ? 1.0f : -1.0f;
+                float lam = 0.0f;
+                if (ph.dissipation) {
+                    const float nn = fsqrt(n0 * n0 + n1 * n1 + n2 * n2);
+                    const float lo = fabsf(so.u0 * n0 + so.u1 * n1 + so.u2 * n2) + fsqrt(ref.gamma * node_RT(so.dbn, ref)) * nn;
+                    const float ln = fabsf(sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2) + fsqrt(ref.gamma * node_RT(sn.dbn, ref)) * nn;
+                    lam = 0.5f * fmaxf(lo, ln);
+                }
+                const float wi = ops.winv[jo];
+                float* A = sA + l * 5 * N3;
+    #pragma unroll
+                for (int v = 0; v < 5; ++v) A[v * N3 + own] += (-E * F[v] - lam * (sQ[v * N3 + own] - qn[v])) * wi;
+                float* wf = sWf + (2 * l + side) * 4 * N2 + fi;
+                const float tb = two_beta(sn, ref);
+                wf[0] = tb * sn.u0;
+                wf[N2] = tb * sn.u1;
+                wf[2 * N2] = tb * sn.u2;
+                wf[3 * N2] = -ref.two_beta0 * sn.dbn;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-
     if (ph.viscous) {
         float Ft[NPT][3][4];
         if (active) {
