@@ -491,7 +491,7 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
         }
     } else {
         if (active) {
-    #pragma unroll
+#pragma unroll
             for (int f = 0; f < FPT; ++f) {
                 const int fn = tl + f * TE;
                 if (fn >= 6 * N2) break;
@@ -503,7 +503,7 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
                 const int own = base + (side ? (N - 1) * st : 0);
                 const int jo = side ? N - 1 : 0;
                 float qn[5];
-    #pragma unroll
+#pragma unroll
                 for (int v = 0; v < 5; ++v) qn[v] = sNq[v * 6 * N2 + fn];
                 PrimF so, sn;
                 const int own0 = lidx<N>(own / N, own % N);    // the natural order is direction 0's
@@ -536,7 +536,7 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
                 }
                 const float wi = ops.winv[jo];
                 float* A = sA + l * 5 * N3;
-    #pragma unroll
+#pragma unroll
                 for (int v = 0; v < 5; ++v) A[v * N3 + own] += (-E * F[v] - lam * (sQ[v * N3 + own] - qn[v])) * wi;
                 float* wf = sWf + (2 * l + side) * 4 * N2 + fi;
                 const float tb = two_beta(sn, ref);
@@ -546,8 +546,9 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
                 wf[3 * N2] = -ref.two_beta0 * sn.dbn;
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
+
     if (ph.viscous) {
         float Ft[NPT][3][4];
         if (active) {
