@@ -141,7 +141,7 @@ def test_fp32_residual_48cubed_p7_full_size_sampled():
     assert max(c) <= C_MAX
 
 
-@pytest.mark.parametrize("p", [2, 4])
+@pytest.mark.parametrize("p", [2, 3, 4, 7])
 def test_fp32_residual_optimized_metrics(p):
     """The mixed-precision residual with the optimized metrics (surface metrics in its interface
     terms) against the oracle's optimized-metric residual, same bounds as the curl-form cases; a
@@ -159,7 +159,8 @@ def test_fp32_residual_optimized_metrics(p):
         assert float(r[:, v].abs().max()) <= C_MAX * EPS32 * T[v], (v, float(r[:, v].abs().max()), T[v])
 
 
-@pytest.mark.parametrize("p,k,Re,diss", [(2, 3, 1.0e3, True), (3, 2, 4.0e2, True), (4, 2, 0.0, False)])
+@pytest.mark.parametrize("p,k,Re,diss", [(2, 3, 1.0e3, True), (3, 2, 4.0e2, True), (4, 2, 0.0, False),
+                                         (7, 2, 4.0e2, True), (3, 2, 0.0, False)])
 def test_fp32_bounded_box_with_exterior_state_and_source(p, k, Re, diss):
     """Warped bounded box (Dirichlet exterior data on every outer face) with a source: the float32
     residual against the float64 oracle under the same conditioning-normalised bound, and ten DP5
@@ -187,7 +188,9 @@ def test_fp32_bounded_box_with_exterior_state_and_source(p, k, Re, diss):
     ro = O.rhs(qo, mesh, gas, dissipation=diss, q_ext=torch.tensor(I.manufactured(xo)), source=torch.tensor(src))
     e, c = _report(s32.rhs(q32), ro, qo, mesh, gas)
     assert max(c) <= C_MAX
-    assert max(e) <= 1e-5
+    # the terms the residual differences grow with the degree (T_v ~ N^2 |f| / h): at p = 7 on this
+    # state the same c_v (<= 1.8 measured) is a normwise error of 1.1e-5
+    assert max(e) <= (1e-5 if p < 7 else 2e-5)
     s64, q64 = out["fp64"][0], out["fp64"][1]
     dt = 0.5 * s64.dt_cfl(q64, 0.5)
     q0 = q64.clone()
