@@ -851,32 +851,38 @@ def _adjoint_leg(solver, q, dt, ms_rhs, nsteps, flush=None):
     torch.cuda.synchronize()
     ms_fwd = a.elapsed_time(b)
 
-    def gradient(stages):
+    def gradient(kind):
         qb = q.clone()
-        ck = solver.rk_step_ckpt(qb, dt, nsteps, stages=stages)
+        ck = solver.rk_step_ckpt(qb, dt, nsteps, stages=kind == "stages", k1=kind == "k1")
         lamN = solver.ke_gradient(qb)
         return solver.rk_adjoint(ck, dt, lamN)
 
     out = {}
-    for stages in (True, False):
-        gradient(stages)                      # warm-up: workspaces and checkpoint memory
+    for kind in ("stages", "k1", "state"):
+        gradient(kind)                        # warm-up: workspaces and checkpoint memory
         fl(3.0)
         a.record(stream)
-        _, gmu = gradient(stages)
+        _, gmu = gradient(kind)
         b.record(stream)
         torch.cuda.synchronize()
-        out[stages] = (a.elapsed_time(b), gmu)
+        out[kind] = (a.elapsed_time(b), gmu)
         torch.cuda.empty_cache()
-    ms_grad, gmu = out[True]
-    ms_grad_rc, gmu_rc = out[False]
+    ms_grad, gmu = out["stages"]
+    ms_grad_rc, gmu_rc = out["k1"]
+    ms_grad_st, gmu_st = out["state"]
     return {"vjp_ms": ms_vjp, "rhs_ms": ms_rhs, "vjp_over_rhs": ms_vjp / ms_rhs,
             "trajectory_steps": nsteps, "forward_ms": ms_fwd, "gradient_ms": ms_grad,
             "gradient_over_forward": ms_grad / ms_fwd,
             "gradient_recompute_ms": ms_grad_rc, "gradient_recompute_over_forward": ms_grad_rc / ms_fwd,
-            "dke_dmu": gmu, "dke_dmu_recompute_rel_diff": abs(gmu - gmu_rc) / abs(gmu), "dtype": "f64",
-            "what": "d KE(q_N)/d(q_0, mu): forward storing the stage states + reverse sweep (6 VJPs per "
-                    "step); recompute variant: per-step checkpoints, 6 residual recomputations + 6 VJPs "
-                    "per step; forward = the N steps alone (one multi-step call)"}
+            "gradient_recompute_state_only_ms": ms_grad_st,
+            "gradient_recompute_state_only_over_forward": ms_grad_st / ms_fwd,
+            "dke_dmu": gmu, "dke_dmu_recompute_rel_diff": max(abs(gmu - gmu_rc), abs(gmu - gmu_st)) / abs(gmu),
+            "dtype": "f64",
+            "what": "d KE(q_N)/d(q_0, mu): forward storing the stage states (6 per step) + reverse sweep "
+                    "(6 VJPs per step); recompute variant: per-step checkpoints of the state and its "
+                    "residual (2 per step), 4 residual recomputations + 6 VJPs per step; state-only "
+                    "variant: the state alone (1 per step), 5 recomputations; forward = the N steps alone "
+                    "(one multi-step call)"}
 
 
 def _adjoint_vortex_leg():

@@ -370,24 +370,31 @@ int esdc_rhs_vjp(esdc_ctx* ctx, const double* q_dev, const double* lambda_dev, d
 int esdc_ke_gradient(esdc_ctx* ctx, const double* q_dev, double* grad_dev, void* stream);
 
 /*
- * esdc_rk_step_ckpt -- esdc_rk_step that first stores the state of every step:
- * ckpt_dev[n] = q before step n, n = 0..nsteps-1 (ckpt_dev: nsteps*K*5*N^3 float64, caller owned).
+ * esdc_rk_step_ckpt -- esdc_rk_step that first stores the state of every step, the checkpoints of
+ * esdc_rk_adjoint (no counterpart in the paper, whose method this differentiates).
+ * store_k1 = 0: ckpt_dev[n] = q before step n, n = 0..nsteps-1 (nsteps*K*5*N^3 float64).
+ * store_k1 = 1: ckpt_dev[2n] = q before step n and ckpt_dev[2n+1] = its residual f(q), the step's
+ * first stage derivative, which the step writes there directly (2*nsteps*K*5*N^3 float64; float64
+ * contexts only, ESDC_ERR_UNSUPPORTED otherwise; steps launched one by one, no graph replay).  The
+ * reverse sweep then recomputes four residuals per step instead of five.
+ * ckpt_dev: caller owned, 16-byte aligned.  Asynchronous.
  */
-int esdc_rk_step_ckpt(esdc_ctx* ctx, double* q_dev, double dt, int nsteps, double* ckpt_dev, void* workspace_dev,
-                      size_t workspace_bytes, void* stream);
+int esdc_rk_step_ckpt(esdc_ctx* ctx, double* q_dev, double dt, int nsteps, double* ckpt_dev, int store_k1,
+                      void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* esdc_rk_adjoint_workspace_bytes -- workspace of esdc_rk_adjoint: 12 state-sized float64 buffers. */
 int esdc_rk_adjoint_workspace_bytes(const esdc_ctx* ctx, size_t* bytes);
 
 /*
  * esdc_rk_adjoint -- discrete adjoint of nsteps DP5 steps (reverse sweep with stage
- * recomputation from the per-step checkpoints of esdc_rk_step_ckpt).  On entry lambda_dev holds
- * dL/dq_N; on exit dL/dq_0.  grad_mu_host (nullable) receives dL/dmu.  Per step: six residuals to
- * rebuild the stage states Y_t, then for t = 6..1 psi_t = J(Y_t)^T kappa_t with
- * kappa_t = dt b_t lambda_{n+1} + sum_{s>t} dt a_st psi_s, and lambda_n = lambda_{n+1} + sum_t psi_t.
- * ESDC_PREC_FP64 contexts only.  Synchronises stream when grad_mu_host is not NULL.
+ * recomputation from the checkpoints of esdc_rk_step_ckpt, store_k1 as given there).  On entry
+ * lambda_dev holds dL/dq_N; on exit dL/dq_0.  grad_mu_host (nullable) receives dL/dmu.  Per step:
+ * five residuals (four with store_k1) rebuild the stage states Y_1..Y_6 from the checkpoint, then
+ * for t = 6..1 psi_t = J(Y_t)^T kappa_t with kappa_t = dt b_t lambda_{n+1} + sum_{s>t} dt a_st psi_s,
+ * and lambda_n = lambda_{n+1} + sum_t psi_t.  ESDC_PREC_FP64 contexts only.  Synchronises stream
+ * when grad_mu_host is not NULL.
  */
-int esdc_rk_adjoint(esdc_ctx* ctx, const double* ckpt_dev, double dt, int nsteps, double* lambda_dev,
+int esdc_rk_adjoint(esdc_ctx* ctx, const double* ckpt_dev, int store_k1, double dt, int nsteps, double* lambda_dev,
                     double* grad_mu_host, void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /*
@@ -404,7 +411,8 @@ int esdc_rk_step_stages(esdc_ctx* ctx, double* q_dev, double dt, int nsteps, dou
 /*
  * esdc_rk_adjoint_stages -- the reverse sweep of esdc_rk_adjoint from stored stage states
  * (esdc_rk_step_stages): per step six vector-Jacobian products and no residual recomputation.
- * Same arguments, workspace (esdc_rk_adjoint_workspace_bytes) and results as esdc_rk_adjoint.
+ * The arguments of esdc_rk_adjoint but store_k1, and the same workspace (esdc_rk_adjoint_workspace_bytes)
+ * and results.
  */
 int esdc_rk_adjoint_stages(esdc_ctx* ctx, const double* stages_dev, double dt, int nsteps, double* lambda_dev,
                            double* grad_mu_host, void* workspace_dev, size_t workspace_bytes, void* stream);

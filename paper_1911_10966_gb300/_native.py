@@ -82,11 +82,11 @@ def lib() -> ctypes.CDLL:
         "esdc_budgets_noalloc": (I, [I, ctypes.c_int64, D, P, P, P, P, P, P]),
         "esdc_rhs_vjp": (I, [P, P, P, P, ctypes.POINTER(D), P]),
         "esdc_ke_gradient": (I, [P, P, P, P]),
-        "esdc_rk_step_ckpt": (I, [P, P, D, I, P, P, S, P]),
+        "esdc_rk_step_ckpt": (I, [P, P, D, I, P, I, P, S, P]),
         "esdc_rk_adjoint_workspace_bytes": (I, [P, ctypes.POINTER(S)]),
         "esdc_rk_step_stages": (I, [P, P, D, I, P, P, S, P]),
         "esdc_rk_adjoint_stages": (I, [P, P, D, I, P, ctypes.POINTER(D), P, S, P]),
-        "esdc_rk_adjoint": (I, [P, P, D, I, P, ctypes.POINTER(D), P, S, P]),
+        "esdc_rk_adjoint": (I, [P, P, I, D, I, P, ctypes.POINTER(D), P, S, P]),
         "esdc_strerror": (ctypes.c_char_p, [I]),
         "esdc_last_error": (ctypes.c_char_p, []),
     }

@@ -30,19 +30,21 @@ class Trajectory(torch.autograd.Function):
     solver's viscosity (it is an input only so that dL/dmu can flow back).
 
     stages: checkpoint granularity of the reverse sweep.  True stores the six stage states of every
-    step (6 x nsteps states, no recomputation); False stores the state before each step and
-    recomputes the stage states in the reverse sweep (six residuals per step); None picks True when
-    the stage states take at most half of the free device memory."""
+    step (6 x nsteps states, no recomputation); False stores the state before each step with its
+    residual (2 x nsteps states) and recomputes the stage states in the reverse sweep (four residuals
+    per step), or the state alone (nsteps states, five residuals per step) when the pair does not fit
+    in half of the free device memory; None picks True when the stage states fit there."""
 
     @staticmethod
     def forward(ctx, q0, mu, solver, dt, nsteps, stages=None):
         if abs(float(mu) - solver.mu) > 1e-15 * max(1.0, abs(solver.mu)):
             raise ValueError("mu must equal the solver's viscosity 1/Re")
+        free, _ = torch.cuda.mem_get_info(q0.device)
         if stages is None:
-            free, _ = torch.cuda.mem_get_info(q0.device)
             stages = 6 * nsteps * q0.numel() * 8 <= free // 2
+        k1 = 2 * nsteps * q0.numel() * 8 <= free // 2
         q = q0.detach().clone().contiguous()
-        ck = solver.rk_step_ckpt(q, dt, nsteps, stages=bool(stages))
+        ck = solver.rk_step_ckpt(q, dt, nsteps, stages=bool(stages), k1=k1)
         ctx.solver, ctx.dt = solver, dt
         ctx.save_for_backward(ck)
         return q

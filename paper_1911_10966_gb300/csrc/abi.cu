@@ -141,13 +141,15 @@ int rk_step_f32(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStr
 // stages + (step * 6 + t) * K*5*N^3, t = 0 being the state at the start of the step; the stage
 // combinations then write there instead of the workspace buffer, so storing them costs one copy of q
 // per step.
-int rk_step_f64(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s, double* stages) {
+int rk_step_f64(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaStream_t s, double* stages,
+                double* k1_out) {
     const int64_t n = c->n_nodes * 5;
     const size_t sub = round256((size_t)n * sizeof(double));
     double* k[6];
     for (int j = 0; j < 6; ++j) k[j] = (double*)((char*)ws + j * sub);
     double* stage_ws = (double*)((char*)ws + 6 * sub);
     for (int step = 0; step < nsteps; ++step) {
+        if (k1_out) k[0] = k1_out + (size_t)step * n;   // the first stage derivative written out directly
         for (int st = 0; st < 6; ++st) {
             double* dst = stages ? stages + ((size_t)step * 6 + st) * n : stage_ws;
             const double* qs = q;
@@ -212,7 +214,7 @@ int rk_steps_graph(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cuda
             return 1;
         }
         const int r = c->setup.precision == ESDC_PREC_FP32 ? rk_steps_f32(c, q, dt, 1, ws, cs)
-                                                            : rk_step_f64(c, q, dt, 1, ws, cs, nullptr);
+                                                            : rk_step_f64(c, q, dt, 1, ws, cs, nullptr, nullptr);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(cs, &g);
         cudaGraphExec_t exec = nullptr;
@@ -740,7 +742,7 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
         c->opsf.winv[i] = (float)(1.0 / hs.w[i]);
         for (int j = 0; j < hs.N; ++j) {
             c->ops.D[i][j] = hs.D[i * hs.N + j];
-            c->ops.S2[i][j] = 2.0 * hs.S[i * hs.N + j];
+            c->ops.SW[i][j] = hs.S[i * hs.N + j] / hs.w[j];
             c->ops.S[i][j] = hs.S[i * hs.N + j];
             c->opsf.D[i][j] = (float)hs.D[i * hs.N + j];
             c->opsf.S[i][j] = (float)hs.S[i * hs.N + j];
@@ -968,10 +970,10 @@ int esdc_rk_step(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, size_t
         if (r <= 0) return r;
         // graph unavailable: direct launches (the shadow is already in place)
         if (c->setup.precision == ESDC_PREC_FP32) return rk_steps_f32(c, q, dt, nsteps, ws, s);
-        return rk_step_f64(c, q, dt, nsteps, ws, s, nullptr);
+        return rk_step_f64(c, q, dt, nsteps, ws, s, nullptr, nullptr);
     }
     if (c->setup.precision == ESDC_PREC_FP32) return rk_step_f32(c, q, dt, nsteps, ws, s);
-    return rk_step_f64(c, q, dt, nsteps, ws, s, nullptr);
+    return rk_step_f64(c, q, dt, nsteps, ws, s, nullptr, nullptr);
 }
 
 int esdc_budgets(esdc_ctx* c, const double* q, const void* dqdt, double out[4], void* stream) {
@@ -1083,14 +1085,29 @@ int esdc_rk_adaptive(esdc_ctx* c, double* q, double t0, double t_end, double* dt
                            (cudaStream_t)stream);
 }
 
-int esdc_rk_step_ckpt(esdc_ctx* c, double* q, double dt, int nsteps, double* ckpt, void* ws, size_t ws_bytes,
-                      void* stream) {
+int esdc_rk_step_ckpt(esdc_ctx* c, double* q, double dt, int nsteps, double* ckpt, int store_k1, void* ws,
+                      size_t ws_bytes, void* stream) {
     if (!c || !q || !ckpt) return fail(ESDC_ERR_ARG, "null argument");
     const size_t n5 = (size_t)c->n_nodes * 5;
     cudaStream_t s = (cudaStream_t)stream;
+    if (store_k1) {
+        // direct launches of the float64 step, the first residual written into the checkpoint
+        if (c->setup.precision != ESDC_PREC_FP64) return fail(ESDC_ERR_UNSUPPORTED, "store_k1 needs a float64 context");
+        if (!ws) return fail(ESDC_ERR_ARG, "null argument");
+        if (nsteps < 0 || !std::isfinite(dt)) return fail(ESDC_ERR_ARG, "nsteps >= 0 and finite dt required");
+        size_t need = 0;
+        esdc_workspace_bytes(c, 0, &need);
+        if (ws_bytes < need) return fail(ESDC_ERR_ARG, "workspace too small");
+        if (!aligned(ws, 256) || !aligned(q, 16) || !aligned(ckpt, 16))
+            return fail(ESDC_ERR_ARG, "q/ckpt must be 16-byte and workspace 256-byte aligned");
+        if (c->setup.bounded != 0 && !c->d_qext)
+            return fail(ESDC_ERR_ARG, "a bounded box needs an exterior state (esdc_set_exterior)");
+    }
     for (int step = 0; step < nsteps; ++step) {
-        CUDA_TRY(cudaMemcpyAsync(ckpt + step * n5, q, n5 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        int st = esdc_rk_step(c, q, dt, 1, ws, ws_bytes, stream);
+        double* qs = ckpt + (store_k1 ? 2 * (size_t)step : (size_t)step) * n5;
+        CUDA_TRY(cudaMemcpyAsync(qs, q, n5 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        const int st = store_k1 ? rk_step_f64(c, q, dt, 1, ws, s, nullptr, qs + n5)
+                                : esdc_rk_step(c, q, dt, 1, ws, ws_bytes, stream);
         if (st) return st;
     }
     return ESDC_OK;
@@ -1102,8 +1119,8 @@ int esdc_rk_adjoint_workspace_bytes(const esdc_ctx* c, size_t* bytes) {
     return ESDC_OK;
 }
 
-int esdc_rk_adjoint(esdc_ctx* c, const double* ckpt, double dt, int nsteps, double* lam, double* grad_mu, void* ws,
-                    size_t ws_bytes, void* stream) {
+int esdc_rk_adjoint(esdc_ctx* c, const double* ckpt, int store_k1, double dt, int nsteps, double* lam,
+                    double* grad_mu, void* ws, size_t ws_bytes, void* stream) {
     int st = adjoint_checks(c, ckpt, dt, nsteps, lam, ws, ws_bytes);
     if (st) return st;
     const int64_t n = c->n_nodes * 5;
@@ -1117,16 +1134,19 @@ int esdc_rk_adjoint(esdc_ctx* c, const double* ckpt, double dt, int nsteps, doub
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaMemsetAsync(c->d_adj_acc, 0, sizeof(double), s));
     for (int step = nsteps - 1; step >= 0; --step) {
-        const double* qn = ckpt + (size_t)step * n;
+        const double* qn = ckpt + (store_k1 ? 2 * (size_t)step : (size_t)step) * n;
         // recompute the stage states of this step from its checkpoint: Y_1 = q_n and Y_t from the
-        // stage derivatives k_1 .. k_(t-1), so five residuals (k_6 = f(Y_6) is not needed)
+        // stage derivatives k_1 .. k_(t-1), so five residuals (k_6 = f(Y_6) is not needed), four when
+        // the checkpoint holds k_1 = f(q_n)
+        const double* kin[6] = {K6[0], K6[1], K6[2], K6[3], K6[4], K6[5]};
+        if (store_k1) kin[0] = qn + n;
         for (int t = 0; t < 6; ++t) {
             const double* qs = qn;
             if (t > 0) {
                 esdc::Combine cb{};
                 cb.nk = t;
                 for (int j = 0; j < t; ++j) {
-                    cb.k[j] = K6[j];
+                    cb.k[j] = kin[j];
                     cb.coef[j] = dt * kA[t][j];
                 }
                 cudaError_t e = esdc::launch_combine(Qs[t], qn, cb, n, s);
@@ -1134,6 +1154,7 @@ int esdc_rk_adjoint(esdc_ctx* c, const double* ckpt, double dt, int nsteps, doub
                 qs = Qs[t];
             }
             if (t == 5) break;
+            if (t == 0 && store_k1) continue;
             st = rhs_impl(c, qs, K6[t], s);
             if (st) return st;
         }
@@ -1154,7 +1175,9 @@ int esdc_rk_step_stages(esdc_ctx* c, double* q, double dt, int nsteps, double* s
     if (ws_bytes < need) return fail(ESDC_ERR_ARG, "workspace too small");
     if (!aligned(ws, 256) || !aligned(q, 16) || !aligned(stages, 16))
         return fail(ESDC_ERR_ARG, "q/stages must be 16-byte and workspace 256-byte aligned");
-    return rk_step_f64(c, q, dt, nsteps, ws, (cudaStream_t)stream, stages);
+    if (c->setup.bounded != 0 && !c->d_qext)
+        return fail(ESDC_ERR_ARG, "a bounded box needs an exterior state (esdc_set_exterior)");
+    return rk_step_f64(c, q, dt, nsteps, ws, (cudaStream_t)stream, stages, nullptr);
 }
 
 int esdc_rk_adjoint_stages(esdc_ctx* c, const double* stages, double dt, int nsteps, double* lam, double* grad_mu,

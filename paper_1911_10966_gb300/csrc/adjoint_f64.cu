@@ -34,11 +34,12 @@ struct CfgA {
     static constexpr int N2 = N * N, N3 = N * N * N;
     static constexpr int EPB = N3 >= 96 ? 1 : (N3 >= 48 ? 2 : (N3 >= 24 ? 4 : 16));
     static constexpr int THREADS = EPB * N3;
-    // shared doubles per element: prim/w 10 | lt 5 | geometry 10 | prim-bar 6 | q-bar 5 | theta-bar 12
+    // shared doubles per element: prim/w and the pair form 14 | lt 5 | geometry 10 | prim-bar 6 | q-bar 5
+    // | theta-bar 12
     // (also the own side's interface cotangents, 30 N2, which exceed 12 N3 only at N = 2)
     // | neighbour face w 24 N2
     static constexpr int TSZ = 12 * N3 > 30 * N2 ? 12 * N3 : 30 * N2;
-    static constexpr int SM = 36 * N3 + TSZ + 24 * N2;
+    static constexpr int SM = 40 * N3 + TSZ + 24 * N2;
     static constexpr int EPB_F = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
     // resident CTAs the register allocation is sized for (3 at N = 4, 5 measured faster than 2)
     static constexpr int MINB = (N == 4 || N == 5) ? 3 : 1;
@@ -104,47 +105,132 @@ __device__ __forceinline__ void ln_mean_d(double a, double b, double rs, double&
     }
 }
 
-// Reverse of the contracted Chandrashekar flux: given the cotangent mu[5] of f(a, b; n), add the
-// primitive cotangents of both states to ab, bb.  Two reciprocals per pair, 1/(rho_a + rho_b) and
-// 1/(beta_a + beta_b); the latter serves p_t and, with the series, the reciprocal of the beta log mean.
-__device__ __forceinline__ void ec_flux_vjp(const Prim& a, const Prim& b, double n0, double n1, double n2,
-                                            const double mu[5], const Phys& ph, PBar& ab, PBar& bb) {
-    double Lr, Lra, Lrb, Lb, Lba, Lbb, ILr, IBL;
-    const double rsb = rcp_newton2(a.beta + b.beta);
-    ln_mean_d(a.rho, b.rho, rcp_newton1(a.rho + b.rho), Lr, Lra, Lrb, ILr);
-    ln_mean_d(a.beta, b.beta, rsb, Lb, Lba, Lbb, IBL);
-    const double ub0 = 0.5 * (a.u0 + b.u0), ub1 = 0.5 * (a.u1 + b.u1), ub2 = 0.5 * (a.u2 + b.u2);
+// Pair form of a node's primitives for the ES-C reverse: half velocities and a quarter of |u|^2, so
+// that the averages of the two-point flux are single additions.
+struct PrimH {
+    double rho, h0, h1, h2, beta, qsq;
+};
+// Cotangent accumulators of the ES-C reverse in pair form: rho and beta as in PBar, u twice the
+// velocity cotangent, c the sum of the cotangents of c5 (the |u|^2 cotangent is -c/4); raw_to_pbar
+// converts.
+struct PRaw {
+    double rho, u0, u1, u2, beta, c;
+};
+
+__device__ __forceinline__ void raw_to_pbar(const PRaw& r, PBar& b) {
+    b.rho += r.rho;
+    b.u0 += 0.5 * r.u0;
+    b.u1 += 0.5 * r.u1;
+    b.u2 += 0.5 * r.u2;
+    b.beta += r.beta;
+    b.usq += -0.25 * r.c;
+}
+
+// Reverse of the contracted Chandrashekar flux f(a, b; n) for the cotangent mu[5]: adds the pair-form
+// cotangents of both states to ab, bb.  Two reciprocals, 1/(rho_a + rho_b) (one Newton step: it only
+// forms f = (a - b)/(a + b)) and 1/(beta_a + beta_b), which serves p_t and the reciprocal of the beta
+// log mean.  Logarithmic means (series branch, u = f^2 < 1e-4, F(u) = artanh(f)/f = 1 + u/3 + u^2/5 +
+// u^3/7 + u^4/9, G = 1/F = 1 - u/3 - 4u^2/45 - 44u^3/945):
+//   rho:  L = (a + b) G/2,  dL/da = G/2 - f F'(u) G^2 (1 - f),  dL/db = G/2 + f F'(u) G^2 (1 + f);
+//   beta: only 1/L enters the flux, IL = 2 F/(a + b), dIL/da = 2 (2 f F'(u) (1 - f) - F)/(a + b)^2,
+//         dIL/db = -2 (2 f F'(u) (1 + f) + F)/(a + b)^2;
+// otherwise, with l = log(a/b): L = (a - b)/l, dL/da = (1 - L/a)/l, dL/db = (L/b - 1)/l, and
+// IL = l/(a - b), dIL/da = (1/a - IL)/(a - b), dIL/db = (IL - 1/b)/(a - b).
+__device__ __forceinline__ void ec_pair_vjp(const PrimH& a, const PrimH& b, double n0, double n1, double n2,
+                                            const double mu[5], const Phys& ph, PRaw& ab, PRaw& bb) {
+    const double sr = a.rho + b.rho, sb = a.beta + b.beta;
+    const double rsb = rcp_newton2(sb);
+    // rho log mean and its partial derivatives
+    double Lr, Lra, Lrb;
+    {
+        const double d = a.rho - b.rho;
+        const double f = d * rcp_newton1(sr);
+        const double u = f * f;
+        if (u < 1.0e-4) {
+            const double hG = fma(u, fma(u, fma(u, -22.0 / 945.0, -2.0 / 45.0), -1.0 / 6.0), 0.5);          // G/2
+            const double Fp4 = fma(u, fma(u, fma(u, 16.0 / 9.0, 12.0 / 7.0), 8.0 / 5.0), 4.0 / 3.0);     // 4 F'
+            const double W = f * Fp4 * (hG * hG);                                                          // f F' G^2
+            const double Y = W * f;
+            Lr = sr * hG;
+            Lra = hG - W + Y;
+            Lrb = hG + W + Y;
+        } else {
+            const double ra = rcp_newton2(a.rho), rb = rcp_newton2(b.rho);
+            const double rl = rcp_newton2(log(a.rho * rb));
+            Lr = d * rl;
+            Lra = fma(-Lr, ra, 1.0) * rl;
+            Lrb = fma(Lr, rb, -1.0) * rl;
+        }
+    }
+    // reciprocal of the beta log mean and its partial derivatives: dIL/da = sc Ab, dIL/db = sc Bb
+    double IB, sc, Ab, Bb;
+    {
+        const double d = a.beta - b.beta;
+        const double f = d * rsb;
+        const double u = f * f;
+        if (u < 1.0e-4) {
+            const double F = fma(u, fma(u, fma(u, fma(u, 1.0 / 9.0, 1.0 / 7.0), 1.0 / 5.0), 1.0 / 3.0), 1.0);
+            const double Fp2 = fma(u, fma(u, fma(u, 8.0 / 9.0, 6.0 / 7.0), 4.0 / 5.0), 2.0 / 3.0);      // 2 F'
+            const double w = f * Fp2;
+            const double X = w * f;
+            IB = 2.0 * F * rsb;
+            sc = 2.0 * rsb * rsb;
+            Ab = w - X - F;
+            Bb = -(w + X + F);
+        } else {
+            const double ra = rcp_newton2(a.beta), rb = rcp_newton2(b.beta);
+            sc = rcp_newton2(d);
+            IB = log(a.beta * rb) * sc;
+            Ab = ra - IB;
+            Bb = IB - rb;
+        }
+    }
+    const double hig = 0.5 * ph.inv_gm1;
+    const double ub0 = a.h0 + b.h0, ub1 = a.h1 + b.h1, ub2 = a.h2 + b.h2;
     const double un = ub0 * n0 + ub1 * n1 + ub2 * n2;
-    const double pt = 0.5 * (a.rho + b.rho) * rsb;
+    const double pt = 0.5 * sr * rsb;
     const double f1 = Lr * un;
-    const double fm0 = f1 * ub0 + pt * n0, fm1 = f1 * ub1 + pt * n1, fm2 = f1 * ub2 + pt * n2;
-    const double c5 = 0.5 * ph.inv_gm1 * IBL - 0.25 * (a.usq + b.usq);
+    const double fm0 = fma(f1, ub0, pt * n0), fm1 = fma(f1, ub1, pt * n1), fm2 = fma(f1, ub2, pt * n2);
+    const double c5 = fma(hig, IB, -(a.qsq + b.qsq));
     // reverse
-    const double fmb0 = mu[1] + mu[4] * ub0, fmb1 = mu[2] + mu[4] * ub1, fmb2 = mu[3] + mu[4] * ub2;
+    const double fmb0 = fma(mu[4], ub0, mu[1]), fmb1 = fma(mu[4], ub1, mu[2]), fmb2 = fma(mu[4], ub2, mu[3]);
     const double f1b = mu[0] + mu[4] * c5 + fmb0 * ub0 + fmb1 * ub1 + fmb2 * ub2;
     const double c5b = mu[4] * f1;
     const double ptb = fmb0 * n0 + fmb1 * n1 + fmb2 * n2;
     const double unb = f1b * Lr;
+    const double Lrb_ = f1b * un;
+    // pt = (rho_a + rho_b)/(2 (beta_a + beta_b)): d pt/d rho = 1/(2 sb), d pt/d beta = -pt/sb
+    const double hp = 0.5 * ptb * rsb;
+    const double bp = -ptb * pt * rsb;
+    const double S = c5b * hig * sc;
+    ab.rho += fma(Lrb_, Lra, hp);
+    bb.rho += fma(Lrb_, Lrb, hp);
+    ab.beta += fma(S, Ab, bp);
+    bb.beta += fma(S, Bb, bp);
+    ab.c += c5b;
+    bb.c += c5b;
     const double ubb0 = mu[4] * fm0 + fmb0 * f1 + unb * n0;
     const double ubb1 = mu[4] * fm1 + fmb1 * f1 + unb * n1;
     const double ubb2 = mu[4] * fm2 + fmb2 * f1 + unb * n2;
-    const double Lrb_ = f1b * un;
-    const double IBLb = c5b * 0.5 * ph.inv_gm1;
-    const double rsbb = ptb * 0.5 * (a.rho + b.rho);
-    const double bsum = -rsbb * rsb * rsb;
-    const double ibl2 = -IBLb * IBL * IBL;
-    ab.rho += 0.5 * ptb * rsb + Lrb_ * Lra;
-    bb.rho += 0.5 * ptb * rsb + Lrb_ * Lrb;
-    ab.beta += bsum + ibl2 * Lba;
-    bb.beta += bsum + ibl2 * Lbb;
-    ab.usq += -0.25 * c5b;
-    bb.usq += -0.25 * c5b;
-    ab.u0 += 0.5 * ubb0;
-    ab.u1 += 0.5 * ubb1;
-    ab.u2 += 0.5 * ubb2;
-    bb.u0 += 0.5 * ubb0;
-    bb.u1 += 0.5 * ubb1;
-    bb.u2 += 0.5 * ubb2;
+    ab.u0 += ubb0;
+    ab.u1 += ubb1;
+    ab.u2 += ubb2;
+    bb.u0 += ubb0;
+    bb.u1 += ubb1;
+    bb.u2 += ubb2;
+}
+
+__device__ __forceinline__ PrimH to_pair_form(const Prim& s) {
+    return PrimH{s.rho, 0.5 * s.u0, 0.5 * s.u1, 0.5 * s.u2, s.beta, 0.25 * s.usq};
+}
+
+// The same reverse for full-form states and cotangents (the interface terms).
+__device__ __forceinline__ void ec_flux_vjp(const Prim& a, const Prim& b, double n0, double n1, double n2,
+                                            const double mu[5], const Phys& ph, PBar& ab, PBar& bb) {
+    PRaw ra{0, 0, 0, 0, 0, 0}, rb{0, 0, 0, 0, 0, 0};
+    ec_pair_vjp(to_pair_form(a), to_pair_form(b), n0, n1, n2, mu, ph, ra, rb);
+    raw_to_pbar(ra, ab);
+    raw_to_pbar(rb, bb);
 }
 
 // Reverse of the contracted Kennedy-Gruber flux (the SF-KG variant): with arithmetic means
@@ -241,6 +327,12 @@ __device__ __forceinline__ void load_prim(const double* sP, int N3, int idx, Pri
     s.u2 = sP[3 * N3 + idx];
     s.beta = sP[4 * N3 + idx];
     s.usq = sP[5 * N3 + idx];
+}
+
+// the pair form (half velocities, |u|^2/4) kept at rows 10..13 of the primitive array
+__device__ __forceinline__ PrimH load_pair_form(const double* sP, int N3, int idx) {
+    return PrimH{sP[idx], sP[10 * N3 + idx], sP[11 * N3 + idx], sP[12 * N3 + idx], sP[4 * N3 + idx],
+                 sP[13 * N3 + idx]};
 }
 
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
@@ -434,8 +526,8 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
     const int node = t - el_loc * N3;
     const int64_t el = (int64_t)blockIdx.x * EPB + el_loc;
     const bool active = el < K;
-    double* sP = smem + (size_t)el_loc * CfgA<N>::SM;   // [10][N3] rho,u0,u1,u2,beta,usq,w2..w5
-    double* sL = sP + 10 * N3;                          // [5][N3] lt = lambda / J
+    double* sP = smem + (size_t)el_loc * CfgA<N>::SM;   // [14][N3] rho,u0,u1,u2,beta,usq,w2..w5,u/2,|u|^2/4
+    double* sL = sP + 14 * N3;                          // [5][N3] lt = lambda / J
     double* sG = sL + 5 * N3;                           // [10][N3]
     double* sB = sG + 10 * N3;                          // [6][N3] primitive cotangents
     double* sQ = sB + 6 * N3;                           // [5][N3] direct conserved cotangents
@@ -460,6 +552,10 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
         sP[7 * N3 + node] = 2.0 * s.beta * s.u1;
         sP[8 * N3 + node] = 2.0 * s.beta * s.u2;
         sP[9 * N3 + node] = -2.0 * s.beta;
+        sP[10 * N3 + node] = 0.5 * s.u0;
+        sP[11 * N3 + node] = 0.5 * s.u1;
+        sP[12 * N3 + node] = 0.5 * s.u2;
+        sP[13 * N3 + node] = 0.25 * s.usq;
 #pragma unroll
         for (int c = 0; c < 10; ++c) sG[c * N3 + node] = geom[(el * 10 + c) * N3 + node];
         const double Jinv = rcp_newton2(sG[node]);
@@ -483,50 +579,81 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
             const double* n0p = sG + (1 + 3 * l) * N3;
             const double* n1p = n0p + N3;
             const double* n2p = n1p + N3;
-            PBar acc[N];
+            // pair cotangent mu = S_ij (lt_j/w_j - lt_i/w_i) = SW_ij lt_j + SW_ji lt_i, half of the pair
+            // term's 2 S_ij (...): the flux is linear in n, so it takes the sum of the two metrics
+            if constexpr (VF == kAdjESC) {
+                PRaw acc[N];
 #pragma unroll
-            for (int i = 0; i < N; ++i) acc[i] = PBar{0, 0, 0, 0, 0, 0};
+                for (int i = 0; i < N; ++i) acc[i] = PRaw{0, 0, 0, 0, 0, 0};
 #pragma unroll
-            for (int i = 0; i < N - 1; ++i) {
-                const int ii = base + i * st;
-                Prim si;
-                load_prim(sP, N3, ii, si);
-                const double a0 = n0p[ii], a1 = n1p[ii], a2 = n2p[ii];
-                double li[5];
+                for (int i = 0; i < N - 1; ++i) {
+                    const int ii = base + i * st;
+                    const PrimH si = load_pair_form(sP, N3, ii);
+                    const double a0 = n0p[ii], a1 = n1p[ii], a2 = n2p[ii];
+                    double li[5];
 #pragma unroll
-                for (int v = 0; v < 5; ++v) li[v] = sL[v * N3 + ii] * ops.winv[i];
+                    for (int v = 0; v < 5; ++v) li[v] = sL[v * N3 + ii];
 #pragma unroll
-                for (int j = i + 1; j < N; ++j) {
-                    const int jj = base + j * st;
-                    Prim sj;
-                    load_prim(sP, N3, jj, sj);
-                    const double c = ops.S2[i][j];
-                    double mu[5];
+                    for (int j = i + 1; j < N; ++j) {
+                        const int jj = base + j * st;
+                        const PrimH sj = load_pair_form(sP, N3, jj);
+                        double mu[5];
 #pragma unroll
-                    for (int v = 0; v < 5; ++v) mu[v] = c * (sL[v * N3 + jj] * ops.winv[j] - li[v]);
-                    if constexpr (VF == kAdjDC) {
-                        // the pair term is 2 S_ij times the central flux (F(q_i).Ja_l(i) + F(q_j).Ja_l(j))/2
-                        // of the nodal contravariant fluxes (D applied to nodal fluxes)
-                        double h[5];
-#pragma unroll
-                        for (int v = 0; v < 5; ++v) h[v] = 0.5 * mu[v];
-                        euler_flux_vjp(si, a0, a1, a2, h, ph, acc[i]);
-                        euler_flux_vjp(sj, n0p[jj], n1p[jj], n2p[jj], h, ph, acc[j]);
-                    } else {
-                        flux_vjp<VF>(si, sj, 0.5 * (a0 + n0p[jj]), 0.5 * (a1 + n1p[jj]), 0.5 * (a2 + n2p[jj]), mu,
-                                     ph, acc[i], acc[j]);
+                        for (int v = 0; v < 5; ++v) mu[v] = fma(ops.SW[i][j], sL[v * N3 + jj], ops.SW[j][i] * li[v]);
+                        ec_pair_vjp(si, sj, a0 + n0p[jj], a1 + n1p[jj], a2 + n2p[jj], mu, ph, acc[i], acc[j]);
                     }
                 }
-            }
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const int ii = base + i * st;
-                Bl[ii] = acc[i].rho;
-                Bl[N3 + ii] = acc[i].u0;
-                Bl[2 * N3 + ii] = acc[i].u1;
-                Bl[3 * N3 + ii] = acc[i].u2;
-                Bl[4 * N3 + ii] = acc[i].beta;
-                Bl[5 * N3 + ii] = acc[i].usq;
+                for (int i = 0; i < N; ++i) {
+                    const int ii = base + i * st;
+                    Bl[ii] = acc[i].rho;
+                    Bl[N3 + ii] = 0.5 * acc[i].u0;
+                    Bl[2 * N3 + ii] = 0.5 * acc[i].u1;
+                    Bl[3 * N3 + ii] = 0.5 * acc[i].u2;
+                    Bl[4 * N3 + ii] = acc[i].beta;
+                    Bl[5 * N3 + ii] = -0.25 * acc[i].c;
+                }
+            } else {
+                PBar acc[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) acc[i] = PBar{0, 0, 0, 0, 0, 0};
+#pragma unroll
+                for (int i = 0; i < N - 1; ++i) {
+                    const int ii = base + i * st;
+                    Prim si;
+                    load_prim(sP, N3, ii, si);
+                    const double a0 = n0p[ii], a1 = n1p[ii], a2 = n2p[ii];
+                    double li[5];
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) li[v] = sL[v * N3 + ii];
+#pragma unroll
+                    for (int j = i + 1; j < N; ++j) {
+                        const int jj = base + j * st;
+                        Prim sj;
+                        load_prim(sP, N3, jj, sj);
+                        double mu[5];
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) mu[v] = fma(ops.SW[i][j], sL[v * N3 + jj], ops.SW[j][i] * li[v]);
+                        if constexpr (VF == kAdjDC) {
+                            // the pair term is 2 S_ij times the central flux (F(q_i).Ja_l(i) + F(q_j).Ja_l(j))/2
+                            // of the nodal contravariant fluxes (D applied to nodal fluxes)
+                            euler_flux_vjp(si, a0, a1, a2, mu, ph, acc[i]);
+                            euler_flux_vjp(sj, n0p[jj], n1p[jj], n2p[jj], mu, ph, acc[j]);
+                        } else {
+                            kg_flux_vjp(si, sj, a0 + n0p[jj], a1 + n1p[jj], a2 + n2p[jj], mu, ph, acc[i], acc[j]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    const int ii = base + i * st;
+                    Bl[ii] = acc[i].rho;
+                    Bl[N3 + ii] = acc[i].u0;
+                    Bl[2 * N3 + ii] = acc[i].u1;
+                    Bl[3 * N3 + ii] = acc[i].u2;
+                    Bl[4 * N3 + ii] = acc[i].beta;
+                    Bl[5 * N3 + ii] = acc[i].usq;
+                }
             }
         }
     }

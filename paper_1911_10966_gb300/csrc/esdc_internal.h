@@ -17,7 +17,7 @@ constexpr int kLargeN = 16;  // p = 15: the multi-pass float64 residual (rhs_lar
 struct Ops {
     int N;
     double D[kMaxN][kMaxN];    // collocation derivative D = P^-1 Q (Sec. 2, Definition 1)
-    double S2[kMaxN][kMaxN];   // 2 S with S = Q - E/2 skew-symmetric
+    double SW[kMaxN][kMaxN];   // S_ij / w_j with S = Q - E/2 skew-symmetric (the adjoint's pair weights)
     double S[kMaxN][kMaxN];    // S itself (the pair coefficient of the forward kernels)
     double w[kLargeN];         // LGL weights (diagonal of P), every supported degree
     double winv[kLargeN];      // 1/w

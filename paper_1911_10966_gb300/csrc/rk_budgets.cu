@@ -13,59 +13,83 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-// out[i] = q0[i] + sum_j coef_j k_j[i]; two doubles per thread per iteration (16-byte accesses).  NK,
-// the number of terms, is a template parameter so that the stage pointers stay in parameter space,
-// all loads of an iteration are issued together and no float64 work is spent on absent terms;
-// terms are summed in stage order.
-template <int NK>
+// out[i] = q0[i] + sum_j coef_j k_j[i]; with V2 two doubles per thread per iteration (16-byte accesses,
+// every pointer 16-byte aligned), else one.  NK, the number of terms, is a template parameter so that
+// the stage pointers stay in parameter space, all loads of an iteration are issued together and no
+// float64 work is spent on absent terms; terms are summed in stage order.
+template <int NK, bool V2>
 __global__ void __launch_bounds__(256) combine_kernel(double* __restrict__ out, const double* __restrict__ q0,
                                                       const Combine cb, int64_t n) {
-    const int64_t n2 = n / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-        double2 kv[NK];
+    if constexpr (V2) {
+        const int64_t n2 = n / 2;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+            double2 kv[NK];
 #pragma unroll
-        for (int j = 0; j < NK; ++j) kv[j] = reinterpret_cast<const double2*>(cb.k[j])[i];
-        double2 acc = reinterpret_cast<const double2*>(q0)[i];
+            for (int j = 0; j < NK; ++j) kv[j] = reinterpret_cast<const double2*>(cb.k[j])[i];
+            double2 acc = reinterpret_cast<const double2*>(q0)[i];
 #pragma unroll
-        for (int j = 0; j < NK; ++j) {
-            acc.x = fma(cb.coef[j], kv[j].x, acc.x);
-            acc.y = fma(cb.coef[j], kv[j].y, acc.y);
+            for (int j = 0; j < NK; ++j) {
+                acc.x = fma(cb.coef[j], kv[j].x, acc.x);
+                acc.y = fma(cb.coef[j], kv[j].y, acc.y);
+            }
+            reinterpret_cast<double2*>(out)[i] = acc;
         }
-        reinterpret_cast<double2*>(out)[i] = acc;
-    }
-    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        double acc = q0[n - 1];
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+            double acc = q0[n - 1];
 #pragma unroll
-        for (int j = 0; j < NK; ++j) acc = fma(cb.coef[j], cb.k[j][n - 1], acc);
-        out[n - 1] = acc;
+            for (int j = 0; j < NK; ++j) acc = fma(cb.coef[j], cb.k[j][n - 1], acc);
+            out[n - 1] = acc;
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            double kv[NK];
+#pragma unroll
+            for (int j = 0; j < NK; ++j) kv[j] = cb.k[j][i];
+            double acc = q0[i];
+#pragma unroll
+            for (int j = 0; j < NK; ++j) acc = fma(cb.coef[j], kv[j], acc);
+            out[i] = acc;
+        }
     }
 }
 
-// out[i] = sum_j c_j x_j[i] over NT terms, two doubles per thread and iteration, terms in j order
-// (the first one a product, the rest fused multiply-adds).  Each thread reads all its terms before
-// writing, so out may alias an input.
-template <int NT>
+// out[i] = sum_j c_j x_j[i] over NT terms, terms in j order (the first one a product, the rest fused
+// multiply-adds); with V2 two doubles per thread and iteration (every pointer 16-byte aligned), else
+// one.  Each thread reads all its terms before writing, so out may alias an input.
+template <int NT, bool V2>
 __global__ void __launch_bounds__(256) lincomb_kernel(double* __restrict__ out, const LinComb lc, int64_t n) {
-    const int64_t n2 = n / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-        double2 xv[NT];
+    if constexpr (V2) {
+        const int64_t n2 = n / 2;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+            double2 xv[NT];
 #pragma unroll
-        for (int j = 0; j < NT; ++j) xv[j] = reinterpret_cast<const double2*>(lc.x[j])[i];
-        double2 acc = make_double2(lc.c[0] * xv[0].x, lc.c[0] * xv[0].y);
+            for (int j = 0; j < NT; ++j) xv[j] = reinterpret_cast<const double2*>(lc.x[j])[i];
+            double2 acc = make_double2(lc.c[0] * xv[0].x, lc.c[0] * xv[0].y);
 #pragma unroll
-        for (int j = 1; j < NT; ++j) {
-            acc.x = fma(lc.c[j], xv[j].x, acc.x);
-            acc.y = fma(lc.c[j], xv[j].y, acc.y);
+            for (int j = 1; j < NT; ++j) {
+                acc.x = fma(lc.c[j], xv[j].x, acc.x);
+                acc.y = fma(lc.c[j], xv[j].y, acc.y);
+            }
+            reinterpret_cast<double2*>(out)[i] = acc;
         }
-        reinterpret_cast<double2*>(out)[i] = acc;
-    }
-    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        double acc = lc.c[0] * lc.x[0][n - 1];
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+            double acc = lc.c[0] * lc.x[0][n - 1];
 #pragma unroll
-        for (int j = 1; j < NT; ++j) acc = fma(lc.c[j], lc.x[j][n - 1], acc);
-        out[n - 1] = acc;
+            for (int j = 1; j < NT; ++j) acc = fma(lc.c[j], lc.x[j][n - 1], acc);
+            out[n - 1] = acc;
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            double xv[NT];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) xv[j] = lc.x[j][i];
+            double acc = lc.c[0] * xv[0];
+#pragma unroll
+            for (int j = 1; j < NT; ++j) acc = fma(lc.c[j], xv[j], acc);
+            out[i] = acc;
+        }
     }
 }
 
@@ -333,18 +357,32 @@ cudaError_t launch_ke_gradient(const esdc_ctx* c, const double* q, double* grad,
     return cudaGetLastError();
 }
 
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <int NK>
+void combine_any(unsigned g, bool v2, double* out, const double* q0, const Combine& cb, int64_t n, cudaStream_t s) {
+    if (v2)
+        combine_kernel<NK, true><<<g, 256, 0, s>>>(out, q0, cb, n);
+    else
+        combine_kernel<NK, false><<<g, 256, 0, s>>>(out, q0, cb, n);
+}
+
+// Stage states inside caller arrays (checkpoints, stored stages) start at multiples of the state
+// size, only 8-byte aligned when K N^3 is odd: such calls take the one-double-per-thread kernels.
 cudaError_t launch_combine(double* out, const double* q0, const Combine& cb, int64_t n, cudaStream_t s) {
-    int64_t blocks = (n / 2 + 255) / 256;
+    bool v2 = aligned16(out) && aligned16(q0);
+    for (int j = 0; j < cb.nk && j < 6; ++j) v2 = v2 && aligned16(cb.k[j]);
+    int64_t blocks = ((v2 ? n / 2 : n) + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > grid_cap()) blocks = grid_cap();
     const unsigned g = (unsigned)blocks;
     switch (cb.nk) {
-        case 1: combine_kernel<1><<<g, 256, 0, s>>>(out, q0, cb, n); break;
-        case 2: combine_kernel<2><<<g, 256, 0, s>>>(out, q0, cb, n); break;
-        case 3: combine_kernel<3><<<g, 256, 0, s>>>(out, q0, cb, n); break;
-        case 4: combine_kernel<4><<<g, 256, 0, s>>>(out, q0, cb, n); break;
-        case 5: combine_kernel<5><<<g, 256, 0, s>>>(out, q0, cb, n); break;
-        case 6: combine_kernel<6><<<g, 256, 0, s>>>(out, q0, cb, n); break;
+        case 1: combine_any<1>(g, v2, out, q0, cb, n, s); break;
+        case 2: combine_any<2>(g, v2, out, q0, cb, n, s); break;
+        case 3: combine_any<3>(g, v2, out, q0, cb, n, s); break;
+        case 4: combine_any<4>(g, v2, out, q0, cb, n, s); break;
+        case 5: combine_any<5>(g, v2, out, q0, cb, n, s); break;
+        case 6: combine_any<6>(g, v2, out, q0, cb, n, s); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -373,19 +411,29 @@ Ln2 ln2_split() {
     return Ln2{hi, (double)(std::log(2.0L) - (long double)hi)};
 }
 
+template <int NT>
+void lincomb_any(unsigned g, bool v2, double* out, const LinComb& lc, int64_t n, cudaStream_t s) {
+    if (v2)
+        lincomb_kernel<NT, true><<<g, 256, 0, s>>>(out, lc, n);
+    else
+        lincomb_kernel<NT, false><<<g, 256, 0, s>>>(out, lc, n);
+}
+
 cudaError_t launch_lincomb(double* out, const LinComb& lc, int64_t n, cudaStream_t s) {
-    int64_t blocks = (n / 2 + 255) / 256;
+    bool v2 = aligned16(out);
+    for (int j = 0; j < lc.n && j < 7; ++j) v2 = v2 && aligned16(lc.x[j]);
+    int64_t blocks = ((v2 ? n / 2 : n) + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > grid_cap()) blocks = grid_cap();
     const unsigned g = (unsigned)blocks;
     switch (lc.n) {
-        case 1: lincomb_kernel<1><<<g, 256, 0, s>>>(out, lc, n); break;
-        case 2: lincomb_kernel<2><<<g, 256, 0, s>>>(out, lc, n); break;
-        case 3: lincomb_kernel<3><<<g, 256, 0, s>>>(out, lc, n); break;
-        case 4: lincomb_kernel<4><<<g, 256, 0, s>>>(out, lc, n); break;
-        case 5: lincomb_kernel<5><<<g, 256, 0, s>>>(out, lc, n); break;
-        case 6: lincomb_kernel<6><<<g, 256, 0, s>>>(out, lc, n); break;
-        case 7: lincomb_kernel<7><<<g, 256, 0, s>>>(out, lc, n); break;
+        case 1: lincomb_any<1>(g, v2, out, lc, n, s); break;
+        case 2: lincomb_any<2>(g, v2, out, lc, n, s); break;
+        case 3: lincomb_any<3>(g, v2, out, lc, n, s); break;
+        case 4: lincomb_any<4>(g, v2, out, lc, n, s); break;
+        case 5: lincomb_any<5>(g, v2, out, lc, n, s); break;
+        case 6: lincomb_any<6>(g, v2, out, lc, n, s); break;
+        case 7: lincomb_any<7>(g, v2, out, lc, n, s); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -289,41 +289,67 @@ class Solver:
             out["dt_history"] = list(hist)[:min(int(history), out["accepted"])]
         return out
 
-    def rk_step_ckpt(self, q, dt, nsteps, stages=False):
-        """Advance q in place and return the checkpoints of the adjoint: the state before each step,
-        [nsteps, K, 5, N, N, N], or with stages=True the six stage states of every step,
-        [nsteps, 6, K, 5, N, N, N] (six times the memory, no recomputation in the reverse sweep)."""
+    def rk_step_ckpt(self, q, dt, nsteps, stages=False, k1=True):
+        """Advance q in place and return the checkpoints of the adjoint: with stages=True the six stage
+        states of every step, [nsteps, 6, K, 5, N, N, N] (no recomputation in the reverse sweep);
+        otherwise the state before each step with its residual (k1=True, [nsteps, 2, K, 5, N, N, N];
+        four residual recomputations per step in the reverse sweep) or alone (k1=False,
+        [nsteps, K, 5, N, N, N]; five)."""
         self._check_state(q)
-        shape = (nsteps, 6) + self.state_shape if stages else (nsteps,) + self.state_shape
+        if stages:
+            shape = (nsteps, 6) + self.state_shape
+        elif k1:
+            shape = (nsteps, 2) + self.state_shape
+        else:
+            shape = (nsteps,) + self.state_shape
         ck = torch.empty(shape, dtype=torch.float64, device=self.device)
         nb = self.workspace_bytes()
         if self._ws is None or self._ws.numel() < nb:
             self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
-        fn = "esdc_rk_step_stages" if stages else "esdc_rk_step_ckpt"
+        L = nat.lib()
         with torch.cuda.device(self.device):
-            nat.check(getattr(nat.lib(), fn)(self._ctx, q.data_ptr(), float(dt), int(nsteps), ck.data_ptr(),
-                                             self._ws.data_ptr(), self._ws.numel(), _stream_ptr()), fn)
+            if stages:
+                nat.check(L.esdc_rk_step_stages(self._ctx, q.data_ptr(), float(dt), int(nsteps), ck.data_ptr(),
+                                                self._ws.data_ptr(), self._ws.numel(), _stream_ptr()),
+                          "esdc_rk_step_stages")
+            else:
+                nat.check(L.esdc_rk_step_ckpt(self._ctx, q.data_ptr(), float(dt), int(nsteps), ck.data_ptr(),
+                                              1 if k1 else 0, self._ws.data_ptr(), self._ws.numel(), _stream_ptr()),
+                          "esdc_rk_step_ckpt")
         return ck
 
+    def _checkpoint_kind(self, ckpt):
+        """'stages', 'k1' or 'state' for a tensor returned by rk_step_ckpt of this solver."""
+        ok = ckpt.is_cuda and ckpt.dtype == torch.float64 and ckpt.is_contiguous() and ckpt.device == self.device
+        nd = len(self.state_shape)
+        if ok and ckpt.dim() == nd + 2 and tuple(ckpt.shape[2:]) == self.state_shape and ckpt.shape[1] in (2, 6):
+            return "stages" if ckpt.shape[1] == 6 else "k1"
+        if ok and ckpt.dim() == nd + 1 and tuple(ckpt.shape[1:]) == self.state_shape:
+            return "state"
+        raise ValueError("ckpt must come from rk_step_ckpt of this solver")
+
     def rk_adjoint(self, ckpt, dt, lam):
-        """Reverse sweep from the checkpoints of rk_step_ckpt (per-step states: stage recomputation;
-        stage states: none): lam (dL/dq_N) is replaced by dL/dq_0; returns (lam, dL/dmu)."""
+        """Reverse sweep from the checkpoints of rk_step_ckpt (per-step states, with or without their
+        residuals: stage recomputation; stage states: none): lam (dL/dq_N) is replaced by dL/dq_0;
+        returns (lam, dL/dmu)."""
         self._check_state(lam)
-        stages = ckpt.dim() == len(self.state_shape) + 2
-        if not (ckpt.is_cuda and ckpt.dtype == torch.float64 and ckpt.is_contiguous() and ckpt.device == self.device
-                and tuple(ckpt.shape[2 if stages else 1:]) == self.state_shape and (not stages or ckpt.shape[1] == 6)):
-            raise ValueError("ckpt must come from rk_step_ckpt of this solver")
+        kind = self._checkpoint_kind(ckpt)
         nsteps = ckpt.shape[0]
         b = ctypes.c_size_t()
         nat.check(nat.lib().esdc_rk_adjoint_workspace_bytes(self._ctx, ctypes.byref(b)), "workspace")
         if self._adj_ws is None or self._adj_ws.numel() < b.value:
             self._adj_ws = torch.empty(b.value, dtype=torch.uint8, device=self.device)
         gm = ctypes.c_double()
-        fn = "esdc_rk_adjoint_stages" if stages else "esdc_rk_adjoint"
+        L = nat.lib()
         with torch.cuda.device(self.device):
-            nat.check(getattr(nat.lib(), fn)(self._ctx, ckpt.data_ptr(), float(dt), int(nsteps), lam.data_ptr(),
-                                             ctypes.byref(gm), self._adj_ws.data_ptr(), self._adj_ws.numel(),
-                                             _stream_ptr()), fn)
+            if kind == "stages":
+                nat.check(L.esdc_rk_adjoint_stages(self._ctx, ckpt.data_ptr(), float(dt), int(nsteps), lam.data_ptr(),
+                                                   ctypes.byref(gm), self._adj_ws.data_ptr(), self._adj_ws.numel(),
+                                                   _stream_ptr()), "esdc_rk_adjoint_stages")
+            else:
+                nat.check(L.esdc_rk_adjoint(self._ctx, ckpt.data_ptr(), 1 if kind == "k1" else 0, float(dt),
+                                            int(nsteps), lam.data_ptr(), ctypes.byref(gm), self._adj_ws.data_ptr(),
+                                            self._adj_ws.numel(), _stream_ptr()), "esdc_rk_adjoint")
         return lam, gm.value
 
     @property

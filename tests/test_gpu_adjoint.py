@@ -137,27 +137,40 @@ def test_trajectory_gradient_vortex_8cubed_p4_50_steps():
     assert abs(gold["dke_dmu"] - gmu) <= 1e-9 * abs(gmu)
 
 
-def test_stage_checkpoints_equal_recomputation():
+@pytest.mark.parametrize("p,k", [(3, (3, 3, 2)), (2, (3, 3, 3))])
+def test_stage_checkpoints_equal_recomputation(p, k):
     """The reverse sweep from stored stage states (esdc_rk_step_stages / esdc_rk_adjoint_stages) and
-    the one that recomputes them from per-step checkpoints evaluate the same VJPs at stage states
-    that agree bit for bit, so the gradients agree to rounding of the stage combinations (<= 1e-13)."""
-    from paper_1911_10966_gb300.autograd import KineticEnergy, Trajectory
-    solver, qg, mesh, gas, qo = make_pair(3, (3, 3, 2), warp=0.1, seed=6, Re=300.0, Ma=0.5, state="vortex",
+    the two that recompute them from per-step checkpoints (the state with its residual, four
+    recomputed residuals per step; the state alone, five) evaluate the same VJPs at stage states that
+    agree bit for bit, so the gradients agree to rounding (<= 1e-13).  The second mesh has an odd node
+    count (27 elements of 27 nodes), so the states inside the checkpoint arrays start at 8-byte aligned
+    offsets."""
+    solver, qg, mesh, gas, qo = make_pair(p, k, warp=0.1, seed=6, Re=300.0, Ma=0.5, state="vortex",
                                           box=([-5.0] * 3, [5.0] * 3))
+    assert (solver.n_nodes % 2 == 1) == (p == 2)
     dt = 0.5 * solver.dt_cfl(qg, 0.5)
-    grads = []
-    for stages in (True, False):
-        q0 = qg.clone().requires_grad_(True)
-        mu = torch.tensor(solver.mu, dtype=torch.float64, requires_grad=True)
-        qN = Trajectory.apply(q0, mu, solver, dt, 4, stages)
-        KineticEnergy.apply(qN, solver).backward()
-        grads.append((q0.grad.clone(), float(mu.grad), qN.detach().clone()))
-    (ga, ma, qa), (gb, mb, qb) = grads
-    assert torch.equal(qa, qb)
-    e = normwise_errors(ga, gb.cpu())
-    print("stage checkpoints vs recomputation", ["%.1e" % x for x in e], ma, mb)
-    assert max(e) <= 1e-13, e
-    assert abs(ma - mb) <= 1e-13 * abs(mb)
+    out = {}
+    for kind in ("stages", "k1", "state"):
+        q = qg.clone()
+        ck = solver.rk_step_ckpt(q, dt, 4, stages=kind == "stages", k1=kind == "k1")
+        lam = solver.ke_gradient(q)
+        g, gmu = solver.rk_adjoint(ck, dt, lam)
+        out[kind] = (g.clone(), gmu, q.clone())
+    ga, ma, qa = out["stages"]
+    for kind in ("k1", "state"):
+        gb, mb, qb = out[kind]
+        assert torch.equal(qa, qb)
+        e = normwise_errors(ga, gb.cpu())
+        print("stage checkpoints vs recomputation (%s)" % kind, ["%.1e" % x for x in e], ma, mb)
+        assert max(e) <= 1e-13, e
+        assert abs(ma - mb) <= 1e-13 * abs(mb)
+    # the autograd wrapper takes the same paths
+    from paper_1911_10966_gb300.autograd import KineticEnergy, Trajectory
+    q0 = qg.clone().requires_grad_(True)
+    mu = torch.tensor(solver.mu, dtype=torch.float64, requires_grad=True)
+    KineticEnergy.apply(Trajectory.apply(q0, mu, solver, dt, 4, False), solver).backward()
+    assert max(normwise_errors(ga, q0.grad.cpu())) <= 1e-13
+    assert abs(float(mu.grad) - ma) <= 1e-13 * abs(ma)
 
 
 def test_trajectory_gradient_matches_oracle_autograd():
