@@ -705,9 +705,9 @@ def _fp32_object(p, n, ms_step, kernel_ms, face_ms, peak32, e_v, ws, dist, devic
             "dtype": "f32 residual, f64 state/update/budgets", "roofline": roof,
             "residual_error_vs_f64": {"per_variable": e_v, "variables": ["rho", "rho u1", "rho u2", "rho u3", "rho E"],
                                       "state": "Taylor-Green initial state, whole mesh, normwise"},
-            # per step: shadow state, element + viscous face kernel per residual (stage states are
-            # formed inside the element kernel), the float64 update, budgets + final sum
-            "gpu_launches_per_step": 1 + RHS_PER_STEP * 2 + 1 + 2}
+            # per step: shadow state, element + viscous face kernel per residual, the float32 stage
+            # states of the five later stages, the float64 update, budgets + final sum
+            "gpu_launches_per_step": 1 + RHS_PER_STEP * 2 + (RHS_PER_STEP - 1) + 1 + 2}
 
 
 def _precision_run(s64, s32, q64, q32, dt, done, total):

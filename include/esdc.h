@@ -229,9 +229,10 @@ int esdc_rhs_host(esdc_ctx* ctx, const double* q_host, void* dqdt_host, void* st
 /*
  * esdc_workspace_bytes -- device workspace needed by esdc_rk_step (what = 0): for ESDC_PREC_FP64
  * six stage derivatives and one stage state, each K*5*N^3 float64; for ESDC_PREC_FP32 six float32
- * stage derivatives and one float32 perturbation state (each sub-buffer 256-byte aligned).
+ * stage derivatives and two float32 perturbation states, the step's base and the current stage
+ * state (each sub-buffer 256-byte aligned).
  * what = 1: esdc_rk_adaptive's workspace: for ESDC_PREC_FP64 nine K*5*N^3 float64 buffers; for
- * ESDC_PREC_FP32 nine K*5*N^3 float32 buffers and one float64 buffer.
+ * ESDC_PREC_FP32 ten K*5*N^3 float32 buffers and one float64 buffer.
  */
 int esdc_workspace_bytes(const esdc_ctx* ctx, int what, size_t* bytes);
 

@@ -87,8 +87,29 @@ int rhs_impl(esdc_ctx* c, const double* q, void* dqdt, cudaStream_t s) {
 }
 
 // Mixed precision: nsteps DP5 steps with float32 residuals on float32 perturbation stage states
-// (formed inside the residual kernel from the step's shadow state and the earlier stage
-// derivatives) and the float64 solution update q += dt sum_j b_j k_j (accumulated in float64).
+// (formed by a streaming kernel from the step's shadow state and the earlier stage derivatives) and
+// the float64 solution update q += dt sum_j b_j k_j (accumulated in float64).
+// Stage st of a float32-mixed DP5 step of size h: the stage state base + h sum_j a_st,j k_j (into y;
+// the base itself for st = 0), then its residual into out.
+cudaError_t stage_then_rhs_f32(esdc_ctx* c, const float* base, float* const k[], int st, double h, float* y,
+                               float* out, cudaStream_t s) {
+    esdc::StageF in{};
+    in.base = base;
+    for (int j = 0; j < st; ++j) {
+        if (kA[st][j] == 0.0) continue;
+        in.k[in.nk] = k[j];
+        in.c[in.nk] = (float)(h * kA[st][j]);
+        ++in.nk;
+    }
+    if (in.nk > 0) {
+        const cudaError_t e = esdc::launch_stage_f32(c, in, y, s);
+        if (e != cudaSuccess) return e;
+        in = esdc::StageF{};
+        in.base = y;
+    }
+    return esdc::launch_rhs_f32(c, in, out, s, next_events(c));
+}
+
 // the float32 shadow of q in the workspace (the base state of the first step)
 int rk_shadow_f32(esdc_ctx* c, const double* q, void* ws, cudaStream_t s) {
     const size_t sub = round256((size_t)c->n_nodes * 5 * sizeof(float));
@@ -105,19 +126,12 @@ int rk_steps_f32(esdc_ctx* c, double* q, double dt, int nsteps, void* ws, cudaSt
     float* k[6];
     for (int j = 0; j < 6; ++j) k[j] = (float*)((char*)ws + j * sub);
     float* base = (float*)((char*)ws + 6 * sub);
+    float* ystage = (float*)((char*)ws + 7 * sub);
     cudaError_t e;
     for (int step = 0; step < nsteps; ++step) {
         for (int st = 0; st < 6; ++st) {
-            esdc::StageF in{};
-            in.base = base;
-            for (int j = 0; j < st; ++j) {
-                if (kA[st][j] == 0.0) continue;
-                in.k[in.nk] = k[j];
-                in.c[in.nk] = (float)(dt * kA[st][j]);
-                ++in.nk;
-            }
-            e = esdc::launch_rhs_f32(c, in, k[st], s, next_events(c));
-            if (e != cudaSuccess) return cuda_fail(e, "residual (float32)");
+            e = stage_then_rhs_f32(c, base, k, st, dt, ystage, k[st], s);
+            if (e != cudaSuccess) return cuda_fail(e, "stage residual (float32)");
         }
         esdc::Combine64F cb{};
         for (int j = 0; j < 6; ++j)
@@ -375,7 +389,8 @@ int rk_adaptive_f32(esdc_ctx* c, double* q, double t0, double t_end, double* dt_
     for (int j = 0; j < 7; ++j) k[j] = (float*)((char*)ws + j * sub);
     float* base = (float*)((char*)ws + 7 * sub);
     float* base_n = (float*)((char*)ws + 8 * sub);
-    double* qn = (double*)((char*)ws + 9 * sub);
+    float* ystage = (float*)((char*)ws + 9 * sub);
+    double* qn = (double*)((char*)ws + 10 * sub);
     double t = t0, dt = *dt_io;
     int acc = 0, rej = 0;
     int64_t nrhs = 0;
@@ -394,16 +409,8 @@ int rk_adaptive_f32(esdc_ctx* c, double* q, double t0, double t_end, double* dt_
         const bool last = t + dt >= t_end;
         const double h = last ? t_end - t : dt;
         for (int st = 1; st < 6; ++st) {
-            esdc::StageF in{};
-            in.base = base;
-            for (int j = 0; j < st; ++j) {
-                if (kA[st][j] == 0.0) continue;
-                in.k[in.nk] = k[j];
-                in.c[in.nk] = (float)(h * kA[st][j]);
-                ++in.nk;
-            }
-            e = esdc::launch_rhs_f32(c, in, k[st], s, next_events(c));
-            if (e != cudaSuccess) return cuda_fail(e, "residual (float32)");
+            e = stage_then_rhs_f32(c, base, k, st, h, ystage, k[st], s);
+            if (e != cudaSuccess) return cuda_fail(e, "stage residual (float32)");
         }
         // candidate: qn = q + h sum_j b_j k_j in float64, and its shadow
         CUDA_TRY(cudaMemcpyAsync(qn, q, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -943,10 +950,10 @@ int esdc_workspace_bytes(const esdc_ctx* c, int what, size_t* bytes) {
     if (!c || !bytes) return fail(ESDC_ERR_ARG, "null argument");
     if (what != 0 && what != 1) return fail(ESDC_ERR_ARG, "unknown workspace kind");
     if (what == 1 && c->setup.precision == ESDC_PREC_FP32)
-        *bytes = 9 * round256((size_t)c->n_nodes * 5 * sizeof(float)) + round256((size_t)c->n_nodes * 5 * sizeof(double));
+        *bytes = 10 * round256((size_t)c->n_nodes * 5 * sizeof(float)) + round256((size_t)c->n_nodes * 5 * sizeof(double));
     else if (what == 1) *bytes = 9 * round256((size_t)c->n_nodes * 5 * sizeof(double));
     else if (c->setup.precision == ESDC_PREC_FP64) *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(double));
-    else *bytes = 7 * round256((size_t)c->n_nodes * 5 * sizeof(float));
+    else *bytes = 8 * round256((size_t)c->n_nodes * 5 * sizeof(float));
     return ESDC_OK;
 }
 

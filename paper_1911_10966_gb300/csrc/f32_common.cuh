@@ -122,20 +122,6 @@ __device__ __forceinline__ int dir_stride_f(int l) {
     return l == 0 ? 1 : (l == 1 ? N : N * N);
 }
 
-// The residual's input state value at flat index i: base[i] + sum_j c_j k_j[i] (a Runge-Kutta stage
-// formed on the fly; nk = 0 for a plain state).  NK >= nk terms are compiled (the kernel is built
-// for NK = 0, 2 and 5), so only up to NK - nk loads and multiply-adds are predicated off.
-template <int NK>
-__device__ __forceinline__ float stage_value(const StageF& in, int64_t i) {
-    // all loads independent and issued together (predicated on nk), read-only path
-    float kv[NK > 0 ? NK : 1];
-#pragma unroll
-    for (int j = 0; j < NK; ++j) kv[j] = j < in.nk ? __ldg(in.k[j] + i) : 0.0f;
-    float a = __ldg(in.base + i);
-#pragma unroll
-    for (int j = 0; j < NK; ++j) a = fmaf(in.c[j], kv[j], a);
-    return a;
-}
 
 
 // The reference constants of the split flux for a float32-mixed context.

@@ -81,7 +81,8 @@ cudaError_t launch_scale(double* out, const double* x, double a, int64_t n, cuda
 cudaError_t launch_ke_gradient(const esdc_ctx* c, const double* q, double* grad, cudaStream_t s);
 
 // mixed-precision form
-struct StageF {             // residual input base + sum_j c_j k_j (float32 perturbation state)
+struct StageF {             // a stage state base + sum_j c_j k_j (float32 perturbation state); the
+                            // residual kernels take nk = 0, launch_stage_f32 forms the others
     const float* base;
     const float* k[6];
     float c[6];
@@ -100,6 +101,8 @@ struct Combine64F {         // float64 accumulation of float32 stage derivatives
     int nk;
 };
 cudaError_t launch_shadow(const esdc_ctx* c, const double* q, float* dq, cudaStream_t s);
+// y = in.base + sum_j in.c[j] in.k[j] (float32, 1 <= in.nk <= 5; y, base, k 16-byte aligned)
+cudaError_t launch_stage_f32(const esdc_ctx* c, const StageF& in, float* y, cudaStream_t s);
 cudaError_t launch_final_f32(const esdc_ctx* c, double* q, float* dq_new, const Combine64F& cb, cudaStream_t s);
 
 }  // namespace esdc

@@ -4,8 +4,8 @@
 // pressure and enthalpy.
 //
 // Input: the shadow state dq = (rho - rho0, rho u, rho E - E0) in float32 (written by a float64
-// kernel from the float64 state), optionally plus float32 Runge-Kutta stage increments
-// sum_j c_j k_j added on load, float32 geometry, neighbour table.  Reference state rho0 = 1,
+// kernel from the float64 state, or a Runge-Kutta stage state formed from it in float32 by
+// launch_stage_f32), float32 geometry, neighbour table.  Reference state rho0 = 1,
 // p0 = R (T0 = 1), beta0 = 1/(2R), E0 = p0/(gamma-1).
 //
 // The Chandrashekar flux is split exactly as f = f_ref + df with
@@ -97,7 +97,7 @@ __device__ __forceinline__ void load_prim_half(const float4* sP4, int N3, int id
 
 // XF: boundary faces (bounded boxes) and a source term, compiled only into the instantiations that
 // need them (a run-time test for them cost 2% on periodic boxes)
-template <int N, int NK, bool XF, bool KG>
+template <int N, bool XF, bool KG>
 __global__ void __launch_bounds__(CfgF<N>::THREADS, CfgF<N, KG>::MINB)
 rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom,
              const int32_t* __restrict__ nbr, float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph,
@@ -127,7 +127,7 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             float d[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-                d[v] = stage_value<NK>(in, eoff + v * N3 + node);
+                d[v] = __ldg(in.base + eoff + v * N3 + node);
                 sQ[v * N3 + node] = d[v];
             }
             PrimF s;
@@ -221,7 +221,7 @@ rhs_main_f32(const StageF in, float* __restrict__ out, const float* __restrict__
             float qn[5];
             if (!XF || nb >= 0) {
 #pragma unroll
-                for (int v = 0; v < 5; ++v) qn[v] = stage_value<NK>(in, nb * 5 * N3 + v * N3 + nbn);
+                for (int v = 0; v < 5; ++v) qn[v] = __ldg(in.base + nb * 5 * N3 + v * N3 + nbn);
             } else {
                 // boundary face of a bounded box: the float64 exterior state at the own nodes, less
                 // the reference state, rounded once
@@ -433,7 +433,7 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaSt
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     const PhysF& ph = c->physf;
     const Ref ref = make_ref(c);
-    if (in.nk < 0 || in.nk > 5) return cudaErrorInvalidValue;
+    if (in.nk != 0) return cudaErrorInvalidValue;   // stage states are formed by launch_stage_f32
     if (ev) cudaEventRecord(ev[0], s);
     const bool xf = c->setup.bounded != 0 || c->d_src != nullptr;
     const bool kg = c->setup.volume_flux == ESDC_FLUX_KG;
@@ -442,20 +442,10 @@ cudaError_t launch_f32_n(const esdc_ctx* c, const StageF& in, float* out, cudaSt
                                              ref, c->d_nsurff, c->d_qext, c->d_src);
     };
     const size_t smem_kg = (size_t)C::EPB * CfgF<N, true>::SM * sizeof(float);
-    if (kg) {
-        if (in.nk == 0)
-            xf ? go(rhs_main_f32<N, 0, true, true>, smem_kg) : go(rhs_main_f32<N, 0, false, true>, smem_kg);
-        else if (in.nk <= 2)
-            xf ? go(rhs_main_f32<N, 2, true, true>, smem_kg) : go(rhs_main_f32<N, 2, false, true>, smem_kg);
-        else
-            xf ? go(rhs_main_f32<N, 5, true, true>, smem_kg) : go(rhs_main_f32<N, 5, false, true>, smem_kg);
-    } else if (in.nk == 0) {
-        xf ? go(rhs_main_f32<N, 0, true, false>, smem) : go(rhs_main_f32<N, 0, false, false>, smem);
-    } else if (in.nk <= 2) {
-        xf ? go(rhs_main_f32<N, 2, true, false>, smem) : go(rhs_main_f32<N, 2, false, false>, smem);
-    } else {
-        xf ? go(rhs_main_f32<N, 5, true, false>, smem) : go(rhs_main_f32<N, 5, false, false>, smem);
-    }
+    if (kg)
+        xf ? go(rhs_main_f32<N, true, true>, smem_kg) : go(rhs_main_f32<N, false, true>, smem_kg);
+    else
+        xf ? go(rhs_main_f32<N, true, false>, smem) : go(rhs_main_f32<N, false, false>, smem);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (ph.viscous) {
@@ -473,18 +463,10 @@ cudaError_t prepare_f32_n() {
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(float);
     constexpr cudaFuncAttribute kAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     const int sk = (int)((size_t)C::EPB * CfgF<N, true>::SM * sizeof(float));
-    cudaError_t e = cudaFuncSetAttribute(rhs_main_f32<N, 0, false, false>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, false, false>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, false, false>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 0, true, false>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, true, false>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, true, false>, kAttr, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 0, false, true>, kAttr, sk);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, false, true>, kAttr, sk);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, false, true>, kAttr, sk);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 0, true, true>, kAttr, sk);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 2, true, true>, kAttr, sk);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, 5, true, true>, kAttr, sk);
+    cudaError_t e = cudaFuncSetAttribute(rhs_main_f32<N, false, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, true, false>, kAttr, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, false, true>, kAttr, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_main_f32<N, true, true>, kAttr, sk);
     return e;
 }
 

@@ -241,7 +241,7 @@ __device__ __forceinline__ PrimP to_prim2(const f2p dq[5], const Ref& r) {
     return s;
 }
 
-template <int N, int NK, bool XF>
+template <int N, bool XF>
 __global__ void __launch_bounds__(CfgP<N>::THREADS, CfgP<N>::MINB)
 rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict__ geom, const int32_t* __restrict__ nbr,
               float* __restrict__ trace, int64_t K, const OpsF ops, const PhysF ph, const Ref ref,
@@ -276,7 +276,7 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
             const int node = tl + r * TE;
             if (node < N3) {
 #pragma unroll
-                for (int v = 0; v < 5; ++v) d[r][v] = stage_value<NK>(in, eoff + v * N3 + node);
+                for (int v = 0; v < 5; ++v) d[r][v] = __ldg(in.base + eoff + v * N3 + node);
 #pragma unroll
                 for (int c = 0; c < 10; ++c) gv[r][c] = geom[(el * 10 + c) * N3 + node];
             }
@@ -294,7 +294,7 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
                 if (!XF || nb >= 0) {
                     const int nbn = base + (side ? 0 : (N - 1) * st);
 #pragma unroll
-                    for (int v = 0; v < 5; ++v) qn[f][v] = stage_value<NK>(in, nb * 5 * N3 + v * N3 + nbn);
+                    for (int v = 0; v < 5; ++v) qn[f][v] = __ldg(in.base + nb * 5 * N3 + v * N3 + nbn);
                 } else {
                     // boundary face of a bounded box: the float64 exterior state at the own nodes, less
                     // the reference state, rounded once
@@ -710,16 +710,14 @@ cudaError_t launch_pairs_n(const esdc_ctx* c, const StageF& in, float* out, cuda
     const size_t smem = (size_t)C::EPB * C::SM * sizeof(float);
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     const Ref ref = make_ref(c);
-    if (in.nk < 0 || in.nk > 5) return cudaErrorInvalidValue;
+    if (in.nk != 0) return cudaErrorInvalidValue;   // stage states are formed by launch_stage_f32
     if (ev) cudaEventRecord(ev[0], s);
     const bool xf = c->setup.bounded != 0 || c->d_src != nullptr;
     auto go = [&](auto kern) {
         kern<<<grid, C::THREADS, smem, s>>>(in, out, c->d_geomf, c->d_nbr, (float*)c->d_trace, c->K, c->opsf,
                                             c->physf, ref, c->d_nsurff, c->d_qext, c->d_src);
     };
-    if (in.nk == 0) xf ? go(rhs_pairs_f32<N, 0, true>) : go(rhs_pairs_f32<N, 0, false>);
-    else if (in.nk <= 2) xf ? go(rhs_pairs_f32<N, 2, true>) : go(rhs_pairs_f32<N, 2, false>);
-    else xf ? go(rhs_pairs_f32<N, 5, true>) : go(rhs_pairs_f32<N, 5, false>);
+    xf ? go(rhs_pairs_f32<N, true>) : go(rhs_pairs_f32<N, false>);
     if (ev) cudaEventRecord(ev[1], s);
     if (ev) cudaEventRecord(ev[2], s);
     if (c->physf.viscous) {
@@ -735,12 +733,8 @@ template <int N>
 cudaError_t prepare_pairs_n() {
     const int smem = (int)((size_t)CfgP<N>::EPB * CfgP<N>::SM * sizeof(float));
     constexpr cudaFuncAttribute kAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(rhs_pairs_f32<N, 0, false>, kAttr, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 2, false>, kAttr, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 5, false>, kAttr, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 0, true>, kAttr, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 2, true>, kAttr, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, 5, true>, kAttr, smem);
+    cudaError_t e = cudaFuncSetAttribute(rhs_pairs_f32<N, false>, kAttr, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rhs_pairs_f32<N, true>, kAttr, smem);
     return e;
 }
 

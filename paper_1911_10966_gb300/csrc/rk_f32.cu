@@ -1,4 +1,5 @@
-// Float64 <-> float32 state kernels of the mixed-precision form.
+// Float64 <-> float32 state kernels of the mixed-precision form, and its float32 stage states.
+//   stage:   y = base + sum_j c_j k_j in float32 (the input of a stage's residual).
 //   shadow:  dq = float(q - q_ref) with q_ref = (rho0, 0, 0, 0, E0): the float32 perturbation state
 //            the float32 residual reads (float64 subtraction before rounding).
 //   final:   q += sum_j c_j k_j accumulated in float64 (the Runge-Kutta solution update), then the
@@ -96,6 +97,36 @@ __global__ void __launch_bounds__(256) final_kernel(double* __restrict__ q, floa
         }
 }
 
+// y = base + sum_j c_j k_j: a float32 stage state of the mixed-precision step, the terms added in
+// stage order with float32 fused multiply-adds; four entries per thread and iteration (16-byte
+// accesses; workspace buffers), all loads of an iteration issued together.
+template <int NK>
+__global__ void __launch_bounds__(256) stage_kernel(float* __restrict__ y, const StageF in, int64_t n) {
+    const int64_t n4 = n / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
+        float4 kv[NK];
+#pragma unroll
+        for (int j = 0; j < NK; ++j) kv[j] = __ldg(reinterpret_cast<const float4*>(in.k[j]) + t);
+        float4 a = __ldg(reinterpret_cast<const float4*>(in.base) + t);
+#pragma unroll
+        for (int j = 0; j < NK; ++j) {
+            a.x = fmaf(in.c[j], kv[j].x, a.x);
+            a.y = fmaf(in.c[j], kv[j].y, a.y);
+            a.z = fmaf(in.c[j], kv[j].z, a.z);
+            a.w = fmaf(in.c[j], kv[j].w, a.w);
+        }
+        reinterpret_cast<float4*>(y)[t] = a;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = 4 * n4; i < n; ++i) {
+            float a = in.base[i];
+#pragma unroll
+            for (int j = 0; j < NK; ++j) a = fmaf(in.c[j], in.k[j][i], a);
+            y[i] = a;
+        }
+}
+
 unsigned grid_for(int64_t n) {
     int64_t b = (n + 255) / 256;
     if (b < 1) b = 1;
@@ -109,6 +140,20 @@ cudaError_t launch_shadow(const esdc_ctx* c, const double* q, float* dq, cudaStr
     const double E0 = c->phys.R / (c->phys.gamma - 1.0);
     shadow_kernel<<<grid_for(c->n_nodes * 5 / 4), 256, 0, s>>>(q, dq, c->n_nodes, DivU64::make(c->N3),
                                                                DivU64::make(5), 1.0, E0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_f32(const esdc_ctx* c, const StageF& in, float* y, cudaStream_t s) {
+    const int64_t n = c->n_nodes * 5;
+    const unsigned g = grid_for(n / 4);
+    switch (in.nk) {
+        case 1: stage_kernel<1><<<g, 256, 0, s>>>(y, in, n); break;
+        case 2: stage_kernel<2><<<g, 256, 0, s>>>(y, in, n); break;
+        case 3: stage_kernel<3><<<g, 256, 0, s>>>(y, in, n); break;
+        case 4: stage_kernel<4><<<g, 256, 0, s>>>(y, in, n); break;
+        case 5: stage_kernel<5><<<g, 256, 0, s>>>(y, in, n); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
