@@ -568,6 +568,10 @@ def run_ours(args):
     if fp32 is not None:
         if args.precision_steps > 0:
             fp32["trajectory"] = _precision_run(s64, s32, q, q32, dt, done, args.precision_steps)
+        # every bounded wait of the element kernel's bulk copies completed during the whole leg
+        fp32["device_status"] = s32.device_status()
+        if fp32["device_status"] != 0:
+            raise RuntimeError("a bounded wait for bulk shared-memory copies gave up: results invalid")
         s32.close()
         del q32
         torch.cuda.empty_cache()

@@ -419,6 +419,16 @@ int esdc_rk_adjoint_stages(esdc_ctx* ctx, const double* stages_dev, double dt, i
                            double* grad_mu_host, void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /*
+ * esdc_device_status -- status bits the context's kernels recorded on the device since the last
+ * clear: 1 (ESDC_STATUS_BULK_WAIT) = a kernel's bounded wait for its bulk shared-memory copies gave
+ * up (no longer than about a second), and it left its elements' results unwritten.  0 when all
+ * waits completed.  clear = 1 resets the bits.  Synchronises stream (the read is ordered after the
+ * work already on it).
+ */
+#define ESDC_STATUS_BULK_WAIT 1
+int esdc_device_status(esdc_ctx* ctx, int* status_host, int clear, void* stream);
+
+/*
  * esdc_profile -- enable (on = 1) or disable CUDA-event timing of the residual kernels of this
  * context: every esdc_rhs (also inside esdc_rk_step) then records an event pair around the fused
  * element kernel and another around the viscous interface kernel on the call's stream.

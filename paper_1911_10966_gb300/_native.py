@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
         "esdc_mms_fields": (I, [D, D, D, D, D, P, ctypes.c_int64, P, P, P]),
         "esdc_dt_cfl": (I, [P, P, D, ctypes.POINTER(D), P]),
         "esdc_profile": (I, [P, I]),
+        "esdc_device_status": (I, [P, ctypes.POINTER(I), I, P]),
         "esdc_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)]),
         "esdc_probe_fma": (I, [I, ctypes.POINTER(D), P]),
         "esdc_budgets_noalloc": (I, [I, ctypes.c_int64, D, P, P, P, P, P, P]),

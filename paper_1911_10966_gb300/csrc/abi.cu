@@ -530,6 +530,7 @@ void free_ctx(esdc_ctx* c) {
     cudaFree(c->d_shadow);
     cudaFree(c->d_red);
     cudaFree(c->d_red_out);
+    cudaFree(c->d_status);
     cudaFree(c->d_lntab);
     cudaFree(c->d_stage_q);
     cudaFree(c->d_adj_g);
@@ -788,6 +789,8 @@ int esdc_create(const esdc_setup_t* setup, const double* xyz, esdc_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->d_trace, (size_t)c->K * 6 * 4 * N2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_red, (size_t)c->red_blocks * 5 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_red_out, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_lntab, esdc::kLnTab * 3 * sizeof(double));
     if (e == cudaSuccess) {
         std::vector<double> tab(esdc::kLnTab * 3);
@@ -1205,6 +1208,15 @@ int esdc_rk_adjoint_stages(esdc_ctx* c, const double* stages, double dt, int nst
         if (st) return st;
     }
     return adjoint_finish(c, grad_mu, s);
+}
+
+int esdc_device_status(esdc_ctx* c, int* status, int clear, void* stream) {
+    if (!c || !status) return fail(ESDC_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (clear) CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return ESDC_OK;
 }
 
 int esdc_profile(esdc_ctx* c, int on) {

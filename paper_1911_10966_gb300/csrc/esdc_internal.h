@@ -122,6 +122,7 @@ struct esdc_ctx {
     double* d_red = nullptr;         // reduction partials
     double* d_red_out = nullptr;     // reduction results
     double* d_lntab = nullptr;       // [128][3] logarithm table of the budgets (T_k, -ln T_k head, tail)
+    int* d_status = nullptr;         // device status bits (kStatusBulkWait), read by esdc_device_status
     int red_blocks = 0;
     // adjoint buffers, allocated on the first vector-Jacobian product
     double* d_adj_g = nullptr;       // [K][6][5][N2] interface cotangents for the neighbour

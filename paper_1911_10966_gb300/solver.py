@@ -356,6 +356,15 @@ class Solver:
     def mu(self):
         return 1.0 / self.Re if self.Re > 0 else 0.0
 
+    def device_status(self, clear=True):
+        """Status bits the kernels recorded on the device (0: every bounded wait completed; 1: a
+        wait for bulk shared-memory copies gave up and its elements were left unevaluated)."""
+        st = ctypes.c_int()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().esdc_device_status(self._ctx, ctypes.byref(st), 1 if clear else 0, _stream_ptr()),
+                      "esdc_device_status")
+        return st.value
+
     def profile(self, on=True):
         """Record CUDA events around the residual kernels of every following evaluation."""
         nat.check(nat.lib().esdc_profile(self._ctx, 1 if on else 0), "esdc_profile")

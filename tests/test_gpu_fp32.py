@@ -51,6 +51,18 @@ def test_fp32_residual_every_degree_warped(p):
     e, c = _report(solver.rhs(qg), O.rhs(qo, mesh, gas), qo, mesh, gas)
     assert max(c) <= C_MAX
     assert max(e) <= 1e-5
+    assert solver.device_status() == 0
+
+
+@pytest.mark.parametrize("p", [3, 7])
+def test_fp32_packed_kernel_ragged_element_count(p):
+    """The packed kernel's bulk copies on an odd element count (27): at p = 3 two elements share a
+    CTA, so the last CTA copies one; every bounded wait completes (device status 0)."""
+    solver, qg, mesh, gas, qo = make_pair(p, (3, 3, 3), warp=0.1, seed=4, Re=200.0, noise=0.02, precision="fp32")
+    e, c = _report(solver.rhs(qg), O.rhs(qo, mesh, gas), qo, mesh, gas)
+    assert max(c) <= C_MAX
+    assert max(e) <= 1e-5
+    assert solver.device_status() == 0
 
 
 def test_fp32_residual_16cubed_p4_warped_sampled():
@@ -139,6 +151,7 @@ def test_fp32_residual_48cubed_p7_full_size_sampled():
     r = solver.rhs(qg)
     e, c = _report(r[E.cuda()], O.rhs(qo, mesh, gas, elems=mesh.rows), qo, mesh, gas, elems=mesh.rows)
     assert max(c) <= C_MAX
+    assert solver.device_status() == 0
 
 
 @pytest.mark.parametrize("p", [2, 3, 4, 7])
