@@ -1017,6 +1017,25 @@ def study_rhs(p=4, k=16, volume_flux="esc", Re=1600.0, precision="fp64", warp=0.
     s.close()
 
 
+def study_steps(p=7, k=20, precision="fp32", warp=0.0, Re=1600.0, steps=3, warmup=1):
+    """DP5 steps of the bench's step form (one step per call, the float64 budgets of every step into
+    device memory) on the Taylor-Green box of k^3 elements at degree p: the command the kernel
+    profiles of the step's other kernels (stage states, update, budgets) are taken on."""
+    from paper_1911_10966_gb300.solver import Solver
+    p, k, steps, warmup = int(p), int(k), int(steps), int(warmup)
+    s = Solver.box(p, k, k, k, warp=float(warp), Re=float(Re), precision=precision)
+    q = s.init_state("tgv")
+    dt = s.dt_cfl(q, 0.5)
+    for _ in range(warmup):
+        s.rk_step(q, dt, 1)
+        s.budgets(q)
+    ms, ms_main, ms_face, nres = timed_steps(s, q, dt, steps, lambda: None)
+    print(json.dumps({"study": "steps", "p": p, "k": k, "nodes": s.n_nodes, "precision": precision, "steps": steps,
+                      "ms_per_step": ms, "element_kernel_ms": ms_main / max(nres, 1),
+                      "face_kernel_ms": ms_face / max(nres, 1), "device_status": s.device_status()}), flush=True)
+    s.close()
+
+
 def study_variants(degrees="1,3,7,15"):
     """The paper's cost comparison (Sec. 5.2, "Error vs. cost" figure): Taylor-Green at Ma 0.05,
     Re 1600, 256^3 nodes at p = 1, 3, 7, 15, time per fixed DP5 step (six residuals) with the ES-C,
@@ -1203,8 +1222,8 @@ def _lgl_nodes(p):
     return lgl(p)[0]
 
 
-STUDIES = {"rhs": study_rhs, "variants": study_variants, "mms": study_mms, "hconv": study_hconv,
-           "ipsweep": study_ipsweep}
+STUDIES = {"rhs": study_rhs, "steps": study_steps, "variants": study_variants, "mms": study_mms,
+           "hconv": study_hconv, "ipsweep": study_ipsweep}
 
 
 def _study(name, kw):
