@@ -10,11 +10,17 @@
 
 namespace esdc {
 
+// The hardware conversions of the rare cases, kept out of line: inline, the compiler would evaluate
+// them unconditionally beside the integer path and select, putting one float64-pipe conversion on
+// every element again.
+static __device__ __noinline__ double f2d_hw(float f) { return (double)f; }
+static __device__ __noinline__ float d2f_hw(double x) { return (float)x; }
+
 // exact float -> double: rebias the exponent (127 -> 1023) and widen the 23-bit significand
 __device__ __forceinline__ double f2d_int(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xFFu;
-    if (e == 0u || e == 0xFFu) return (double)f;
+    if (e == 0u || e == 0xFFu) return f2d_hw(f);
     const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xFFFFFu);
     return __hiloint2double((int)hi, (int)(u << 29));
 }
@@ -25,7 +31,7 @@ __device__ __forceinline__ double f2d_int(float f) {
 __device__ __forceinline__ float d2f_int(double x) {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
     const unsigned e = (hi >> 20) & 0x7FFu;
-    if (e < 897u || e > 1150u) return (float)x;          // float zero/subnormal/overflow/inf/nan range
+    if (e < 897u || e > 1150u) return d2f_hw(x);         // float zero/subnormal/overflow/inf/nan range
     const unsigned kept = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // 23 bits
     const unsigned rest = lo & 0x1FFFFFFFu;                       // 29 dropped bits
     const unsigned half = 0x10000000u;
