@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(CfgA<N>::THREADS, CfgA<N>::MINB)
 adj_main(const double* __restrict__ q, const double* __restrict__ lam, const double* __restrict__ geom,
          const int32_t* __restrict__ nbr, double* __restrict__ grad, double* __restrict__ gbuf,
          double* __restrict__ tbuf, double* __restrict__ mupart, int64_t K, const Ops ops, const Phys ph,
-         const double* __restrict__ nsurf, const double* __restrict__ qext) {
+         const double* __restrict__ nsurf, const double* __restrict__ qext, const double* __restrict__ fnorm) {
     constexpr int N2 = CfgA<N>::N2, N3 = CfgA<N>::N3, EPB = CfgA<N>::EPB;
     extern __shared__ double smem[];
     __shared__ double red[CfgA<N>::THREADS];
@@ -668,6 +668,7 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
     // face buffer (sT, free until the viscous part), gathered per node below; the neighbour's
     // cotangents to gbuf
     double* sFo = sT;                                   // [5][6 N2]
+    const double igam = rcp_newton2(ph.gamma);
     if (active) {
 #pragma unroll 1
         for (int fn = node; fn < 6 * N2; fn += N3) {
@@ -720,11 +721,11 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                 mu_acc += face_avg_vjp(so, sn, n0, n1, n2, ph, ph.dissipation == 2, cip, dmb, bo, bn);
             }
             if (ph.dissipation == 1) {
-                const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+                const double nn = fnorm[(el * 6 + 2 * l + side) * N2 + fi];     // |n_J|, as the forward
                 const double uo = so.u0 * n0 + so.u1 * n1 + so.u2 * n2;
                 const double un_ = sn.u0 * n0 + sn.u1 * n1 + sn.u2 * n2;
-                const double ibo = rcp_newton2(so.beta), ibn = rcp_newton2(sn.beta);
-                const double co = sqrt(0.5 * ph.gamma * ibo), cn = sqrt(0.5 * ph.gamma * ibn);
+                // c = sqrt(gamma/(2 beta)) = (2 beta/gamma)^(-1/2), and dc/dbeta = -c/(2 beta) = -c^3/gamma
+                const double co = rsqrt_newton2(2.0 * so.beta * igam), cn = rsqrt_newton2(2.0 * sn.beta * igam);
                 const double lo = fabs(uo) + co * nn, ln = fabs(un_) + cn * nn;
                 const double lam2 = 0.5 * fmax(lo, ln);
                 double lb = 0.0;
@@ -743,8 +744,8 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
                 bn.u0 += sn_ * n0;
                 bn.u1 += sn_ * n1;
                 bn.u2 += sn_ * n2;
-                bo.beta += lob * nn * (-0.5 * co * ibo);
-                bn.beta += lnb * nn * (-0.5 * cn * ibn);
+                bo.beta -= lob * nn * (co * co * co * igam);
+                bn.beta -= lnb * nn * (cn * cn * cn * igam);
             }
             double qb[5];
             pbar_to_q(so, bo, ph, qb);
@@ -870,36 +871,43 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
             for (int m = 0; m < 3; ++m)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) mu_acc += Psi[m][k] * FV[m][k];
-            // reverse FV -> tau, u, hc, g
-            double gb[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-            double dub[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-            double hcb = 0.0, divb = 0.0;
+            // reverse FV -> tau, u, hc, g.  With Tb_mi = Psi_mi + Psi_m3 u_i, the cotangent of du is
+            // mu (Tb + Tb^T) - (2/3) mu tr(Tb) I, symmetric; E = RT times it.  Since du = RT (g_mk +
+            // u_k g_m3), E_km feeds g_mk directly, g_m3 through u_k, u_k through g_m3, and RT through
+            // du_km / RT; with dRT/dbeta = -2 RT^2 that last part gives -2 sum du_km E_km.
+            double Tb[3][3];
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) Tb[m][i] = fma(Psi[m][3], u[i], Psi[m][i]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ub[i] += Psi[0][3] * FV[0][i] + Psi[1][3] * FV[1][i] + Psi[2][3] * FV[2][i];
+            const double hcb = Psi[0][3] * g[0][3] + Psi[1][3] * g[1][3] + Psi[2][3] * g[2][3];
+            const double rm = RT * ph.mu;
+            const double dtr = (-2.0 / 3.0) * (Tb[0][0] + Tb[1][1] + Tb[2][2]);
+            double E[3][3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                E[k][k] = rm * fma(2.0, Tb[k][k], dtr);
+#pragma unroll
+                for (int m = k + 1; m < 3; ++m) E[k][m] = E[m][k] = rm * (Tb[k][m] + Tb[m][k]);
+            }
+            double gb[3][4];
+            double sdE = 0.0;
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const double Tb = Psi[m][i] + Psi[m][3] * u[i];
-                    ub[i] += Psi[m][3] * FV[m][i];
-                    dub[i][m] += ph.mu * Tb;
-                    dub[m][i] += ph.mu * Tb;
-                    if (i == m) divb -= (2.0 / 3.0) * ph.mu * Tb;
-                }
-                hcb += Psi[m][3] * g[m][3];
-                gb[m][3] += Psi[m][3] * hc;
+                for (int k = 0; k < 3; ++k) gb[m][k] = E[k][m];
+                gb[m][3] = fma(Psi[m][3], hc, u[0] * E[0][m] + u[1] * E[1][m] + u[2] * E[2][m]);
             }
 #pragma unroll
-            for (int k = 0; k < 3; ++k) dub[k][k] += divb;
-            double RTb = hcb * ph.kappa / ph.R * 2.0 * RT;
+            for (int k = 0; k < 3; ++k) {
+                ub[k] += g[0][3] * E[k][0] + g[1][3] * E[k][1] + g[2][3] * E[k][2];
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    gb[m][k] += RT * dub[k][m];
-                    gb[m][3] += RT * u[k] * dub[k][m];
-                    ub[k] += RT * g[m][3] * dub[k][m];
-                    RTb += (g[m][k] + u[k] * g[m][3]) * dub[k][m];
-                }
-            bb += RTb * (-2.0 * RT * RT);                 // dRT/dbeta = -1/(2 beta^2) = -2 RT^2
+                for (int m = 0; m < 3; ++m) sdE = fma(du[k][m], E[k][m], sdE);
+            }
+            // hc = kappa/R RT^2: its cotangent reaches beta as hcb (kappa/R) 2 RT (-2 RT^2)
+            bb -= fma(4.0 * ph.kappa / ph.R * RT * RT * RT, hcb, 2.0 * sdE);
             // g = J^-1 sum_a Ja_am theta_a  ->  theta-bar
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -1047,13 +1055,16 @@ cudaError_t launch_adj_n(const esdc_ctx* c, const double* q, const double* lam, 
     const unsigned grid = (unsigned)((c->K + C::EPB - 1) / C::EPB);
     if (c->setup.volume_flux == ESDC_FLUX_KG)
         adj_main<N, kAdjKG><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
-                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext);
+                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext,
+                                                           c->d_fnorm);
     else if (c->setup.volume_flux == ESDC_FLUX_DC)
         adj_main<N, kAdjDC><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
-                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext);
+                                                           c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext,
+                                                           c->d_fnorm);
     else
         adj_main<N, kAdjESC><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
-                                                            c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext);
+                                                            c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext,
+                                                           c->d_fnorm);
     const unsigned g2 = (unsigned)((c->K + C::EPB_F - 1) / C::EPB_F);
     adj_face<N><<<g2, C::EPB_F * 2 * C::N2, 0, s>>>(q, c->d_nbr, c->d_adj_g, c->d_adj_t, grad, c->K, c->ops, c->phys);
     if (mu_acc) {
