@@ -40,7 +40,6 @@ struct CfgA {
     // | neighbour face w 24 N2
     static constexpr int TSZ = 12 * N3 > 30 * N2 ? 12 * N3 : 30 * N2;
     static constexpr int SM = 40 * N3 + TSZ + 24 * N2;
-    static constexpr int EPB_F = (2 * N2) >= 128 ? 1 : 128 / (2 * N2);
     // resident CTAs the register allocation is sized for (3 at N = 4, 5 measured faster than 2)
     static constexpr int MINB = (N == 4 || N == 5) ? 3 : 1;
 };
@@ -983,54 +982,58 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
 
 // Add the neighbours' contributions on this element's face nodes: the inviscid interface
 // cotangent they computed for our state (gbuf) and the lift part of their gradient cotangent
-// (tbuf), pulled back through w(q).
+// (tbuf), pulled back through w(q).  One thread per node: a node on up to three faces sums their
+// contributions (the pull-back is linear, so once for the summed entropy-variable cotangent) and
+// updates its gradient once, so no two threads touch the same entry.
 template <int N>
-__global__ void __launch_bounds__(CfgA<N>::EPB_F * 2 * CfgA<N>::N2)
+__global__ void __launch_bounds__(CfgA<N>::THREADS)
 adj_face(const double* __restrict__ q, const int32_t* __restrict__ nbr, const double* __restrict__ gbuf,
          const double* __restrict__ tbuf, double* __restrict__ grad, int64_t K, const Ops ops, const Phys ph) {
     constexpr int N2 = CfgA<N>::N2, N3 = CfgA<N>::N3;
     const int t = threadIdx.x;
-    const int el_loc = t / (2 * N2);
-    const int r = t - el_loc * 2 * N2;
-    const int side = r / N2, fi = r - side * N2;
-    const int64_t el = (int64_t)blockIdx.x * CfgA<N>::EPB_F + el_loc;
-    const bool active = el < K;
-#pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-        // a boundary face (neighbour -1) receives nothing; every thread still reaches the barrier
-        const int64_t nb = active ? nbr[el * 6 + 2 * l + side] : -1;
-        if (nb >= 0) {
-            const int st = dir_stride<N>(l);
-            const int own = line_base<N>(l, fi % N, fi / N) + (side ? (N - 1) * st : 0);
-            const int nside = 1 - side;
-            const double* gb = gbuf + ((nb * 6 + 2 * l + nside) * 5) * N2 + fi;
-            double add[5];
+    const int el_loc = t / N3;
+    const int node = t - el_loc * N3;
+    const int64_t el = (int64_t)blockIdx.x * CfgA<N>::EPB + el_loc;
+    if (el >= K) return;
+    const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
+    double add[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, wb[4] = {0.0, 0.0, 0.0, 0.0};
+    bool any = false;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) add[v] = gb[v * N2];
-            if (ph.viscous) {
-                const double* tb = tbuf + ((nb * 6 + 2 * l + nside) * 4) * N2 + fi;
-                const double En = nside ? 0.5 : -0.5;
-                const double wi = ops.winv[nside ? N - 1 : 0];
-                double wb[4];
+    for (int a = 0; a < 3; ++a) {
+        const int ia = a == 0 ? i1 : (a == 1 ? i2 : i3);
+        if (ia != 0 && ia != N - 1) continue;
+        const int side = ia == N - 1;
+        const int64_t nb = nbr[el * 6 + 2 * a + side];
+        if (nb < 0) continue;               // a boundary face receives nothing
+        any = true;
+        const int fi = a == 0 ? (i2 + N * i3) : (a == 1 ? (i1 + N * i3) : (i1 + N * i2));
+        const int nside = 1 - side;
+        const double* gb = gbuf + ((nb * 6 + 2 * a + nside) * 5) * N2 + fi;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) wb[k] = En * wi * tb[k * N2];
-                double qv[5];
+        for (int v = 0; v < 5; ++v) add[v] += gb[v * N2];
+        if (ph.viscous) {
+            const double* tb = tbuf + ((nb * 6 + 2 * a + nside) * 4) * N2 + fi;
+            const double c = (nside ? 0.5 : -0.5) * ops.winv[nside ? N - 1 : 0];
 #pragma unroll
-                for (int v = 0; v < 5; ++v) qv[v] = q[(el * 5 + v) * N3 + own];
-                Prim s;
-                to_prim(qv, ph, s);
-                PBar b{0.0, 2.0 * s.beta * wb[0], 2.0 * s.beta * wb[1], 2.0 * s.beta * wb[2],
-                       2.0 * (s.u0 * wb[0] + s.u1 * wb[1] + s.u2 * wb[2]) - 2.0 * wb[3], 0.0};
-                double qb[5];
-                pbar_to_q(s, b, ph, qb);
-#pragma unroll
-                for (int v = 0; v < 5; ++v) add[v] += qb[v];
-            }
-#pragma unroll
-            for (int v = 0; v < 5; ++v) grad[(el * 5 + v) * N3 + own] += add[v];
+            for (int k = 0; k < 4; ++k) wb[k] = fma(c, tb[k * N2], wb[k]);
         }
-        __syncthreads();
     }
+    if (!any) return;
+    if (ph.viscous) {
+        double qv[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qv[v] = q[(el * 5 + v) * N3 + node];
+        Prim s;
+        to_prim(qv, ph, s);
+        PBar b{0.0, 2.0 * s.beta * wb[0], 2.0 * s.beta * wb[1], 2.0 * s.beta * wb[2],
+               2.0 * (s.u0 * wb[0] + s.u1 * wb[1] + s.u2 * wb[2]) - 2.0 * wb[3], 0.0};
+        double qb[5];
+        pbar_to_q(s, b, ph, qb);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) add[v] += qb[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) grad[(el * 5 + v) * N3 + node] += add[v];
 }
 
 __global__ void __launch_bounds__(kAdjRed) finish_mu(const double* __restrict__ part, int64_t n, double scale,
@@ -1065,8 +1068,7 @@ cudaError_t launch_adj_n(const esdc_ctx* c, const double* q, const double* lam, 
         adj_main<N, kAdjESC><<<grid, C::THREADS, smem, s>>>(q, lam, c->d_geom, c->d_nbr, grad, c->d_adj_g, c->d_adj_t,
                                                             c->d_adj_mu, c->K, c->ops, c->phys, c->d_nsurf, c->d_qext,
                                                            c->d_fnorm);
-    const unsigned g2 = (unsigned)((c->K + C::EPB_F - 1) / C::EPB_F);
-    adj_face<N><<<g2, C::EPB_F * 2 * C::N2, 0, s>>>(q, c->d_nbr, c->d_adj_g, c->d_adj_t, grad, c->K, c->ops, c->phys);
+    adj_face<N><<<grid, C::THREADS, 0, s>>>(q, c->d_nbr, c->d_adj_g, c->d_adj_t, grad, c->K, c->ops, c->phys);
     if (mu_acc) {
         const double scale = c->phys.mu > 0.0 ? 1.0 / c->phys.mu : 0.0;
         finish_mu<<<1, kAdjRed, 0, s>>>(c->d_adj_mu, grid, scale, mu_acc);
