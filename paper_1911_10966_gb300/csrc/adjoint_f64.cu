@@ -29,6 +29,16 @@ namespace {
 
 constexpr int kAdjRed = 256;
 
+// Float64 reciprocal square root by Newton-Raphson on g(y) = 1/y^2 - x from the hardware
+// approximation (about 23 bits): each step y <- y (3/2 - x y^2/2) doubles the number of correct bits.
+__device__ __forceinline__ double rsqrt_newton2(double x) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double h = 0.5 * x;
+    y = y * fma(-h * y, y, 1.5);
+    return y * fma(-h * y, y, 1.5);
+}
+
 template <int N>
 struct CfgA {
     static constexpr int N2 = N * N, N3 = N * N * N;

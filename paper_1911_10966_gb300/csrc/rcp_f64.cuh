@@ -1,6 +1,6 @@
 // Float64 reciprocal by Newton-Raphson on g(r) = 1/r - x from the hardware approximation (about 23
 // bits): each step r <- r + r (1 - x r) doubles the number of correct bits.  Shared by the float64
-// residual kernels and the adjoint; the reciprocal square root below serves the adjoint.
+// residual kernels and the adjoint.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,20 +19,6 @@ __device__ __forceinline__ double rcp_newton1(double x) {     // ~46 bits
 __device__ __forceinline__ double rcp_newton2(double x) {     // full double precision (within an ulp)
     double r = rcp_newton1(x);
     return fma(r, fma(-x, r, 1.0), r);
-}
-
-// Float64 reciprocal square root by Newton-Raphson on g(y) = 1/y^2 - x from the hardware
-// approximation: each step y <- y (3/2 - x y^2/2) doubles the number of correct bits.
-__device__ __forceinline__ double rsqrt_approx(double x) {
-    double r;
-    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    return r;
-}
-__device__ __forceinline__ double rsqrt_newton2(double x) {   // full double precision (within ulps)
-    const double h = 0.5 * x;
-    double y = rsqrt_approx(x);
-    y = y * fma(-h * y, y, 1.5);
-    return y * fma(-h * y, y, 1.5);
 }
 
 }  // namespace esdc
