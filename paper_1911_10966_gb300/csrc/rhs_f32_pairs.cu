@@ -19,11 +19,12 @@
 // Shared memory per element (floats):
 //   sW4 [N3] float4   entropy variables (w2, w3, w4, w5 - w5_ref), for the viscous gradient
 //   sA  [3][5][N3]    the bulk-copied state [5][N3] and metrics [10][N3] (N >= 6) | then the
-//                     per-direction volume + interface sums | then the contravariant viscous
-//                     fluxes, float4 [3][N3]
+//                     per-direction volume + interface sums | then the lifted gradients theta_l,
+//                     float4 [3][N3], each replaced by the contravariant viscous flux of its node
 //   sL  [3][8][N3]    pair-loop inputs per direction l with the line's nodes contiguous:
 //                     (hdr, dbn, hu0, hu1, hu2, Ja_l0, Ja_l1, Ja_l2) at (l 8 + c) N3 + line N + j',
-//                     j' = j ^ lsw(line) (a bank swizzle, below)
+//                     j' = j ^ lsw(line) (a bank swizzle, below) | then the divergence terms
+//                     D_l Ftilde_l, float4 [3][N3]
 //   sJi [N3]          1/J
 //   sQ  [5][N3]       own dq (interface dissipation) | then the sum of the three directions
 //   sWf [6][4][N2]    neighbour entropy variables
@@ -302,7 +303,6 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
     float* base_sm = reinterpret_cast<float*>(smp4) + (size_t)el_loc * C::SM;
     float4* sW4 = reinterpret_cast<float4*>(base_sm);          // [N3]
     float* sA = base_sm + 4 * N3;                               // [3][5][N3] | float4 [3][N3] Ftilde
-    float4* sF4 = reinterpret_cast<float4*>(sA);
     float* sL = sA + 15 * N3;                                   // [3][8][N3]
     float* sJi = sL + 24 * N3;                                  // [N3]
     float* sQ = sJi + N3;                                       // [5][N3] | [5][N3] direction sum
@@ -621,42 +621,63 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
     __syncthreads();
 
     if (ph.viscous) {
-        float Ft[NPT][3][4];
+        // The two line derivatives of the viscous chain (the lifted gradient of the entropy variables
+        // and the divergence of the contravariant viscous fluxes) run one thread per line, each line's
+        // eight float4 values loaded once; the node-wise part between them (metric contraction, shear
+        // stress and heat flux) runs one thread per node.
+        float4* sT4 = reinterpret_cast<float4*>(sA);     // [3][N3] theta_l, then Ftilde_l
+        float4* sD4 = reinterpret_cast<float4*>(sL);     // [3][N3] D_l Ftilde_l (the direction copies are dead)
+        // the node's three directions of volume and interface sums (sQ is free after the SAT)
         if (active) {
+            for (int node = tl; node < N3; node += TE) {
 #pragma unroll
-            for (int r = 0; r < NPT; ++r) {
-                const int node = tl + r * TE;
-                if (node >= N3) continue;
+                for (int v = 0; v < 5; ++v)
+                    sQ[v * N3 + node] = sA[v * N3 + node] + (sA[(5 + v) * N3 + node] + sA[(10 + v) * N3 + node]);
+            }
+        }
+        __syncthreads();
+        // theta_l = D_l w + (E/2)(w_nbr - w_own)/w_end at the line ends
+        if (active && tl < 3 * N2) {
+            const int l = tl / N2, line = tl - l * N2;
+            const int st = dir_stride_f<N>(l);
+            const int base = line_base_f<N>(l, line % N, line / N);
+            float4 w[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) w[j] = sW4[base + j * st];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                f2p s01 = 0ull, s23 = 0ull;
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const f2p d = ldp(ops.D2[i][j]);
+                    s01 = fma2(d, pk(w[j].x, w[j].y), s01);
+                    s23 = fma2(d, pk(w[j].z, w[j].w), s23);
+                }
+                float2 a01 = upk(s01), a23 = upk(s23);
+                if (i == 0 || i == N - 1) {
+                    const float E = (i == N - 1 ? 0.5f : -0.5f) * ops.winv[i];
+                    const float* wf = sWf + (2 * l + (i == N - 1)) * 4 * N2 + line;
+                    a01.x += E * (wf[0] - w[i].x);
+                    a01.y += E * (wf[N2] - w[i].y);
+                    a23.x += E * (wf[2 * N2] - w[i].z);
+                    a23.y += E * (wf[3 * N2] - w[i].w);
+                }
+                sT4[l * N3 + base + i * st] = make_float4(a01.x, a01.y, a23.x, a23.y);
+            }
+        }
+        __syncthreads();
+        // node-wise: gradient, viscous flux, its contravariant components (over theta) and face traces
+        if (active) {
+            for (int node = tl; node < N3; node += TE) {
                 const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
-                const float4 w4 = sW4[node];
-                const float wown[4] = {w4.x, w4.y, w4.z, w4.w};
                 float th[3][4];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const int ia = a == 0 ? i1 : (a == 1 ? i2 : i3);
-                    const int st = dir_stride_f<N>(a);
-                    const int lb = node - ia * st;
-                    f2p s01 = 0ull, s23 = 0ull;
-#pragma unroll
-                    for (int j = 0; j < N; ++j) {
-                        const f2p d = ldp(ops.D2[ia][j]);
-                        const float4 wj = sW4[lb + j * st];
-                        s01 = fma2(d, pk(wj.x, wj.y), s01);
-                        s23 = fma2(d, pk(wj.z, wj.w), s23);
-                    }
-                    const float2 a01 = upk(s01), a23 = upk(s23);
-                    th[a][0] = a01.x;
-                    th[a][1] = a01.y;
-                    th[a][2] = a23.x;
-                    th[a][3] = a23.y;
-                    if (ia == 0 || ia == N - 1) {
-                        const int side = ia == N - 1;
-                        const int fi = a == 0 ? (i2 + N * i3) : (a == 1 ? (i1 + N * i3) : (i1 + N * i2));
-                        const float E = side ? 0.5f : -0.5f;
-                        const float* wf = sWf + (2 * a + side) * 4 * N2 + fi;
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) th[a][kk] += E * (wf[kk * N2] - wown[kk]) * ops.winv[ia];
-                    }
+                    const float4 t4 = sT4[a * N3 + node];
+                    th[a][0] = t4.x;
+                    th[a][1] = t4.y;
+                    th[a][2] = t4.z;
+                    th[a][3] = t4.w;
                 }
                 float Ja[3][3];
 #pragma unroll
@@ -693,58 +714,49 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
                 }
 #pragma unroll
                 for (int l = 0; l < 3; ++l) {
+                    float Ft[4];
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        Ft[r][l][kk] = Ja[l][0] * FV[0][kk] + Ja[l][1] * FV[1][kk] + Ja[l][2] * FV[2][kk];
+                    for (int kk = 0; kk < 4; ++kk) Ft[kk] = Ja[l][0] * FV[0][kk] + Ja[l][1] * FV[1][kk] + Ja[l][2] * FV[2][kk];
+                    sT4[l * N3 + node] = make_float4(Ft[0], Ft[1], Ft[2], Ft[3]);
                     const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
                     if (il == 0 || il == N - 1) {
                         const int side = il == N - 1;
                         const int fi = l == 0 ? (i2 + N * i3) : (l == 1 ? (i1 + N * i3) : (i1 + N * i2));
                         float* tr = trace + ((el * 6 + 2 * l + side) * 4) * N2 + fi;
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) tr[kk * N2] = Ft[r][l][kk];
+                        for (int kk = 0; kk < 4; ++kk) tr[kk * N2] = Ft[kk];
                     }
                 }
-                // the node's three directions of volume and interface sums (sQ is free after the SAT)
+            }
+        }
+        __syncthreads();
+        // D_l Ftilde_l along the lines
+        if (active && tl < 3 * N2) {
+            const int l = tl / N2, line = tl - l * N2;
+            const int st = dir_stride_f<N>(l);
+            const int base = line_base_f<N>(l, line % N, line / N);
+            float4 f[N];
 #pragma unroll
-                for (int v = 0; v < 5; ++v)
-                    sQ[v * N3 + node] = sA[v * N3 + node] + (sA[(5 + v) * N3 + node] + sA[(10 + v) * N3 + node]);
+            for (int j = 0; j < N; ++j) f[j] = sT4[l * N3 + base + j * st];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                f2p s01 = 0ull, s23 = 0ull;
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const f2p d = ldp(ops.D2[i][j]);
+                    s01 = fma2(d, pk(f[j].x, f[j].y), s01);
+                    s23 = fma2(d, pk(f[j].z, f[j].w), s23);
+                }
+                const float2 a01 = upk(s01), a23 = upk(s23);
+                sD4[l * N3 + base + i * st] = make_float4(a01.x, a01.y, a23.x, a23.y);
             }
         }
         __syncthreads();
         if (active) {
-#pragma unroll
-            for (int r = 0; r < NPT; ++r) {
-                const int node = tl + r * TE;
-                if (node >= N3) continue;
-#pragma unroll
-                for (int l = 0; l < 3; ++l)
-                    sF4[l * N3 + node] = make_float4(Ft[r][l][0], Ft[r][l][1], Ft[r][l][2], Ft[r][l][3]);
-            }
-        }
-        __syncthreads();
-        if (active) {
-#pragma unroll
-            for (int r = 0; r < NPT; ++r) {
-                const int node = tl + r * TE;
-                if (node >= N3) continue;
-                const int i1 = node % N, i2 = (node / N) % N, i3 = node / N2;
-                f2p v01 = 0ull, v23 = 0ull;
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
-                    const int st = dir_stride_f<N>(l);
-                    const int lb = node - il * st;
-#pragma unroll
-                    for (int j = 0; j < N; ++j) {
-                        const f2p d = ldp(ops.D2[il][j]);
-                        const float4 f = sF4[l * N3 + lb + j * st];
-                        v01 = fma2(d, pk(f.x, f.y), v01);
-                        v23 = fma2(d, pk(f.z, f.w), v23);
-                    }
-                }
-                const float2 a01 = upk(v01), a23 = upk(v23);
-                const float vs[4] = {a01.x, a01.y, a23.x, a23.y};
+            for (int node = tl; node < N3; node += TE) {
+                const float4 d0 = sD4[node], d1 = sD4[N3 + node], d2 = sD4[2 * N3 + node];
+                const float vs[4] = {d0.x + (d1.x + d2.x), d0.y + (d1.y + d2.y), d0.z + (d1.z + d2.z),
+                                     d0.w + (d1.w + d2.w)};
                 const float Jinv = sJi[node];
                 float sv[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
                 if (XF && src) {
