@@ -20,11 +20,12 @@
 //   sW4 [N3] float4   entropy variables (w2, w3, w4, w5 - w5_ref), for the viscous gradient
 //   sA  [3][5][N3]    the bulk-copied state [5][N3] and metrics [10][N3] (N >= 6) | then the
 //                     per-direction volume + interface sums | then the lifted gradients theta_l,
-//                     float4 [3][N3], each replaced by the contravariant viscous flux of its node
+//                     float4 [3][N3 + N2] (padded), each replaced by the contravariant viscous flux
+//                     of its node
 //   sL  [3][8][N3]    pair-loop inputs per direction l with the line's nodes contiguous:
 //                     (hdr, dbn, hu0, hu1, hu2, Ja_l0, Ja_l1, Ja_l2) at (l 8 + c) N3 + line N + j',
 //                     j' = j ^ lsw(line) (a bank swizzle, below) | then the divergence terms
-//                     D_l Ftilde_l, float4 [3][N3]
+//                     D_l Ftilde_l, float4 [3][N3 + N2] (padded)
 //   sJi [N3]          1/J
 //   sQ  [5][N3]       own dq (interface dissipation) | then the sum of the three directions
 //   sWf [6][4][N2]    neighbour entropy variables
@@ -106,6 +107,11 @@ __device__ __forceinline__ int lsw(int line) {
 template <int N>
 __device__ __forceinline__ int lidx(int line, int j) {
     return line * N + (j ^ lsw<N>(line));
+}
+// Padded position of node n in the viscous chain's float4 arrays (one float4 of padding per N).
+template <int N>
+__device__ __forceinline__ int vpad(int n) {
+    return n + n / N;
 }
 // Position of node (i1, i2, i3) in the direction-l copy.
 template <int N>
@@ -625,8 +631,11 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
         // and the divergence of the contravariant viscous fluxes) run one thread per line, each line's
         // eight float4 values loaded once; the node-wise part between them (metric contraction, shear
         // stress and heat flux) runs one thread per node.
-        float4* sT4 = reinterpret_cast<float4*>(sA);     // [3][N3] theta_l, then Ftilde_l
-        float4* sD4 = reinterpret_cast<float4*>(sL);     // [3][N3] D_l Ftilde_l (the direction copies are dead)
+        // [3][NP] float4 with node n at vpad(n) = n + n / N: the lines of direction 0 (stride N float4)
+        // then fall on different banks
+        constexpr int NP = N3 + N2;
+        float4* sT4 = reinterpret_cast<float4*>(sA);     // theta_l, then Ftilde_l
+        float4* sD4 = reinterpret_cast<float4*>(sL);     // D_l Ftilde_l (the direction copies are dead)
         // the node's three directions of volume and interface sums (sQ is free after the SAT)
         if (active) {
             for (int node = tl; node < N3; node += TE) {
@@ -662,7 +671,7 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
                     a23.x += E * (wf[2 * N2] - w[i].z);
                     a23.y += E * (wf[3 * N2] - w[i].w);
                 }
-                sT4[l * N3 + base + i * st] = make_float4(a01.x, a01.y, a23.x, a23.y);
+                sT4[l * NP + vpad<N>(base + i * st)] = make_float4(a01.x, a01.y, a23.x, a23.y);
             }
         }
         __syncthreads();
@@ -673,7 +682,7 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
                 float th[3][4];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const float4 t4 = sT4[a * N3 + node];
+                    const float4 t4 = sT4[a * NP + vpad<N>(node)];
                     th[a][0] = t4.x;
                     th[a][1] = t4.y;
                     th[a][2] = t4.z;
@@ -717,7 +726,7 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
                     float Ft[4];
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) Ft[kk] = Ja[l][0] * FV[0][kk] + Ja[l][1] * FV[1][kk] + Ja[l][2] * FV[2][kk];
-                    sT4[l * N3 + node] = make_float4(Ft[0], Ft[1], Ft[2], Ft[3]);
+                    sT4[l * NP + vpad<N>(node)] = make_float4(Ft[0], Ft[1], Ft[2], Ft[3]);
                     const int il = l == 0 ? i1 : (l == 1 ? i2 : i3);
                     if (il == 0 || il == N - 1) {
                         const int side = il == N - 1;
@@ -737,7 +746,7 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
             const int base = line_base_f<N>(l, line % N, line / N);
             float4 f[N];
 #pragma unroll
-            for (int j = 0; j < N; ++j) f[j] = sT4[l * N3 + base + j * st];
+            for (int j = 0; j < N; ++j) f[j] = sT4[l * NP + vpad<N>(base + j * st)];
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 f2p s01 = 0ull, s23 = 0ull;
@@ -748,13 +757,14 @@ rhs_pairs_f32(const StageF in, float* __restrict__ out, const float* __restrict_
                     s23 = fma2(d, pk(f[j].z, f[j].w), s23);
                 }
                 const float2 a01 = upk(s01), a23 = upk(s23);
-                sD4[l * N3 + base + i * st] = make_float4(a01.x, a01.y, a23.x, a23.y);
+                sD4[l * NP + vpad<N>(base + i * st)] = make_float4(a01.x, a01.y, a23.x, a23.y);
             }
         }
         __syncthreads();
         if (active) {
             for (int node = tl; node < N3; node += TE) {
-                const float4 d0 = sD4[node], d1 = sD4[N3 + node], d2 = sD4[2 * N3 + node];
+                const int vp = vpad<N>(node);
+                const float4 d0 = sD4[vp], d1 = sD4[NP + vp], d2 = sD4[2 * NP + vp];
                 const float vs[4] = {d0.x + (d1.x + d2.x), d0.y + (d1.y + d2.y), d0.z + (d1.z + d2.z),
                                      d0.w + (d1.w + d2.w)};
                 const float Jinv = sJi[node];
