@@ -100,9 +100,12 @@ struct CfgP {
 // Swizzle of the position along a line in the direction copies: j ^ lsw(line) with an even lsw, so
 // that the node pairs (j, j + 1), j even, stay adjacent while consecutive lines (the threads of a
 // warp) spread over the shared-memory banks (N = 8: 16 threads' 64-bit loads on 32 distinct banks).
+// At N = 8 the four values for q = (line >> 2) & 3 are 0, 4, 2, 6: lines four apart (q and q + 1
+// with q even) then differ in bit 2, so the node-wise stores into the direction-1 copy, whose
+// 32 threads are lines i1 + N i3 at four positions i2 each, also land on distinct banks.
 template <int N>
 __device__ __forceinline__ int lsw(int line) {
-    return N == 8 ? 2 * ((line >> 2) & 3) : (N == 4 ? 2 * ((line >> 3) & 1) : 0);
+    return N == 8 ? 4 * ((line >> 2) & 1) + 2 * ((line >> 3) & 1) : (N == 4 ? 2 * ((line >> 3) & 1) : 0);
 }
 template <int N>
 __device__ __forceinline__ int lidx(int line, int j) {
