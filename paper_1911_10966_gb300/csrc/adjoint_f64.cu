@@ -199,7 +199,6 @@ __device__ __forceinline__ void ec_pair_vjp(const PrimH& a, const PrimH& b, doub
     const double un = ub0 * n0 + ub1 * n1 + ub2 * n2;
     const double pt = 0.5 * sr * rsb;
     const double f1 = Lr * un;
-    const double fm0 = fma(f1, ub0, pt * n0), fm1 = fma(f1, ub1, pt * n1), fm2 = fma(f1, ub2, pt * n2);
     const double c5 = fma(hig, IB, -(a.qsq + b.qsq));
     // reverse
     const double fmb0 = fma(mu[4], ub0, mu[1]), fmb1 = fma(mu[4], ub1, mu[2]), fmb2 = fma(mu[4], ub2, mu[3]);
@@ -209,8 +208,9 @@ __device__ __forceinline__ void ec_pair_vjp(const PrimH& a, const PrimH& b, doub
     const double unb = f1b * Lr;
     const double Lrb_ = f1b * un;
     // pt = (rho_a + rho_b)/(2 (beta_a + beta_b)): d pt/d rho = 1/(2 sb), d pt/d beta = -pt/sb
-    const double hp = 0.5 * ptb * rsb;
-    const double bp = -ptb * pt * rsb;
+    const double ptr = ptb * rsb;
+    const double hp = 0.5 * ptr;
+    const double bp = -pt * ptr;
     const double S = c5b * hig * sc;
     ab.rho += fma(Lrb_, Lra, hp);
     bb.rho += fma(Lrb_, Lrb, hp);
@@ -218,9 +218,12 @@ __device__ __forceinline__ void ec_pair_vjp(const PrimH& a, const PrimH& b, doub
     bb.beta += fma(S, Bb, bp);
     ab.c += c5b;
     bb.c += c5b;
-    const double ubb0 = mu[4] * fm0 + fmb0 * f1 + unb * n0;
-    const double ubb1 = mu[4] * fm1 + fmb1 * f1 + unb * n1;
-    const double ubb2 = mu[4] * fm2 + fmb2 * f1 + unb * n2;
+    // ubar cotangent mu_5 f_m + fmb f1 + unb n with f_m = f1 ubar + p_t n:
+    // f1 (mu_5 ubar + fmb) + (mu_5 p_t + unb) n
+    const double An = fma(mu[4], pt, unb);
+    const double ubb0 = fma(f1, fma(mu[4], ub0, fmb0), An * n0);
+    const double ubb1 = fma(f1, fma(mu[4], ub1, fmb1), An * n1);
+    const double ubb2 = fma(f1, fma(mu[4], ub2, fmb2), An * n2);
     ab.u0 += ubb0;
     ab.u1 += ubb1;
     ab.u2 += ubb2;
