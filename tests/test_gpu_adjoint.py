@@ -243,3 +243,17 @@ def test_variant_vjp_matches_oracle_autograd(vf, p, diss, Re):
     (gt,) = torch.autograd.grad(ke, qq)
     e = normwise_errors(q0.grad, gt)
     assert max(e) <= 1e-9, e
+
+
+def test_checkpoint_argument_checks():
+    """Checkpoints holding the first residual are a float64 feature: a float32-mixed context refuses
+    them; a checkpoint tensor of the wrong shape is refused before any launch."""
+    from paper_1911_10966_gb300 import _native as nat
+    s32, q32, _, _, _ = make_pair(3, (2, 2, 2), Re=400.0, precision="fp32", noise=1e-3)
+    with pytest.raises(nat.EsdcError) as ei:
+        s32.rk_step_ckpt(q32.clone(), 1e-4, 2, k1=True)
+    assert ei.value.code == nat.ESDC_ERR_UNSUPPORTED
+    solver, qg, _, _, _ = make_pair(3, (2, 2, 2), Re=400.0, noise=1e-3)
+    bad = torch.zeros((2, 3) + tuple(qg.shape), dtype=torch.float64, device=qg.device)
+    with pytest.raises(ValueError):
+        solver.rk_adjoint(bad, 1e-4, torch.ones_like(qg))
