@@ -34,8 +34,8 @@ def _dirs(q, seed):
     return torch.randn(q.shape, generator=g, dtype=torch.float64) * scale
 
 
-@pytest.mark.parametrize("p,diss,Re", [(2, True, 200.0), (3, True, 1600.0), (3, False, 0.0), (4, True, 100.0),
-                                       (5, True, 400.0)])
+@pytest.mark.parametrize("p,diss,Re", [(1, True, 300.0), (2, True, 200.0), (3, True, 1600.0), (3, False, 0.0),
+                                       (4, True, 100.0), (5, True, 400.0), (6, True, 800.0), (7, True, 1600.0)])
 def test_vjp_matches_oracle_autograd(p, diss, Re):
     solver, qg, mesh, gas, qo = make_pair(p, (3, 2, 2), warp=0.1, seed=3, Re=Re, dissipation=diss, noise=2e-2)
     lam = torch.randn(qo.shape, generator=torch.Generator().manual_seed(11), dtype=torch.float64)
@@ -219,7 +219,8 @@ def test_vjp_and_trajectory_gradient_ignore_a_constant_source():
 
 
 @pytest.mark.parametrize("vf,p,diss,Re", [("kg", 2, True, 200.0), ("kg", 3, False, 0.0), ("kg", 4, True, 800.0),
-                                          ("dc", 2, True, 200.0), ("dc", 3, True, 400.0), ("dc", 4, False, 0.0)])
+                                          ("kg", 7, True, 1600.0), ("dc", 2, True, 200.0), ("dc", 3, True, 400.0),
+                                          ("dc", 4, False, 0.0), ("dc", 6, True, 800.0)])
 def test_variant_vjp_matches_oracle_autograd(vf, p, diss, Re):
     """The adjoint of the SF-KG (Kennedy-Gruber two-point flux) and DC (nodal Euler fluxes, central
     interface flux) variants against the oracle's autograd VJP, and a two-step trajectory gradient
