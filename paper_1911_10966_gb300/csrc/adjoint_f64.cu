@@ -42,6 +42,8 @@ __device__ __forceinline__ double rsqrt_newton2(double x) {
 template <int N>
 struct CfgA {
     static constexpr int N2 = N * N, N3 = N * N * N;
+    // (two elements per CTA at N = 5, one CTA of 250 threads per SM, made the VJP 8.5% slower on
+    // 16^3 elements and 17% faster on 8^3: fewer warps per SM against fuller ones and fewer waves)
     static constexpr int EPB = N3 >= 96 ? 1 : (N3 >= 48 ? 2 : (N3 >= 24 ? 4 : 16));
     static constexpr int THREADS = EPB * N3;
     // shared doubles per element: prim/w and the pair form 14 | lt 5 | geometry 10 | prim-bar 6 | q-bar 5
@@ -581,9 +583,21 @@ adj_main(const double* __restrict__ q, const double* __restrict__ lam, const dou
 
     // ---- volume term: the 3 N^2 lines of all directions at once, one per thread; direction l
     // assigns its primitive cotangents to its own array (sB for l = 0, the two halves of the
-    // theta-bar buffer sT for l = 1, 2, which is free until the viscous part)
-    if (active) {
-        for (int lt = node; lt < 3 * N2; lt += N3) {
+    // theta-bar buffer sT for l = 1, 2, which is free until the viscous part).  With several
+    // elements per CTA their lines are numbered consecutively over the CTA's threads, so that the
+    // lines fill whole warps (a warp instruction costs the float64 pipe its full time whatever its
+    // active lanes).
+    {
+        for (int g = t; g < EPB * 3 * N2; g += CfgA<N>::THREADS) {
+            const int eidx = g / (3 * N2);
+            if ((int64_t)blockIdx.x * EPB + eidx >= K) continue;
+            const int lt = g - eidx * (3 * N2);
+            // the arrays of element eidx (the same layout as the thread's own element's above)
+            double* const sP = smem + (size_t)eidx * CfgA<N>::SM;
+            double* const sL = sP + 14 * N3;
+            double* const sG = sL + 5 * N3;
+            double* const sB = sG + 10 * N3;
+            double* const sT = sB + 11 * N3;
             const int l = lt / N2, line = lt - l * N2;
             double* Bl = l == 0 ? sB : sT + (l - 1) * 6 * N3;
             const int base = line_base<N>(l, line % N, line / N);
